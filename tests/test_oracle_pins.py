@@ -1,0 +1,343 @@
+"""Pins of the CPU oracle against what the paper and mathematics fix.
+
+None of these tests retypes the oracle's binary64 operation order: they use
+the paper's printed worked example (Sec. II, Examples 1-5), 50-digit
+evaluations of the definitions, closed forms, library DCTs, and invariants
+(linearity of the pre-quantization stages, Sec. I and Eq. eqdct2)."""
+import numpy as np
+import pytest
+import scipy.fft
+
+import oracle as O
+import workloads as W
+from conftest import load_golden
+
+mpmath = pytest.importorskip("mpmath")
+
+
+def example_block():
+    return np.fromfunction(lambda i, j: (0.1 * i) * (0.1 * j), (8, 8))
+
+
+def _mat(rows, dtype=float):
+    return np.array([[dtype(x) for x in r] for r in rows])
+
+
+# --- Sec. II, Examples 1-5 ------------------------------------------------
+def test_worked_example_all_stages():
+    g = load_golden("example_xy.txt")
+    A = example_block()
+    assert np.allclose(A, _mat(g["A"]), atol=5e-4)
+    st = O.block_stages(A)
+    assert np.all(np.abs(st["delta"] - _mat(g["A_N"])) <= 5e-4 + 1e-12)
+    assert abs(st["s"] - float(g["s"][0][0])) < 1e-12
+    assert np.all(np.abs(st["dprime"] - _mat(g["A'_N"])) <= 5e-4 + 1e-9)
+    assert np.array_equal(st["psi"], _mat(g["P"], int))
+    assert st["phi"] == int(g["phi"][0][0])
+    assert st["f"] == float(g["f"][0][0])
+    P1 = _mat(g["P'"], int)
+    full = np.trunc(st["dct"] * st["phi"]).astype(int)
+    assert np.array_equal(full, P1)            # all 64, including dropped (3,3)
+    kept = O.kept_positions()
+    assert np.array_equal(st["code"], P1[kept[:, 0], kept[:, 1]])
+    dropped = np.ones((8, 8), bool)
+    dropped[kept[:, 0], kept[:, 1]] = False
+    assert list(zip(*np.nonzero(P1 * dropped))) == [(3, 3)]
+
+
+def test_kept_positions_layout():
+    kept = O.kept_positions()
+    assert len({tuple(p) for p in kept}) == 28
+    assert all(i < 2 or j < 2 for i, j in kept)
+    assert [tuple(p) for p in kept[:16]] == [(i, j) for i in range(2) for j in range(8)]
+
+
+# --- DCT constants and transform ---------------------------------------------
+def test_dct_tables_are_correctly_rounded():
+    mpmath.mp.dps = 50
+    cos_t, aa_t = O.dct_tables()
+    alpha = [mpmath.sqrt(mpmath.mpf(1) / 8)] + [mpmath.mpf(1) / 2] * 7
+    for k in range(8):
+        for x in range(8):
+            want = float(mpmath.cos((2 * x + 1) * k * mpmath.pi / 16))
+            assert cos_t[k, x] == want, (k, x)
+    for i in range(8):
+        for j in range(8):
+            assert aa_t[i, j] == float(alpha[i] * alpha[j]), (i, j)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_dct_stage_equals_orthonormal_dct2(seed):
+    rng = np.random.default_rng(seed)
+    M = np.cumsum(np.cumsum(rng.standard_normal((8, 8)), 0), 1) + rng.uniform(-5, 5, (8, 8))
+    st = O.block_stages(M)
+    ref = scipy.fft.dctn(st["dprime"], type=2, norm="ortho")
+    assert np.max(np.abs(st["dct"] - ref)) <= 1e-14 * max(1.0, np.max(np.abs(ref)))
+
+
+# --- normalization and slope: closed forms --------------------------------------
+@pytest.mark.parametrize("a,b", [(0.25, 0.5), (-1.0, 0.125), (3.0, -2.0), (0.0, 1.0)])
+def test_plane_block_closed_form(a, b):
+    M = np.fromfunction(lambda i, j: a * i + b * j + 1.5, (8, 8))
+    st = O.block_stages(M)
+    d = st["delta"]
+    assert d[0, 0] == 0.0
+    assert np.all(d[0, 1:] == b) and np.all(d[1:, 0] == a)
+    assert np.all(d[1:, 1:] == (a + b) / 2)
+    vals = [b] * 7 + [a] * 7 + [(a + b) / 2] * 49
+    K = sum(1 for v in vals if v != 0)
+    assert st["K"] == K
+    assert st["f"] == 1.5
+    assert st["s"] == pytest.approx(sum(abs(v) for v in vals) / K, rel=1e-15)
+
+
+def test_constant_block_is_lossless():
+    M = np.full((8, 8), -3.25)
+    st = O.block_stages(M)
+    assert st["K"] == 0 and st["s"] == 0.0 and st["phi"] == 255
+    assert not st["code"].any()
+    back = O.decompress_block(st["f"], st["s"], st["phi"], st["code"])
+    assert np.array_equal(back, M)
+
+
+# --- brute force against a 50-digit evaluation of the definitions --------------
+def _mp_compress(M):
+    """Real-arithmetic compress (Eqs. eqnorm, eqslope, eqdct, eqphi) at 50 digits."""
+    mp = mpmath.mp
+    mp.dps = 50
+    Mm = [[mpmath.mpf(float(M[i, j])) for j in range(8)] for i in range(8)]
+    d = [[mpmath.mpf(0)] * 8 for _ in range(8)]
+    for i in range(8):
+        for j in range(8):
+            if i == 0 and j == 0:
+                continue
+            if i == 0:
+                d[i][j] = Mm[0][j] - Mm[0][j - 1]
+            elif j == 0:
+                d[i][j] = Mm[i][0] - Mm[i - 1][0]
+            else:
+                d[i][j] = ((Mm[i][j] - Mm[i - 1][j]) + (Mm[i][j] - Mm[i][j - 1])) / 2
+    K = sum(1 for i in range(8) for j in range(8) if d[i][j] != 0)
+    if K == 0:
+        return 0, None, 255, None
+    s = sum(abs(d[i][j]) for i in range(8) for j in range(8)) / K
+    dp = [[d[i][j] / s for j in range(8)] for i in range(8)]
+    al = [mpmath.sqrt(mpmath.mpf(1) / 8)] + [mpmath.mpf(1) / 2] * 7
+    c = [[mpmath.cos((2 * x + 1) * k * mpmath.pi / 16) for x in range(8)] for k in range(8)]
+    D = [[al[i] * al[j] * mpmath.fsum(dp[u][v] * c[i][u] * c[j][v] for u in range(8) for v in range(8))
+          for j in range(8)] for i in range(8)]
+    m = max(abs(D[i][j]) for i in range(8) for j in range(8))
+    q = 127 / m
+    return K, s, q, D
+
+
+def _dyadic_blocks():
+    rng = np.random.default_rng(123)
+    yield np.fromfunction(lambda i, j: i + j, (8, 8))
+    yield np.fromfunction(lambda i, j: i * j / 16.0, (8, 8))
+    spike = np.zeros((8, 8)); spike[3, 5] = 1.0
+    yield spike
+    yield np.fromfunction(lambda i, j: ((i + j) % 2) * 0.5, (8, 8))
+    yield np.fromfunction(lambda i, j: (i - 3.5) ** 2 / 8 - j / 4.0, (8, 8))
+    for _ in range(12):
+        yield rng.integers(-64, 64, (8, 8)) / 32.0
+    for _ in range(8):
+        yield np.cumsum(rng.integers(-8, 9, (8, 8)), axis=1) / 16.0
+
+
+def test_brute_force_against_real_arithmetic():
+    kept = O.kept_positions()
+    n_checked = n_near = 0
+    for M in _dyadic_blocks():
+        st = O.block_stages(M)
+        K, s, q, D = _mp_compress(M)
+        assert st["K"] == K
+        if K == 0:
+            assert st["phi"] == 255 and not st["code"].any()
+            continue
+        assert st["s"] == pytest.approx(float(s), rel=1e-15)
+        if abs(q - mpmath.nint(q)) > 1e-9:
+            assert st["phi"] == min(255, max(1, int(mpmath.floor(q))))
+        phi = st["phi"]
+        for t, (i, j) in enumerate(kept):
+            v = D[i][j] * phi
+            if abs(v - mpmath.nint(v)) < 1e-9 and mpmath.nint(v) != 0:
+                n_near += 1           # decided by binary64 rounding; not pinned
+                continue
+            want = int(mpmath.floor(abs(v))) * (1 if v >= 0 else -1)
+            want = max(-127, min(127, want))
+            assert st["code"][t] == want, (M, t)
+            n_checked += 1
+    assert n_checked > 500
+
+
+# --- decompression ---------------------------------------------------------------
+@pytest.mark.parametrize("c,phi,s,f", [(100, 16, 0.5, 1.0), (-77, 3, 2.0, -4.0), (127, 255, 1e-3, 0.0)])
+def test_decompress_dc_only_closed_form(c, phi, s, f):
+    code = np.zeros(28, np.int8); code[0] = c
+    M = O.decompress_block(f, s, phi, code)
+    d = s * c / (8.0 * phi)
+    want = np.fromfunction(lambda i, j: f + (i + j) * d, (8, 8))
+    assert np.allclose(M, want, rtol=0, atol=1e-13 * (abs(f) + 14 * abs(d)))
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_decompress_inverts_normalization(seed):
+    rng = np.random.default_rng(seed)
+    code = rng.integers(-127, 128, 28).astype(np.int8)
+    phi, s, f = int(rng.integers(1, 256)), float(rng.uniform(0.01, 3)), float(rng.normal())
+    M = O.decompress_block(f, s, phi, code)
+    kept = O.kept_positions()
+    X = np.zeros((8, 8)); X[kept[:, 0], kept[:, 1]] = code / phi
+    dh = s * scipy.fft.idctn(X, type=2, norm="ortho")
+    # forward Eq. eqnorm applied to the decompressed block recovers s*IDCT(X)
+    assert M[0, 0] == f
+    assert np.allclose(M[0, 1:] - M[0, :-1], dh[0, 1:], atol=1e-12)
+    assert np.allclose(M[1:, 0] - M[:-1, 0], dh[1:, 0], atol=1e-12)
+    inner = ((M[1:, 1:] - M[:-1, 1:]) + (M[1:, 1:] - M[1:, :-1])) / 2
+    assert np.allclose(inner, dh[1:, 1:], atol=1e-12)
+
+
+def _roundtrip_bound(st):
+    kept = O.kept_positions()
+    X = np.zeros((8, 8)); X[kept[:, 0], kept[:, 1]] = st["code"] / st["phi"]
+    err = np.linalg.norm(X - st["dct"])
+    return np.fromfunction(lambda i, j: (i + j), (8, 8)) * st["s"] * err
+
+
+def test_round_trip_within_quantization_bound():
+    A, _ = W.plain_pair()
+    c = O.compress(A)
+    back = O.decompress(c)
+    for b in range(0, c.nb, 7):
+        bi, bj = divmod(b, A.shape[1] // 8)
+        M = A[8 * bi:8 * bi + 8, 8 * bj:8 * bj + 8]
+        st = O.block_stages(M)
+        assert st["phi"] == c.phi[b] and np.array_equal(st["code"], c.code[b])
+        bound = _roundtrip_bound(st) + 1e-12 * (1 + np.abs(M).max())
+        assert np.all(np.abs(back[8 * bi:8 * bi + 8, 8 * bj:8 * bj + 8] - M) <= bound)
+
+
+# --- Algorithms 1 and 2 -------------------------------------------------------------
+def _blocks(X):
+    r, cc = X.shape
+    return X.reshape(r // 8, 8, cc // 8, 8).transpose(0, 2, 1, 3).reshape(-1, 8, 8)
+
+
+def test_add_linearity_within_quantization_bound():
+    A, B = W.plain_pair()
+    ca, cb = O.compress(A), O.compress(B)
+    cs = O.add(ca, cb)
+    assert np.array_equal(cs.f, ca.f + cb.f) and np.array_equal(cs.s, ca.s + cb.s)
+    assert np.array_equal(cs.phi.astype(int),
+                          np.maximum(1, (ca.phi.astype(int) * cb.phi) // (ca.phi.astype(int) + cb.phi)))
+    da, db, ds = _blocks(O.decompress(ca)), _blocks(O.decompress(cb)), _blocks(O.decompress(cs))
+    w = np.fromfunction(lambda i, j: i + j, (8, 8))
+    for b in range(cs.nb):
+        bound = w * abs(cs.s[b]) * np.sqrt(28) / cs.phi[b] + 1e-12 * (1 + np.abs(da[b] + db[b]).max())
+        assert np.all(np.abs(ds[b] - (da[b] + db[b])) <= bound), b
+
+
+def test_add_of_compressed_approximates_the_sum_within_bounds():
+    """|U(C(A)+C(B)) - (A+B)| <= add quantization bound + both round-trip bounds."""
+    A, B = W.plain_pair()
+    ca, cb = O.compress(A), O.compress(B)
+    cs = O.add(ca, cb)
+    ds = _blocks(O.decompress(cs))
+    ba, bb = _blocks(A), _blocks(B)
+    w = np.fromfunction(lambda i, j: i + j, (8, 8))
+    for b in range(0, cs.nb, 5):
+        bound = (w * abs(cs.s[b]) * np.sqrt(28) / cs.phi[b] + _roundtrip_bound(O.block_stages(ba[b]))
+                 + _roundtrip_bound(O.block_stages(bb[b])) + 1e-12 * (1 + np.abs(ba[b] + bb[b]).max()))
+        assert np.all(np.abs(ds[b] - (ba[b] + bb[b])) <= bound), b
+
+
+def test_add_constant_block_and_zero_slope():
+    M = np.fromfunction(lambda i, j: np.sin(i / 3) + j / 5, (8, 16))
+    M[:, 8:] = 2.0                      # second block constant
+    c = O.compress(M)
+    z = O.add(c, O.scale(c, -1.0))
+    assert z.s[1] == 0.0 and not z.code[1].any()
+    assert z.s[0] == 0.0 and not z.code[0].any()
+    assert np.allclose(O.decompress(z), 0.0)
+
+
+@pytest.mark.parametrize("cst", [3.5, -2.0, 0.0, 1e-3])
+def test_scale_is_exact_on_f_and_s(cst):
+    A, _ = W.plain_pair()
+    c = O.compress(A)
+    d = O.scale(c, cst)
+    assert np.array_equal(d.phi, c.phi) and np.array_equal(d.code, c.code)
+    assert np.array_equal(d.f, c.f * cst) and np.array_equal(d.s, c.s * cst)
+    assert np.allclose(O.decompress(d), cst * O.decompress(c), rtol=1e-13, atol=1e-13)
+
+
+# --- dot products and the matrix product ------------------------------------------
+def test_dot_products_and_matmul_match_library():
+    A, B = W.plain_pair()
+    ca, cb = O.compress(A), O.compress(B)
+    Ah, Bh = O.decompress(ca), O.decompress(cb)
+    v, av = O.dot(ca, cb)
+    assert abs(v - np.dot(Ah.ravel(), Bh.ravel())) <= 1e-13 * av
+    P = Ah @ Bh
+    for i, j in [(17, 200), (0, 0), (255, 255), (100, 3)]:
+        r, ar = O.dot_rowcol(ca, cb, i, j)
+        assert abs(r - P[i, j]) <= 1e-13 * ar
+    Bd = W.smoothed_normal(256, 48, seed=7)
+    C = O.matmul(ca, Bd)
+    assert np.allclose(C, Ah @ Bd, rtol=0, atol=1e-13 * np.abs(Ah) .max() * np.abs(Bd).sum(0).max())
+    ii = np.array([0, 5, 5, 255]); jj = np.array([0, 1, 47, 13])
+    e, ae = O.matmul_entries(ca, Bd, ii, jj)
+    assert np.allclose(e, C[ii, jj], rtol=1e-14, atol=1e-14)
+
+
+def test_dot_rowcol_is_an_entry_of_the_product():
+    A = W.random_block_matrix(16, 24, 3)
+    B = W.random_block_matrix(24, 32, 4)
+    ca, cb = O.compress(A), O.compress(B)
+    P = O.decompress(ca) @ O.decompress(cb)
+    for i in range(0, 16, 5):
+        for j in range(0, 32, 7):
+            r, ar = O.dot_rowcol(ca, cb, i, j)
+            assert abs(r - P[i, j]) <= 1e-13 * ar
+
+
+# --- Table I sanity band (grid size unstated: a band, not parity) -----------------------
+@pytest.mark.parametrize("k,paper", [(1, 0.0043), (2, 0.0039), (3, 0.0053), (4, 0.0044), (5, 0.0195), (6, 0.0117)])
+def test_table1_round_trip_error_band(k, paper):
+    M = W.paper_function(k, 1000)
+    back = O.decompress(O.compress(M))
+    e = np.mean(np.abs((back - M) / M))
+    assert paper / 10 < e < paper * 10, e
+
+
+def test_add_codes_against_exact_rational_algorithm1():
+    """Algorithm 1 in exact rational arithmetic; slopes of opposite sign make
+    the combined codes saturate at +-127 (Sec. III, Algorithm 2 allows c < 0)."""
+    from fractions import Fraction as Fr
+
+    A = W.random_block_matrix(32, 32, 5)
+    ca = O.compress(A)
+    cb = O.compress(np.ascontiguousarray(A.T))      # same slopes block-by-block up to order
+    for cst in (1.0, -0.97, 2.5, -0.5):
+        cbs = O.scale(cb, cst)
+        out = O.add(ca, cbs)
+        n_sat = 0
+        for b in range(out.nb):
+            s = Fr(ca.s[b]) + Fr(cbs.s[b])
+            if s == 0:
+                assert not out.code[b].any()
+                continue
+            ph = max(1, (int(ca.phi[b]) * int(cbs.phi[b])) // (int(ca.phi[b]) + int(cbs.phi[b])))
+            assert out.phi[b] == ph
+            b1 = Fr(ca.s[b]) / s / int(ca.phi[b]) * ph
+            b2 = Fr(cbs.s[b]) / s / int(cbs.phi[b]) * ph
+            for t in range(28):
+                v = b1 * int(ca.code[b, t]) + b2 * int(cbs.code[b, t])
+                if v != 0 and abs(v - round(v)) < Fr(1, 10**9):
+                    continue
+                want = max(-127, min(127, int(v)))          # int() truncates toward zero
+                n_sat += abs(want) == 127
+                assert out.code[b, t] == want, (cst, b, t)
+        if cst == -0.97:
+            assert n_sat > 0
