@@ -1,0 +1,145 @@
+/*
+ * blaz.h -- C ABI of the GB300 (sm_103a) implementation of the blaz
+ * compressed-matrix method of "Compressed Matrix Computations"
+ * (M. Martel, arXiv 2202.13007).
+ *
+ * A binary64 matrix whose sides are multiples of 8 is cut into 8x8 blocks
+ * (Sec. II, "Block Splitting").  Each block is stored as
+ *     f    binary64  first element M00                      (Sec. II, Eq. eqnorm)
+ *     s    binary64  mean slope of the normalized block      (Eq. eqslope)
+ *     phi  uint8     re-scaling factor 127/m, truncated      (Eq. eqphi)
+ *     code int8[28]  truncated phi*DCT coefficients of the first two rows
+ *                    and first two columns                   (Sec. II, Ex. 5)
+ * i.e. 360 bits per block instead of 4096 (compression ratio 11.37).
+ *
+ * Conventions for every entry point below:
+ *   - Matrices are row-major; lda/ldb/ldc are leading dimensions in elements.
+ *   - Blocks are numbered row-major over the (rows/8) x (cols/8) block grid;
+ *     kept code t of a block sits at code[block*28 + t], in the order
+ *     row 0 (j = 0..7), row 1 (j = 0..7), then (i,0),(i,1) for i = 2..7.
+ *   - Every pointer marked "device" must point to memory of the current CUDA
+ *     device; "host" pointers are ordinary host memory.  The caller owns all
+ *     buffers and streams it passes; the library keeps no reference to them
+ *     after the call returns.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  All work is enqueued asynchronously on it in stream order;
+ *     the functions do not synchronize unless stated.
+ *   - Return value: BLAZ_OK (0) or a negative BLAZ_ERR_* code.  Argument
+ *     errors are detected on the host before anything is enqueued; a CUDA
+ *     launch error is reported as BLAZ_ERR_CUDA (blaz_last_cuda_error() gives
+ *     the CUDA error code).
+ */
+#ifndef BLAZ_H
+#define BLAZ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BLAZ_NKEEP 28
+
+enum {
+    BLAZ_OK = 0,
+    BLAZ_ERR_SHAPE = -1,    /* a side is negative or not a multiple of 8, or shapes differ */
+    BLAZ_ERR_NULL = -2,     /* a required pointer is NULL                                  */
+    BLAZ_ERR_LD = -3,       /* leading dimension smaller than the row length               */
+    BLAZ_ERR_OOM = -4,      /* device allocation failed                                    */
+    BLAZ_ERR_CUDA = -5,     /* a CUDA runtime call or kernel launch failed                 */
+    BLAZ_ERR_BUSY = -6,     /* server: no free slot right now                              */
+    BLAZ_ERR_TIMEOUT = -7,  /* a bounded device wait ran out                               */
+    BLAZ_ERR_BUDGET = -8,   /* server: request exceeds the admission budget                */
+    BLAZ_ERR_ARG = -9,      /* any other invalid argument (mode, index, count)             */
+    BLAZ_ERR_RANGE = -10    /* an index is outside the matrix                              */
+};
+
+/* A compressed matrix: structure of arrays in device memory, nb = (rows/8)*(cols/8).
+ * f and s must be 8-byte aligned and code 4-byte aligned (BLAZ_ERR_ARG otherwise). */
+typedef struct blaz_cmat {
+    int64_t rows, cols;   /* multiples of 8                               */
+    double *f;            /* device, [nb]                                 */
+    double *s;            /* device, [nb]                                 */
+    uint8_t *phi;         /* device, [nb]                                 */
+    int8_t *code;         /* device, [nb][28]                             */
+} blaz_cmat;
+
+/* Human-readable name of a status code (static string). */
+const char *blaz_strerror(int status);
+/* CUDA error code (cudaError_t as int) of the last BLAZ_ERR_CUDA on this thread. */
+int blaz_last_cuda_error(void);
+
+/* Library-owned storage for a compressed matrix (stream-ordered allocation
+ * on `stream`).  rows, cols >= 0 and multiples of 8.  The arrays are not
+ * initialised.  Free with blaz_cmat_free on a stream ordered after last use. */
+int blaz_cmat_alloc(blaz_cmat *m, int64_t rows, int64_t cols, void *stream);
+int blaz_cmat_free(blaz_cmat *m, void *stream);
+
+/* The binary64 constants of the library's DCT (Sec. III, Eq. eqdct):
+ * cos_out[k*8+x] = RN(cos((2x+1) k pi / 16)), aa_out[i*8+j] = RN(alpha_i alpha_j)
+ * with alpha_0 = sqrt(1/8), alpha_k = 1/2; kept_out[2t], kept_out[2t+1] =
+ * (row, col) of kept code t.  Host pointers; no GPU needed. */
+void blaz_constants(double cos_out[64], double aa_out[64], int32_t kept_out[56]);
+
+/* Compression, Sec. II (Fig. 1 pipeline; Eqs. eqnorm, eqslope, eqdct, eqphi):
+ * A: device, rows x cols binary64, row-major with leading dimension lda >= cols.
+ * out: rows/cols set by the caller, arrays preallocated (device).
+ * Codes, phi and s are bit-identical to the binary64 operation order
+ *   D(i,j) per Eq. eqnorm, interior ((Mij - Mi-1,j) + (Mij - Mi,j-1)) * 0.5;
+ *   K = #{D != 0}; S = sum |D| row-major left to right; s = S / K (0 if K = 0);
+ *   D' = D * (1/s); T[u][j] = sum_v D'[u][v] cos_jv (v ascending);
+ *   U[i][j] = sum_u cos_iu T[u][j] (u ascending); X = RN(alpha_i alpha_j) * U;
+ *   m = max |X|; phi = trunc(127/m) clamped to [1,255];
+ *   code = trunc(X * phi) saturated to [-127,127], NaN -> 0.  */
+int blaz_compress(const double *A, int64_t lda, blaz_cmat *out, void *stream);
+
+/* Decompression (inverse of Sec. II; Eq. eqbbb read as the exact inverse of
+ * Eq. eqnorm): X = code/phi on the kept positions, 0 elsewhere;
+ * D_hat = s * IDCT(X); B00 = f, B0j = B0,j-1 + D_hat0j, Bi0 = Bi-1,0 + D_hati0,
+ * Bij = (Bi-1,j + Bi,j-1)/2 + D_hatij.  A: device, lda >= cols. */
+int blaz_decompress(const blaz_cmat *a, double *A, int64_t lda, void *stream);
+
+/* Addition of compressed matrices, Algorithm 1 (Sec. III, Eq. eq55), per block:
+ * f = f1+f2, s = s1+s2, phi = max(1, (phi1*phi2) div (phi1+phi2)),
+ * alpha_k = s_k/s, beta_k = (alpha_k/phi_k)*phi,
+ * code = trunc(beta1*c1 + beta2*c2) saturated to [-127,127] (0 when s == 0).
+ * a, b, out: same shape; out may alias a or b entirely. Bit-exact binary64. */
+int blaz_add(const blaz_cmat *a, const blaz_cmat *b, blaz_cmat *out, void *stream);
+
+/* Subtraction (Sec. III states it works like addition; not detailed there):
+ * f = f1-f2, s = s1+s2, phi as in blaz_add, code = trunc(beta1*c1 - beta2*c2). */
+int blaz_sub(const blaz_cmat *a, const blaz_cmat *b, blaz_cmat *out, void *stream);
+
+/* Multiplication by a constant, Algorithm 2: f = f1*c, s = s1*c, phi and code
+ * copied.  out may equal a (in place: only f and s are rewritten). */
+int blaz_scale(const blaz_cmat *a, double c, blaz_cmat *out, void *stream);
+
+/* Flattened dot product <vec A_hat, vec B_hat> = sum_ij A_hat_ij B_hat_ij of
+ * two compressed matrices of the same shape (A_hat, B_hat the decompressed
+ * matrices).  result: device, one binary64, written in stream order.
+ * Deterministic: same inputs give the same bits.  Uses stream-ordered scratch
+ * (cudaMallocAsync on `stream`). */
+int blaz_dot(const blaz_cmat *a, const blaz_cmat *b, double *result, void *stream);
+
+/* Dot product of line i of A_hat and column j of B_hat, Algorithm 3 (Eqs.
+ * eqbbb0, eqbbb) applied block-wise: sum_k A_hat[i][k] B_hat[k][j].
+ * a: n x k, b: k x m; 0 <= i < n, 0 <= j < m.  result: device, one binary64. */
+int blaz_dot_rowcol(const blaz_cmat *a, const blaz_cmat *b, int64_t i, int64_t j, double *result,
+                    void *stream);
+
+/* Matrix product C = A_hat * B of a compressed n x k matrix by a dense
+ * binary64 k x m matrix (Sec. III, "Matrix multiplication": each block is
+ * decompressed once).  B: device, ldb >= m; C: device, ldc >= m.
+ * mode BLAZ_MM_FP64: binary64 products on the FP64 tensor path (DMMA);
+ * mode BLAZ_MM_SPLIT_BF16: A_hat and B split into bf16 slices, slice products
+ * on the 5th-generation tensor cores (tcgen05, fp32 accumulation), combined
+ * in binary64.  Uses stream-ordered scratch for the decompressed operand. */
+enum { BLAZ_MM_FP64 = 0, BLAZ_MM_SPLIT_BF16 = 1 };
+int blaz_matmul(const blaz_cmat *a, const double *B, int64_t ldb, int64_t m, double *C, int64_t ldc,
+                int mode, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BLAZ_H */

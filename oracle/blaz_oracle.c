@@ -283,12 +283,15 @@ void blazo_decompress_block(double f, double s, uint8_t phi, const int8_t *code,
         }
 }
 
-/* Algorithm 1: addition of two compressed blocks. */
-void blazo_add_block(double f1, double s1, uint8_t phi1, const int8_t *c1,
-                     double f2, double s2, uint8_t phi2, const int8_t *c2,
-                     double *f, double *s, uint8_t *phi, int8_t *c)
+/* Algorithm 1: addition of two compressed blocks.  With sub != 0 the same
+ * algorithm subtracts (Sec. III: subtraction works like addition): the first
+ * elements are subtracted, the slopes still add (s = s1 + s2 keeps the
+ * combined block's scale positive) and the rescaled codes are subtracted. */
+static void addsub_block(int sub, double f1, double s1, uint8_t phi1, const int8_t *c1,
+                         double f2, double s2, uint8_t phi2, const int8_t *c2,
+                         double *f, double *s, uint8_t *phi, int8_t *c)
 {
-    double fs = f1 + f2;
+    double fs = sub ? f1 - f2 : f1 + f2;
     double ss = s1 + s2;
     int p1 = phi1, p2 = phi2;
     int ph = (p1 * p2) / (p1 + p2);         /* integer product and quotient */
@@ -305,7 +308,22 @@ void blazo_add_block(double f1, double s1, uint8_t phi1, const int8_t *c1,
     double b1 = (a1 / (double)p1) * (double)ph;
     double b2 = (a2 / (double)p2) * (double)ph;
     for (int t = 0; t < NKEEP; ++t)
-        c[t] = quantize_code(b1 * (double)c1[t] + b2 * (double)c2[t]);
+        c[t] = quantize_code(sub ? b1 * (double)c1[t] - b2 * (double)c2[t]
+                                 : b1 * (double)c1[t] + b2 * (double)c2[t]);
+}
+
+void blazo_add_block(double f1, double s1, uint8_t phi1, const int8_t *c1,
+                     double f2, double s2, uint8_t phi2, const int8_t *c2,
+                     double *f, double *s, uint8_t *phi, int8_t *c)
+{
+    addsub_block(0, f1, s1, phi1, c1, f2, s2, phi2, c2, f, s, phi, c);
+}
+
+void blazo_sub_block(double f1, double s1, uint8_t phi1, const int8_t *c1,
+                     double f2, double s2, uint8_t phi2, const int8_t *c2,
+                     double *f, double *s, uint8_t *phi, int8_t *c)
+{
+    addsub_block(1, f1, s1, phi1, c1, f2, s2, phi2, c2, f, s, phi, c);
 }
 
 /* Algorithm 2: multiplication of a compressed block by a constant. */
@@ -396,6 +414,17 @@ int blazo_add(int64_t nb,
 {
     for (int64_t b = 0; b < nb; ++b)
         blazo_add_block(f1[b], s1[b], phi1[b], &c1[b * NKEEP], f2[b], s2[b], phi2[b], &c2[b * NKEEP],
+                        &f[b], &s[b], &phi[b], &c[b * NKEEP]);
+    return ORC_OK;
+}
+
+int blazo_sub(int64_t nb,
+              const double *f1, const double *s1, const uint8_t *phi1, const int8_t *c1,
+              const double *f2, const double *s2, const uint8_t *phi2, const int8_t *c2,
+              double *f, double *s, uint8_t *phi, int8_t *c)
+{
+    for (int64_t b = 0; b < nb; ++b)
+        blazo_sub_block(f1[b], s1[b], phi1[b], &c1[b * NKEEP], f2[b], s2[b], phi2[b], &c2[b * NKEEP],
                         &f[b], &s[b], &phi[b], &c[b * NKEEP]);
     return ORC_OK;
 }

@@ -83,12 +83,13 @@ def _declare(L):
     L.blazo_compress_blocks.argtypes = [_D, _i64, _i64, _i64, _I64, _i64, _D, _D, _U8, _I8]
     L.blazo_decompress.argtypes = [_D, _D, _U8, _I8, _i64, _i64, _D, _i64]
     L.blazo_add.argtypes = [_i64, _D, _D, _U8, _I8, _D, _D, _U8, _I8, _D, _D, _U8, _I8]
+    L.blazo_sub.argtypes = [_i64, _D, _D, _U8, _I8, _D, _D, _U8, _I8, _D, _D, _U8, _I8]
     L.blazo_scale.argtypes = [_i64, _D, _D, _U8, _I8, ctypes.c_double, _D, _D, _U8, _I8]
     L.blazo_dot.argtypes = [_D, _D, _U8, _I8, _D, _D, _U8, _I8, _i64, _D, _D]
     L.blazo_dot_rowcol.argtypes = [_D, _D, _U8, _I8, _i64, _i64, _D, _D, _U8, _I8, _i64, _i64, _i64, _D, _D]
     L.blazo_matmul_entries.argtypes = [_D, _D, _U8, _I8, _i64, _i64, _D, _i64, _i64, _I64, _I64, _i64, _D, _D]
     L.blazo_matmul.argtypes = [_D, _D, _U8, _I8, _i64, _i64, _D, _i64, _i64, _D, _i64]
-    for name in ("blazo_compress", "blazo_compress_blocks", "blazo_decompress", "blazo_add", "blazo_scale",
+    for name in ("blazo_compress", "blazo_compress_blocks", "blazo_decompress", "blazo_add", "blazo_sub", "blazo_scale",
                  "blazo_dot", "blazo_dot_rowcol", "blazo_matmul_entries", "blazo_matmul"):
         getattr(L, name).restype = ctypes.c_int
     for name in ("blazo_dct_tables", "blazo_kept_positions", "blazo_block_stages", "blazo_compress_block",
@@ -204,6 +205,16 @@ def add(a: CMat, b: CMat) -> CMat:
     _chk(lib().blazo_add(a.nb, _p(a.f, _D), _p(a.s, _D), _p(a.phi, _U8), _p(a.code, _I8),
                          _p(b.f, _D), _p(b.s, _D), _p(b.phi, _U8), _p(b.code, _I8),
                          _p(out.f, _D), _p(out.s, _D), _p(out.phi, _U8), _p(out.code, _I8)), "add")
+    return out
+
+
+def sub(a: CMat, b: CMat) -> CMat:
+    """Subtraction read from Sec. III (works like Algorithm 1)."""
+    assert (a.rows, a.cols) == (b.rows, b.cols)
+    out = CMat.empty(a.rows, a.cols)
+    _chk(lib().blazo_sub(a.nb, _p(a.f, _D), _p(a.s, _D), _p(a.phi, _U8), _p(a.code, _I8),
+                         _p(b.f, _D), _p(b.s, _D), _p(b.phi, _U8), _p(b.code, _I8),
+                         _p(out.f, _D), _p(out.s, _D), _p(out.phi, _U8), _p(out.code, _I8)), "sub")
     return out
 
 

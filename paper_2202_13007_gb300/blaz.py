@@ -1,0 +1,223 @@
+"""Thin ctypes binding of libblaz (include/blaz.h), same names as the C ABI.
+
+Argument marshalling only: every step of the compressed-matrix path runs in
+the library's CUDA kernels.  PyTorch provides device memory and streams.
+There is no fallback: if libblaz.so is missing or no GPU is present, calls
+raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+from . import _build
+
+NKEEP = 28
+MM_FP64 = 0
+MM_SPLIT_BF16 = 1
+_MODES = {"fp64": MM_FP64, "split_bf16": MM_SPLIT_BF16}
+
+
+class BlazError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        msg = lib().blaz_strerror(status).decode()
+        if status == -5:
+            msg += f" (cudaError {lib().blaz_last_cuda_error()})"
+        super().__init__(f"{what}: {msg} [{status}]")
+        self.status = status
+
+
+class _CMatDesc(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_int64), ("cols", ctypes.c_int64), ("f", ctypes.c_void_p),
+                ("s", ctypes.c_void_p), ("phi", ctypes.c_void_p), ("code", ctypes.c_void_p)]
+
+
+_lib = None
+
+# Every entry point of include/blaz.h with its ctypes signature.
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_DESC = ctypes.POINTER(_CMatDesc)
+SIGNATURES = {
+    "blaz_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "blaz_last_cuda_error": (ctypes.c_int, []),
+    "blaz_constants": (None, [_P, _P, _P]),
+    "blaz_cmat_alloc": (ctypes.c_int, [_DESC, _I64, _I64, _P]),
+    "blaz_cmat_free": (ctypes.c_int, [_DESC, _P]),
+    "blaz_compress": (ctypes.c_int, [_P, _I64, _DESC, _P]),
+    "blaz_decompress": (ctypes.c_int, [_DESC, _P, _I64, _P]),
+    "blaz_add": (ctypes.c_int, [_DESC, _DESC, _DESC, _P]),
+    "blaz_sub": (ctypes.c_int, [_DESC, _DESC, _DESC, _P]),
+    "blaz_scale": (ctypes.c_int, [_DESC, ctypes.c_double, _DESC, _P]),
+    "blaz_dot": (ctypes.c_int, [_DESC, _DESC, _P, _P]),
+    "blaz_dot_rowcol": (ctypes.c_int, [_DESC, _DESC, _I64, _I64, _P, _P]),
+    "blaz_matmul": (ctypes.c_int, [_DESC, _P, _I64, _I64, _P, _I64, ctypes.c_int, _P]),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libblaz.so (build it first with ``__graft_entry__.build()``)."""
+    global _lib
+    if _lib is None:
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libblaz.so is not built ({path}); run __graft_entry__.build()")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise BlazError(rc, what)
+
+
+def _dev_f64(t: torch.Tensor, name: str):
+    if not (t.is_cuda and t.dtype == torch.float64 and t.dim() == 2):
+        raise TypeError(f"{name} must be a 2-D float64 CUDA tensor")
+    if t.stride(1) != 1:
+        raise TypeError(f"{name} must have unit column stride")
+
+
+@dataclass
+class CMat:
+    """A compressed matrix in device memory (structure of arrays, Sec. II)."""
+
+    rows: int
+    cols: int
+    f: torch.Tensor      # float64 [nb]
+    s: torch.Tensor      # float64 [nb]
+    phi: torch.Tensor    # uint8   [nb]
+    code: torch.Tensor   # int8    [nb, 28]
+
+    @property
+    def nb(self) -> int:
+        return (self.rows // 8) * (self.cols // 8)
+
+    @property
+    def nbytes(self) -> int:
+        return self.nb * (8 + 8 + 1 + NKEEP)
+
+    @staticmethod
+    def empty(rows: int, cols: int, device=None) -> "CMat":
+        device = device or torch.device("cuda", torch.cuda.current_device())
+        if rows % 8 or cols % 8 or rows < 0 or cols < 0:
+            raise ValueError("sides must be non-negative multiples of 8")
+        nb = (rows // 8) * (cols // 8)
+        return CMat(rows, cols, torch.empty(nb, dtype=torch.float64, device=device),
+                    torch.empty(nb, dtype=torch.float64, device=device),
+                    torch.empty(nb, dtype=torch.uint8, device=device),
+                    torch.empty((nb, NKEEP), dtype=torch.int8, device=device))
+
+    def desc(self) -> _CMatDesc:
+        return _CMatDesc(self.rows, self.cols, self.f.data_ptr(), self.s.data_ptr(), self.phi.data_ptr(),
+                         self.code.data_ptr())
+
+    def to_host(self):
+        return (self.f.cpu().numpy(), self.s.cpu().numpy(), self.phi.cpu().numpy(), self.code.cpu().numpy())
+
+
+def constants():
+    """(cos table [8,8], alpha_i alpha_j table [8,8], kept positions [28,2]) of the library."""
+    import numpy as np
+
+    c = np.zeros(64)
+    a = np.zeros(64)
+    k = np.zeros(56, np.int32)
+    lib().blaz_constants(c.ctypes.data, a.ctypes.data, k.ctypes.data)
+    return c.reshape(8, 8), a.reshape(8, 8), k.reshape(28, 2)
+
+
+def blaz_compress(A: torch.Tensor, out: CMat | None = None, stream=None) -> CMat:
+    _dev_f64(A, "A")
+    rows, cols = A.shape
+    out = out or CMat.empty(rows, cols, A.device)
+    if (out.rows, out.cols) != (rows, cols):
+        raise ValueError("out shape mismatch")
+    d = out.desc()
+    _check(lib().blaz_compress(A.data_ptr(), A.stride(0), ctypes.byref(d), _stream(stream)), "blaz_compress")
+    return out
+
+
+def blaz_decompress(a: CMat, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    if out is None:
+        out = torch.empty((a.rows, a.cols), dtype=torch.float64, device=a.f.device)
+    _dev_f64(out, "out")
+    d = a.desc()
+    _check(lib().blaz_decompress(ctypes.byref(d), out.data_ptr(), out.stride(0), _stream(stream)),
+           "blaz_decompress")
+    return out
+
+
+def _binary(name, a: CMat, b: CMat, out: CMat | None, stream):
+    out = out or CMat.empty(a.rows, a.cols, a.f.device)
+    da, db, do = a.desc(), b.desc(), out.desc()
+    _check(getattr(lib(), name)(ctypes.byref(da), ctypes.byref(db), ctypes.byref(do), _stream(stream)), name)
+    return out
+
+
+def blaz_add(a: CMat, b: CMat, out: CMat | None = None, stream=None) -> CMat:
+    return _binary("blaz_add", a, b, out, stream)
+
+
+def blaz_sub(a: CMat, b: CMat, out: CMat | None = None, stream=None) -> CMat:
+    return _binary("blaz_sub", a, b, out, stream)
+
+
+def blaz_scale(a: CMat, c: float, out: CMat | None = None, stream=None) -> CMat:
+    out = out or CMat.empty(a.rows, a.cols, a.f.device)
+    da, do = a.desc(), out.desc()
+    _check(lib().blaz_scale(ctypes.byref(da), float(c), ctypes.byref(do), _stream(stream)), "blaz_scale")
+    return out
+
+
+def blaz_dot(a: CMat, b: CMat, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    out = out if out is not None else torch.empty((), dtype=torch.float64, device=a.f.device)
+    da, db = a.desc(), b.desc()
+    _check(lib().blaz_dot(ctypes.byref(da), ctypes.byref(db), out.data_ptr(), _stream(stream)), "blaz_dot")
+    return out
+
+
+def blaz_dot_rowcol(a: CMat, b: CMat, i: int, j: int, out: torch.Tensor | None = None, stream=None):
+    out = out if out is not None else torch.empty((), dtype=torch.float64, device=a.f.device)
+    da, db = a.desc(), b.desc()
+    _check(lib().blaz_dot_rowcol(ctypes.byref(da), ctypes.byref(db), int(i), int(j), out.data_ptr(),
+                                 _stream(stream)), "blaz_dot_rowcol")
+    return out
+
+
+def blaz_matmul(a: CMat, B: torch.Tensor, mode: str = "fp64", out: torch.Tensor | None = None,
+                stream=None) -> torch.Tensor:
+    _dev_f64(B, "B")
+    if B.shape[0] != a.cols:
+        raise ValueError("inner dimensions differ")
+    m = B.shape[1]
+    if out is None:
+        out = torch.empty((a.rows, m), dtype=torch.float64, device=B.device)
+    _dev_f64(out, "out")
+    da = a.desc()
+    _check(lib().blaz_matmul(ctypes.byref(da), B.data_ptr(), B.stride(0), m, out.data_ptr(), out.stride(0),
+                             _MODES[mode], _stream(stream)), "blaz_matmul")
+    return out
+
+
+# short aliases
+compress, decompress, add, sub, scale = blaz_compress, blaz_decompress, blaz_add, blaz_sub, blaz_scale
+dot, dot_rowcol, matmul = blaz_dot, blaz_dot_rowcol, blaz_matmul

@@ -1,0 +1,265 @@
+// blaz_api.cu -- the extern "C" entry points declared in include/blaz.h:
+// argument validation on the host, then stream-ordered kernel launches.
+#include <cstdio>
+#include <mutex>
+#include <vector>
+
+#include "blaz_internal.cuh"
+
+namespace blaz {
+
+static thread_local int g_last_cuda = 0;
+
+int set_cuda_error(cudaError_t e)
+{
+    g_last_cuda = (int)e;
+    return BLAZ_ERR_CUDA;
+}
+
+int launch_status()
+{
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? BLAZ_OK : set_cuda_error(e);
+}
+
+int num_sms()
+{
+    static std::mutex mu;
+    static std::vector<int> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    std::lock_guard<std::mutex> lk(mu);
+    if ((int)cache.size() <= dev) cache.resize(dev + 1, 0);
+    if (cache[dev] == 0) {
+        int n = 0;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        cache[dev] = n > 0 ? n : 1;
+    }
+    return cache[dev];
+}
+
+static int check_dims(int64_t rows, int64_t cols)
+{
+    if (rows < 0 || cols < 0 || rows % 8 || cols % 8) return BLAZ_ERR_SHAPE;
+    return BLAZ_OK;
+}
+
+static int64_t nblocks(const blaz_cmat *m) { return (m->rows / 8) * (m->cols / 8); }
+
+// A compressed matrix descriptor is valid when its sides are multiples of 8
+// and, unless it is empty, all four arrays are set.
+static int check_cmat(const blaz_cmat *m)
+{
+    if (!m) return BLAZ_ERR_NULL;
+    int rc = check_dims(m->rows, m->cols);
+    if (rc) return rc;
+    if (nblocks(m) > 0 && (!m->f || !m->s || !m->phi || !m->code)) return BLAZ_ERR_NULL;
+    // f and s are read as binary64, the codes as 32-bit words.
+    if ((uintptr_t)m->f % 8 || (uintptr_t)m->s % 8 || (uintptr_t)m->code % 4) return BLAZ_ERR_ARG;
+    return BLAZ_OK;
+}
+
+static int same_shape(const blaz_cmat *a, const blaz_cmat *b)
+{
+    return (a->rows == b->rows && a->cols == b->cols) ? BLAZ_OK : BLAZ_ERR_SHAPE;
+}
+
+// Stream-ordered scratch that is released on the same stream.
+struct Scratch {
+    void *p = nullptr;
+    cudaStream_t st;
+    explicit Scratch(cudaStream_t s) : st(s) {}
+    int alloc(size_t bytes)
+    {
+        cudaError_t e = cudaMallocAsync(&p, bytes ? bytes : 16, st);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            cudaGetLastError();
+            return e == cudaErrorMemoryAllocation ? BLAZ_ERR_OOM : set_cuda_error(e);
+        }
+        return BLAZ_OK;
+    }
+    ~Scratch()
+    {
+        if (p) cudaFreeAsync(p, st);
+    }
+};
+
+}  // namespace blaz
+
+using namespace blaz;
+
+extern "C" {
+
+const char *blaz_strerror(int status)
+{
+    switch (status) {
+    case BLAZ_OK: return "ok";
+    case BLAZ_ERR_SHAPE: return "shape: sides must be non-negative multiples of 8 and operands must conform";
+    case BLAZ_ERR_NULL: return "a required pointer is NULL";
+    case BLAZ_ERR_LD: return "leading dimension smaller than the row length";
+    case BLAZ_ERR_OOM: return "device allocation failed";
+    case BLAZ_ERR_CUDA: return "CUDA runtime or launch error";
+    case BLAZ_ERR_BUSY: return "no free slot";
+    case BLAZ_ERR_TIMEOUT: return "bounded device wait ran out";
+    case BLAZ_ERR_BUDGET: return "request exceeds the admission budget";
+    case BLAZ_ERR_ARG: return "invalid argument";
+    case BLAZ_ERR_RANGE: return "index out of range";
+    default: return "unknown status";
+    }
+}
+
+int blaz_last_cuda_error(void) { return g_last_cuda; }
+
+void blaz_constants(double cos_out[64], double aa_out[64], int32_t kept_out[56])
+{
+    for (int k = 0; k < 8; ++k)
+        for (int x = 0; x < 8; ++x) {
+            if (cos_out) cos_out[k * 8 + x] = cos_tab(k, x);
+            if (aa_out) aa_out[k * 8 + x] = aa_tab(k, x);
+        }
+    if (kept_out)
+        for (int t = 0; t < kKeep; ++t) {
+            kept_out[2 * t] = kept_row(t);
+            kept_out[2 * t + 1] = kept_col(t);
+        }
+}
+
+int blaz_cmat_alloc(blaz_cmat *m, int64_t rows, int64_t cols, void *stream)
+{
+    if (!m) return BLAZ_ERR_NULL;
+    int rc = check_dims(rows, cols);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    m->rows = rows;
+    m->cols = cols;
+    m->f = m->s = nullptr;
+    m->phi = nullptr;
+    m->code = nullptr;
+    const int64_t nb = nblocks(m);
+    if (nb == 0) return BLAZ_OK;
+    // One allocation: f | s | code | phi (each 256-byte aligned).
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t of = 0, os = up(of + 8 * nb), oc = up(os + 8 * nb), op = up(oc + (size_t)kKeep * nb);
+    const size_t total = up(op + nb);
+    void *base = nullptr;
+    cudaError_t e = cudaMallocAsync(&base, total, st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? BLAZ_ERR_OOM : set_cuda_error(e);
+    }
+    char *b = (char *)base;
+    m->f = (double *)(b + of);
+    m->s = (double *)(b + os);
+    m->code = (int8_t *)(b + oc);
+    m->phi = (uint8_t *)(b + op);
+    return BLAZ_OK;
+}
+
+int blaz_cmat_free(blaz_cmat *m, void *stream)
+{
+    if (!m) return BLAZ_ERR_NULL;
+    if (m->f) {
+        cudaError_t e = cudaFreeAsync(m->f, (cudaStream_t)stream);
+        if (e != cudaSuccess) return set_cuda_error(e);
+    }
+    m->f = m->s = nullptr;
+    m->phi = nullptr;
+    m->code = nullptr;
+    return BLAZ_OK;
+}
+
+int blaz_compress(const double *A, int64_t lda, blaz_cmat *out, void *stream)
+{
+    int rc = check_cmat(out);
+    if (rc) return rc;
+    if (nblocks(out) == 0) return BLAZ_OK;
+    if (!A) return BLAZ_ERR_NULL;
+    if (lda < out->cols) return BLAZ_ERR_LD;
+    return launch_compress(A, lda, out, (cudaStream_t)stream);
+}
+
+int blaz_decompress(const blaz_cmat *a, double *A, int64_t lda, void *stream)
+{
+    int rc = check_cmat(a);
+    if (rc) return rc;
+    if (nblocks(a) == 0) return BLAZ_OK;
+    if (!A) return BLAZ_ERR_NULL;
+    if (lda < a->cols) return BLAZ_ERR_LD;
+    return launch_decompress(a, A, lda, (cudaStream_t)stream);
+}
+
+static int add_or_sub(const blaz_cmat *a, const blaz_cmat *b, blaz_cmat *out, bool sub, void *stream)
+{
+    int rc;
+    if ((rc = check_cmat(a)) || (rc = check_cmat(b)) || (rc = check_cmat(out))) return rc;
+    if ((rc = same_shape(a, b)) || (rc = same_shape(a, out))) return rc;
+    return launch_add(a, b, out, sub, (cudaStream_t)stream);
+}
+
+int blaz_add(const blaz_cmat *a, const blaz_cmat *b, blaz_cmat *out, void *stream)
+{
+    return add_or_sub(a, b, out, false, stream);
+}
+
+int blaz_sub(const blaz_cmat *a, const blaz_cmat *b, blaz_cmat *out, void *stream)
+{
+    return add_or_sub(a, b, out, true, stream);
+}
+
+int blaz_scale(const blaz_cmat *a, double c, blaz_cmat *out, void *stream)
+{
+    int rc;
+    if ((rc = check_cmat(a)) || (rc = check_cmat(out))) return rc;
+    if ((rc = same_shape(a, out))) return rc;
+    return launch_scale(a, c, out, (cudaStream_t)stream);
+}
+
+int blaz_dot(const blaz_cmat *a, const blaz_cmat *b, double *result, void *stream)
+{
+    int rc;
+    if ((rc = check_cmat(a)) || (rc = check_cmat(b))) return rc;
+    if ((rc = same_shape(a, b))) return rc;
+    if (!result) return BLAZ_ERR_NULL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int grid = dot_grid(nblocks(a));
+    Scratch ws(st);
+    if ((rc = ws.alloc(sizeof(double) * grid + 256))) return rc;
+    double *partials = (double *)ws.p;
+    unsigned *counter = (unsigned *)((char *)ws.p + ((sizeof(double) * grid + 255) & ~(size_t)255));
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    return launch_dot(a, b, result, partials, counter, grid, st);
+}
+
+int blaz_dot_rowcol(const blaz_cmat *a, const blaz_cmat *b, int64_t i, int64_t j, double *result, void *stream)
+{
+    int rc;
+    if ((rc = check_cmat(a)) || (rc = check_cmat(b))) return rc;
+    if (a->cols != b->rows) return BLAZ_ERR_SHAPE;
+    if (!result) return BLAZ_ERR_NULL;
+    if (i < 0 || i >= a->rows || j < 0 || j >= b->cols) return BLAZ_ERR_RANGE;
+    return launch_dot_rowcol(a, b, i, j, result, (cudaStream_t)stream);
+}
+
+int blaz_matmul(const blaz_cmat *a, const double *B, int64_t ldb, int64_t m, double *C, int64_t ldc, int mode,
+                void *stream)
+{
+    int rc;
+    if ((rc = check_cmat(a))) return rc;
+    if (m < 0) return BLAZ_ERR_SHAPE;
+    if (mode != BLAZ_MM_FP64 && mode != BLAZ_MM_SPLIT_BF16) return BLAZ_ERR_ARG;
+    const int64_t n = a->rows, k = a->cols;
+    if (n == 0 || m == 0) return BLAZ_OK;
+    if (!C || (k > 0 && !B)) return BLAZ_ERR_NULL;
+    if (ldc < m || (k > 0 && ldb < m)) return BLAZ_ERR_LD;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (mode == BLAZ_MM_SPLIT_BF16) return BLAZ_ERR_ARG;
+    Scratch ws(st);
+    if ((rc = ws.alloc(sizeof(double) * (size_t)(n * k)))) return rc;
+    double *Ah = (double *)ws.p;
+    if (k > 0 && (rc = launch_decompress(a, Ah, k, st))) return rc;
+    return launch_gemm_fp64(Ah, k, B, ldb, C, ldc, n, k, m, st);
+}
+
+}  // extern "C"

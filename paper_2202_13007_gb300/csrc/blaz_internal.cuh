@@ -1,0 +1,93 @@
+// blaz_internal.cuh -- device constants and helpers shared by the blaz CUDA
+// kernels (GB300, sm_103a).  Block format and constants follow Sec. II/III of
+// "Compressed Matrix Computations" (arXiv 2202.13007).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/blaz.h"
+
+namespace blaz {
+
+constexpr int kKeep = BLAZ_NKEEP;  // 28 kept coefficients per block (Sec. II, Ex. 5)
+
+// RN(cos((2x+1) k pi / 16)), k = row, x = column (Sec. III, Eq. eqdct).
+// Correctly rounded binary64 values of the mathematical constants.
+#define BLAZ_C1 0x1.f6297cff75cb0p-1   // cos(1 pi/16)
+#define BLAZ_C2 0x1.d906bcf328d46p-1   // cos(2 pi/16)
+#define BLAZ_C3 0x1.a9b66290ea1a3p-1   // cos(3 pi/16)
+#define BLAZ_C4 0x1.6a09e667f3bcdp-1   // cos(4 pi/16)
+#define BLAZ_C5 0x1.1c73b39ae68c8p-1   // cos(5 pi/16)
+#define BLAZ_C6 0x1.87de2a6aea963p-2   // cos(6 pi/16)
+#define BLAZ_C7 0x1.8f8b83c69a60bp-3   // cos(7 pi/16)
+// RN(alpha_i alpha_j): alpha_0^2 = 1/8, alpha_0 alpha_k = sqrt(2)/8, alpha_k^2 = 1/4.
+#define BLAZ_A00 0x1.0000000000000p-3
+#define BLAZ_A0K 0x1.6a09e667f3bcdp-3
+#define BLAZ_AKK 0x1.0000000000000p-2
+
+// COS[k][x] as a compile-time table (used with constant indices only, so it
+// folds into immediates).
+__host__ __device__ constexpr double cos_tab(int k, int x)
+{
+#define C(a, b, c, d, e, f, g, h) \
+    (x == 0 ? (a) : x == 1 ? (b) : x == 2 ? (c) : x == 3 ? (d) : x == 4 ? (e) : x == 5 ? (f) : x == 6 ? (g) : (h))
+    return k == 0   ? 1.0
+           : k == 1 ? C(BLAZ_C1, BLAZ_C3, BLAZ_C5, BLAZ_C7, -BLAZ_C7, -BLAZ_C5, -BLAZ_C3, -BLAZ_C1)
+           : k == 2 ? C(BLAZ_C2, BLAZ_C6, -BLAZ_C6, -BLAZ_C2, -BLAZ_C2, -BLAZ_C6, BLAZ_C6, BLAZ_C2)
+           : k == 3 ? C(BLAZ_C3, -BLAZ_C7, -BLAZ_C1, -BLAZ_C5, BLAZ_C5, BLAZ_C1, BLAZ_C7, -BLAZ_C3)
+           : k == 4 ? C(BLAZ_C4, -BLAZ_C4, -BLAZ_C4, BLAZ_C4, BLAZ_C4, -BLAZ_C4, -BLAZ_C4, BLAZ_C4)
+           : k == 5 ? C(BLAZ_C5, -BLAZ_C1, BLAZ_C7, BLAZ_C3, -BLAZ_C3, -BLAZ_C7, BLAZ_C1, -BLAZ_C5)
+           : k == 6 ? C(BLAZ_C6, -BLAZ_C2, BLAZ_C2, -BLAZ_C6, -BLAZ_C6, BLAZ_C2, -BLAZ_C2, BLAZ_C6)
+                    : C(BLAZ_C7, -BLAZ_C5, BLAZ_C3, -BLAZ_C1, BLAZ_C1, -BLAZ_C3, BLAZ_C5, -BLAZ_C7);
+#undef C
+}
+
+__host__ __device__ constexpr double aa_tab(int i, int j)
+{
+    return (i == 0 && j == 0) ? BLAZ_A00 : (i == 0 || j == 0) ? BLAZ_A0K : BLAZ_AKK;
+}
+
+// Kept position t -> (row, col): row 0, row 1, then (i,0),(i,1) for i = 2..7.
+__host__ __device__ constexpr int kept_row(int t) { return t < 16 ? t / 8 : 2 + (t - 16) / 2; }
+__host__ __device__ constexpr int kept_col(int t) { return t < 16 ? t % 8 : (t - 16) % 2; }
+// Inverse map: kept index of (i,j), or -1 when the coefficient is dropped.
+__host__ __device__ constexpr int kept_index(int i, int j)
+{
+    return i < 2 ? i * 8 + j : (j < 2 ? 16 + (i - 2) * 2 + j : -1);
+}
+
+// Binary64 operations that the compiler may not fuse or reorder.
+__device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double ddiv(double a, double b) { return __ddiv_rn(a, b); }
+
+// trunc toward zero, saturated to [-127, 127], NaN -> 0.
+__device__ __forceinline__ int8_t quantize(double v)
+{
+    if (v != v) return 0;
+    if (v >= 127.0) return 127;
+    if (v <= -127.0) return -127;
+    return (int8_t)__double2int_rz(v);
+}
+
+// ---- host-side launch plumbing (defined in blaz_api.cu) ------------------------
+int set_cuda_error(cudaError_t e);   // records e, returns BLAZ_ERR_CUDA
+int launch_status();                 // cudaGetLastError -> BLAZ_OK / BLAZ_ERR_CUDA
+int num_sms();                       // SM count of the current device (cached)
+
+// ---- launchers (one per kernel family) ------------------------------------------
+int launch_compress(const double *A, int64_t lda, const blaz_cmat *out, cudaStream_t st);
+int launch_decompress(const blaz_cmat *a, double *A, int64_t lda, cudaStream_t st);
+int launch_add(const blaz_cmat *a, const blaz_cmat *b, const blaz_cmat *out, bool subtract, cudaStream_t st);
+int launch_scale(const blaz_cmat *a, double c, const blaz_cmat *out, cudaStream_t st);
+int launch_dot(const blaz_cmat *a, const blaz_cmat *b, double *result, double *partials, unsigned *counter,
+               int64_t max_ctas, cudaStream_t st);
+int dot_grid(int64_t nb);
+int launch_dot_rowcol(const blaz_cmat *a, const blaz_cmat *b, int64_t i, int64_t j, double *result,
+                      cudaStream_t st);
+int launch_gemm_fp64(const double *A, int64_t lda, const double *B, int64_t ldb, double *C, int64_t ldc,
+                     int64_t n, int64_t k, int64_t m, cudaStream_t st);
+
+}  // namespace blaz

@@ -1,0 +1,113 @@
+// k_blockops.cu -- operations on compressed blocks without decompression:
+// addition / subtraction (Algorithm 1, Eq. eq55) and multiplication by a
+// constant (Algorithm 2) of "Compressed Matrix Computations" (arXiv 2202.13007).
+// Bit-exact binary64 (explicit round-to-nearest intrinsics).
+#include "blaz_internal.cuh"
+
+namespace blaz {
+
+template <bool kSub>
+__global__ void __launch_bounds__(128)
+    k_add(int64_t nb, const double *__restrict__ f1, const double *__restrict__ s1, const uint8_t *__restrict__ p1,
+          const int8_t *__restrict__ c1, const double *__restrict__ f2, const double *__restrict__ s2,
+          const uint8_t *__restrict__ p2, const int8_t *__restrict__ c2, double *f, double *s, uint8_t *p,
+          int8_t *c)
+{
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x) {
+        // Read everything of this block before writing: out may alias an input.
+        const double fa = f1[b], fb = f2[b], sa = s1[b], sb = s2[b];
+        const int pa = p1[b], pb = p2[b];
+        uint32_t wa[7], wb[7];
+        const uint32_t *ca = reinterpret_cast<const uint32_t *>(c1 + b * kKeep);
+        const uint32_t *cb = reinterpret_cast<const uint32_t *>(c2 + b * kKeep);
+#pragma unroll
+        for (int q = 0; q < 7; ++q) {
+            wa[q] = ca[q];
+            wb[q] = cb[q];
+        }
+        const double fs = kSub ? dsub(fa, fb) : dadd(fa, fb);
+        const double ss = dadd(sa, sb);
+        int ph = (pa * pb) / (pa + pb);
+        ph = ph < 1 ? 1 : ph;
+        uint32_t wo[7];
+        if (ss == 0.0) {
+#pragma unroll
+            for (int q = 0; q < 7; ++q) wo[q] = 0u;
+        } else {
+            const double a1 = ddiv(sa, ss);
+            const double a2 = ddiv(sb, ss);
+            const double b1 = dmul(ddiv(a1, (double)pa), (double)ph);
+            const double b2 = dmul(ddiv(a2, (double)pb), (double)ph);
+#pragma unroll
+            for (int q = 0; q < 7; ++q) {
+                uint32_t v = 0;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const double x1 = (double)(int8_t)(uint8_t)(wa[q] >> (8 * k));
+                    const double x2 = (double)(int8_t)(uint8_t)(wb[q] >> (8 * k));
+                    const double y = kSub ? dsub(dmul(b1, x1), dmul(b2, x2)) : dadd(dmul(b1, x1), dmul(b2, x2));
+                    v |= (uint32_t)(uint8_t)quantize(y) << (8 * k);
+                }
+                wo[q] = v;
+            }
+        }
+        f[b] = fs;
+        s[b] = ss;
+        p[b] = (uint8_t)ph;
+        uint32_t *co = reinterpret_cast<uint32_t *>(c + b * kKeep);
+#pragma unroll
+        for (int q = 0; q < 7; ++q) co[q] = wo[q];
+    }
+}
+
+// Algorithm 2.  When out == a (in place) only f and s are touched.
+__global__ void __launch_bounds__(256) k_scale(int64_t nb, const double *f1, const double *s1, double cst, double *f,
+                                               double *s)
+{
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x) {
+        f[b] = dmul(f1[b], cst);
+        s[b] = dmul(s1[b], cst);
+    }
+}
+
+static int grid_for(int64_t n, int threads)
+{
+    int64_t want = (n + threads - 1) / threads;
+    int64_t cap = (int64_t)num_sms() * 32;
+    if (want > cap) want = cap;
+    return (int)(want < 1 ? 1 : want);
+}
+
+int launch_add(const blaz_cmat *a, const blaz_cmat *b, const blaz_cmat *o, bool subtract, cudaStream_t st)
+{
+    const int64_t nb = (a->rows / 8) * (a->cols / 8);
+    if (nb == 0) return BLAZ_OK;
+    const int grid = grid_for(nb, 128);
+    if (subtract)
+        k_add<true><<<grid, 128, 0, st>>>(nb, a->f, a->s, a->phi, a->code, b->f, b->s, b->phi, b->code, o->f, o->s,
+                                          o->phi, o->code);
+    else
+        k_add<false><<<grid, 128, 0, st>>>(nb, a->f, a->s, a->phi, a->code, b->f, b->s, b->phi, b->code, o->f, o->s,
+                                           o->phi, o->code);
+    return launch_status();
+}
+
+int launch_scale(const blaz_cmat *a, double c, const blaz_cmat *o, cudaStream_t st)
+{
+    const int64_t nb = (a->rows / 8) * (a->cols / 8);
+    if (nb == 0) return BLAZ_OK;
+    k_scale<<<grid_for(nb, 256), 256, 0, st>>>(nb, a->f, a->s, c, o->f, o->s);
+    int rc = launch_status();
+    if (rc != BLAZ_OK) return rc;
+    if (o->phi != a->phi) {
+        cudaError_t e = cudaMemcpyAsync(o->phi, a->phi, (size_t)nb, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return set_cuda_error(e);
+    }
+    if (o->code != a->code) {
+        cudaError_t e = cudaMemcpyAsync(o->code, a->code, (size_t)nb * kKeep, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return set_cuda_error(e);
+    }
+    return BLAZ_OK;
+}
+
+}  // namespace blaz

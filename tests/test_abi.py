@@ -1,0 +1,73 @@
+"""The C-ABI library loads here (no GPU) and exports every declared symbol;
+its constant tables are the correctly rounded values of the DCT constants."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+
+HEADERS = [os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h")]
+
+
+def declared_symbols():
+    names = set()
+    for h in HEADERS:
+        txt = open(h).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(blaz_\w+)\s*\(", txt, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def libblaz():
+    from paper_2202_13007_gb300 import _build, blaz
+
+    _build.build()
+    return blaz.lib()
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for n in ["blaz_compress", "blaz_decompress", "blaz_add", "blaz_sub", "blaz_scale", "blaz_dot",
+              "blaz_dot_rowcol", "blaz_matmul", "blaz_cmat_alloc", "blaz_cmat_free", "blaz_strerror"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(libblaz):
+    from paper_2202_13007_gb300 import blaz
+
+    for name in declared_symbols():
+        assert hasattr(libblaz, name), name
+        assert name in blaz.SIGNATURES, f"binding lacks {name}"
+
+
+def test_library_constants_are_correctly_rounded(libblaz):
+    mpmath = pytest.importorskip("mpmath")
+    from paper_2202_13007_gb300 import blaz
+
+    mpmath.mp.dps = 50
+    cos_t, aa_t, kept = blaz.constants()
+    alpha = [mpmath.sqrt(mpmath.mpf(1) / 8)] + [mpmath.mpf(1) / 2] * 7
+    for k in range(8):
+        for x in range(8):
+            assert cos_t[k, x] == float(mpmath.cos((2 * x + 1) * k * mpmath.pi / 16))
+            assert aa_t[k, x] == float(alpha[k] * alpha[x])
+    want = [(i, j) for i in range(2) for j in range(8)] + [(i, j) for i in range(2, 8) for j in range(2)]
+    assert [tuple(p) for p in kept] == want
+
+
+def test_strerror_and_argument_errors_without_gpu(libblaz):
+    from paper_2202_13007_gb300 import blaz
+
+    assert libblaz.blaz_strerror(0) == b"ok"
+    bad = blaz._CMatDesc(12, 8, None, None, None, None)   # 12 is not a multiple of 8
+    assert libblaz.blaz_compress(None, 8, ctypes.byref(bad), None) == -1
+    empty = blaz._CMatDesc(0, 16, None, None, None, None)
+    assert libblaz.blaz_compress(None, 16, ctypes.byref(empty), None) == 0
+    ok = blaz._CMatDesc(8, 8, None, None, None, None)
+    assert libblaz.blaz_compress(None, 8, ctypes.byref(ok), None) == -2   # NULL arrays
+    assert libblaz.blaz_matmul(ctypes.byref(empty), None, 0, 4, None, 4, 7, None) == -9   # bad mode

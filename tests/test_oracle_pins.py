@@ -341,3 +341,29 @@ def test_add_codes_against_exact_rational_algorithm1():
                 assert out.code[b, t] == want, (cst, b, t)
         if cst == -0.97:
             assert n_sat > 0
+
+
+def test_sub_against_exact_rational_and_linearity():
+    """Subtraction (Sec. III, "works similarly to the addition"): exact
+    rational evaluation of the codes and U(C(A)-C(B)) ~ U(C(A)) - U(C(B))."""
+    from fractions import Fraction as Fr
+
+    A, B = W.plain_pair()
+    ca, cb = O.compress(A), O.compress(B)
+    d = O.sub(ca, cb)
+    assert np.array_equal(d.f, ca.f - cb.f) and np.array_equal(d.s, ca.s + cb.s)
+    for b in range(0, d.nb, 9):
+        s = Fr(ca.s[b]) + Fr(cb.s[b])
+        ph = int(d.phi[b])
+        b1 = Fr(ca.s[b]) / s / int(ca.phi[b]) * ph
+        b2 = Fr(cb.s[b]) / s / int(cb.phi[b]) * ph
+        for t in range(28):
+            v = b1 * int(ca.code[b, t]) - b2 * int(cb.code[b, t])
+            if v != 0 and abs(v - round(v)) < Fr(1, 10**9):
+                continue
+            assert d.code[b, t] == max(-127, min(127, int(v)))
+    da, db, dd = _blocks(O.decompress(ca)), _blocks(O.decompress(cb)), _blocks(O.decompress(d))
+    w = np.fromfunction(lambda i, j: i + j, (8, 8))
+    for b in range(d.nb):
+        bound = w * abs(d.s[b]) * np.sqrt(28) / d.phi[b] + 1e-12 * (1 + np.abs(da[b] - db[b]).max())
+        assert np.all(np.abs(dd[b] - (da[b] - db[b])) <= bound), b

@@ -1,0 +1,321 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Codes, phi, f and s of compress / add / sub / scale are compared bit for bit
+(NaN outputs compared as NaN).  Floating-point results use tolerances derived
+from the arithmetic:
+  decompress: |d| <= 1e-12 * (|f| + 14 |s| sum|c|/phi) per block (the
+              recurrence adds at most 14 IDCT terms of size <= |s| sum|c|/phi);
+  dot:        |d| <= 1e-12 * sum |A_hat B_hat|;
+  matmul FP64:|d_ij| <= 1e-12 * (|A_hat| |B|)_ij (componentwise).
+"""
+import concurrent.futures as cf
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="session")
+def B():
+    from paper_2202_13007_gb300 import _build, blaz
+
+    _build.build()
+    blaz.lib()
+    torch.cuda.init()
+    return blaz
+
+
+def dev(A):
+    return torch.from_numpy(np.ascontiguousarray(A)).cuda()
+
+
+def same_bits(x, y):
+    x = np.asarray(x, np.float64)
+    y = np.asarray(y, np.float64)
+    nan = np.isnan(x)
+    assert np.array_equal(nan, np.isnan(y))
+    assert np.array_equal(x[~nan].view(np.uint64), y[~nan].view(np.uint64))
+
+
+def assert_cmat_equal(g, o, idx=None):
+    f, s, phi, code = g.to_host()
+    if idx is not None:
+        f, s, phi, code = f[idx], s[idx], phi[idx], code[idx]
+    assert np.array_equal(phi, o.phi if hasattr(o, "phi") else o[2])
+    assert np.array_equal(code, o.code if hasattr(o, "code") else o[3])
+    same_bits(f, o.f if hasattr(o, "f") else o[0])
+    same_bits(s, o.s if hasattr(o, "s") else o[1])
+
+
+def decompress_tol(oc):
+    scale = np.abs(oc.f) + 14 * np.abs(oc.s) * np.abs(oc.code.astype(np.float64)).sum(1) / oc.phi
+    return 1e-12 * scale
+
+
+def assert_decompress_close(got, oc, rows, cols):
+    ref = O.decompress(oc)
+    tol = decompress_tol(oc).reshape(rows // 8, 1, cols // 8, 1)
+    err = np.abs(got - ref).reshape(rows // 8, 8, cols // 8, 8)
+    assert np.all((err <= tol) | (np.isnan(err) & np.isnan(ref.reshape(err.shape))))
+
+
+# --- compress: bit-exact --------------------------------------------------------------------
+def test_compress_plain_pair(B):
+    A, Bm = W.plain_pair()
+    for X in (A, Bm):
+        assert_cmat_equal(B.compress(dev(X)), O.compress(X))
+
+
+SHAPES = [(8, 8), (8, 1024), (1024, 8), (72, 136), (256, 264), (520, 1032)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("kind", ["smooth", "noise", "wide"])
+def test_compress_shapes_and_value_ranges(B, shape, kind):
+    X = W.random_block_matrix(*shape, seed=sum(shape), kind=kind)
+    assert_cmat_equal(B.compress(dev(X)), O.compress(X))
+
+
+def test_compress_strided_and_unaligned_views(B):
+    big = W.random_block_matrix(64, 200, seed=9)
+    tb = dev(big)
+    view = tb[:, 1:137]               # lda = 200, base 8 bytes off a 16-byte boundary
+    assert view.stride(0) == 200 and view.data_ptr() % 16 == 8
+    assert_cmat_equal(B.compress(view), O.compress(big[:, 1:137]))
+    view2 = tb[8:40, 64:128]          # lda = 200, aligned
+    assert_cmat_equal(B.compress(view2), O.compress(big[8:40, 64:128]))
+
+
+def special_blocks():
+    rng = np.random.default_rng(77)
+    blocks = [np.fromfunction(lambda i, j: (0.1 * i) * (0.1 * j), (8, 8)),   # Sec. II, Example 1
+              np.full((8, 8), 2.5), np.zeros((8, 8)), -np.zeros((8, 8)),
+              np.fromfunction(lambda i, j: ((i + j) % 2) * 1.0, (8, 8))]
+    spike = np.zeros((8, 8)); spike[4, 3] = -7.0; blocks.append(spike)
+    blocks.append(rng.standard_normal((8, 8)) * 1e-310)                     # subnormal
+    blocks.append(rng.standard_normal((8, 8)) * 1e300)
+    nanb = rng.standard_normal((8, 8)); nanb[2, 5] = np.nan; blocks.append(nanb)
+    infb = rng.standard_normal((8, 8)); infb[0, 3] = np.inf; blocks.append(infb)
+    infn = np.full((8, 8), -np.inf); blocks.append(infn)
+    tiny = np.full((8, 8), 1.0); tiny[7, 7] = 1.0 + 2.0 ** -52; blocks.append(tiny)
+    half = np.fromfunction(lambda i, j: np.where(i + j < 8, 0.0, 5e-324), (8, 8)); blocks.append(half)
+    for _ in range(20):
+        blocks.append(rng.integers(-64, 64, (8, 8)) / 32.0)
+        blocks.append(np.cumsum(rng.integers(0, 9, (8, 8)), axis=1) / 16.0)   # sign-coherent
+    return np.concatenate(blocks, axis=1)
+
+
+def test_compress_special_values(B):
+    X = special_blocks()
+    assert_cmat_equal(B.compress(dev(X)), O.compress(X))
+
+
+@pytest.mark.parametrize("shape", [(0, 0), (0, 16), (16, 0)])
+def test_empty_matrices(B, shape):
+    X = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    c = B.compress(X)
+    assert c.nb == 0
+    out = B.decompress(c)
+    assert out.shape == shape
+    assert float(B.dot(c, c).item()) == 0.0 or c.nb == 0
+
+
+def test_shape_errors_are_reported(B):
+    X = torch.zeros((12, 8), dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):
+        B.compress(X)
+    a = B.compress(torch.zeros((8, 16), dtype=torch.float64, device="cuda"))
+    b = B.compress(torch.zeros((16, 8), dtype=torch.float64, device="cuda"))
+    with pytest.raises(B.BlazError) as e:
+        B.add(a, b, out=B.CMat.empty(8, 16))
+    assert e.value.status == -1
+    with pytest.raises(B.BlazError):
+        B.dot_rowcol(a, b, 8, 0)
+
+
+# --- decompress ------------------------------------------------------------------------------
+@pytest.mark.parametrize("shape", [(256, 256), (72, 136), (8, 1024)])
+def test_decompress_parity(B, shape):
+    X = W.random_block_matrix(*shape, seed=5) if shape != (256, 256) else W.plain_pair()[0]
+    oc = O.compress(X)
+    got = B.decompress(B.compress(dev(X))).cpu().numpy()
+    assert_decompress_close(got, oc, *shape)
+
+
+def test_decompress_into_strided_output(B):
+    X = W.plain_pair()[1][:64, :96]
+    oc = O.compress(X)
+    out = torch.full((64, 131), 7.0, dtype=torch.float64, device="cuda")
+    B.decompress(B.compress(dev(X)), out=out[:, 1:97])
+    o = out.cpu().numpy()
+    assert np.all(o[:, 0] == 7.0) and np.all(o[:, 97:] == 7.0)
+    assert_decompress_close(o[:, 1:97], oc, 64, 96)
+
+
+# --- Algorithms 1 and 2: bit-exact ---------------------------------------------------------
+def test_add_sub_scale_plain_pair(B):
+    A, Bm = W.plain_pair()
+    ga, gb = B.compress(dev(A)), B.compress(dev(Bm))
+    oa, ob = O.compress(A), O.compress(Bm)
+    assert_cmat_equal(B.add(ga, gb), O.add(oa, ob))
+    assert_cmat_equal(B.sub(ga, gb), O.sub(oa, ob))
+    assert_cmat_equal(B.scale(ga, 3.5), O.scale(oa, 3.5))
+    # repeated adds shrink phi (Eq. eq55); codes stay exact
+    gs, os_ = ga, oa
+    for _ in range(6):
+        gs, os_ = B.add(gs, ga), O.add(os_, oa)
+        assert_cmat_equal(gs, os_)
+
+
+@pytest.mark.parametrize("cst", [-0.97, -1.0, 2.0, 0.0, 1e-300])
+def test_add_with_scaled_partner(B, cst):
+    X = W.random_block_matrix(64, 64, seed=3)
+    Y = np.ascontiguousarray(X.T)
+    gx, gy = B.compress(dev(X)), B.compress(dev(Y))
+    ox, oy = O.compress(X), O.compress(Y)
+    assert_cmat_equal(B.add(gx, B.scale(gy, cst)), O.add(ox, O.scale(oy, cst)))
+
+
+def test_in_place_and_aliased_outputs(B):
+    A, Bm = W.plain_pair()
+    ga, gb = B.compress(dev(A)), B.compress(dev(Bm))
+    oa, ob = O.compress(A), O.compress(Bm)
+    B.add(ga, gb, out=ga)                  # out aliases a
+    assert_cmat_equal(ga, O.add(oa, ob))
+    B.scale(gb, -2.25, out=gb)             # in place: only f and s rewritten
+    assert_cmat_equal(gb, O.scale(ob, -2.25))
+
+
+def test_add_special_values(B):
+    X = special_blocks()
+    Y = np.roll(X, 8, axis=1)
+    gx, gy = B.compress(dev(X)), B.compress(dev(Y))
+    assert_cmat_equal(B.add(gx, gy), O.add(O.compress(X), O.compress(Y)))
+
+
+# --- dot products and matmul -----------------------------------------------------------------
+def test_dot_plain_pair(B):
+    A, Bm = W.plain_pair()
+    ga, gb = B.compress(dev(A)), B.compress(dev(Bm))
+    v = float(B.dot(ga, gb).item())
+    ref, absref = O.dot(O.compress(A), O.compress(Bm))
+    assert abs(v - ref) <= 1e-12 * absref
+    # deterministic: same bits again
+    assert float(B.dot(ga, gb).item()) == v
+
+
+@pytest.mark.parametrize("ij", [(17, 200), (0, 0), (255, 255), (100, 3)])
+def test_dot_rowcol_plain_pair(B, ij):
+    A, Bm = W.plain_pair()
+    ga, gb = B.compress(dev(A)), B.compress(dev(Bm))
+    v = float(B.dot_rowcol(ga, gb, *ij).item())
+    ref, absref = O.dot_rowcol(O.compress(A), O.compress(Bm), *ij)
+    assert abs(v - ref) <= 1e-12 * absref
+
+
+@pytest.mark.parametrize("n,k,m", [(256, 256, 256), (72, 136, 50), (8, 8, 1), (64, 1024, 129)])
+def test_matmul_fp64(B, n, k, m):
+    A = W.random_block_matrix(n, k, seed=n + k)
+    Bd = W.smoothed_normal(k, m, seed=7)
+    ga = B.compress(dev(A))
+    C = B.matmul(ga, dev(Bd), mode="fp64").cpu().numpy()
+    oa = O.compress(A)
+    ref = O.matmul(oa, Bd)
+    bound = np.abs(O.decompress(oa)) @ np.abs(Bd)
+    assert np.all(np.abs(C - ref) <= 1e-12 * bound + 1e-300)
+
+
+# --- full sizes of the bandwidth sweep (launch configuration of the benchmark) ---------------
+def _sample_blocks(nbr, nbc, rng, count=3000):
+    idx = set(rng.integers(0, nbr * nbc, count).tolist())
+    idx |= set(range(min(nbc, 64)))                        # first block-row head
+    idx |= set(range(nbr * nbc - min(nbc, 64), nbr * nbc))  # last block-row tail
+    idx |= {b * nbc for b in range(0, nbr, max(1, nbr // 64))}
+    return np.array(sorted(idx), dtype=np.int64)
+
+
+def _gather_blocks(t, idx, nbc):
+    """Stack the listed 8x8 blocks of a device matrix vertically, on the host."""
+    bi = torch.from_numpy(idx // nbc).cuda()
+    bj = torch.from_numpy(idx % nbc).cuda()
+    r = (bi[:, None] * 8 + torch.arange(8, device="cuda")[None, :])          # [n, 8]
+    c = (bj[:, None] * 8 + torch.arange(8, device="cuda")[None, :])          # [n, 8]
+    blk = t[r[:, :, None], c[:, None, :]]                                      # [n, 8, 8]
+    return blk.reshape(-1, 8).cpu().numpy()
+
+
+@pytest.mark.parametrize("n", [1024, 4096, 16384])
+def test_bandwidth_sweep_full_size_sampled(B, n):
+    ta = W.bump_field_torch(n, n, "cuda")
+    tb = W.bump_field_torch(n, n + 1, "cuda")
+    ga, gb = B.compress(ta), B.compress(tb)
+    nbc = n // 8
+    idx = _sample_blocks(nbc, nbc, np.random.default_rng(n))
+    oa = O.compress(_gather_blocks(ta, idx, nbc))     # oracle compresses the same blocks
+    ob = O.compress(_gather_blocks(tb, idx, nbc))
+    assert_cmat_equal(ga, oa, idx)
+    assert_cmat_equal(gb, ob, idx)
+    gs = B.add(ga, gb)
+    assert_cmat_equal(gs, O.add(oa, ob), idx)
+    gc = B.scale(ga, 3.5)
+    assert_cmat_equal(gc, O.scale(oa, 3.5), idx)
+    dec = B.decompress(ga)
+    got = _gather_blocks(dec, idx, nbc)
+    assert_decompress_close(got, oa, got.shape[0], 8)
+    del dec, ta, tb
+    torch.cuda.empty_cache()
+
+
+def _oracle_dot_chunked(A, Bm, nchunks):
+    """Oracle dot of the oracle's own compressions, evaluated over disjoint
+    block-row chunks in parallel threads and summed exactly (math.fsum)."""
+    O.dct_tables()                        # initialise the oracle's tables before threading
+    rows = A.shape[0]
+    step = max(8, (rows // nchunks) // 8 * 8)
+    spans = [(r, min(rows, r + step)) for r in range(0, rows, step)]
+
+    def one(sp):
+        a = O.compress(A[sp[0]:sp[1]])
+        b = O.compress(Bm[sp[0]:sp[1]])
+        return O.dot(a, b)
+
+    with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 4)) as ex:
+        parts = list(ex.map(one, spans))
+    return math.fsum(p[0] for p in parts), math.fsum(p[1] for p in parts)
+
+
+@pytest.mark.parametrize("n", [1024, 4096])
+def test_bandwidth_sweep_dot_full_size(B, n):
+    A = W.bump_field(n, n)
+    Bm = W.bump_field(n, n + 1)
+    v = float(B.dot(B.compress(dev(A)), B.compress(dev(Bm))).item())
+    ref, absref = _oracle_dot_chunked(A, Bm, 16)
+    assert abs(v - ref) <= 1e-12 * absref
+
+
+def test_precision_config_matmul_fp64_sampled(B):
+    n = 4096
+    ta = W.bump_field_torch(n, n, "cuda")
+    Bd = W.smoothed_normal(n, n, seed=7)
+    ga = B.compress(ta)
+    C = B.matmul(ga, dev(Bd), mode="fp64")
+    rng = np.random.default_rng(1)
+    rows = np.sort(rng.choice(n, 12, replace=False))
+    # the oracle compresses the rows' block-rows itself
+    blockrows = sorted({r // 8 for r in rows})
+    for br in blockrows:
+        Arow = ta[br * 8:(br + 1) * 8].cpu().numpy()
+        oa = O.compress(Arow)
+        jj = rng.choice(n, 64, replace=False)
+        ii = np.repeat(np.array([r - br * 8 for r in rows if r // 8 == br]), len(jj))
+        jj = np.tile(jj, len(ii) // len(jj))
+        ref, bound = O.matmul_entries(oa, Bd, ii, jj)
+        got = C[torch.from_numpy(ii + br * 8).cuda(), torch.from_numpy(jj).cuda()].cpu().numpy()
+        assert np.all(np.abs(got - ref) <= 1e-12 * bound)
