@@ -1,0 +1,371 @@
+"""Benchmark of the blaz compressed-matrix hot path on GB300.
+
+One step = one pass of the path over the bandwidth-sweep workload: two
+16384 x 16384 binary64 smooth fields A and B (16 Gaussian bumps + 1e-4
+noise), resident in HBM:
+    compress A, compress B, decompress A, A+B (compressed), 3.5*A
+    (compressed), flattened dot <A,B>, and one line-column dot (Algorithm 3).
+value = algorithmic bytes of the step (557 B per block for compress and
+decompress, 135 for add, 90 for scale and for the dot inputs) / step time,
+in GB/s, summed over all ranks.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl blaz|reference]
+
+--impl reference times the CPU oracle (single-threaded C, the method as the
+paper defines it) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "compressed add/scale/dot GB/s (% HBM peak), matmul TFLOP/s, serve p50/p99"
+BYTES_PER_BLOCK = {"compress": 557, "decompress": 557, "add": 135, "scale": 90, "dot": 90}
+STEP_OPS = ["compress", "compress", "decompress", "add", "scale", "dot"]
+# binary64 IEEE operations per block of the compressor's operation order:
+# normalization 210, |D| sum 64, s and 1/s 2, D*(1/s) 64, DCT 896 + 896,
+# alpha_i alpha_j 64, 127/m 1, codes 28.
+COMPRESS_FLOPS_PER_BLOCK = 2225
+FP64_PEAK_DERIVED = 2 * 152 * 2070e6  # 2 FP64 lanes/clk/SM x 152 SMs x 2070 MHz (1.25 TFLOP/s nominal, FMA=2)
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="blaz", choices=["blaz", "reference"])
+    p.add_argument("--side", type=int, default=16384)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def step_bytes(side: int) -> int:
+    nb = (side // 8) ** 2
+    return nb * sum(BYTES_PER_BLOCK[o] for o in STEP_OPS)
+
+
+KERNEL_SOURCES = {"k_compress": ["paper_2202_13007_gb300/csrc/k_codec.cu",
+                                  "paper_2202_13007_gb300/csrc/block_codec.cuh",
+                                  "paper_2202_13007_gb300/csrc/blaz_internal.cuh"]}
+
+
+def kernel_sha(name: str) -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[name]:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(name: str, blocks: int):
+    """DRAM bytes per launch from the committed ncu summary, scaled to `blocks`
+    blocks; None when the kernel source changed since the capture."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            d = json.load(fh)[name]
+    except Exception:
+        return None
+    if d.get("source_sha") != kernel_sha(name):
+        return None
+    return d["dram_bytes_per_block"] * blocks
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.gpu)], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        busy = [x for x in sm if x >= 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(busy), "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def run_oracle_step(O, A, Bm):
+    """One step of the path evaluated by the CPU oracle (the line-column dot,
+    whose bytes the step does not count, is left out); returns seconds."""
+    t = time.perf_counter()
+    ca = O.compress(A)
+    cb = O.compress(Bm)
+    O.decompress(ca)
+    O.add(ca, cb)
+    O.scale(ca, 3.5)
+    O.dot(ca, cb)
+    return time.perf_counter() - t
+
+
+def oracle_sample(side: int, rows: int):
+    import workloads as W
+
+    A = W.bump_field(side, side, rows=rows)
+    Bm = W.bump_field(side, side + 1, rows=rows)
+    return A, Bm
+
+
+def cpu_baseline(side: int, rows: int = 8192):
+    """The oracle (single-threaded C) on the first `rows` rows of both fields."""
+    import oracle as O
+
+    O.build()
+    A, Bm = oracle_sample(side, rows)
+    secs = run_oracle_step(O, A, Bm)
+    nb = (rows // 8) * (side // 8)
+    byts = nb * sum(BYTES_PER_BLOCK[o] for o in STEP_OPS)
+    return {"value": byts / secs / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"one oracle step on the first {rows} rows of both {side}x{side} fields "
+                      f"({nb} blocks, {secs:.1f} s)"}
+
+
+def reference_arm(args, rank: int, world: int):
+    """--impl reference: the oracle as it stands, timed on the host cores."""
+    if rank != 0:
+        return
+    import oracle as O
+
+    O.build()
+    rows = 2048
+    A, Bm = oracle_sample(args.side, rows)
+    for _ in range(args.warmup):
+        run_oracle_step(O, A, Bm)
+    secs = [run_oracle_step(O, A, Bm) for _ in range(args.steps)]
+    nb = (rows // 8) * (args.side // 8)
+    byts = nb * sum(BYTES_PER_BLOCK[o] for o in STEP_OPS)
+    total = sum(secs)
+    value = byts * args.steps / total / 1e9
+    sample = (f"each step: one oracle step on the first {rows} rows of both {args.side}x{args.side} fields "
+              f"({nb} blocks)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config(args.side),
+            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config(side):
+    return {"workload": f"bandwidth sweep {side}x{side} binary64 bump fields: compress A, compress B, "
+                        "decompress A, A+B, 3.5*A, dot <A,B>, dot line 17 . column 200",
+            "side": side, "blocks_per_matrix": (side // 8) ** 2,
+            "l2": "inputs larger than L2 (2 GiB per field), no flush", "parallelism": "replicas"}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+
+    import torch
+
+    import workloads as W
+    from paper_2202_13007_gb300 import blaz as B
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    B.lib()
+    n = args.side
+    dev = torch.device("cuda", local)
+    st = torch.cuda.current_stream()
+    ta = W.bump_field_torch(n, n + 2 * rank, dev)
+    tb = W.bump_field_torch(n, n + 1 + 2 * rank, dev)
+    ca, cb, cs, cc = (B.CMat.empty(n, n, dev) for _ in range(4))
+    dec = torch.empty((n, n), dtype=torch.float64, device=dev)
+    res = torch.empty(2, dtype=torch.float64, device=dev)
+    ev_pairs = []
+
+    def step(record=False):
+        if record:
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            e[0].record(st)
+        B.compress(ta, out=ca)
+        if record:
+            e[1].record(st)
+            e[2].record(st)
+        B.compress(tb, out=cb)
+        if record:
+            e[3].record(st)
+            ev_pairs.extend([(e[0], e[1]), (e[2], e[3])])
+        B.decompress(ca, out=dec)
+        B.add(ca, cb, out=cs)
+        B.scale(ca, 3.5, out=cc)
+        B.dot(ca, cb, out=res[0])
+        B.dot_rowcol(ca, cb, 17, 200, out=res[1])
+
+    launches_per_step = 7   # compress x2, decompress, add, scale, dot, dot_rowcol
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        t0.record(st)
+        for _ in range(args.steps):
+            step(record=True)
+        t1.record(st)
+        torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    if dist:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+        dist.barrier()
+    ms_step = ms / args.steps
+    value = world * step_bytes(n) * args.steps / (ms * 1e-3) / 1e9
+
+    comp_ms = statistics.mean(a.elapsed_time(b) for a, b in ev_pairs)
+    nb = (n // 8) ** 2
+    achieved = COMPRESS_FLOPS_PER_BLOCK * nb / (comp_ms * 1e-3) / 1e9
+    hbm, hbm_src = peaks()
+
+    # End to end through the public API with host buffers: pinned host -> device
+    # copies of A and B, the step, device -> host copies of A+B (compressed) and
+    # of both dot results, every step.
+    e2e = None
+    if not args.no_e2e:
+        ha = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
+        hb = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
+        ha.copy_(ta)
+        hb.copy_(tb)
+        hs = [torch.empty(x.shape, dtype=x.dtype, pin_memory=True) for x in (cs.f, cs.s, cs.phi, cs.code)]
+        hr = torch.empty(2, dtype=torch.float64, pin_memory=True)
+
+        def e2e_step():
+            ta.copy_(ha, non_blocking=True)
+            tb.copy_(hb, non_blocking=True)
+            step()
+            for h, d in zip(hs, (cs.f, cs.s, cs.phi, cs.code)):
+                h.copy_(d, non_blocking=True)
+            hr.copy_(res, non_blocking=True)
+
+        for _ in range(args.warmup):
+            e2e_step()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(args.steps):
+            e2e_step()
+        e1.record(st)
+        torch.cuda.synchronize()
+        ems = e0.elapsed_time(e1)
+        if dist:
+            tt = torch.tensor([ems], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ems = float(tt.item())
+        h2d = 2 * n * n * 8
+        d2h = cs.nbytes + 16
+        e2e = {"value": world * step_bytes(n) * args.steps / (ems * 1e-3) / 1e9, "unit": "GB/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ems / args.steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(n)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config(n),
+            "frac_of_hbm_peak": value / world / hbm,
+            "roofline": {"kernel": "k_compress", "bound": "alu", "achieved": achieved,
+                         "peak": FP64_PEAK_DERIVED / 1e9, "unit": "GFLOP/s",
+                         "frac": achieved * 1e9 / FP64_PEAK_DERIVED, "traffic": profiled_traffic("k_compress", nb),
+                         "traffic_unit": "bytes per launch", "source_sha": kernel_sha("k_compress"),
+                         "peak_source": "derived: 2 FP64 lanes/clk/SM x 152 SMs x 2070 MHz",
+                         "ms_per_launch": comp_ms, "algorithmic_flops_per_launch": COMPRESS_FLOPS_PER_BLOCK * nb,
+                         "hbm_frac": 557 * nb / (comp_ms * 1e-3) / 1e9 / hbm, "hbm_peak_source": hbm_src},
+            "clocks": clk.summary(),
+            "e2e": e2e,
+            "gpu_launches": launches_per_step * args.steps,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -60,13 +60,24 @@ __global__ void __launch_bounds__(128)
     }
 }
 
-// Algorithm 2.  When out == a (in place) only f and s are touched.
-__global__ void __launch_bounds__(256) k_scale(int64_t nb, const double *f1, const double *s1, double cst, double *f,
-                                               double *s)
+// Algorithm 2.  When out == a (in place) only f and s are touched; otherwise
+// phi and the codes are copied by the same kernel (one pass over the data).
+template <bool kCopy>
+__global__ void __launch_bounds__(256) k_scale(int64_t nb, const double *f1, const double *s1, const uint8_t *p1,
+                                               const int8_t *c1, double cst, double *f, double *s, uint8_t *p,
+                                               int8_t *c)
 {
-    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nb; b += stride) {
         f[b] = dmul(f1[b], cst);
         s[b] = dmul(s1[b], cst);
+        if (kCopy) p[b] = p1[b];
+    }
+    if (kCopy) {
+        // codes: nb*28 bytes = nb*7 32-bit words
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(c1);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(c);
+        for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < nb * 7; w += stride) dst[w] = src[w];
     }
 }
 
@@ -96,18 +107,13 @@ int launch_scale(const blaz_cmat *a, double c, const blaz_cmat *o, cudaStream_t 
 {
     const int64_t nb = (a->rows / 8) * (a->cols / 8);
     if (nb == 0) return BLAZ_OK;
-    k_scale<<<grid_for(nb, 256), 256, 0, st>>>(nb, a->f, a->s, c, o->f, o->s);
-    int rc = launch_status();
-    if (rc != BLAZ_OK) return rc;
-    if (o->phi != a->phi) {
-        cudaError_t e = cudaMemcpyAsync(o->phi, a->phi, (size_t)nb, cudaMemcpyDeviceToDevice, st);
-        if (e != cudaSuccess) return set_cuda_error(e);
-    }
-    if (o->code != a->code) {
-        cudaError_t e = cudaMemcpyAsync(o->code, a->code, (size_t)nb * kKeep, cudaMemcpyDeviceToDevice, st);
-        if (e != cudaSuccess) return set_cuda_error(e);
-    }
-    return BLAZ_OK;
+    if (o->code != a->code || o->phi != a->phi)
+        k_scale<true><<<grid_for(nb * 7, 256), 256, 0, st>>>(nb, a->f, a->s, a->phi, a->code, c, o->f, o->s, o->phi,
+                                                           o->code);
+    else
+        k_scale<false><<<grid_for(nb, 256), 256, 0, st>>>(nb, a->f, a->s, a->phi, a->code, c, o->f, o->s, o->phi,
+                                                            o->code);
+    return launch_status();
 }
 
 }  // namespace blaz
