@@ -121,6 +121,26 @@ int blaz_scale(const blaz_cmat *a, double c, blaz_cmat *out, void *stream);
  * (cudaMallocAsync on `stream`). */
 int blaz_dot(const blaz_cmat *a, const blaz_cmat *b, double *result, void *stream);
 
+/* blaz_dot without any device allocation (the paper has no counterpart; this
+ * entry point exists for callers that cannot let a library allocate device
+ * memory: a framework or server that owns all of HBM through its own
+ * allocator or budget, a device or driver without stream-ordered allocation,
+ * or a step that must not risk an allocation failure midway).
+ * Same arguments, result and determinism as blaz_dot.  Its scratch is a fixed
+ * 8448-byte array in the library's device memory (every GPU that loads the
+ * library holds it until the process exits): 1024 per-CTA partial sums and a
+ * counter.  A call needs one partial per CTA it launches, min(ceil(nb/256),
+ * 4 x SM count), i.e. at most 608 on a 152-SM GB300, so every matrix size fits
+ * there; a launch that would need more than 1024 partials is rejected with
+ * BLAZ_ERR_RANGE before anything is enqueued.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls share
+ * the one array (the counter is cleared on the stream at the start of each
+ * call): calls that can overlap on the GPU -- on different streams without
+ * ordering between them -- race and must not be issued.  No cudaMalloc,
+ * cudaFree or allocating library routine is called. */
+int blaz_dot_noalloc(const blaz_cmat *a, const blaz_cmat *b, double *result, void *stream);
+
 /* Dot product of line i of A_hat and column j of B_hat, Algorithm 3 (Eqs.
  * eqbbb0, eqbbb) applied block-wise: sum_k A_hat[i][k] B_hat[k][j].
  * a: n x k, b: k x m; 0 <= i < n, 0 <= j < m.  result: device, one binary64. */

@@ -53,6 +53,7 @@ SIGNATURES = {
     "blaz_sub": (ctypes.c_int, [_DESC, _DESC, _DESC, _P]),
     "blaz_scale": (ctypes.c_int, [_DESC, ctypes.c_double, _DESC, _P]),
     "blaz_dot": (ctypes.c_int, [_DESC, _DESC, _P, _P]),
+    "blaz_dot_noalloc": (ctypes.c_int, [_DESC, _DESC, _P, _P]),
     "blaz_dot_rowcol": (ctypes.c_int, [_DESC, _DESC, _I64, _I64, _P, _P]),
     "blaz_matmul": (ctypes.c_int, [_DESC, _P, _I64, _I64, _P, _I64, ctypes.c_int, _P]),
 }
@@ -192,6 +193,16 @@ def blaz_dot(a: CMat, b: CMat, out: torch.Tensor | None = None, stream=None) -> 
     out = out if out is not None else torch.empty((), dtype=torch.float64, device=a.f.device)
     da, db = a.desc(), b.desc()
     _check(lib().blaz_dot(ctypes.byref(da), ctypes.byref(db), out.data_ptr(), _stream(stream)), "blaz_dot")
+    return out
+
+
+def blaz_dot_noalloc(a: CMat, b: CMat, out: torch.Tensor, stream=None) -> torch.Tensor:
+    """blaz_dot for callers that cannot let the library allocate: scratch is a
+    fixed array inside the library; ``out`` must be given (one float64 on the
+    device).  Calls that may overlap on the GPU must not be issued."""
+    da, db = a.desc(), b.desc()
+    _check(lib().blaz_dot_noalloc(ctypes.byref(da), ctypes.byref(db), out.data_ptr(), _stream(stream)),
+           "blaz_dot_noalloc")
     return out
 
 

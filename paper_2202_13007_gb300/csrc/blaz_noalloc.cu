@@ -1,0 +1,86 @@
+// blaz_noalloc.cu -- blaz_dot_noalloc: the flattened dot product without any
+// device allocation.
+//
+// Some callers cannot let a library allocate device memory: a framework or a
+// serving runtime that owns every byte of HBM through its own allocator or a
+// fixed budget, a process on a driver or device without stream-ordered
+// allocation (memory pools), or a hot loop that must not risk an
+// out-of-memory failure or an allocator stall halfway through a step.
+// blaz_dot needs a little scratch (one partial sum per CTA and an arrival
+// counter) and takes it from cudaMallocAsync; this entry point takes it from
+// a fixed array in the library's own device memory instead.
+#include <mutex>
+#include <vector>
+
+#include "blaz_internal.cuh"
+
+namespace blaz {
+
+// Maximum number of per-CTA partial sums the static scratch holds.
+constexpr int kNoAllocMaxCtas = 1024;
+constexpr size_t kNoAllocCounterOffset = kNoAllocMaxCtas * sizeof(double);
+constexpr size_t kNoAllocBytes = kNoAllocCounterOffset + 256;
+
+// Scratch of blaz_dot_noalloc: [0, 8192) partial sums, then the 32-bit arrival
+// counter.  Every GPU that loads the library holds these 8448 bytes until the
+// process exits.  Host code must not use the symbol itself as a pointer (on
+// the host it is only a stand-in); the device address comes from
+// cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned char g_dot_scratch[kNoAllocBytes];
+
+// Device address of g_dot_scratch, looked up once per device with that
+// device current.
+static void *scratch_address(int &status)
+{
+    static std::mutex mu;
+    static std::vector<void *> addr;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        status = set_cuda_error(e);
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    if ((int)addr.size() <= dev) addr.resize(dev + 1, nullptr);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_dot_scratch);
+        if (e != cudaSuccess || !p) {
+            status = set_cuda_error(e != cudaSuccess ? e : cudaErrorInvalidSymbol);
+            return nullptr;
+        }
+        addr[dev] = p;
+    }
+    status = BLAZ_OK;
+    return addr[dev];
+}
+
+}  // namespace blaz
+
+using namespace blaz;
+
+extern "C" int blaz_dot_noalloc(const blaz_cmat *a, const blaz_cmat *b, double *result, void *stream)
+{
+    if (!a || !b || !result) return BLAZ_ERR_NULL;
+    if (a->rows < 0 || a->cols < 0 || a->rows % 8 || a->cols % 8) return BLAZ_ERR_SHAPE;
+    if (a->rows != b->rows || a->cols != b->cols) return BLAZ_ERR_SHAPE;
+    const int64_t nb = (a->rows / 8) * (a->cols / 8);
+    if (nb > 0 && (!a->f || !a->s || !a->phi || !a->code || !b->f || !b->s || !b->phi || !b->code))
+        return BLAZ_ERR_NULL;
+    if ((uintptr_t)a->f % 8 || (uintptr_t)a->s % 8 || (uintptr_t)a->code % 4 || (uintptr_t)b->f % 8 ||
+        (uintptr_t)b->s % 8 || (uintptr_t)b->code % 4)
+        return BLAZ_ERR_ARG;
+    // The launch needs one partial-sum slot per CTA.
+    const int grid = dot_grid(nb);
+    if (grid > kNoAllocMaxCtas) return BLAZ_ERR_RANGE;
+    int status = BLAZ_OK;
+    char *base = (char *)scratch_address(status);
+    if (!base) return status;
+    double *partials = (double *)base;
+    unsigned *counter = (unsigned *)(base + kNoAllocCounterOffset);
+    cudaStream_t st = (cudaStream_t)stream;
+    // The array keeps the previous call's contents: the counter must start at 0.
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    return launch_dot(a, b, result, partials, counter, grid, st);
+}
