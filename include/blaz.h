@@ -69,6 +69,13 @@ const char *blaz_strerror(int status);
 /* CUDA error code (cudaError_t as int) of the last BLAZ_ERR_CUDA on this thread. */
 int blaz_last_cuda_error(void);
 
+/* Status of the library's kernels on the current device: synchronizes
+ * `stream`, then returns BLAZ_ERR_TIMEOUT if a kernel's bounded wait ran out
+ * since the last call (and clears the flag), else BLAZ_OK.  Kernels that wait
+ * on barriers (the tensor-core product) give up after about two seconds
+ * instead of hanging, record the timeout here and return. */
+int blaz_device_status(void *stream);
+
 /* Library-owned storage for a compressed matrix (stream-ordered allocation
  * on `stream`).  rows, cols >= 0 and multiples of 8.  The arrays are not
  * initialised.  Free with blaz_cmat_free on a stream ordered after last use. */
@@ -151,9 +158,12 @@ int blaz_dot_rowcol(const blaz_cmat *a, const blaz_cmat *b, int64_t i, int64_t j
  * binary64 k x m matrix (Sec. III, "Matrix multiplication": each block is
  * decompressed once).  B: device, ldb >= m; C: device, ldc >= m.
  * mode BLAZ_MM_FP64: binary64 products on the FP64 tensor path (DMMA);
- * mode BLAZ_MM_SPLIT_BF16: A_hat and B split into bf16 slices, slice products
- * on the 5th-generation tensor cores (tcgen05, fp32 accumulation), combined
- * in binary64.  Uses stream-ordered scratch for the decompressed operand. */
+ * mode BLAZ_MM_SPLIT_BF16: A_hat and B each split into three bf16 slices; the
+ * six slice products with i+j <= 4 run as one bf16 GEMM of inner dimension 6k
+ * on the 5th-generation tensor cores (tcgen05, fp32 accumulation in tensor
+ * memory), stored as binary64; relative error about 1e-6 of (|A_hat||B|)_ij.
+ * Uses stream-ordered scratch: 8nk bytes for the decompressed operand, plus
+ * 12k(n+m) bytes of slices in split mode. */
 enum { BLAZ_MM_FP64 = 0, BLAZ_MM_SPLIT_BF16 = 1 };
 int blaz_matmul(const blaz_cmat *a, const double *B, int64_t ldb, int64_t m, double *C, int64_t ldc,
                 int mode, void *stream);

@@ -44,6 +44,7 @@ _DESC = ctypes.POINTER(_CMatDesc)
 SIGNATURES = {
     "blaz_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "blaz_last_cuda_error": (ctypes.c_int, []),
+    "blaz_device_status": (ctypes.c_int, [_P]),
     "blaz_constants": (None, [_P, _P, _P]),
     "blaz_cmat_alloc": (ctypes.c_int, [_DESC, _I64, _I64, _P]),
     "blaz_cmat_free": (ctypes.c_int, [_DESC, _P]),
@@ -133,6 +134,12 @@ class CMat:
 
     def to_host(self):
         return (self.f.cpu().numpy(), self.s.cpu().numpy(), self.phi.cpu().numpy(), self.code.cpu().numpy())
+
+
+def device_status(stream=None) -> int:
+    """Synchronize `stream` and return (and clear) the device status word:
+    0, or -7 (BLAZ_ERR_TIMEOUT) if a kernel's bounded wait ran out."""
+    return lib().blaz_device_status(_stream(stream))
 
 
 def constants():

@@ -111,6 +111,8 @@ const char *blaz_strerror(int status)
 
 int blaz_last_cuda_error(void) { return g_last_cuda; }
 
+int blaz_device_status(void *stream) { return device_status((cudaStream_t)stream); }
+
 void blaz_constants(double cos_out[64], double aa_out[64], int32_t kept_out[56])
 {
     for (int k = 0; k < 8; ++k)
@@ -254,11 +256,14 @@ int blaz_matmul(const blaz_cmat *a, const double *B, int64_t ldb, int64_t m, dou
     if (!C || (k > 0 && !B)) return BLAZ_ERR_NULL;
     if (ldc < m || (k > 0 && ldb < m)) return BLAZ_ERR_LD;
     cudaStream_t st = (cudaStream_t)stream;
-    if (mode == BLAZ_MM_SPLIT_BF16) return BLAZ_ERR_ARG;
+    const size_t ah_bytes = (sizeof(double) * (size_t)(n * k) + 255) & ~(size_t)255;
+    const size_t extra = mode == BLAZ_MM_SPLIT_BF16 ? split_bf16_scratch_bytes(n, k, m) : 0;
     Scratch ws(st);
-    if ((rc = ws.alloc(sizeof(double) * (size_t)(n * k)))) return rc;
+    if ((rc = ws.alloc(ah_bytes + extra))) return rc;
     double *Ah = (double *)ws.p;
     if (k > 0 && (rc = launch_decompress(a, Ah, k, st))) return rc;
+    if (mode == BLAZ_MM_SPLIT_BF16)
+        return launch_matmul_split_bf16(Ah, k, B, ldb, C, ldc, n, k, m, (char *)ws.p + ah_bytes, st);
     return launch_gemm_fp64(Ah, k, B, ldb, C, ldc, n, k, m, st);
 }
 

@@ -319,3 +319,60 @@ def test_precision_config_matmul_fp64_sampled(B):
         ref, bound = O.matmul_entries(oa, Bd, ii, jj)
         got = C[torch.from_numpy(ii + br * 8).cuda(), torch.from_numpy(jj).cuda()].cpu().numpy()
         assert np.all(np.abs(got - ref) <= 1e-12 * bound)
+
+
+# --- split-precision tensor-core product -----------------------------------------------------
+def split_bf16_tol(k):
+    """(|A_hat||B|)_ij multiplier: fp32 accumulation over the 6k slice products
+    plus the three-slice representation error (about 2^-24 of each operand)."""
+    return (6 * k + 8) * 2.0 ** -24
+
+
+@pytest.mark.parametrize("n,k,m", [(256, 256, 256), (72, 136, 50), (8, 8, 1), (64, 1024, 129), (384, 64, 520)])
+def test_matmul_split_bf16(B, n, k, m):
+    A = W.random_block_matrix(n, k, seed=n + k)
+    Bd = W.smoothed_normal(k, m, seed=7)
+    ga = B.compress(dev(A))
+    C = B.matmul(ga, dev(Bd), mode="split_bf16").cpu().numpy()
+    assert B.device_status() == 0
+    oa = O.compress(A)
+    ref = O.matmul(oa, Bd)
+    bound = np.abs(O.decompress(oa)) @ np.abs(Bd)
+    err = np.abs(C - ref)
+    assert np.all(err <= split_bf16_tol(k) * bound + 1e-300), np.max(err / (bound + 1e-300))
+
+
+def test_matmul_split_bf16_empty_inner_dimension(B):
+    ga = B.compress(torch.zeros((16, 0), dtype=torch.float64, device="cuda"))
+    C = B.matmul(ga, torch.zeros((0, 24), dtype=torch.float64, device="cuda"), mode="split_bf16")
+    assert C.shape == (16, 24) and float(C.abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("mode", ["fp64", "split_bf16"])
+def test_precision_config_max_relative_error(B, mode, record_property):
+    """Precision workload: compressed 4096^2 bump field times a smoothed N(0,1)
+    4096^2 matrix; sampled entries against the oracle (which compresses the
+    sampled block-rows itself).  Reports the max relative errors."""
+    n = 4096
+    ta = W.bump_field_torch(n, n, "cuda")
+    Bd = W.smoothed_normal(n, n, seed=7)
+    ga = B.compress(ta)
+    C = B.matmul(ga, dev(Bd), mode=mode)
+    assert B.device_status() == 0
+    rng = np.random.default_rng(2)
+    worst_comp = worst_rel = 0.0
+    for br in sorted(rng.choice(n // 8, 6, replace=False)):
+        oa = O.compress(ta[br * 8:(br + 1) * 8].cpu().numpy())
+        ii = np.repeat(np.arange(8), 48)
+        jj = np.tile(rng.choice(n, 48, replace=False), 8)
+        ref, bound = O.matmul_entries(oa, Bd, ii, jj)
+        got = C[torch.from_numpy(ii + br * 8).cuda(), torch.from_numpy(jj).cuda()].cpu().numpy()
+        comp = np.abs(got - ref) / bound
+        worst_comp = max(worst_comp, float(comp.max()))
+        big = np.abs(ref) > 1e-8 * np.abs(ref).max()
+        worst_rel = max(worst_rel, float((np.abs(got - ref)[big] / np.abs(ref[big])).max()))
+    tol = 1e-12 if mode == "fp64" else split_bf16_tol(n)
+    print(f"\n[{mode}] max componentwise error {worst_comp:.3e}, max relative error {worst_rel:.3e}")
+    record_property("max_componentwise_error", worst_comp)
+    record_property("max_relative_error", worst_rel)
+    assert worst_comp <= tol
