@@ -168,6 +168,69 @@ enum { BLAZ_MM_FP64 = 0, BLAZ_MM_SPLIT_BF16 = 1 };
 int blaz_matmul(const blaz_cmat *a, const double *B, int64_t ldb, int64_t m, double *C, int64_t ldc,
                 int mode, void *stream);
 
+/* ---- Batched mixed operations: one persistent, graph-captured launch ----------
+ * Many compressed-matrix operations of different kinds and sizes (the
+ * block-wise algorithms of Sec. III applied to whole matrices) run as one
+ * persistent kernel: the plan cuts every operation into work items (a range
+ * of 8x8 blocks, or a 64x64 tile of a matrix product), the CTAs take items
+ * from a device-side queue in order, and the launch is captured once in a
+ * CUDA graph and replayed by blaz_batch_run.  Results are the same as the
+ * single-operation entry points: bit-identical for compress / add / sub /
+ * scale, within the dot and product tolerances otherwise (the dot sums
+ * item partials in item order, deterministically). */
+enum {
+    BLAZ_OP_COMPRESS = 0,   /* out = compress(A)             uses A, lda, out        */
+    BLAZ_OP_DECOMPRESS = 1, /* C = decompress(a)             uses a, C, ldc          */
+    BLAZ_OP_ADD = 2,        /* out = a + b (Algorithm 1)     uses a, b, out          */
+    BLAZ_OP_SUB = 3,        /* out = a - b                   uses a, b, out          */
+    BLAZ_OP_SCALE = 4,      /* out = c * a (Algorithm 2)     uses a, c, out          */
+    BLAZ_OP_DOT = 5,        /* *result = <vec a, vec b>      uses a, b, result       */
+    BLAZ_OP_MATMUL = 6      /* C = a_hat * B (binary64 DMMA) uses a, B, ldb, m, C, ldc */
+};
+
+typedef struct blaz_op {
+    int32_t kind;           /* BLAZ_OP_*                                              */
+    blaz_cmat a, b, out;    /* compressed operands and result (descriptors copied)   */
+    const double *A;        /* COMPRESS: dense input (device), leading dimension lda */
+    int64_t lda;
+    double c;               /* SCALE: the constant                                    */
+    double *result;         /* DOT: one binary64 (device)                             */
+    const double *B;        /* MATMUL: dense k x m right operand (device), ldb        */
+    int64_t ldb, m;
+    double *C;              /* MATMUL / DECOMPRESS: dense output (device), ldc        */
+    int64_t ldc;
+} blaz_op;
+
+typedef struct blaz_batch_cfg {
+    int32_t blocks_per_item;  /* 8x8 blocks per work item (0: default 256)              */
+    int32_t ctas_per_sm;      /* persistent CTAs per SM (0: default 2)                  */
+    int32_t autotune;         /* 1: time candidate (blocks_per_item, ctas_per_sm) pairs
+                                 on this batch and keep the fastest; the batch is then
+                                 run several times, so no output may alias an input   */
+} blaz_batch_cfg;
+
+typedef struct blaz_batch_info {
+    int64_t ops, items, gemm_tiles;
+    int32_t blocks_per_item, ctas_per_sm, grid;
+    int64_t scratch_bytes;      /* device memory owned by the plan                        */
+    double tuned_ms;            /* autotune: time of the chosen configuration (else 0)    */
+} blaz_batch_info;
+
+typedef struct blaz_plan blaz_plan;
+
+/* Validate `ops` (host array, copied), build the work list, allocate the
+ * plan's device memory (descriptors, counters, partial sums, decompressed
+ * operands of the products) and capture the launch in a CUDA graph.  Work is
+ * enqueued on `stream` only when autotuning.  Errors: as the single-op entry
+ * points, plus BLAZ_ERR_ARG for an unknown kind or an aliased output with
+ * autotune. */
+int blaz_batch_plan(const blaz_op *ops, int64_t nops, const blaz_batch_cfg *cfg, blaz_plan **plan, void *stream);
+/* Replay the captured launch on `stream`. */
+int blaz_batch_run(blaz_plan *plan, void *stream);
+int blaz_batch_info_get(const blaz_plan *plan, blaz_batch_info *info);
+/* Release the plan (synchronizes the device first). */
+int blaz_batch_free(blaz_plan *plan);
+
 #ifdef __cplusplus
 }
 #endif

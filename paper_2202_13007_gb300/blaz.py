@@ -35,6 +35,25 @@ class _CMatDesc(ctypes.Structure):
                 ("s", ctypes.c_void_p), ("phi", ctypes.c_void_p), ("code", ctypes.c_void_p)]
 
 
+class _Op(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("a", _CMatDesc), ("b", _CMatDesc), ("out", _CMatDesc),
+                ("A", ctypes.c_void_p), ("lda", ctypes.c_int64), ("c", ctypes.c_double),
+                ("result", ctypes.c_void_p), ("B", ctypes.c_void_p), ("ldb", ctypes.c_int64),
+                ("m", ctypes.c_int64), ("C", ctypes.c_void_p), ("ldc", ctypes.c_int64)]
+
+
+class _BatchCfg(ctypes.Structure):
+    _fields_ = [("blocks_per_item", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("autotune", ctypes.c_int32)]
+
+
+class _BatchInfo(ctypes.Structure):
+    _fields_ = [("ops", ctypes.c_int64), ("items", ctypes.c_int64), ("gemm_tiles", ctypes.c_int64),
+                ("blocks_per_item", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("grid", ctypes.c_int32),
+                ("scratch_bytes", ctypes.c_int64), ("tuned_ms", ctypes.c_double)]
+
+
+OP_COMPRESS, OP_DECOMPRESS, OP_ADD, OP_SUB, OP_SCALE, OP_DOT, OP_MATMUL = range(7)
+
 _lib = None
 
 # Every entry point of include/blaz.h with its ctypes signature.
@@ -57,6 +76,11 @@ SIGNATURES = {
     "blaz_dot_noalloc": (ctypes.c_int, [_DESC, _DESC, _P, _P]),
     "blaz_dot_rowcol": (ctypes.c_int, [_DESC, _DESC, _I64, _I64, _P, _P]),
     "blaz_matmul": (ctypes.c_int, [_DESC, _P, _I64, _I64, _P, _I64, ctypes.c_int, _P]),
+    "blaz_batch_plan": (ctypes.c_int, [ctypes.POINTER(_Op), _I64, ctypes.POINTER(_BatchCfg),
+                                       ctypes.POINTER(ctypes.c_void_p), _P]),
+    "blaz_batch_run": (ctypes.c_int, [_P, _P]),
+    "blaz_batch_info_get": (ctypes.c_int, [_P, ctypes.POINTER(_BatchInfo)]),
+    "blaz_batch_free": (ctypes.c_int, [_P]),
 }
 
 
@@ -234,6 +258,67 @@ def blaz_matmul(a: CMat, B: torch.Tensor, mode: str = "fp64", out: torch.Tensor 
     _check(lib().blaz_matmul(ctypes.byref(da), B.data_ptr(), B.stride(0), m, out.data_ptr(), out.stride(0),
                              _MODES[mode], _stream(stream)), "blaz_matmul")
     return out
+
+
+class Batch:
+    """A planned batch of mixed operations (one persistent, graph-captured launch).
+
+    ``ops`` is a list of dicts: {"op": "compress", "A": tensor, "out": CMat},
+    {"op": "decompress", "a": CMat, "C": tensor}, {"op": "add"|"sub", "a", "b",
+    "out"}, {"op": "scale", "a", "c", "out"}, {"op": "dot", "a", "b", "result":
+    float64 tensor (one element)}, {"op": "matmul", "a": CMat, "B": tensor,
+    "C": tensor}.  The tensors must stay alive while the plan exists."""
+
+    _KIND = {"compress": OP_COMPRESS, "decompress": OP_DECOMPRESS, "add": OP_ADD, "sub": OP_SUB,
+             "scale": OP_SCALE, "dot": OP_DOT, "matmul": OP_MATMUL}
+
+    def __init__(self, ops, blocks_per_item: int = 0, ctas_per_sm: int = 0, autotune: bool = False, stream=None):
+        arr = (_Op * max(1, len(ops)))()
+        self._keep = []
+        for i, d in enumerate(ops):
+            o = arr[i]
+            o.kind = self._KIND[d["op"]]
+            for key in ("a", "b", "out"):
+                if key in d:
+                    setattr(o, key, d[key].desc())
+            if "A" in d:
+                _dev_f64(d["A"], "A")
+                o.A, o.lda = d["A"].data_ptr(), d["A"].stride(0)
+            if "c" in d:
+                o.c = float(d["c"])
+            if "result" in d:
+                o.result = d["result"].data_ptr()
+            if "B" in d:
+                _dev_f64(d["B"], "B")
+                o.B, o.ldb, o.m = d["B"].data_ptr(), d["B"].stride(0), d["B"].shape[1]
+            if "C" in d:
+                _dev_f64(d["C"], "C")
+                o.C, o.ldc = d["C"].data_ptr(), d["C"].stride(0)
+            self._keep.append(d)
+        cfg = _BatchCfg(blocks_per_item, ctas_per_sm, 1 if autotune else 0)
+        h = ctypes.c_void_p()
+        _check(lib().blaz_batch_plan(arr, len(ops), ctypes.byref(cfg), ctypes.byref(h), _stream(stream)),
+               "blaz_batch_plan")
+        self._h = h
+
+    def run(self, stream=None):
+        _check(lib().blaz_batch_run(self._h, _stream(stream)), "blaz_batch_run")
+
+    def info(self) -> dict:
+        inf = _BatchInfo()
+        _check(lib().blaz_batch_info_get(self._h, ctypes.byref(inf)), "blaz_batch_info_get")
+        return {k: getattr(inf, k) for k, _ in _BatchInfo._fields_}
+
+    def free(self):
+        if self._h:
+            lib().blaz_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
 
 
 # short aliases

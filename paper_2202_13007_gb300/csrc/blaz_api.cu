@@ -48,7 +48,7 @@ static int64_t nblocks(const blaz_cmat *m) { return (m->rows / 8) * (m->cols / 8
 
 // A compressed matrix descriptor is valid when its sides are multiples of 8
 // and, unless it is empty, all four arrays are set.
-static int check_cmat(const blaz_cmat *m)
+int validate_cmat(const blaz_cmat *m)
 {
     if (!m) return BLAZ_ERR_NULL;
     int rc = check_dims(m->rows, m->cols);
@@ -111,7 +111,12 @@ const char *blaz_strerror(int status)
 
 int blaz_last_cuda_error(void) { return g_last_cuda; }
 
-int blaz_device_status(void *stream) { return device_status((cudaStream_t)stream); }
+int blaz_device_status(void *stream)
+{
+    int a = device_status((cudaStream_t)stream);
+    int b = batch_device_status();
+    return a != BLAZ_OK ? a : b;
+}
 
 void blaz_constants(double cos_out[64], double aa_out[64], int32_t kept_out[56])
 {
@@ -173,7 +178,7 @@ int blaz_cmat_free(blaz_cmat *m, void *stream)
 
 int blaz_compress(const double *A, int64_t lda, blaz_cmat *out, void *stream)
 {
-    int rc = check_cmat(out);
+    int rc = validate_cmat(out);
     if (rc) return rc;
     if (nblocks(out) == 0) return BLAZ_OK;
     if (!A) return BLAZ_ERR_NULL;
@@ -183,7 +188,7 @@ int blaz_compress(const double *A, int64_t lda, blaz_cmat *out, void *stream)
 
 int blaz_decompress(const blaz_cmat *a, double *A, int64_t lda, void *stream)
 {
-    int rc = check_cmat(a);
+    int rc = validate_cmat(a);
     if (rc) return rc;
     if (nblocks(a) == 0) return BLAZ_OK;
     if (!A) return BLAZ_ERR_NULL;
@@ -194,7 +199,7 @@ int blaz_decompress(const blaz_cmat *a, double *A, int64_t lda, void *stream)
 static int add_or_sub(const blaz_cmat *a, const blaz_cmat *b, blaz_cmat *out, bool sub, void *stream)
 {
     int rc;
-    if ((rc = check_cmat(a)) || (rc = check_cmat(b)) || (rc = check_cmat(out))) return rc;
+    if ((rc = validate_cmat(a)) || (rc = validate_cmat(b)) || (rc = validate_cmat(out))) return rc;
     if ((rc = same_shape(a, b)) || (rc = same_shape(a, out))) return rc;
     return launch_add(a, b, out, sub, (cudaStream_t)stream);
 }
@@ -212,7 +217,7 @@ int blaz_sub(const blaz_cmat *a, const blaz_cmat *b, blaz_cmat *out, void *strea
 int blaz_scale(const blaz_cmat *a, double c, blaz_cmat *out, void *stream)
 {
     int rc;
-    if ((rc = check_cmat(a)) || (rc = check_cmat(out))) return rc;
+    if ((rc = validate_cmat(a)) || (rc = validate_cmat(out))) return rc;
     if ((rc = same_shape(a, out))) return rc;
     return launch_scale(a, c, out, (cudaStream_t)stream);
 }
@@ -220,7 +225,7 @@ int blaz_scale(const blaz_cmat *a, double c, blaz_cmat *out, void *stream)
 int blaz_dot(const blaz_cmat *a, const blaz_cmat *b, double *result, void *stream)
 {
     int rc;
-    if ((rc = check_cmat(a)) || (rc = check_cmat(b))) return rc;
+    if ((rc = validate_cmat(a)) || (rc = validate_cmat(b))) return rc;
     if ((rc = same_shape(a, b))) return rc;
     if (!result) return BLAZ_ERR_NULL;
     cudaStream_t st = (cudaStream_t)stream;
@@ -237,7 +242,7 @@ int blaz_dot(const blaz_cmat *a, const blaz_cmat *b, double *result, void *strea
 int blaz_dot_rowcol(const blaz_cmat *a, const blaz_cmat *b, int64_t i, int64_t j, double *result, void *stream)
 {
     int rc;
-    if ((rc = check_cmat(a)) || (rc = check_cmat(b))) return rc;
+    if ((rc = validate_cmat(a)) || (rc = validate_cmat(b))) return rc;
     if (a->cols != b->rows) return BLAZ_ERR_SHAPE;
     if (!result) return BLAZ_ERR_NULL;
     if (i < 0 || i >= a->rows || j < 0 || j >= b->cols) return BLAZ_ERR_RANGE;
@@ -248,7 +253,7 @@ int blaz_matmul(const blaz_cmat *a, const double *B, int64_t ldb, int64_t m, dou
                 void *stream)
 {
     int rc;
-    if ((rc = check_cmat(a))) return rc;
+    if ((rc = validate_cmat(a))) return rc;
     if (m < 0) return BLAZ_ERR_SHAPE;
     if (mode != BLAZ_MM_FP64 && mode != BLAZ_MM_SPLIT_BF16) return BLAZ_ERR_ARG;
     const int64_t n = a->rows, k = a->cols;

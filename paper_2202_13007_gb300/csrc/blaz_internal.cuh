@@ -76,6 +76,8 @@ __device__ __forceinline__ int8_t quantize(double v)
 int set_cuda_error(cudaError_t e);   // records e, returns BLAZ_ERR_CUDA
 int launch_status();                 // cudaGetLastError -> BLAZ_OK / BLAZ_ERR_CUDA
 int num_sms();                       // SM count of the current device (cached)
+int validate_cmat(const blaz_cmat *m);   // shape, NULL and alignment checks of a descriptor
+int batch_device_status();           // reads and clears the batch kernel's status word
 
 // ---- launchers (one per kernel family) ------------------------------------------
 int launch_compress(const double *A, int64_t lda, const blaz_cmat *out, cudaStream_t st);

@@ -2,7 +2,7 @@
 // addition / subtraction (Algorithm 1, Eq. eq55) and multiplication by a
 // constant (Algorithm 2) of "Compressed Matrix Computations" (arXiv 2202.13007).
 // Bit-exact binary64 (explicit round-to-nearest intrinsics).
-#include "blaz_internal.cuh"
+#include "block_ops.cuh"
 
 namespace blaz {
 
@@ -13,51 +13,8 @@ __global__ void __launch_bounds__(128)
           const uint8_t *__restrict__ p2, const int8_t *__restrict__ c2, double *f, double *s, uint8_t *p,
           int8_t *c)
 {
-    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x) {
-        // Read everything of this block before writing: out may alias an input.
-        const double fa = f1[b], fb = f2[b], sa = s1[b], sb = s2[b];
-        const int pa = p1[b], pb = p2[b];
-        uint32_t wa[7], wb[7];
-        const uint32_t *ca = reinterpret_cast<const uint32_t *>(c1 + b * kKeep);
-        const uint32_t *cb = reinterpret_cast<const uint32_t *>(c2 + b * kKeep);
-#pragma unroll
-        for (int q = 0; q < 7; ++q) {
-            wa[q] = ca[q];
-            wb[q] = cb[q];
-        }
-        const double fs = kSub ? dsub(fa, fb) : dadd(fa, fb);
-        const double ss = dadd(sa, sb);
-        int ph = (pa * pb) / (pa + pb);
-        ph = ph < 1 ? 1 : ph;
-        uint32_t wo[7];
-        if (ss == 0.0) {
-#pragma unroll
-            for (int q = 0; q < 7; ++q) wo[q] = 0u;
-        } else {
-            const double a1 = ddiv(sa, ss);
-            const double a2 = ddiv(sb, ss);
-            const double b1 = dmul(ddiv(a1, (double)pa), (double)ph);
-            const double b2 = dmul(ddiv(a2, (double)pb), (double)ph);
-#pragma unroll
-            for (int q = 0; q < 7; ++q) {
-                uint32_t v = 0;
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const double x1 = (double)(int8_t)(uint8_t)(wa[q] >> (8 * k));
-                    const double x2 = (double)(int8_t)(uint8_t)(wb[q] >> (8 * k));
-                    const double y = kSub ? dsub(dmul(b1, x1), dmul(b2, x2)) : dadd(dmul(b1, x1), dmul(b2, x2));
-                    v |= (uint32_t)(uint8_t)quantize(y) << (8 * k);
-                }
-                wo[q] = v;
-            }
-        }
-        f[b] = fs;
-        s[b] = ss;
-        p[b] = (uint8_t)ph;
-        uint32_t *co = reinterpret_cast<uint32_t *>(c + b * kKeep);
-#pragma unroll
-        for (int q = 0; q < 7; ++q) co[q] = wo[q];
-    }
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x)
+        add_block<kSub>(b, f1, s1, p1, c1, f2, s2, p2, c2, f, s, p, c);
 }
 
 // Algorithm 2.  When out == a (in place) only f and s are touched; otherwise

@@ -8,115 +8,6 @@
 
 namespace blaz {
 
-// One thread per 8x8 block.  Loads the block (eight rows of 64 B) with 16-byte
-// vector loads when the matrix allows it.
-template <bool kVec>
-__device__ __forceinline__ void load_block(const double *__restrict__ A, int64_t lda, int64_t bi, int64_t bj,
-                                           double (&d)[64])
-{
-    const double *p = A + (bi * 8) * lda + bj * 8;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        if (kVec) {
-            const double2 *q = reinterpret_cast<const double2 *>(p + i * lda);
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                double2 v = __ldg(q + h);
-                d[i * 8 + 2 * h] = v.x;
-                d[i * 8 + 2 * h + 1] = v.y;
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < 8; ++j) d[i * 8 + j] = __ldg(p + i * lda + j);
-        }
-    }
-}
-
-// Compress one block held in d (overwritten).  Writes s, phi and the 28 codes.
-__device__ __forceinline__ void compress_block(double (&d)[64], double &s_out, uint8_t &phi_out,
-                                               int8_t (&code)[kKeep])
-{
-    // Eq. eqnorm, evaluated in place from the last element backwards so that
-    // M(i-1,j) and M(i,j-1) are still the inputs when D(i,j) is formed.
-#pragma unroll
-    for (int i = 7; i >= 0; --i) {
-#pragma unroll
-        for (int j = 7; j >= 0; --j) {
-            if (i == 0 && j == 0) {
-                d[0] = 0.0;
-            } else if (i == 0) {
-                d[j] = dsub(d[j], d[j - 1]);
-            } else if (j == 0) {
-                d[i * 8] = dsub(d[i * 8], d[(i - 1) * 8]);
-            } else {
-                double a = dsub(d[i * 8 + j], d[(i - 1) * 8 + j]);
-                double b = dsub(d[i * 8 + j], d[i * 8 + j - 1]);
-                d[i * 8 + j] = dmul(dadd(a, b), 0.5);
-            }
-        }
-    }
-    // Eqs. eqslope / eqslope2: K nonzero entries, S = sum |D| row-major.
-    int K = 0;
-    double S = 0.0;
-#pragma unroll
-    for (int p = 0; p < 64; ++p) {
-        K += (d[p] != 0.0);
-        S = dadd(S, fabs(d[p]));
-    }
-    if (K == 0) {  // constant block: s = 0, all coefficients 0, phi = 127/0 -> 255
-        s_out = 0.0;
-        phi_out = 255;
-#pragma unroll
-        for (int t = 0; t < kKeep; ++t) code[t] = 0;
-        return;
-    }
-    const double s = ddiv(S, (double)K);
-    const double r = ddiv(1.0, s);
-#pragma unroll
-    for (int p = 0; p < 64; ++p) d[p] = dmul(d[p], r);
-    s_out = s;
-
-    // Eq. eqdct, one output column j at a time: inner sums T[u] over v, outer
-    // sums over u, then the alpha_i alpha_j factor.  Multiplications by
-    // cos(0) = 1 are exact and therefore omitted.
-    double kept[kKeep];
-    double m = 0.0;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        double T[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            double acc = (j == 0) ? d[u * 8] : dmul(d[u * 8], cos_tab(j, 0));
-#pragma unroll
-            for (int v = 1; v < 8; ++v) acc = dadd(acc, (j == 0) ? d[u * 8 + v] : dmul(d[u * 8 + v], cos_tab(j, v)));
-            T[u] = acc;
-        }
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            double acc = (i == 0) ? T[0] : dmul(cos_tab(i, 0), T[0]);
-#pragma unroll
-            for (int u = 1; u < 8; ++u) acc = dadd(acc, (i == 0) ? T[u] : dmul(cos_tab(i, u), T[u]));
-            const double X = dmul(aa_tab(i, j), acc);
-            const double ax = fabs(X);
-            m = (ax > m) ? ax : m;
-            const int t = kept_index(i, j);
-            if (t >= 0) kept[t] = X;
-        }
-    }
-    // Eq. eqphi
-    const double q = ddiv(127.0, m);
-    int phi;
-    if (!(q < 255.0)) phi = 255;
-    else {
-        phi = __double2int_rz(q);
-        phi = phi < 1 ? 1 : phi;
-    }
-    phi_out = (uint8_t)phi;
-    const double phid = (double)phi;
-#pragma unroll
-    for (int t = 0; t < kKeep; ++t) code[t] = quantize(dmul(kept[t], phid));
-}
-
 template <bool kVec>
 __global__ void __launch_bounds__(128) k_compress(const double *__restrict__ A, int64_t lda, int64_t nbc, int64_t nb,
                                                   double *__restrict__ f, double *__restrict__ s,
