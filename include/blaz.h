@@ -231,6 +231,74 @@ int blaz_batch_info_get(const blaz_plan *plan, blaz_batch_info *info);
 /* Release the plan (synchronizes the device first). */
 int blaz_batch_free(blaz_plan *plan);
 
+/* ---- Request server: resident compressed matrices, continuous batching ------
+ * A server owns a set of resident compressed matrices (handles) on the current
+ * device and a scheduler thread.  Requests are submitted from any host
+ * thread; the scheduler admits them in arrival order while the device-memory
+ * budget allows (a request that does not fit waits until memory is released
+ * by completing work; one that can never fit is rejected), gathers the
+ * admitted requests whose operands are ready into one persistent batch launch
+ * (the batch kernel above), and keeps up to `streams` such launches in flight
+ * on separate streams, so requests arriving while others run are admitted as
+ * slots and memory free up and their work overlaps on the device.  Every
+ * result equals the single-operation entry points' result (same kernels). */
+enum { BLAZ_REQ_RELEASE = 7 };  /* request kinds: BLAZ_OP_* above, plus RELEASE */
+
+typedef struct blaz_server_cfg {
+    int64_t budget_bytes;   /* device bytes for resident matrices + in-flight work  */
+    int32_t streams;        /* launches in flight at once (0: 4)                     */
+    int32_t max_batch;      /* requests per launch (0: 512; 1 = one per launch)      */
+    int32_t max_wait_us;    /* longest a ready request waits for company (0: 100)   */
+    int32_t queue_capacity; /* submitted-but-unadmitted requests (0: 65536)          */
+} blaz_server_cfg;
+
+typedef struct blaz_request {
+    int32_t kind;           /* BLAZ_OP_COMPRESS .. BLAZ_OP_MATMUL, BLAZ_REQ_RELEASE  */
+    int64_t rows, cols;     /* COMPRESS: shape of host_A                             */
+    const double *host_A;   /* COMPRESS: host input, leading dimension lda (copied
+                               during blaz_server_submit)                          */
+    int64_t lda;
+    uint64_t a, b;          /* operand handles (ADD/SUB/DOT: a, b; others: a)       */
+    double c;               /* SCALE                                                 */
+    const double *host_B;   /* MATMUL: host right operand, a.cols x m, ldb (copied)  */
+    int64_t ldb, m;
+    double *host_out;       /* DECOMPRESS: rows x cols, MATMUL: rows x m, leading
+                               dimension ldo; DOT: one double.  Written by the
+                               server before the request reports completion; must
+                               stay valid until then.                             */
+    int64_t ldo;
+} blaz_request;
+
+typedef struct blaz_result {
+    int32_t status;         /* BLAZ_OK, 1 = still pending, or a BLAZ_ERR_* code      */
+    uint64_t handle;        /* COMPRESS/ADD/SUB/SCALE: the new resident matrix       */
+    double value;           /* DOT                                                   */
+    double latency_us;      /* submission to completion                              */
+} blaz_result;
+
+typedef struct blaz_server_stats {
+    int64_t submitted, completed, rejected, launches, resident_matrices, resident_bytes, peak_bytes;
+    double p50_us, p99_us, mean_batch, throughput_rps;
+} blaz_server_stats;
+
+typedef struct blaz_server blaz_server;
+
+int blaz_server_create(const blaz_server_cfg *cfg, blaz_server **srv);
+/* Validates and enqueues; returns a ticket.  BLAZ_ERR_BUSY when the queue is
+ * full (retry later), BLAZ_ERR_BUDGET when the request alone exceeds the
+ * budget, BLAZ_ERR_SHAPE / NULL / LD / ARG for invalid requests. */
+int blaz_server_submit(blaz_server *srv, const blaz_request *req, uint64_t *ticket);
+/* Non-blocking: status 1 while pending.  A completed ticket is forgotten after
+ * it is reported once. */
+int blaz_server_poll(blaz_server *srv, uint64_t ticket, blaz_result *res);
+/* Blocks until the ticket completes or timeout_us passes (BLAZ_ERR_TIMEOUT). */
+int blaz_server_wait(blaz_server *srv, uint64_t ticket, blaz_result *res, int64_t timeout_us);
+/* Device descriptor of a resident matrix (read-only view, valid until released). */
+int blaz_server_cmat(blaz_server *srv, uint64_t handle, blaz_cmat *out);
+int blaz_server_stats_get(blaz_server *srv, blaz_server_stats *st);
+/* Drains in-flight work, frees every resident matrix, stops the scheduler. */
+int blaz_server_destroy(blaz_server *srv);
+
 #ifdef __cplusplus
 }
 #endif

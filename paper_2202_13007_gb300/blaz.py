@@ -53,6 +53,32 @@ class _BatchInfo(ctypes.Structure):
 
 
 OP_COMPRESS, OP_DECOMPRESS, OP_ADD, OP_SUB, OP_SCALE, OP_DOT, OP_MATMUL = range(7)
+REQ_RELEASE = 7
+
+
+class _ServerCfg(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_int64), ("streams", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+                ("max_wait_us", ctypes.c_int32), ("queue_capacity", ctypes.c_int32)]
+
+
+class _Request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("rows", ctypes.c_int64), ("cols", ctypes.c_int64),
+                ("host_A", ctypes.c_void_p), ("lda", ctypes.c_int64), ("a", ctypes.c_uint64),
+                ("b", ctypes.c_uint64), ("c", ctypes.c_double), ("host_B", ctypes.c_void_p),
+                ("ldb", ctypes.c_int64), ("m", ctypes.c_int64), ("host_out", ctypes.c_void_p),
+                ("ldo", ctypes.c_int64)]
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("handle", ctypes.c_uint64), ("value", ctypes.c_double),
+                ("latency_us", ctypes.c_double)]
+
+
+class _ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("rejected", ctypes.c_int64),
+                ("launches", ctypes.c_int64), ("resident_matrices", ctypes.c_int64),
+                ("resident_bytes", ctypes.c_int64), ("peak_bytes", ctypes.c_int64), ("p50_us", ctypes.c_double),
+                ("p99_us", ctypes.c_double), ("mean_batch", ctypes.c_double), ("throughput_rps", ctypes.c_double)]
 
 _lib = None
 
@@ -81,6 +107,13 @@ SIGNATURES = {
     "blaz_batch_run": (ctypes.c_int, [_P, _P]),
     "blaz_batch_info_get": (ctypes.c_int, [_P, ctypes.POINTER(_BatchInfo)]),
     "blaz_batch_free": (ctypes.c_int, [_P]),
+    "blaz_server_create": (ctypes.c_int, [ctypes.POINTER(_ServerCfg), ctypes.POINTER(ctypes.c_void_p)]),
+    "blaz_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(_Request), ctypes.POINTER(ctypes.c_uint64)]),
+    "blaz_server_poll": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(_Result)]),
+    "blaz_server_wait": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(_Result), _I64]),
+    "blaz_server_cmat": (ctypes.c_int, [_P, ctypes.c_uint64, _DESC]),
+    "blaz_server_stats_get": (ctypes.c_int, [_P, ctypes.POINTER(_ServerStats)]),
+    "blaz_server_destroy": (ctypes.c_int, [_P]),
 }
 
 
@@ -319,6 +352,104 @@ class Batch:
             self.free()
         except Exception:
             pass
+
+
+class Server:
+    """Request server: resident compressed matrices on the current device,
+    admission by a device-memory budget, continuous batching (C++ scheduler
+    thread inside libblaz).  Host inputs are numpy float64 arrays (copied at
+    submission); outputs are written into numpy arrays the caller passes and
+    keeps alive until the request completes."""
+
+    _KIND = dict(Batch._KIND, release=REQ_RELEASE)
+
+    def __init__(self, budget_bytes: int, streams: int = 0, max_batch: int = 0, max_wait_us: int = 0,
+                 queue_capacity: int = 0):
+        cfg = _ServerCfg(int(budget_bytes), streams, max_batch, max_wait_us, queue_capacity)
+        h = ctypes.c_void_p()
+        _check(lib().blaz_server_create(ctypes.byref(cfg), ctypes.byref(h)), "blaz_server_create")
+        self._h = h
+
+    def submit(self, op: str, *, A=None, a: int = 0, b: int = 0, c: float = 0.0, B=None, out=None) -> int:
+        import numpy as np
+
+        r = _Request()
+        r.kind = self._KIND[op]
+        if A is not None:
+            assert A.dtype == np.float64 and A.ndim == 2 and A.strides[1] == 8
+            r.rows, r.cols = A.shape
+            r.host_A, r.lda = A.ctypes.data, A.strides[0] // 8
+        r.a, r.b, r.c = a, b, float(c)
+        if B is not None:
+            assert B.dtype == np.float64 and B.ndim == 2 and B.strides[1] == 8
+            r.host_B, r.ldb, r.m = B.ctypes.data, B.strides[0] // 8, B.shape[1]
+        if out is not None:
+            assert out.dtype == np.float64 and out.strides[-1] == 8
+            r.host_out = out.ctypes.data
+            r.ldo = out.strides[0] // 8 if out.ndim == 2 else 1
+        t = ctypes.c_uint64()
+        rc = lib().blaz_server_submit(self._h, ctypes.byref(r), ctypes.byref(t))
+        if rc != 0:
+            raise BlazError(rc, "blaz_server_submit")
+        return t.value
+
+    def poll(self, ticket: int):
+        res = _Result()
+        _check(lib().blaz_server_poll(self._h, ticket, ctypes.byref(res)), "blaz_server_poll")
+        return {k: getattr(res, k) for k, _ in _Result._fields_}
+
+    def wait(self, ticket: int, timeout_s: float = 60.0):
+        res = _Result()
+        _check(lib().blaz_server_wait(self._h, ticket, ctypes.byref(res), int(timeout_s * 1e6)), "blaz_server_wait")
+        return {k: getattr(res, k) for k, _ in _Result._fields_}
+
+    def cmat(self, handle: int) -> "CMat":
+        """A copy of a resident matrix as a CMat (device tensors)."""
+        d = _CMatDesc()
+        _check(lib().blaz_server_cmat(self._h, handle, ctypes.byref(d)), "blaz_server_cmat")
+        nb = (d.rows // 8) * (d.cols // 8)
+        dev = torch.device("cuda", torch.cuda.current_device())
+
+        def view(ptr, n, dtype, shape):
+            if n == 0:
+                return torch.empty(shape, dtype=dtype, device=dev)
+            nbytes = n * torch.empty((), dtype=dtype).element_size()
+            return _from_ptr(ptr, nbytes, dtype, shape, dev)
+
+        return CMat(d.rows, d.cols, view(d.f, nb, torch.float64, (nb,)), view(d.s, nb, torch.float64, (nb,)),
+                    view(d.phi, nb, torch.uint8, (nb,)), view(d.code, nb * NKEEP, torch.int8, (nb, NKEEP)))
+
+    def stats(self) -> dict:
+        st = _ServerStats()
+        _check(lib().blaz_server_stats_get(self._h, ctypes.byref(st)), "blaz_server_stats_get")
+        return {k: getattr(st, k) for k, _ in _ServerStats._fields_}
+
+    def destroy(self):
+        if self._h:
+            lib().blaz_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+class _DevArray:
+    """Minimal __cuda_array_interface__ exporter for a raw device pointer."""
+
+    _TYPESTR = {torch.float64: "<f8", torch.uint8: "|u1", torch.int8: "|i1"}
+
+    def __init__(self, ptr: int, dtype, shape):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": self._TYPESTR[dtype],
+                                         "data": (int(ptr), False), "version": 3, "strides": None}
+
+
+def _from_ptr(ptr: int, nbytes: int, dtype, shape, dev):
+    """Copy device memory at `ptr` into a new tensor (reading a server-owned
+    matrix; the copy keeps the server's lifetime rules simple)."""
+    return torch.as_tensor(_DevArray(ptr, dtype, shape), device=dev).clone()
 
 
 # short aliases

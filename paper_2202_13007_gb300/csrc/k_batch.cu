@@ -17,6 +17,7 @@
 #include <cstring>
 #include <vector>
 
+#include "batch_internal.cuh"
 #include "block_codec.cuh"
 #include "block_ops.cuh"
 #include "gemm_fp64.cuh"
@@ -29,40 +30,6 @@ namespace batch {
 
 constexpr int kThreads = kGemmThreads;  // 128: also the thread count of a DMMA tile
 constexpr long long kWaitCycles = 4000000000LL;
-
-struct DevOp {
-    int32_t kind;
-    int32_t vec;          // COMPRESS: 16-byte vector loads allowed
-    int64_t nbc;          // blocks per block-row of the block loop's matrix
-    const double *fa, *sa;
-    const uint8_t *pa;
-    const int8_t *ca;
-    const double *fb, *sb;
-    const uint8_t *pb;
-    const int8_t *cb;
-    double *fo, *so;
-    uint8_t *po;
-    int8_t *co;
-    const double *A;
-    int64_t lda;
-    double c;
-    double *result;
-    const double *B;
-    int64_t ldb, m;
-    double *C;
-    int64_t ldc;
-    double *scratch;      // MATMUL: decompressed a (n x k, leading dimension k)
-    int64_t n, k;
-    int32_t first_item;   // first block item of the op
-    int32_t nitems;       // number of block items of the op
-    int64_t partial_base; // DOT: first slot of the op in partials[]
-};
-
-struct Item {
-    int32_t op;
-    int32_t tile;   // 0: blocks [b0, b1); 1: product tile at rows b0, columns b1
-    int64_t b0, b1;
-};
 
 __device__ __forceinline__ double cta_sum128(double v, double *red)
 {
@@ -202,6 +169,14 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
+int launch(const DevOp *d_ops, const Item *d_items, int nitems, unsigned *d_counters, double *d_partials, int grid,
+           cudaStream_t st)
+{
+    if (nitems <= 0) return BLAZ_OK;
+    k_batch<<<grid, kThreads, 0, st>>>(d_ops, d_items, nitems, d_counters, d_counters + 1, d_partials);
+    return launch_status();
+}
+
 }  // namespace batch
 
 int batch_device_status()
@@ -238,10 +213,10 @@ struct blaz_plan {
 };
 
 namespace {
-
 int64_t nblk(const blaz_cmat &m) { return (m.rows / 8) * (m.cols / 8); }
+}  // namespace
 
-int check_op(const blaz_op &o)
+int blaz::batch::check_op(const blaz_op &o)
 {
     int rc;
     switch (o.kind) {
@@ -281,6 +256,8 @@ int check_op(const blaz_op &o)
     }
 }
 
+namespace {
+
 // Output and input base pointers of an op (for the autotune aliasing check).
 void op_ptrs(const blaz_op &o, std::vector<const void *> &in, std::vector<const void *> &out)
 {
@@ -301,37 +278,27 @@ void op_ptrs(const blaz_op &o, std::vector<const void *> &in, std::vector<const 
     }
 }
 
-// Build the device descriptors and the work list for a configuration.
-int build(blaz_plan *p, const blaz_batch_cfg &cfg)
+}  // namespace
+
+void blaz::batch::build_work(const blaz_op *ops, int nops, int64_t bpi, char *scratch, std::vector<DevOp> &dops,
+                             std::vector<Item> &all, int64_t &partials, size_t &scratch_bytes_out, int &ngemm)
 {
-    const int64_t bpi = cfg.blocks_per_item > 0 ? cfg.blocks_per_item : 256;
-    const int nops = (int)p->ops.size();
-    std::vector<batch::DevOp> dops(nops);
-    std::vector<batch::Item> first, middle, tiles;
-    int64_t partials = 0;
-    size_t scratch = 0;
+    dops.assign(nops, DevOp{});
+    std::vector<Item> first, middle, tiles;
+    partials = 0;
+    size_t sbytes = 0;
     std::vector<size_t> scratch_off(nops, 0);
     for (int i = 0; i < nops; ++i) {
-        const blaz_op &o = p->ops[i];
+        const blaz_op &o = ops[i];
         if (o.kind == BLAZ_OP_MATMUL && o.a.rows && o.m) {
-            scratch_off[i] = scratch;
-            scratch += ((size_t)(o.a.rows * o.a.cols) * 8 + 255) & ~(size_t)255;
+            scratch_off[i] = sbytes;
+            sbytes += ((size_t)(o.a.rows * o.a.cols) * 8 + 255) & ~(size_t)255;
         }
     }
-    if (scratch > p->scratch_bytes) {
-        if (p->d_scratch) cudaFree(p->d_scratch);
-        p->d_scratch = nullptr;
-        cudaError_t e = cudaMalloc(&p->d_scratch, scratch);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            p->scratch_bytes = 0;
-            return e == cudaErrorMemoryAllocation ? BLAZ_ERR_OOM : set_cuda_error(e);
-        }
-        p->scratch_bytes = scratch;
-    }
+    scratch_bytes_out = sbytes;
     for (int i = 0; i < nops; ++i) {
-        const blaz_op &o = p->ops[i];
-        batch::DevOp &d = dops[i];
+        const blaz_op &o = ops[i];
+        DevOp &d = dops[i];
         std::memset(&d, 0, sizeof(d));
         d.kind = o.kind;
         const blaz_cmat &drive = (o.kind == BLAZ_OP_COMPRESS) ? o.out : o.a;
@@ -349,9 +316,9 @@ int build(blaz_plan *p, const blaz_batch_cfg &cfg)
         d.n = o.a.rows; d.k = o.a.cols;
         if (o.kind == BLAZ_OP_MATMUL) {
             if (!o.a.rows || !o.m) continue;                   // empty product: nothing to do
-            d.scratch = (double *)(p->d_scratch + scratch_off[i]);
+            d.scratch = scratch ? (double *)(scratch + scratch_off[i]) : nullptr;
         }
-        std::vector<batch::Item> &dst = (o.kind == BLAZ_OP_MATMUL) ? first : middle;
+        std::vector<Item> &dst = (o.kind == BLAZ_OP_MATMUL) ? first : middle;
         d.first_item = (int32_t)dst.size();
         int cnt = 0;
         for (int64_t b0 = 0; b0 < nb; b0 += bpi) {
@@ -371,18 +338,43 @@ int build(blaz_plan *p, const blaz_batch_cfg &cfg)
             for (int64_t r = 0; r < o.a.rows; r += kGemmBM)
                 for (int64_t c = 0; c < o.m; c += kGemmBN) tiles.push_back({i, 1, r, c});
     }
-    // Item index of the middle section's ops is offset by the first section.
     const int off = (int)first.size();
     for (int i = 0; i < nops; ++i)
-        if (p->ops[i].kind != BLAZ_OP_MATMUL) dops[i].first_item += off;
-    std::vector<batch::Item> all;
+        if (ops[i].kind != BLAZ_OP_MATMUL) dops[i].first_item += off;
+    all.clear();
     all.reserve(first.size() + middle.size() + tiles.size());
     all.insert(all.end(), first.begin(), first.end());
     all.insert(all.end(), middle.begin(), middle.end());
     all.insert(all.end(), tiles.begin(), tiles.end());
-    // K == 0 products: C = 0 needs no decompression; tiles still run and write zeros.
-    if (all.size() > 0x7fffffff) return BLAZ_ERR_ARG;
+    ngemm = (int)tiles.size();
+}
 
+namespace {
+
+// Build the device descriptors and the work list of a plan for a configuration.
+int build(blaz_plan *p, const blaz_batch_cfg &cfg)
+{
+    const int64_t bpi = cfg.blocks_per_item > 0 ? cfg.blocks_per_item : 256;
+    const int nops = (int)p->ops.size();
+    std::vector<batch::DevOp> dops;
+    std::vector<batch::Item> all;
+    int64_t partials = 0;
+    size_t scratch = 0;
+    int ngemm = 0;
+    batch::build_work(p->ops.data(), nops, bpi, nullptr, dops, all, partials, scratch, ngemm);
+    if (scratch > p->scratch_bytes) {
+        if (p->d_scratch) cudaFree(p->d_scratch);
+        p->d_scratch = nullptr;
+        cudaError_t e = cudaMalloc(&p->d_scratch, scratch);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            p->scratch_bytes = 0;
+            return e == cudaErrorMemoryAllocation ? BLAZ_ERR_OOM : set_cuda_error(e);
+        }
+        p->scratch_bytes = scratch;
+    }
+    batch::build_work(p->ops.data(), nops, bpi, p->d_scratch, dops, all, partials, scratch, ngemm);
+    if (all.size() > 0x7fffffff) return BLAZ_ERR_ARG;
     cudaError_t e;
     if (!p->d_ops) {
         if ((e = cudaMalloc(&p->d_ops, sizeof(batch::DevOp) * std::max(1, nops))) != cudaSuccess) return set_cuda_error(e);
@@ -409,7 +401,7 @@ int build(blaz_plan *p, const blaz_batch_cfg &cfg)
             cudaSuccess)
         return set_cuda_error(e);
     p->nitems = (int)all.size();
-    p->ngemm = (int)tiles.size();
+    p->ngemm = ngemm;
     const int cps = cfg.ctas_per_sm > 0 ? cfg.ctas_per_sm : 2;
     p->grid = std::max(1, std::min<int>(num_sms() * cps, std::max(1, p->nitems)));
     p->cfg = cfg;
@@ -427,9 +419,7 @@ int build(blaz_plan *p, const blaz_batch_cfg &cfg)
     if ((e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) rc = set_cuda_error(e);
     if (!rc) {
         cudaMemsetAsync(p->d_counters, 0, sizeof(unsigned) * (1 + std::max(1, nops)), cap);
-        if (p->nitems > 0)
-            batch::k_batch<<<p->grid, batch::kThreads, 0, cap>>>(p->d_ops, p->d_items, p->nitems, p->d_counters,
-                                                                 p->d_counters + 1, p->d_partials);
+        batch::launch(p->d_ops, p->d_items, p->nitems, p->d_counters, p->d_partials, p->grid, cap);
         e = cudaStreamEndCapture(cap, &p->graph);
         if (e != cudaSuccess) rc = set_cuda_error(e);
     }
@@ -448,7 +438,7 @@ int blaz_batch_plan(const blaz_op *ops, int64_t nops, const blaz_batch_cfg *cfg,
     if (nops < 0) return BLAZ_ERR_ARG;
     *plan = nullptr;
     for (int64_t i = 0; i < nops; ++i) {
-        int rc = check_op(ops[i]);
+        int rc = batch::check_op(ops[i]);
         if (rc) return rc;
     }
     blaz_batch_cfg c = cfg ? *cfg : blaz_batch_cfg{0, 0, 0};
