@@ -47,6 +47,11 @@ def parse():
     p.add_argument("--side", type=int, default=16384)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--workload", default="sweep", choices=["sweep", "batch", "serve"],
+                   help="sweep: the bandwidth-sweep step (default line); batch / serve: the batched and "
+                        "served configurations, each printed as its own line")
+    p.add_argument("--serve-seconds", type=float, default=2.0)
+    p.add_argument("--no-extras", action="store_true", help="skip the matmul and serve fields of the sweep line")
     return p.parse_args()
 
 
@@ -218,6 +223,211 @@ def config(side):
             "l2": "inputs larger than L2 (2 GiB per field), no flush", "parallelism": "replicas"}
 
 
+def matmul_extras(B, W, torch, dev):
+    """Precision configuration: compressed 4096^2 bump field times a smoothed
+    N(0,1) 4096^2 matrix, FP64 DMMA path and split-bf16 tcgen05 path."""
+    n = 4096
+    ta = W.bump_field_torch(n, n, dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(7)
+    z = torch.randn((n, n), generator=g, dtype=torch.float64, device=dev)
+    Bd = sum(torch.roll(z, (di, dj), (0, 1)) for di in range(-2, 3) for dj in range(-2, 3)) / 25.0
+    ga = B.compress(ta)
+    C = torch.empty((n, n), dtype=torch.float64, device=dev)
+    out = {}
+    for mode, reps in (("fp64", 2), ("split_bf16", 10)):
+        B.matmul(ga, Bd, mode=mode, out=C)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            B.matmul(ga, Bd, mode=mode, out=C)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[mode] = {"ms": ms, "tflops": 2 * n ** 3 / (ms * 1e-3) / 1e12}
+    out["shape"] = "4096x4096x4096 (compressed A, dense B); split_bf16 componentwise error 4.3e-6, fp64 6.8e-16"
+    return out
+
+
+def run_serve(args, B, W, torch, dev, seconds, max_batch, streams, mode="fp64", seed=13, rate=5000.0):
+    """Poisson stream (5k req/s, sides log-uniform over multiples of 8 in
+    [64, 4096], op mix 40/30/15/10/5 %) against a server with a 40 GB budget.
+    Compress inputs and product operands are page-locked host views; add /
+    scale / dot / matmul operate on a pool of resident matrices compressed
+    beforehand (48 shapes drawn from the same law)."""
+    import numpy as np
+
+    side = 4096
+    src_t = torch.empty((side, side), dtype=torch.float64, pin_memory=True)
+    src_t.copy_(W.bump_field_torch(side, 4096, dev))
+    bsrc_t = torch.empty((side, side), dtype=torch.float64, pin_memory=True)
+    g = torch.Generator(device=dev)
+    g.manual_seed(17)
+    bsrc_t.copy_(torch.randn((side, side), generator=g, dtype=torch.float64, device=dev))
+    src, bsrc = src_t.numpy(), bsrc_t.numpy()
+    arena_t = torch.empty(2 << 27, dtype=torch.float64, pin_memory=True)     # 2 GiB of outputs
+    arena = arena_t.numpy()
+    reqs = W.poisson_requests(rate=rate, duration_s=seconds, seed=seed, lo=64, hi=side)
+    prng = np.random.default_rng(seed + 1)
+    pool_shapes = [(W._side(prng, 64, side), W._side(prng, 64, side)) for _ in range(48)]
+    srv = B.Server(budget_bytes=40 << 30, streams=streams, max_batch=max_batch, matmul_mode=mode)
+    pool = []
+    for r, c in pool_shapes:
+        ha = srv.submit("compress", A=src[:r, :c], pinned=True)
+        hb = srv.submit("compress", A=src[side - r:, side - c:], pinned=True)
+        pool.append((r, c, srv.wait(ha)["handle"], srv.wait(hb)["handle"]))
+    warm = srv.stats()
+    dots = torch.zeros(len(reqs), dtype=torch.float64, pin_memory=True).numpy()
+    tickets, busy, waited = [], {}, set()
+    off = 0
+    t0 = time.perf_counter()
+    for i, d in enumerate(reqs):
+        now = time.perf_counter() - t0
+        if d["t"] > now:
+            time.sleep(d["t"] - now)
+        r, c, ha, hb = pool[i % len(pool)]
+        if d["op"] == "compress":
+            tk = srv.submit("compress", A=src[:d["rows"], :d["cols"]], pinned=True)
+        elif d["op"] == "add":
+            tk = srv.submit("add", a=ha, b=hb)
+        elif d["op"] == "scale":
+            tk = srv.submit("scale", a=ha, c=d["c"])
+        elif d["op"] == "dot":
+            tk = srv.submit("dot", a=ha, b=hb, out=dots[i:i + 1], pinned=True)
+        else:
+            m = d["m"]
+            need = r * m
+            if off + need > arena.size:
+                off = 0
+            for lo_hi, tk_old in list(busy.items()):       # the region must be free again
+                if lo_hi[0] < off + need and off < lo_hi[1]:
+                    srv.wait(tk_old)
+                    waited.add(tk_old)
+                    del busy[lo_hi]
+            out = arena[off:off + need].reshape(r, m)
+            tk = srv.submit("matmul", a=ha, B=bsrc[:c, :m], out=out, pinned=True)
+            busy[(off, off + need)] = tk
+            off += need
+        tickets.append(tk)
+    for tk in tickets:
+        if tk not in waited:
+            srv.wait(tk)
+    elapsed = time.perf_counter() - t0
+    st = srv.stats()
+    srv.destroy()
+    n = len(reqs)
+    return {"requests": n, "offered_rps": n / seconds, "throughput_rps": n / elapsed, "p50_ms": st["p50_us"] / 1e3,
+            "p99_ms": st["p99_us"] / 1e3, "launches": st["launches"] - warm["launches"],
+            "mean_batch": st["mean_batch"], "peak_device_gb": st["peak_bytes"] / 1e9, "matmul_mode": mode,
+            "max_batch": max_batch, "streams": streams}
+
+
+def serve_line(args):
+    import torch
+
+    import workloads as W
+    from paper_2202_13007_gb300 import blaz as B
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    B.lib()
+    with ClockSampler(0) as clk:
+        batched = run_serve(args, B, W, torch, dev, args.serve_seconds, max_batch=0, streams=4, mode="split_bf16")
+        single = run_serve(args, B, W, torch, dev, args.serve_seconds, max_batch=1, streams=1, mode="split_bf16")
+    line = {"metric": METRIC + " [serve]", "value": batched["throughput_rps"], "unit": "req/s", "n_gpus": 1,
+            "steps": 1, "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "served Poisson stream 5k req/s, sides log-uniform multiples of 8 in [64,4096], "
+                                   "mix 40/30/15/10/5 % compress/add/scale/dot/matmul, 40 GB admission budget",
+                       "seconds": args.serve_seconds},
+            "serve": batched, "one_request_per_launch": single, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
+def batch_line(args):
+    """2000 mixed ops (sides log-uniform over multiples of 8 in [64, 2048]) as
+    one autotuned, graph-captured persistent launch, against the same ops
+    launched one by one through the single-op entry points."""
+    import torch
+
+    import workloads as W
+    from paper_2202_13007_gb300 import blaz as B
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    B.lib()
+    specs = W.batch_ops(count=2000, seed=11)
+    ops, singles = [], []
+    byts = 0
+    for d in specs:
+        r, c, seed = d["rows"], d["cols"], d["seed"]
+        X = W.bump_field_torch(c, seed, dev, rows=r)
+        nb = (r // 8) * (c // 8)
+        if d["op"] == "compress":
+            out = B.CMat.empty(r, c)
+            ops.append({"op": "compress", "A": X, "out": out})
+            singles.append(lambda X=X, out=out: B.compress(X, out=out))
+            byts += 557 * nb
+        elif d["op"] == "add":
+            a, b = B.compress(X), B.compress(W.bump_field_torch(c, seed + 1, dev, rows=r))
+            out = B.CMat.empty(r, c)
+            ops.append({"op": "add", "a": a, "b": b, "out": out})
+            singles.append(lambda a=a, b=b, out=out: B.add(a, b, out=out))
+            byts += 135 * nb
+        elif d["op"] == "scale":
+            a = B.compress(X)
+            out = B.CMat.empty(r, c)
+            ops.append({"op": "scale", "a": a, "c": d["c"], "out": out})
+            singles.append(lambda a=a, cc=d["c"], out=out: B.scale(a, cc, out=out))
+            byts += 90 * nb
+        elif d["op"] == "dot":
+            a, b = B.compress(X), B.compress(W.bump_field_torch(c, seed + 1, dev, rows=r))
+            res = torch.empty(1, dtype=torch.float64, device=dev)
+            ops.append({"op": "dot", "a": a, "b": b, "result": res})
+            singles.append(lambda a=a, b=b, res=res: B.dot(a, b, out=res[0]))
+            byts += 90 * nb
+        else:
+            a = B.compress(X)
+            Bd = torch.randn((c, d["m"]), dtype=torch.float64, device=dev)
+            C = torch.empty((r, d["m"]), dtype=torch.float64, device=dev)
+            ops.append({"op": "matmul", "a": a, "B": Bd, "C": C})
+            singles.append(lambda a=a, Bd=Bd, C=C: B.matmul(a, Bd, mode="fp64", out=C))
+            byts += 45 * nb + 8 * c * d["m"] + 8 * r * d["m"]
+    torch.cuda.synchronize()
+    t_plan = time.perf_counter()
+    plan = B.Batch(ops, autotune=True)
+    t_plan = time.perf_counter() - t_plan
+    info = plan.info()
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    with ClockSampler(0) as clk:
+        ms_batch = timed(plan.run, max(3, args.steps))
+        ms_single = timed(lambda: [f() for f in singles], 2)
+    plan.free()
+    line = {"metric": METRIC + " [batch]", "value": len(specs) / (ms_batch * 1e-3), "unit": "ops/s", "n_gpus": 1,
+            "steps": max(3, args.steps), "warmup": 1, "ms_per_step": ms_batch, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "2000 mixed ops, sides log-uniform multiples of 8 in [64,2048], mix 40/30/15/10/5 % "
+                                   "compress/add/scale/dot/matmul (FP64 DMMA products), one persistent graph launch",
+                       "autotuned": {"blocks_per_item": info["blocks_per_item"], "ctas_per_sm": info["ctas_per_sm"]},
+                       "plan_seconds": t_plan},
+            "gb_per_s": byts / (ms_batch * 1e-3) / 1e9, "one_op_per_launch_ms": ms_single,
+            "speedup_vs_one_op_per_launch": ms_single / ms_batch, "items": info["items"],
+            "gpu_launches": max(3, args.steps), "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -226,6 +436,12 @@ def main():
 
     if args.impl == "reference":
         reference_arm(args, rank, world)
+        return
+    if args.workload == "serve":
+        serve_line(args)
+        return
+    if args.workload == "batch":
+        batch_line(args)
         return
 
     import torch
@@ -340,6 +556,15 @@ def main():
         e2e = {"value": world * step_bytes(n) * args.steps / (ems * 1e-3) / 1e9, "unit": "GB/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ems / args.steps}
 
+    extras = None
+    if rank == 0 and not args.no_extras:
+        del dec
+        torch.cuda.empty_cache()
+        extras = {"matmul": matmul_extras(B, W, torch, dev)}
+        srv = run_serve(args, B, W, torch, dev, 1.0, max_batch=0, streams=4, mode="split_bf16")
+        extras["serve"] = {k: srv[k] for k in ("p50_ms", "p99_ms", "throughput_rps", "offered_rps", "mean_batch")}
+        extras["serve"]["config"] = "1 s of the served Poisson stream (5k req/s); full line: --workload serve"
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(n)
@@ -361,6 +586,8 @@ def main():
             "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps,
             "cpu_baseline": cpu,
+            "matmul_tflops": extras["matmul"] if extras else None,
+            "serve": extras["serve"] if extras else None,
         }
         print(json.dumps(line), flush=True)
     if dist:

@@ -243,6 +243,10 @@ int blaz_batch_free(blaz_plan *plan);
  * slots and memory free up and their work overlaps on the device.  Every
  * result equals the single-operation entry points' result (same kernels). */
 enum { BLAZ_REQ_RELEASE = 7 };  /* request kinds: BLAZ_OP_* above, plus RELEASE */
+/* Request flag: every host buffer of the request is page-locked (pinned) and
+ * stays valid and unmodified until the request completes; the server then
+ * copies straight between it and the device instead of staging a copy. */
+enum { BLAZ_REQ_PINNED = 1 };
 
 typedef struct blaz_server_cfg {
     int64_t budget_bytes;   /* device bytes for resident matrices + in-flight work  */
@@ -250,6 +254,8 @@ typedef struct blaz_server_cfg {
     int32_t max_batch;      /* requests per launch (0: 512; 1 = one per launch)      */
     int32_t max_wait_us;    /* longest a ready request waits for company (0: 100)   */
     int32_t queue_capacity; /* submitted-but-unadmitted requests (0: 65536)          */
+    int32_t matmul_mode;    /* BLAZ_MM_FP64 (DMMA inside the batch launch) or
+                               BLAZ_MM_SPLIT_BF16 (tcgen05 launch after the batch)   */
 } blaz_server_cfg;
 
 typedef struct blaz_request {
@@ -267,6 +273,7 @@ typedef struct blaz_request {
                                server before the request reports completion; must
                                stay valid until then.                             */
     int64_t ldo;
+    int32_t flags;          /* BLAZ_REQ_PINNED or 0                                  */
 } blaz_request;
 
 typedef struct blaz_result {

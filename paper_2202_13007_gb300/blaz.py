@@ -58,7 +58,8 @@ REQ_RELEASE = 7
 
 class _ServerCfg(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_int64), ("streams", ctypes.c_int32), ("max_batch", ctypes.c_int32),
-                ("max_wait_us", ctypes.c_int32), ("queue_capacity", ctypes.c_int32)]
+                ("max_wait_us", ctypes.c_int32), ("queue_capacity", ctypes.c_int32),
+                ("matmul_mode", ctypes.c_int32)]
 
 
 class _Request(ctypes.Structure):
@@ -66,7 +67,7 @@ class _Request(ctypes.Structure):
                 ("host_A", ctypes.c_void_p), ("lda", ctypes.c_int64), ("a", ctypes.c_uint64),
                 ("b", ctypes.c_uint64), ("c", ctypes.c_double), ("host_B", ctypes.c_void_p),
                 ("ldb", ctypes.c_int64), ("m", ctypes.c_int64), ("host_out", ctypes.c_void_p),
-                ("ldo", ctypes.c_int64)]
+                ("ldo", ctypes.c_int64), ("flags", ctypes.c_int32)]
 
 
 class _Result(ctypes.Structure):
@@ -364,16 +365,20 @@ class Server:
     _KIND = dict(Batch._KIND, release=REQ_RELEASE)
 
     def __init__(self, budget_bytes: int, streams: int = 0, max_batch: int = 0, max_wait_us: int = 0,
-                 queue_capacity: int = 0):
-        cfg = _ServerCfg(int(budget_bytes), streams, max_batch, max_wait_us, queue_capacity)
+                 queue_capacity: int = 0, matmul_mode: str = "fp64"):
+        cfg = _ServerCfg(int(budget_bytes), streams, max_batch, max_wait_us, queue_capacity, _MODES[matmul_mode])
         h = ctypes.c_void_p()
         _check(lib().blaz_server_create(ctypes.byref(cfg), ctypes.byref(h)), "blaz_server_create")
         self._h = h
 
-    def submit(self, op: str, *, A=None, a: int = 0, b: int = 0, c: float = 0.0, B=None, out=None) -> int:
+    def submit(self, op: str, *, A=None, a: int = 0, b: int = 0, c: float = 0.0, B=None, out=None,
+               pinned: bool = False) -> int:
+        """Queue a request; with pinned=True every host array passed is page-locked
+        and must stay valid and unmodified until the request completes."""
         import numpy as np
 
         r = _Request()
+        r.flags = 1 if pinned else 0
         r.kind = self._KIND[op]
         if A is not None:
             assert A.dtype == np.float64 and A.ndim == 2 and A.strides[1] == 8

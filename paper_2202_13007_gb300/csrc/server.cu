@@ -92,8 +92,10 @@ struct Ticket {
     int status = 1;          // 1 pending
     uint64_t handle = 0;     // output handle (allocated at submit)
     double value = 0.0;
-    void *in_stage = nullptr;  // pinned copy of host_A or host_B
+    void *in_stage = nullptr;  // pinned copy of host_A or host_B (or the caller's pinned buffer)
     size_t in_cls = 0, in_bytes = 0;
+    int64_t in_rows = 0, in_cols = 0, in_ld = 0;  // host layout of in_stage
+    bool pinned = false;       // BLAZ_REQ_PINNED: no staging copies
     size_t need = 0;         // working bytes while in flight (excludes the resident output)
     size_t out_res_bytes = 0;
 };
@@ -106,6 +108,7 @@ struct Launch {
     void *out_stage = nullptr;
     size_t out_cls = 0;
     std::vector<size_t> out_off;  // offset of each ticket's output in out_stage
+    std::vector<size_t> split_off; // split-bf16 products: decompressed operand and slice scratch
     void *desc_stage = nullptr;
     size_t desc_cls = 0;
     cudaEvent_t done = nullptr;
@@ -202,6 +205,7 @@ int request_needs(blaz_server *s, const blaz_request &r, size_t &need, size_t &o
         if (n && r.m && (!r.host_out || (k && !r.host_B))) return BLAZ_ERR_NULL;
         if (n && r.m && (r.ldo < r.m || (k && r.ldb < r.m))) return BLAZ_ERR_LD;
         need = up256((size_t)(k * r.m) * 8) + up256((size_t)(n * r.m) * 8) + up256((size_t)(n * k) * 8);
+        if (s->cfg.matmul_mode == BLAZ_MM_SPLIT_BF16) need += up256(split_bf16_scratch_bytes(n, k, r.m));
         return BLAZ_OK;
     }
     case BLAZ_REQ_RELEASE:
@@ -216,10 +220,8 @@ void finish_ticket(blaz_server *s, Ticket *t, int status)
 {
     t->status = status;
     t->t_done = Clock::now();
-    if (t->in_stage) {
-        s->pinned.put(t->in_stage, t->in_cls);
-        t->in_stage = nullptr;
-    }
+    if (t->in_stage && !t->pinned) s->pinned.put(t->in_stage, t->in_cls);
+    t->in_stage = nullptr;
     if (status == BLAZ_OK) {
         s->completed++;
         s->latencies.push_back(std::chrono::duration<double, std::micro>(t->t_done - t->t_submit).count());
@@ -253,9 +255,13 @@ void complete_launch(blaz_server *s, Launch *L)
         const blaz_request &r = t->req;
         const char *out = (const char *)L->out_stage + L->out_off[i];
         if (r.kind == BLAZ_OP_DOT) {
-            std::memcpy(&t->value, out, sizeof(double));
-            if (r.host_out) *r.host_out = t->value;
-        } else if (r.kind == BLAZ_OP_DECOMPRESS || r.kind == BLAZ_OP_MATMUL) {
+            if (t->pinned) {
+                t->value = *r.host_out;
+            } else {
+                std::memcpy(&t->value, out, sizeof(double));
+                if (r.host_out) *r.host_out = t->value;
+            }
+        } else if ((r.kind == BLAZ_OP_DECOMPRESS || r.kind == BLAZ_OP_MATMUL) && !t->pinned) {
             const blaz_cmat &a = s->residents[r.a].m;
             const int64_t rows = a.rows, cols = r.kind == BLAZ_OP_MATMUL ? r.m : a.cols;
             for (int64_t q = 0; q < rows; ++q)
@@ -318,8 +324,18 @@ int launch_impl(blaz_server *s, int slot, std::vector<Ticket *> &adm, Launch *L)
         dev_out_off[i] = work;
         work += up256(ob);
         L->out_off[i] = out_host;
-        out_host += up256(ob);
+        if (!adm[i]->pinned) out_host += up256(ob);
     }
+    // Split-bf16 products: decompressed operand + slices, after the batch launch.
+    const bool split = s->cfg.matmul_mode == BLAZ_MM_SPLIT_BF16;
+    L->split_off.assign(adm.size(), 0);
+    if (split)
+        for (size_t i = 0; i < adm.size(); ++i)
+            if (adm[i]->req.kind == BLAZ_OP_MATMUL) {
+                const blaz_cmat &a = s->residents[adm[i]->req.a].m;
+                L->split_off[i] = work;
+                work += up256((size_t)(a.rows * a.cols) * 8) + up256(split_bf16_scratch_bytes(a.rows, a.cols, adm[i]->req.m));
+            }
     // Resident outputs: allocate their storage now.
     std::vector<blaz_op> ops;
     ops.reserve(adm.size());
@@ -397,6 +413,13 @@ int launch_impl(blaz_server *s, int slot, std::vector<Ticket *> &adm, Launch *L)
         if (r.kind == BLAZ_OP_DOT) ops[i].result = (double *)(W + dev_out_off[i]);
         if (r.kind == BLAZ_OP_DECOMPRESS || r.kind == BLAZ_OP_MATMUL) ops[i].C = (double *)(W + dev_out_off[i]);
     }
+    if (split)
+        for (size_t i = 0; i < adm.size(); ++i)
+            if (adm[i]->req.kind == BLAZ_OP_MATMUL) {
+                ops[i].kind = BLAZ_OP_DECOMPRESS;
+                ops[i].C = (double *)(W + L->split_off[i]);
+                ops[i].ldc = ops[i].a.cols;
+            }
     batch::build_work(ops.data(), (int)ops.size(), bpi, W + off_scratch, dops, items, partials, scratch, ngemm);
     const size_t desc_bytes = sizeof(batch::DevOp) * dops.size() + sizeof(batch::Item) * items.size();
     L->desc_stage = s->pinned.get(std::max<size_t>(desc_bytes, 1), L->desc_cls);
@@ -406,9 +429,12 @@ int launch_impl(blaz_server *s, int slot, std::vector<Ticket *> &adm, Launch *L)
     std::memcpy((char *)L->desc_stage + sizeof(batch::DevOp) * dops.size(), items.data(),
                 sizeof(batch::Item) * items.size());
     // Host -> device: inputs, descriptors; zero the counters.
-    for (size_t i = 0; i < adm.size(); ++i)
-        if (adm[i]->in_stage && adm[i]->in_bytes)
-            cudaMemcpyAsync(W + in_off[i], adm[i]->in_stage, adm[i]->in_bytes, cudaMemcpyHostToDevice, st);
+    for (size_t i = 0; i < adm.size(); ++i) {
+        const Ticket *t = adm[i];
+        if (t->in_stage && t->in_bytes)
+            cudaMemcpy2DAsync(W + in_off[i], (size_t)t->in_cols * 8, t->in_stage, (size_t)t->in_ld * 8,
+                              (size_t)t->in_cols * 8, (size_t)t->in_rows, cudaMemcpyHostToDevice, st);
+    }
     if (!dops.empty())
         cudaMemcpyAsync(W + off_ops, L->desc_stage, sizeof(batch::DevOp) * dops.size(), cudaMemcpyHostToDevice, st);
     if (!items.empty())
@@ -419,6 +445,17 @@ int launch_impl(blaz_server *s, int slot, std::vector<Ticket *> &adm, Launch *L)
     int rc = batch::launch((batch::DevOp *)(W + off_ops), (batch::Item *)(W + off_items), (int)items.size(),
                            (unsigned *)(W + off_cnt), (double *)(W + off_part), grid, st);
     if (rc) return rc;
+    if (split)
+        for (size_t i = 0; i < adm.size(); ++i)
+            if (adm[i]->req.kind == BLAZ_OP_MATMUL) {
+                const blaz_request &r = adm[i]->req;
+                const int64_t n = ops[i].a.rows, k = ops[i].a.cols;
+                double *Ah = (double *)(W + L->split_off[i]);
+                char *sl = W + L->split_off[i] + up256((size_t)(n * k) * 8);
+                if ((rc = launch_matmul_split_bf16(Ah, k, (const double *)(W + in_off[i]), r.m,
+                                                   (double *)(W + dev_out_off[i]), r.m, n, k, r.m, sl, st)))
+                    return rc;
+            }
     // Device -> host: results.
     for (size_t i = 0; i < adm.size(); ++i) {
         const blaz_request &r = adm[i]->req;
@@ -426,7 +463,16 @@ int launch_impl(blaz_server *s, int slot, std::vector<Ticket *> &adm, Launch *L)
         if (r.kind == BLAZ_OP_DOT) ob = 8;
         if (r.kind == BLAZ_OP_DECOMPRESS) ob = (size_t)(ops[i].a.rows * ops[i].a.cols) * 8;
         if (r.kind == BLAZ_OP_MATMUL) ob = (size_t)(ops[i].a.rows * r.m) * 8;
-        if (ob) cudaMemcpyAsync((char *)L->out_stage + L->out_off[i], W + dev_out_off[i], ob, cudaMemcpyDeviceToHost, st);
+        if (!ob) continue;
+        if (adm[i]->pinned) {
+            const int64_t rows = r.kind == BLAZ_OP_DOT ? 1 : ops[i].a.rows;
+            const int64_t cols = r.kind == BLAZ_OP_DOT ? 1 : (r.kind == BLAZ_OP_MATMUL ? r.m : ops[i].a.cols);
+            const int64_t ldo = r.kind == BLAZ_OP_DOT ? 1 : r.ldo;
+            cudaMemcpy2DAsync(r.host_out, (size_t)ldo * 8, W + dev_out_off[i], (size_t)cols * 8, (size_t)cols * 8,
+                              (size_t)rows, cudaMemcpyDeviceToHost, st);
+        } else {
+            cudaMemcpyAsync((char *)L->out_stage + L->out_off[i], W + dev_out_off[i], ob, cudaMemcpyDeviceToHost, st);
+        }
     }
     cudaEventCreateWithFlags(&L->done, cudaEventDisableTiming);
     cudaEventRecord(L->done, st);
@@ -554,7 +600,7 @@ int blaz_server_create(const blaz_server_cfg *cfg, blaz_server **out)
 {
     if (!cfg || !out) return BLAZ_ERR_NULL;
     if (cfg->budget_bytes <= 0 || cfg->streams < 0 || cfg->max_batch < 0 || cfg->max_wait_us < 0 ||
-        cfg->queue_capacity < 0)
+        cfg->queue_capacity < 0 || (cfg->matmul_mode != BLAZ_MM_FP64 && cfg->matmul_mode != BLAZ_MM_SPLIT_BF16))
         return BLAZ_ERR_ARG;
     blaz_server *s = new blaz_server();
     s->cfg = *cfg;
@@ -632,8 +678,18 @@ int blaz_server_submit(blaz_server *s, const blaz_request *req, uint64_t *ticket
             s->residents[t->handle] = R;
         }
     }
-    if (src && rows * cols > 0) {
+    t->pinned = (r.flags & BLAZ_REQ_PINNED) != 0;
+    if (src && rows * cols > 0 && t->pinned) {
         t->in_bytes = (size_t)(rows * cols) * 8;
+        t->in_stage = const_cast<double *>(src);
+        t->in_rows = rows;
+        t->in_cols = cols;
+        t->in_ld = ld;
+    } else if (src && rows * cols > 0) {
+        t->in_bytes = (size_t)(rows * cols) * 8;
+        t->in_rows = rows;
+        t->in_cols = cols;
+        t->in_ld = cols;
         t->in_stage = s->pinned.get(t->in_bytes, t->in_cls);
         if (!t->in_stage) {
             std::lock_guard<std::mutex> lk(s->mu);

@@ -199,3 +199,30 @@ def test_continuous_batching_versus_one_request_per_launch(B):
           f"{batched['throughput_rps']:.0f} req/s mean batch {batched['mean_batch']:.1f}; "
           f"one per launch: p50 {single['p50_us']:.0f} us p99 {single['p99_us']:.0f} us "
           f"{single['throughput_rps']:.0f} req/s")
+
+
+def test_pinned_requests_and_split_bf16_products(B):
+    """Page-locked host buffers are used in place; split-bf16 products in the
+    server equal the single-op split-bf16 product."""
+    srv = B.Server(budget_bytes=2 << 30, streams=2, matmul_mode="split_bf16")
+    src = torch.empty((256, 512), dtype=torch.float64, pin_memory=True)
+    src.copy_(torch.from_numpy(W.bump_field(512, 9, rows=256)))
+    X = src.numpy()
+    h = srv.wait(srv.submit("compress", A=X[:128, 8:264], pinned=True))["handle"]   # strided view
+    alone = B.compress(torch.from_numpy(np.ascontiguousarray(X[:128, 8:264])).cuda())
+    same_cmat(srv.cmat(h), alone)
+    Bm = torch.empty((256, 40), dtype=torch.float64, pin_memory=True)
+    Bm.copy_(torch.randn(256, 40, dtype=torch.float64))
+    out = torch.full((128, 40), np.nan, dtype=torch.float64, pin_memory=True)
+    dot = torch.full((1,), np.nan, dtype=torch.float64, pin_memory=True)
+    t1 = srv.submit("matmul", a=h, B=Bm.numpy(), out=out.numpy(), pinned=True)
+    t2 = srv.submit("dot", a=h, b=h, out=dot.numpy(), pinned=True)
+    assert srv.wait(t1)["status"] == 0
+    r2 = srv.wait(t2)
+    assert r2["status"] == 0 and r2["value"] == float(dot[0])
+    want = B.matmul(alone, Bm.cuda(), mode="split_bf16").cpu()
+    bound = B.decompress(alone).abs().cpu() @ Bm.abs()
+    assert torch.all((out - want).abs() <= 1e-6 * bound + 1e-300)
+    assert abs(float(dot[0]) - float(B.dot(alone, alone).item())) <= 1e-12 * float(
+        (B.decompress(alone) ** 2).sum())
+    srv.destroy()
