@@ -183,7 +183,10 @@ int blaz_compress(const double *A, int64_t lda, blaz_cmat *out, void *stream)
     if (nblocks(out) == 0) return BLAZ_OK;
     if (!A) return BLAZ_ERR_NULL;
     if (lda < out->cols) return BLAZ_ERR_LD;
-    return launch_compress(A, lda, out, (cudaStream_t)stream);
+    cudaStream_t st = (cudaStream_t)stream;
+    Scratch ws(st);
+    if ((rc = ws.alloc(compress_scratch_bytes(nblocks(out))))) return rc;
+    return launch_compress(A, lda, out, ws.p, st);
 }
 
 int blaz_decompress(const blaz_cmat *a, double *A, int64_t lda, void *stream)

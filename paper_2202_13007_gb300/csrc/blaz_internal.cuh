@@ -80,7 +80,8 @@ int validate_cmat(const blaz_cmat *m);   // shape, NULL and alignment checks of 
 int batch_device_status();           // reads and clears the batch kernel's status word
 
 // ---- launchers (one per kernel family) ------------------------------------------
-int launch_compress(const double *A, int64_t lda, const blaz_cmat *out, cudaStream_t st);
+size_t compress_scratch_bytes(int64_t nb);
+int launch_compress(const double *A, int64_t lda, const blaz_cmat *out, void *scratch, cudaStream_t st);
 int launch_decompress(const blaz_cmat *a, double *A, int64_t lda, cudaStream_t st);
 int launch_add(const blaz_cmat *a, const blaz_cmat *b, const blaz_cmat *out, bool subtract, cudaStream_t st);
 int launch_scale(const blaz_cmat *a, double c, const blaz_cmat *out, cudaStream_t st);

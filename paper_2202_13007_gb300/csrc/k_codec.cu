@@ -3,17 +3,59 @@
 //
 // Compression is bit-exact binary64: every operation is an explicit
 // round-to-nearest intrinsic in the order fixed in include/blaz.h, so the
-// result does not depend on -fmad or on the compiler's scheduling.
-#include "block_codec.cuh"
+// result does not depend on -fmad or on the compiler's scheduling.  The
+// compressor runs in two kernels: k_compress_fast decides every block it can
+// certify (compress_fast.cuh) and lists the others; k_compress_fix
+// recompresses the listed blocks with the exact binary64 path, densely (one
+// listed block per thread), so the rare exact blocks cost no warp divergence.
+#include "compress_fast.cuh"
 
 namespace blaz {
 
 template <bool kVec>
-__global__ void __launch_bounds__(128) k_compress(const double *__restrict__ A, int64_t lda, int64_t nbc, int64_t nb,
-                                                  double *__restrict__ f, double *__restrict__ s,
-                                                  uint8_t *__restrict__ phi, int8_t *__restrict__ code)
+__global__ void __launch_bounds__(128)
+    k_compress_fast(const double *__restrict__ A, int64_t lda, int64_t nbc, int64_t nb, double *__restrict__ f,
+                    double *__restrict__ s, uint8_t *__restrict__ phi, int8_t *__restrict__ code,
+                    unsigned *__restrict__ fix_list, unsigned *__restrict__ fix_count)
 {
     for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t bi = b / nbc, bj = b - (b / nbc) * nbc;
+        double d[64];
+        load_block<kVec>(A, lda, bi, bj, d);
+        f[b] = d[0];
+        double sv;
+        uint8_t ph;
+        int8_t c[kKeep];
+        const bool ok = compress_block_fast(d, sv, ph, c);
+        s[b] = sv;
+        if (ok) {
+            phi[b] = ph;
+            store_codes(code + b * kKeep, c);
+        }
+        // Append the blocks left undecided, one atomic per warp.
+        const unsigned act = __activemask();
+        const unsigned need = __ballot_sync(act, !ok);
+        if (need) {
+            const int lane = threadIdx.x & 31;
+            const int leader = __ffs(need) - 1;
+            unsigned base = 0;
+            if (lane == leader) base = atomicAdd(fix_count, (unsigned)__popc(need));
+            base = __shfl_sync(act, base, leader);
+            if (!ok) fix_list[base + __popc(need & ((1u << lane) - 1u))] = (unsigned)b;
+        }
+    }
+}
+
+// The exact binary64 compressor (compress_block) on the listed blocks.
+template <bool kVec>
+__global__ void __launch_bounds__(128)
+    k_compress_fix(const double *__restrict__ A, int64_t lda, int64_t nbc, const unsigned *__restrict__ fix_list,
+                   const unsigned *__restrict__ fix_count, double *__restrict__ f, double *__restrict__ s,
+                   uint8_t *__restrict__ phi, int8_t *__restrict__ code)
+{
+    const int64_t n = *fix_count;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = fix_list[q];
         const int64_t bi = b / nbc, bj = b - (b / nbc) * nbc;
         double d[64];
         load_block<kVec>(A, lda, bi, bj, d);
@@ -65,16 +107,27 @@ static int grid_for(int64_t nb, int threads)
 
 static bool vec_ok(const void *p, int64_t ld) { return ((uintptr_t)p % 16 == 0) && (ld % 2 == 0); }
 
-int launch_compress(const double *A, int64_t lda, const blaz_cmat *out, cudaStream_t st)
+size_t compress_scratch_bytes(int64_t nb) { return ((size_t)nb * 4 + 255) / 256 * 256 + 256; }
+
+int launch_compress(const double *A, int64_t lda, const blaz_cmat *out, void *scratch, cudaStream_t st)
 {
     const int64_t nbc = out->cols / 8, nb = (out->rows / 8) * nbc;
     if (nb == 0) return BLAZ_OK;
+    if (nb > 0xFFFFFFFFll) return BLAZ_ERR_SHAPE;
+    unsigned *list = (unsigned *)scratch;
+    unsigned *count = (unsigned *)((char *)scratch + compress_scratch_bytes(nb) - 256);
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return set_cuda_error(e);
     const int threads = 128;
     const int grid = grid_for(nb, threads);
-    if (vec_ok(A, lda))
-        k_compress<true><<<grid, threads, 0, st>>>(A, lda, nbc, nb, out->f, out->s, out->phi, out->code);
-    else
-        k_compress<false><<<grid, threads, 0, st>>>(A, lda, nbc, nb, out->f, out->s, out->phi, out->code);
+    const int fix_grid = num_sms() * 4;
+    if (vec_ok(A, lda)) {
+        k_compress_fast<true><<<grid, threads, 0, st>>>(A, lda, nbc, nb, out->f, out->s, out->phi, out->code, list, count);
+        k_compress_fix<true><<<fix_grid, threads, 0, st>>>(A, lda, nbc, list, count, out->f, out->s, out->phi, out->code);
+    } else {
+        k_compress_fast<false><<<grid, threads, 0, st>>>(A, lda, nbc, nb, out->f, out->s, out->phi, out->code, list, count);
+        k_compress_fix<false><<<fix_grid, threads, 0, st>>>(A, lda, nbc, list, count, out->f, out->s, out->phi, out->code);
+    }
     return launch_status();
 }
 
