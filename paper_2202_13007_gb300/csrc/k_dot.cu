@@ -2,8 +2,21 @@
 // "Compressed Matrix Computations", arXiv 2202.13007):
 //   * the flattened product <vec A_hat, vec B_hat> of two same-shape matrices;
 //   * Algorithm 3 (Eqs. eqbbb0, eqbbb): line i of A_hat times column j of B_hat.
-// Both partly decompress the blocks they touch.  Reductions follow a fixed
-// tree, so results are bitwise reproducible run to run.
+// Reductions follow a fixed tree, so results are bitwise reproducible run to
+// run.
+//
+// The flattened product never decompresses.  Decompression is linear in the
+// codes: a block is A_hat = f 1 + t G c with t = s/phi and G the fixed 64 x 28
+// map from codes to the block (inverse DCT of the kept coefficients followed
+// by the inverse of Eq. eqnorm).  Hence, per block,
+//     <A_hat, B_hat> = 64 fa fb + fa tb w.cb + fb ta w.ca + ta tb ca^T H cb,
+// with w = G^T 1 and H = G^T G.  H and w are split into five fixed-point
+// slices of 11 bits (integer digits times powers of two); with integer codes
+// every slice product sum is an integer below 2^23, exact in fp32, and only
+// the final combination is rounded (binary64).
+#include <cmath>
+#include <mutex>
+
 #include "block_codec.cuh"
 
 namespace blaz {
@@ -25,26 +38,109 @@ __device__ __forceinline__ double cta_sum(double v, double *red)
     return r;  // valid in thread 0
 }
 
+// Fixed-point slices of w and H (computed once on the host in long double).
+constexpr int kSlices = 5;
+struct GramConsts {
+    float H[kSlices][kKeep][kKeep];  // integer digits, |digit| <= 2^10
+    float w[kSlices][kKeep];
+    double scaleH[kSlices], scaleW[kSlices];
+    double inv_phi[256];             // 1/phi
+};
+
+// Exact conversion of an integer-valued float with |x| < 2^24 to int.
+__device__ __forceinline__ int f2i_exact(float x) { return __float2int_rn(x); }
+
+// Exact int64 -> binary64 for |v| < 2^53 without the FP64 conversion unit.
+__device__ __forceinline__ double i64_to_double(long long v)
+{
+    if (v == 0) return 0.0;
+    const unsigned long long sign = v < 0 ? 0x8000000000000000ull : 0ull;
+    const unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
+    const int e = 63 - __clzll((long long)a);                 // position of the leading one, <= 52
+    const unsigned long long mant = (a << (52 - e)) & 0x000FFFFFFFFFFFFFull;
+    return __longlong_as_double((long long)(sign | ((unsigned long long)(e + 1023) << 52) | mant));
+}
+
+// sum_s scale[s] * (hi_s * 4096 + lo_s), the slices combined in binary64.
+__device__ __forceinline__ double combine(const float (&hi)[kSlices], const float (&lo)[kSlices],
+                                          const double (&scale)[kSlices], float hi_mult)
+{
+    double r = 0.0;
+#pragma unroll
+    for (int s = 0; s < kSlices; ++s) {
+        const long long v = (long long)f2i_exact(hi[s]) * (long long)hi_mult + (long long)f2i_exact(lo[s]);
+        r = fma(scale[s], i64_to_double(v), r);
+    }
+    return r;
+}
+
+__device__ __forceinline__ void codes_to_float(const int8_t *__restrict__ src, float (&x)[kKeep])
+{
+    const uint32_t *w = reinterpret_cast<const uint32_t *>(src);
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+        const uint32_t v = __ldg(w + q);
+#pragma unroll
+        for (int b = 0; b < 4; ++b) x[4 * q + b] = (float)(int)(int8_t)(uint8_t)(v >> (8 * b));
+    }
+}
+
+// <A_hat_b, B_hat_b> of block b from the codes (see the file comment).
+__device__ __forceinline__ double block_dot_gram(const GramConsts &g, double fa, double sa, int pa,
+                                                 const int8_t *__restrict__ ca, double fb, double sb, int pb,
+                                                 const int8_t *__restrict__ cb)
+{
+    float xa[kKeep], xb[kKeep];
+    codes_to_float(ca, xa);
+    codes_to_float(cb, xb);
+    float wa[kSlices], wb[kSlices], zero[kSlices];
+    float qh[kSlices], ql[kSlices];
+#pragma unroll
+    for (int s = 0; s < kSlices; ++s) {
+        float pa_ = 0.0f, pb_ = 0.0f;
+#pragma unroll
+        for (int t = 0; t < kKeep; ++t) {
+            pa_ = fmaf(g.w[s][t], xa[t], pa_);
+            pb_ = fmaf(g.w[s][t], xb[t], pb_);
+        }
+        wa[s] = pa_;
+        wb[s] = pb_;
+        zero[s] = 0.0f;
+        float h = 0.0f, l = 0.0f;
+#pragma unroll
+        for (int k = 0; k < kKeep; ++k) {
+            float y = 0.0f;
+#pragma unroll
+            for (int j = 0; j < kKeep; ++j) y = fmaf(g.H[s][k][j], xb[j], y);
+            const float yh = rintf(y * (1.0f / 4096.0f));
+            const float yl = fmaf(-4096.0f, yh, y);
+            h = fmaf(xa[k], yh, h);
+            l = fmaf(xa[k], yl, l);
+        }
+        qh[s] = h;
+        ql[s] = l;
+    }
+    const double Wa = combine(zero, wa, g.scaleW, 0.0f);
+    const double Wb = combine(zero, wb, g.scaleW, 0.0f);
+    const double Q = combine(qh, ql, g.scaleH, 4096.0f);
+    const double ta = sa * g.inv_phi[pa], tb = sb * g.inv_phi[pb];
+    return 64.0 * fa * fb + fa * tb * Wb + fb * ta * Wa + ta * tb * Q;
+}
+
 // Flattened dot.  Every CTA writes its partial sum; the last CTA to finish
 // adds the partials in CTA order and resets the arrival counter.
 __global__ void __launch_bounds__(kDotThreads)
-    k_dot(int64_t nb, const double *__restrict__ fa, const double *__restrict__ sa, const uint8_t *__restrict__ pa,
-          const int8_t *__restrict__ ca, const double *__restrict__ fb, const double *__restrict__ sb,
-          const uint8_t *__restrict__ pb, const int8_t *__restrict__ cb, double *__restrict__ partials,
-          unsigned *__restrict__ counter, double *__restrict__ result)
+    k_dot(const __grid_constant__ GramConsts g, int64_t nb, const double *__restrict__ fa,
+          const double *__restrict__ sa, const uint8_t *__restrict__ pa, const int8_t *__restrict__ ca,
+          const double *__restrict__ fb, const double *__restrict__ sb, const uint8_t *__restrict__ pb,
+          const int8_t *__restrict__ cb, double *__restrict__ partials, unsigned *__restrict__ counter,
+          double *__restrict__ result)
 {
     __shared__ double red[kDotThreads / 32];
     __shared__ bool last;
     double acc = 0.0;
-    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x) {
-        double x[64], y[64];
-        decompress_block_at(fa[b], sa[b], pa[b], ca + b * kKeep, x);
-        decompress_block_at(fb[b], sb[b], pb[b], cb + b * kKeep, y);
-        double blk = 0.0;
-#pragma unroll
-        for (int p = 0; p < 64; ++p) blk = fma(x[p], y[p], blk);
-        acc += blk;
-    }
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x)
+        acc += block_dot_gram(g, fa[b], sa[b], pa[b], ca + b * kKeep, fb[b], sb[b], pb[b], cb + b * kKeep);
     const double tot = cta_sum(acc, red);
     if (threadIdx.x == 0) {
         partials[blockIdx.x] = tot;
@@ -62,6 +158,75 @@ __global__ void __launch_bounds__(kDotThreads)
         *result = r;
         *counter = 0u;
     }
+}
+
+// Host: G, w = G^T 1, H = G^T G in long double from the definitions, then the
+// fixed-point slices.
+static void slice(const long double *x, int n, float (*digits)[kKeep * kKeep], double *scale, int stride)
+{
+    long double mx = 0.0L;
+    for (int i = 0; i < n; ++i) mx = std::max(mx, fabsl(x[i]));
+    const int E = (mx > 0.0L ? (int)ceill(log2l(mx)) : 0) - 10;  // |x| / 2^E <= 2^10
+    long double r[kKeep * kKeep];
+    for (int i = 0; i < n; ++i) r[i] = x[i];
+    for (int s = 0; s < kSlices; ++s) {
+        const long double sc = ldexpl(1.0L, E - 11 * s);
+        for (int i = 0; i < n; ++i) {
+            const long double d = rintl(r[i] / sc);
+            digits[s][i * stride / stride] = (float)d;
+            r[i] -= d * sc;
+        }
+        scale[s] = (double)sc;
+    }
+}
+
+static const GramConsts &gram_consts()
+{
+    static GramConsts g;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        const long double pi = 3.14159265358979323846264338327950288L;
+        long double c[8][8];
+        for (int k = 0; k < 8; ++k)
+            for (int x = 0; x < 8; ++x) c[k][x] = cosl((long double)((2 * x + 1) * k) * pi / 16.0L);
+        const long double al[8] = {sqrtl(0.125L), 0.5L, 0.5L, 0.5L, 0.5L, 0.5L, 0.5L, 0.5L};
+        static long double G[64][kKeep];
+        for (int t = 0; t < kKeep; ++t) {
+            const int i = kept_row(t), j = kept_col(t);
+            long double B[8][8];
+            for (int u = 0; u < 8; ++u)
+                for (int v = 0; v < 8; ++v) {
+                    const long double P = al[i] * al[j] * c[i][u] * c[j][v];
+                    if (u == 0 && v == 0) B[u][v] = 0.0L;
+                    else if (u == 0) B[u][v] = B[u][v - 1] + P;
+                    else if (v == 0) B[u][v] = B[u - 1][v] + P;
+                    else B[u][v] = (B[u - 1][v] + B[u][v - 1]) * 0.5L + P;
+                    G[u * 8 + v][t] = B[u][v];
+                }
+        }
+        long double H[kKeep * kKeep], w[kKeep];
+        for (int k = 0; k < kKeep; ++k) {
+            w[k] = 0.0L;
+            for (int p = 0; p < 64; ++p) w[k] += G[p][k];
+            for (int l = 0; l < kKeep; ++l) {
+                long double acc = 0.0L;
+                for (int p = 0; p < 64; ++p) acc += G[p][k] * G[p][l];
+                H[k * kKeep + l] = acc;
+            }
+        }
+        float hd[kSlices][kKeep * kKeep], wd[kSlices][kKeep * kKeep];
+        slice(H, kKeep * kKeep, hd, g.scaleH, 1);
+        slice(w, kKeep, wd, g.scaleW, 1);
+        for (int s = 0; s < kSlices; ++s) {
+            for (int k = 0; k < kKeep; ++k) {
+                g.w[s][k] = wd[s][k];
+                for (int l = 0; l < kKeep; ++l) g.H[s][k][l] = hd[s][k * kKeep + l];
+            }
+        }
+        g.inv_phi[0] = 0.0;
+        for (int p = 1; p < 256; ++p) g.inv_phi[p] = 1.0 / (double)p;
+    });
+    return g;
 }
 
 // Algorithm 3 generalised to matrices: one CTA; thread t handles k-blocks
@@ -104,8 +269,8 @@ int launch_dot(const blaz_cmat *a, const blaz_cmat *b, double *result, double *p
     const int64_t nb = (a->rows / 8) * (a->cols / 8);
     int grid = dot_grid(nb);
     if (grid > max_ctas) grid = (int)max_ctas;
-    k_dot<<<grid, kDotThreads, 0, st>>>(nb, a->f, a->s, a->phi, a->code, b->f, b->s, b->phi, b->code, partials,
-                                        counter, result);
+    k_dot<<<grid, kDotThreads, 0, st>>>(gram_consts(), nb, a->f, a->s, a->phi, a->code, b->f, b->s, b->phi,
+                                        b->code, partials, counter, result);
     return launch_status();
 }
 
