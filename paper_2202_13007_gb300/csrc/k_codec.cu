@@ -8,7 +8,12 @@
 // certify (compress_fast.cuh) and lists the others; k_compress_fix
 // recompresses the listed blocks with the exact binary64 path, densely (one
 // listed block per thread), so the rare exact blocks cost no warp divergence.
+#include <mutex>
+
+#include <cuda_fp16.h>
+
 #include "compress_fast.cuh"
+#include "gmap.cuh"
 
 namespace blaz {
 
@@ -70,28 +75,142 @@ __global__ void __launch_bounds__(128)
     }
 }
 
-template <bool kVec>
-__global__ void __launch_bounds__(128) k_decompress(const double *__restrict__ f, const double *__restrict__ s,
-                                                    const uint8_t *__restrict__ phi,
-                                                    const int8_t *__restrict__ code, int64_t nbc, int64_t nb,
-                                                    double *__restrict__ A, int64_t lda)
+// ---------------------------------------------------------------------------------
+// Decompression as a product with the fixed map G (gmap.cuh): Y = C G^T for 16
+// blocks per warp on the tensor cores (mma.sync m16n8k16, fp16 inputs, fp32
+// accumulation).  G is split into four fixed-point slices of 11 bits whose
+// digits (|d| <= 2^10) and the codes (|c| <= 127) are exact in fp16; every
+// product sum is an integer below 2^22, exact in fp32.  The slices are
+// assembled in int64 and each output is one binary64 fma:
+//     out = f + (s / phi) 2^E Y,  Y = sum_s Y_s 2^(11 (3 - s)).
+// G is represented to 2^-43 of its largest entry, so outputs differ from the
+// binary64 evaluation of the definition by far less than 1e-12 of the block's
+// scale |f| + 14 |s| sum|c| / phi.
+constexpr int kDecSlices = 4;
+struct DecConsts {
+    uint2 bfrag[kDecSlices][2][8][32];  // B fragments [slice][k-step][n-tile][lane]
+    double scale;                       // 2^E of the last slice
+    double inv_phi[256];
+};
+
+static const DecConsts &dec_consts()
 {
-    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t bi = b / nbc, bj = b - (b / nbc) * nbc;
-        int8_t c[kKeep];
-        load_codes(code + b * kKeep, c);
-        double out[64];
-        decompress_block(__ldg(f + b), __ldg(s + b), __ldg(phi + b), c, out);
-        double *p = A + (bi * 8) * lda + bj * 8;
+    static DecConsts dc;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        const long double(*G)[kKeep] = decompress_map();
+        long double mx = 0.0L;
+        for (int p = 0; p < 64; ++p)
+            for (int t = 0; t < kKeep; ++t) mx = std::max(mx, fabsl(G[p][t]));
+        const int E = (int)ceill(log2l(mx)) - 10;
+        static float digit[kDecSlices][64][32];  // [slice][n = p][k = t], k >= 28 zero
+        for (int p = 0; p < 64; ++p)
+            for (int t = 0; t < 32; ++t) {
+                long double r = t < kKeep ? G[p][t] : 0.0L;
+                for (int s = 0; s < kDecSlices; ++s) {
+                    const long double sc = ldexpl(1.0L, E - 11 * s);
+                    const long double d = rintl(r / sc);
+                    digit[s][p][t] = (float)d;
+                    r -= d * sc;
+                }
+            }
+        auto h2 = [](float lo, float hi) {
+            const __half a = __float2half_rn(lo), b = __float2half_rn(hi);
+            return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
+        };
+        for (int s = 0; s < kDecSlices; ++s)
+            for (int ks = 0; ks < 2; ++ks)
+                for (int nt = 0; nt < 8; ++nt)
+                    for (int lane = 0; lane < 32; ++lane) {
+                        const int g = lane >> 2, t = lane & 3, n = nt * 8 + g, k = ks * 16 + 2 * t;
+                        dc.bfrag[s][ks][nt][lane].x = h2(digit[s][n][k], digit[s][n][k + 1]);
+                        dc.bfrag[s][ks][nt][lane].y = h2(digit[s][n][k + 8], digit[s][n][k + 9]);
+                    }
+        dc.scale = (double)ldexpl(1.0L, E - 11 * (kDecSlices - 1));
+        dc.inv_phi[0] = 0.0;
+        for (int p = 1; p < 256; ++p) dc.inv_phi[p] = 1.0 / (double)p;
+    });
+    return dc;
+}
+
+__device__ __forceinline__ void mma_f16(float (&c)[4], const uint32_t (&a)[4], uint2 b)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b.x), "r"(b.y));
+}
+
+// Two consecutive int8 codes (k, k+1) of a block as an fp16 pair; zero beyond 28.
+__device__ __forceinline__ uint32_t code_pair(const int8_t *__restrict__ c, int k, bool valid)
+{
+    if (!valid || k >= kKeep) return 0u;
+    const uint16_t v = __ldg(reinterpret_cast<const uint16_t *>(c + k));
+    const __half lo = __short2half_rn((short)(int8_t)(uint8_t)(v & 0xFF));
+    const __half hi = __short2half_rn((short)(int8_t)(uint8_t)(v >> 8));
+    return (uint32_t)__half_as_ushort(lo) | ((uint32_t)__half_as_ushort(hi) << 16);
+}
+
+template <bool kVec>
+__global__ void __launch_bounds__(128)
+    k_decompress(const __grid_constant__ DecConsts dc, const double *__restrict__ f, const double *__restrict__ s,
+                 const uint8_t *__restrict__ phi, const int8_t *__restrict__ code, int64_t nbc, int64_t nb,
+                 double *__restrict__ A, int64_t lda)
+{
+    __shared__ uint2 sb[kDecSlices][2][8][32];
+    for (int i = threadIdx.x; i < kDecSlices * 2 * 8 * 32; i += blockDim.x)
+        (&sb[0][0][0][0])[i] = (&dc.bfrag[0][0][0][0])[i];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int64_t ngroups = (nb + 15) / 16;
+    for (int64_t grp = (int64_t)blockIdx.x * 4 + warp; grp < ngroups; grp += (int64_t)gridDim.x * 4) {
+        const int64_t bA = grp * 16 + g, bB = bA + 8;
+        const bool vA = bA < nb, vB = bB < nb;
+        const int8_t *cA = code + bA * kKeep, *cB = code + bB * kKeep;
+        uint32_t a0[4], a1[4];
+        a0[0] = code_pair(cA, 2 * t, vA);
+        a0[1] = code_pair(cB, 2 * t, vB);
+        a0[2] = code_pair(cA, 2 * t + 8, vA);
+        a0[3] = code_pair(cB, 2 * t + 8, vB);
+        a1[0] = code_pair(cA, 16 + 2 * t, vA);
+        a1[1] = code_pair(cB, 16 + 2 * t, vB);
+        a1[2] = code_pair(cA, 24 + 2 * t, vA);
+        a1[3] = code_pair(cB, 24 + 2 * t, vB);
+        long long acc[8][4];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            if (kVec) {
-                double2 *q = reinterpret_cast<double2 *>(p + i * lda);
+        for (int nt = 0; nt < 8; ++nt)
 #pragma unroll
-                for (int h = 0; h < 4; ++h) q[h] = make_double2(out[i * 8 + 2 * h], out[i * 8 + 2 * h + 1]);
-            } else {
+            for (int q = 0; q < 4; ++q) acc[nt][q] = 0;
 #pragma unroll
-                for (int j = 0; j < 8; ++j) p[i * lda + j] = out[i * 8 + j];
+        for (int sl = 0; sl < kDecSlices; ++sl) {
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt) {
+                float c[4] = {0.f, 0.f, 0.f, 0.f};
+                mma_f16(c, a0, sb[sl][0][nt][lane]);
+                mma_f16(c, a1, sb[sl][1][nt][lane]);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[nt][q] = acc[nt][q] * 2048 + f2i_small(c[q]);
+            }
+        }
+        // c0, c1: block bA, row nt, columns 2t, 2t+1; c2, c3: block bB.
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int64_t b = h ? bB : bA;
+            if (!(h ? vB : vA)) continue;
+            const double fb = __ldg(f + b);
+            const double ts = __ldg(s + b) * dc.inv_phi[__ldg(phi + b)] * dc.scale;
+            const int64_t bi = b / nbc, bj = b - bi * nbc;
+            double *p = A + (bi * 8) * lda + bj * 8 + 2 * t;
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt) {
+                const double o0 = fma(ts, i64_to_double(acc[nt][2 * h]), fb);
+                const double o1 = fma(ts, i64_to_double(acc[nt][2 * h + 1]), fb);
+                if (kVec) {
+                    *reinterpret_cast<double2 *>(p + nt * lda) = make_double2(o0, o1);
+                } else {
+                    p[nt * lda] = o0;
+                    p[nt * lda + 1] = o1;
+                }
             }
         }
     }
@@ -136,11 +255,13 @@ int launch_decompress(const blaz_cmat *a, double *A, int64_t lda, cudaStream_t s
     const int64_t nbc = a->cols / 8, nb = (a->rows / 8) * nbc;
     if (nb == 0) return BLAZ_OK;
     const int threads = 128;
-    const int grid = grid_for(nb, threads);
+    int64_t want = ((nb + 15) / 16 + 3) / 4;
+    const int64_t cap = (int64_t)num_sms() * 16;
+    const int grid = (int)std::max<int64_t>(1, std::min(want, cap));
     if (vec_ok(A, lda))
-        k_decompress<true><<<grid, threads, 0, st>>>(a->f, a->s, a->phi, a->code, nbc, nb, A, lda);
+        k_decompress<true><<<grid, threads, 0, st>>>(dec_consts(), a->f, a->s, a->phi, a->code, nbc, nb, A, lda);
     else
-        k_decompress<false><<<grid, threads, 0, st>>>(a->f, a->s, a->phi, a->code, nbc, nb, A, lda);
+        k_decompress<false><<<grid, threads, 0, st>>>(dec_consts(), a->f, a->s, a->phi, a->code, nbc, nb, A, lda);
     return launch_status();
 }
 

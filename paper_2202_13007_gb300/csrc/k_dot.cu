@@ -18,6 +18,7 @@
 #include <mutex>
 
 #include "block_codec.cuh"
+#include "gmap.cuh"
 
 namespace blaz {
 
@@ -49,17 +50,6 @@ struct GramConsts {
 
 // Exact conversion of an integer-valued float with |x| < 2^24 to int.
 __device__ __forceinline__ int f2i_exact(float x) { return __float2int_rn(x); }
-
-// Exact int64 -> binary64 for |v| < 2^53 without the FP64 conversion unit.
-__device__ __forceinline__ double i64_to_double(long long v)
-{
-    if (v == 0) return 0.0;
-    const unsigned long long sign = v < 0 ? 0x8000000000000000ull : 0ull;
-    const unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
-    const int e = 63 - __clzll((long long)a);                 // position of the leading one, <= 52
-    const unsigned long long mant = (a << (52 - e)) & 0x000FFFFFFFFFFFFFull;
-    return __longlong_as_double((long long)(sign | ((unsigned long long)(e + 1023) << 52) | mant));
-}
 
 // sum_s scale[s] * (hi_s * 4096 + lo_s), the slices combined in binary64.
 __device__ __forceinline__ double combine(const float (&hi)[kSlices], const float (&lo)[kSlices],
@@ -185,25 +175,7 @@ static const GramConsts &gram_consts()
     static GramConsts g;
     static std::once_flag once;
     std::call_once(once, [] {
-        const long double pi = 3.14159265358979323846264338327950288L;
-        long double c[8][8];
-        for (int k = 0; k < 8; ++k)
-            for (int x = 0; x < 8; ++x) c[k][x] = cosl((long double)((2 * x + 1) * k) * pi / 16.0L);
-        const long double al[8] = {sqrtl(0.125L), 0.5L, 0.5L, 0.5L, 0.5L, 0.5L, 0.5L, 0.5L};
-        static long double G[64][kKeep];
-        for (int t = 0; t < kKeep; ++t) {
-            const int i = kept_row(t), j = kept_col(t);
-            long double B[8][8];
-            for (int u = 0; u < 8; ++u)
-                for (int v = 0; v < 8; ++v) {
-                    const long double P = al[i] * al[j] * c[i][u] * c[j][v];
-                    if (u == 0 && v == 0) B[u][v] = 0.0L;
-                    else if (u == 0) B[u][v] = B[u][v - 1] + P;
-                    else if (v == 0) B[u][v] = B[u - 1][v] + P;
-                    else B[u][v] = (B[u - 1][v] + B[u][v - 1]) * 0.5L + P;
-                    G[u * 8 + v][t] = B[u][v];
-                }
-        }
+        const long double(*G)[kKeep] = decompress_map();
         long double H[kKeep * kKeep], w[kKeep];
         for (int k = 0; k < kKeep; ++k) {
             w[k] = 0.0L;
