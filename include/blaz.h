@@ -153,7 +153,9 @@ int blaz_dot_noalloc(const blaz_cmat *a, const blaz_cmat *b, double *result, voi
 
 /* Dot product of line i of A_hat and column j of B_hat, Algorithm 3 (Eqs.
  * eqbbb0, eqbbb) applied block-wise: sum_k A_hat[i][k] B_hat[k][j].
- * a: n x k, b: k x m; 0 <= i < n, 0 <= j < m.  result: device, one binary64. */
+ * a: n x k, b: k x m; 0 <= i < n, 0 <= j < m.  result: device, one binary64.
+ * Only line i of A_hat and column j of B_hat are decompressed; uses
+ * stream-ordered scratch (one partial sum per CTA). */
 int blaz_dot_rowcol(const blaz_cmat *a, const blaz_cmat *b, int64_t i, int64_t j, double *result,
                     void *stream);
 

@@ -249,7 +249,15 @@ int blaz_dot_rowcol(const blaz_cmat *a, const blaz_cmat *b, int64_t i, int64_t j
     if (a->cols != b->rows) return BLAZ_ERR_SHAPE;
     if (!result) return BLAZ_ERR_NULL;
     if (i < 0 || i >= a->rows || j < 0 || j >= b->cols) return BLAZ_ERR_RANGE;
-    return launch_dot_rowcol(a, b, i, j, result, (cudaStream_t)stream);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int grid = rowcol_grid(a->cols / 8);
+    Scratch ws(st);
+    if ((rc = ws.alloc(sizeof(double) * grid + 256))) return rc;
+    double *partials = (double *)ws.p;
+    unsigned *counter = (unsigned *)((char *)ws.p + ((sizeof(double) * grid + 255) & ~(size_t)255));
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    return launch_dot_rowcol(a, b, i, j, result, partials, counter, st);
 }
 
 int blaz_matmul(const blaz_cmat *a, const double *B, int64_t ldb, int64_t m, double *C, int64_t ldc, int mode,

@@ -88,8 +88,9 @@ int launch_scale(const blaz_cmat *a, double c, const blaz_cmat *out, cudaStream_
 int launch_dot(const blaz_cmat *a, const blaz_cmat *b, double *result, double *partials, unsigned *counter,
                int64_t max_ctas, cudaStream_t st);
 int dot_grid(int64_t nb);
+int rowcol_grid(int64_t nkb);
 int launch_dot_rowcol(const blaz_cmat *a, const blaz_cmat *b, int64_t i, int64_t j, double *result,
-                      cudaStream_t st);
+                      double *partials, unsigned *counter, cudaStream_t st);
 size_t split_bf16_scratch_bytes(int64_t n, int64_t k, int64_t m);
 int launch_matmul_split_bf16(const double *Ah, int64_t lda, const double *B, int64_t ldb, double *C, int64_t ldc,
                              int64_t n, int64_t k, int64_t m, void *scratch, cudaStream_t st);

@@ -123,11 +123,11 @@ __global__ void __launch_bounds__(kThreads)
         }
         case BLAZ_OP_ADD:
             for (int64_t b = w.b0 + tid; b < w.b1; b += kThreads)
-                add_block<false>(b, op.fa, op.sa, op.pa, op.ca, op.fb, op.sb, op.pb, op.cb, op.fo, op.so, op.po, op.co);
+                add_block_fast<false>(b, op.fa, op.sa, op.pa, op.ca, op.fb, op.sb, op.pb, op.cb, op.fo, op.so, op.po, op.co);
             break;
         case BLAZ_OP_SUB:
             for (int64_t b = w.b0 + tid; b < w.b1; b += kThreads)
-                add_block<true>(b, op.fa, op.sa, op.pa, op.ca, op.fb, op.sb, op.pb, op.cb, op.fo, op.so, op.po, op.co);
+                add_block_fast<true>(b, op.fa, op.sa, op.pa, op.ca, op.fb, op.sb, op.pb, op.cb, op.fo, op.so, op.po, op.co);
             break;
         case BLAZ_OP_SCALE: {
             const bool copy = (op.po != op.pa) || (op.co != op.ca);

@@ -14,7 +14,7 @@ __global__ void __launch_bounds__(128)
           int8_t *c)
 {
     for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x)
-        add_block<kSub>(b, f1, s1, p1, c1, f2, s2, p2, c2, f, s, p, c);
+        add_block_fast<kSub>(b, f1, s1, p1, c1, f2, s2, p2, c2, f, s, p, c);
 }
 
 // Algorithm 2.  When out == a (in place) only f and s are touched; otherwise

@@ -14,6 +14,7 @@
 // slices of 11 bits (integer digits times powers of two); with integer codes
 // every slice product sum is an integer below 2^23, exact in fp32, and only
 // the final combination is rounded (binary64).
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 
@@ -201,30 +202,79 @@ static const GramConsts &gram_consts()
     return g;
 }
 
-// Algorithm 3 generalised to matrices: one CTA; thread t handles k-blocks
-// t, t + blockDim, ...; each decompresses block (bi, kb) of A and (kb, bj) of B.
+// Algorithm 3 generalised to matrices.  Line ri of block (bi, kb) of A is
+// fa + ta G_r ca (G_r: rows 8 ri .. 8 ri + 7 of the decompression map) and
+// column cj of block (kb, bj) of B is fb + tb G_c cb (rows cj, cj + 8, ...),
+// so only the needed line and column are decompressed (IPREDICT_LINES /
+// IPREDICT_COLS of Algorithm 3).  One thread per k-block; CTA partials are
+// added in order by the last CTA.
+struct RowColConsts {
+    double G[64][kKeep];
+    double inv_phi[256];
+};
+
 __global__ void __launch_bounds__(kDotThreads)
-    k_dot_rowcol(int64_t nkb, int64_t nbc_a, int64_t nbc_b, int64_t i, int64_t j, const double *__restrict__ fa,
-                 const double *__restrict__ sa, const uint8_t *__restrict__ pa, const int8_t *__restrict__ ca,
-                 const double *__restrict__ fb, const double *__restrict__ sb, const uint8_t *__restrict__ pb,
-                 const int8_t *__restrict__ cb, double *__restrict__ result)
+    k_dot_rowcol(const __grid_constant__ RowColConsts g, int64_t nkb, int64_t nbc_a, int64_t nbc_b, int64_t i,
+                 int64_t j, const double *__restrict__ fa, const double *__restrict__ sa,
+                 const uint8_t *__restrict__ pa, const int8_t *__restrict__ ca, const double *__restrict__ fb,
+                 const double *__restrict__ sb, const uint8_t *__restrict__ pb, const int8_t *__restrict__ cb,
+                 double *__restrict__ partials, unsigned *__restrict__ counter, double *__restrict__ result)
 {
     __shared__ double red[kDotThreads / 32];
+    __shared__ bool last;
     const int64_t bi = i / 8, bj = j / 8;
     const int ri = (int)(i % 8), cj = (int)(j % 8);
     double acc = 0.0;
-    for (int64_t kb = threadIdx.x; kb < nkb; kb += blockDim.x) {
+    for (int64_t kb = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; kb < nkb; kb += (int64_t)gridDim.x * blockDim.x) {
         const int64_t ba = bi * nbc_a + kb, bb = kb * nbc_b + bj;
-        double x[64], y[64];
-        decompress_block_at(fa[ba], sa[ba], pa[ba], ca + ba * kKeep, x);
-        decompress_block_at(fb[bb], sb[bb], pb[bb], cb + bb * kKeep, y);
+        int8_t xa[kKeep], xb[kKeep];
+        load_codes(ca + ba * kKeep, xa);
+        load_codes(cb + bb * kKeep, xb);
+        const double ta = sa[ba] * g.inv_phi[pa[ba]], tb = sb[bb] * g.inv_phi[pb[bb]];
+        const double f_a = fa[ba], f_b = fb[bb];
         double blk = 0.0;
 #pragma unroll
-        for (int t = 0; t < 8; ++t) blk = fma(x[ri * 8 + t], y[t * 8 + cj], blk);
+        for (int q = 0; q < 8; ++q) {
+            double ya = 0.0, yb = 0.0;
+#pragma unroll
+            for (int t = 0; t < kKeep; ++t) {
+                ya = fma(g.G[ri * 8 + q][t], (double)xa[t], ya);
+                yb = fma(g.G[q * 8 + cj][t], (double)xb[t], yb);
+            }
+            blk = fma(fma(ta, ya, f_a), fma(tb, yb, f_b), blk);
+        }
         acc += blk;
     }
-    const double r = cta_sum(acc, red);
-    if (threadIdx.x == 0) *result = r;
+    const double tot = cta_sum(acc, red);
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = tot;
+        __threadfence();
+        last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double v = 0.0;
+    for (int q = threadIdx.x; q < (int)gridDim.x; q += blockDim.x) v += __ldcg(partials + q);
+    const double r = cta_sum(v, red);
+    if (threadIdx.x == 0) {
+        *result = r;
+        *counter = 0u;
+    }
+}
+
+static const RowColConsts &rowcol_consts()
+{
+    static RowColConsts g;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        const long double(*G)[kKeep] = decompress_map();
+        for (int p = 0; p < 64; ++p)
+            for (int t = 0; t < kKeep; ++t) g.G[p][t] = (double)G[p][t];
+        g.inv_phi[0] = 0.0;
+        for (int p = 1; p < 256; ++p) g.inv_phi[p] = 1.0 / (double)p;
+    });
+    return g;
 }
 
 int dot_grid(int64_t nb)
@@ -246,10 +296,21 @@ int launch_dot(const blaz_cmat *a, const blaz_cmat *b, double *result, double *p
     return launch_status();
 }
 
-int launch_dot_rowcol(const blaz_cmat *a, const blaz_cmat *b, int64_t i, int64_t j, double *result, cudaStream_t st)
+int rowcol_grid(int64_t nkb)
 {
-    k_dot_rowcol<<<1, kDotThreads, 0, st>>>(a->cols / 8, a->cols / 8, b->cols / 8, i, j, a->f, a->s, a->phi, a->code,
-                                            b->f, b->s, b->phi, b->code, result);
+    int64_t want = (nkb + kDotThreads - 1) / kDotThreads;
+    const int64_t cap = (int64_t)num_sms();
+    return (int)std::max<int64_t>(1, std::min(want, cap));
+}
+
+int launch_dot_rowcol(const blaz_cmat *a, const blaz_cmat *b, int64_t i, int64_t j, double *result,
+                      double *partials, unsigned *counter, cudaStream_t st)
+{
+    const int64_t nkb = a->cols / 8;
+    const int grid = rowcol_grid(nkb);
+    k_dot_rowcol<<<grid, kDotThreads, 0, st>>>(rowcol_consts(), nkb, a->cols / 8, b->cols / 8, i, j, a->f, a->s,
+                                               a->phi, a->code, b->f, b->s, b->phi, b->code, partials, counter,
+                                               result);
     return launch_status();
 }
 
