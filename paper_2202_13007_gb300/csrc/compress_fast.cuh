@@ -26,19 +26,53 @@
 #pragma once
 
 #include "block_codec.cuh"
+#include "gmap.cuh"
 
 namespace blaz {
 
-// x * 0.5 rounded to nearest: an exponent decrement for normal numbers with a
-// biased exponent >= 2 (exact), and zero kept as is; the binary64 multiply
-// for everything else (subnormals, the smallest normals, Inf, NaN).
+// x * 0.5 rounded to nearest even, on the bit pattern (no FP64 instruction):
+// an exponent decrement for normal results; for the smallest normals and the
+// subnormals the significand is halved with round-half-even; Inf and NaN
+// are returned as they are (NaN blocks take the exact path anyway).
 __device__ __forceinline__ double dhalf(double x)
 {
-    const int hi = __double2hiint(x), lo = __double2loint(x);
-    const int e = (hi >> 20) & 0x7FF;
-    if (e > 1 && e < 0x7FF) return __hiloint2double(hi - (1 << 20), lo);
-    if (((hi & 0x7FFFFFFF) | lo) == 0) return x;
-    return dmul(x, 0.5);
+    const long long b = __double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7FF);
+    if (e > 1 && e < 0x7FF) return __longlong_as_double(b - (1ll << 52));
+    if (e == 0x7FF) return x;
+    const unsigned long long sign = (unsigned long long)b & 0x8000000000000000ull;
+    unsigned long long m = (unsigned long long)b & 0x000FFFFFFFFFFFFFull;
+    if (e == 1) m |= 1ull << 52;
+    unsigned long long q = m >> 1;
+    if ((m & 1ull) && (q & 1ull)) q += 1ull;
+    return __longlong_as_double((long long)(sign | q));
+}
+
+// trunc toward zero saturated to [-127, 127], NaN -> 0 (quantize), on the bits.
+__device__ __forceinline__ int8_t quantize_bits(double v)
+{
+    const long long b = __double_as_longlong(v);
+    const bool neg = b < 0;
+    const int e = (int)((b >> 52) & 0x7FF);
+    if (e == 0x7FF) return (b & 0x000FFFFFFFFFFFFFll) ? 0 : (neg ? -127 : 127);
+    if (e < 1023) return 0;
+    if (e >= 1023 + 7) return neg ? -127 : 127;
+    const unsigned long long m = ((unsigned long long)b & 0x000FFFFFFFFFFFFFull) | (1ull << 52);
+    int mag = (int)(m >> (52 - (e - 1023)));
+    mag = mag > 127 ? 127 : mag;
+    return (int8_t)(neg ? -mag : mag);
+}
+
+// Exact float -> double on the bits (normal floats and zero).
+__device__ __forceinline__ double f2d_bits(float x)
+{
+    const unsigned u = __float_as_uint(x);
+    const unsigned e = (u >> 23) & 0xFF;
+    if (e == 0) return 0.0;
+    const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
+                                 ((unsigned long long)(e - 127 + 1023) << 52) |
+                                 ((unsigned long long)(u & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)b);
 }
 
 // binary64 -> binary32 by truncating the significand: relative error < 2^-23
@@ -55,20 +89,34 @@ __device__ __forceinline__ float trunc_f32(double x)
 __host__ __device__ constexpr float cos_f(int k, int x) { return (float)cos_tab(k, x); }
 
 // phi of Eq. eqphi from m: trunc(RN(127/m)) clamped to [1, 255]; monotone
-// non-increasing in m.
+// non-increasing in m.  The comparison and truncation act on the bits.
 __device__ __forceinline__ int phi_of(double m)
 {
     const double q = ddiv(127.0, m);
-    if (!(q < 255.0)) return 255;
-    const int p = __double2int_rz(q);
-    return p < 1 ? 1 : p;
+    const long long b = __double_as_longlong(q);
+    const int e = (int)((b >> 52) & 0x7FF);
+    if (b < 0) return 1;                 // negative (not reached: m >= 0)
+    if (e >= 1023 + 8) return 255;       // q >= 256, Inf, NaN
+    if (e < 1023) return 1;              // q < 1
+    const unsigned long long mm = ((unsigned long long)b & 0x000FFFFFFFFFFFFFull) | (1ull << 52);
+    const int p = (int)(mm >> (52 - (e - 1023)));
+    return p >= 255 ? 255 : p;
 }
 
-// Compress one block held in d (overwritten).  Returns true with s, phi and
-// the codes set when every decision is certified; false when the block must
-// go through compress_block.  s_out is the exact s in both cases.
-__device__ __forceinline__ bool compress_block_fast(double (&d)[64], double &s_out, uint8_t &phi_out,
-                                                    int8_t (&code)[kKeep])
+// Non-negative doubles compare as their bit patterns.
+__device__ __forceinline__ double dmax_nonneg(double a, double b)
+{
+    return __double_as_longlong(a) >= __double_as_longlong(b) ? a : b;
+}
+
+constexpr uint32_t kPendingAll = 0x80000000u;  // phi not certified / non-finite: whole block exact
+
+// Compress one block held in d (overwritten).  Returns 0 when every decision
+// is certified (s, phi and the codes set); kPendingAll when the block must go
+// through compress_block; otherwise a mask of the codes (bit t = code t) left
+// undecided, with s, phi and the other codes set.  s_out is always exact.
+__device__ __forceinline__ uint32_t compress_block_fast(double (&d)[64], double &s_out, uint8_t &phi_out,
+                                                        int8_t (&code)[kKeep])
 {
     // Eq. eqnorm, exactly as compress_block (x * 0.5 by dhalf, bit-identical).
 #pragma unroll
@@ -101,12 +149,14 @@ __device__ __forceinline__ bool compress_block_fast(double (&d)[64], double &s_o
         phi_out = 255;
 #pragma unroll
         for (int t = 0; t < kKeep; ++t) code[t] = 0;
-        return true;
+        return 0u;
     }
-    const double s = ddiv(S, (double)K);
+    const double s = ddiv(S, i64_to_double(K));
     const double r = ddiv(1.0, s);
     s_out = s;
-    if (!(S <= 1.7e308) || !(r <= 1.7e308)) return false;  // Inf / NaN / overflow: exact path
+    // Inf / NaN / overflow (S >= 0, r >= 0): exact path
+    if (((__double_as_longlong(S) >> 52) & 0x7FF) >= 0x7FE || ((__double_as_longlong(r) >> 52) & 0x7FF) >= 0x7FE)
+        return kPendingAll;
 
     // Rows of D' (exact binary64), the exact inner sums of column 0 (the DC
     // chain, cos(0) = 1) and fp32 inner sums T[u][j] for j >= 1.
@@ -160,37 +210,83 @@ __device__ __forceinline__ bool compress_block_fast(double (&d)[64], double &s_o
     // Eq. eqphi.  m = max(|X00|, max over the others), certified when phi is
     // the same at both ends of the interval of possible m.
     const double ax00 = fabs(X00);
-    const double mhi_d = (double)mhi * (1.0 + 0x1p-20);
-    const double mlo_d = (double)mlo * (1.0 - 0x1p-20);
+    // mhi, mlo widened by 2^-20 (relative) in fp32 before the exact conversion
+    const double mhi_d = f2d_bits(mhi * (1.0f + 0x1p-20f));
+    const double mlo_d = f2d_bits(mlo * (1.0f - 0x1p-20f));
     int phi;
-    if (mhi_d < ax00) {
+    if (__double_as_longlong(mhi_d) < __double_as_longlong(ax00)) {
         phi = phi_of(ax00);  // the DC coefficient is the maximum: m is exact
     } else {
-        const int p_lo_m = phi_of(fmax(ax00, mlo_d));
-        const int p_hi_m = phi_of(fmax(ax00, mhi_d));
-        if (p_lo_m != p_hi_m) return false;
+        const int p_lo_m = phi_of(dmax_nonneg(ax00, mlo_d));
+        const int p_hi_m = phi_of(dmax_nonneg(ax00, mhi_d));
+        if (p_lo_m != p_hi_m) return kPendingAll;
         phi = p_hi_m;
     }
     phi_out = (uint8_t)phi;
     const float phif = (float)phi;
-    code[0] = quantize(dmul(X00, (double)phi));
+    code[0] = quantize_bits(dmul(X00, i64_to_double(phi)));
+    uint32_t pending = 0u;
 #pragma unroll
     for (int t = 1; t < kKeep; ++t) {
         const float aa = (float)aa_tab(kept_row(t), kept_col(t));
         const float v = Dk[t] * phif;
         const float Ev = (base * aa * phif) * (1.0f + 0x1p-20f) + 0x1p-22f * (fabsf(v) + 1.0f) + 0x1p-16f;
         const float lo = v - Ev, hi = v + Ev;
-        int c;
+        int c = 0;
         if (lo >= 127.0f) c = 127;
         else if (hi <= -127.0f) c = -127;
         else {
             const int tl = (int)truncf(lo), th = (int)truncf(hi);
-            if (tl != th || tl >= 127 || tl <= -127) return false;
-            c = tl;
+            if (tl != th || tl >= 127 || tl <= -127) pending |= 1u << t;
+            else c = tl;
         }
         code[t] = (int8_t)c;
     }
-    return true;
+    return pending;
+}
+
+// cos and alpha_i alpha_j as tables for run-time indices (the exact fix-up).
+__constant__ double c_cos[64] = {
+#define BLAZ_ROW(k) cos_tab(k, 0), cos_tab(k, 1), cos_tab(k, 2), cos_tab(k, 3), cos_tab(k, 4), cos_tab(k, 5), cos_tab(k, 6), cos_tab(k, 7)
+    BLAZ_ROW(0), BLAZ_ROW(1), BLAZ_ROW(2), BLAZ_ROW(3), BLAZ_ROW(4), BLAZ_ROW(5), BLAZ_ROW(6), BLAZ_ROW(7)
+#undef BLAZ_ROW
+};
+
+// Code t of a block from the exact D' (binary64 order of the specification):
+// T[u] = sum_v D'[u][v] cos[j][v], U = sum_u cos[i][u] T[u], X = aa_ij U,
+// code = quantize(X * phi).
+__device__ __forceinline__ int8_t exact_code(const double (&dp)[64], int t, int phi)
+{
+    const int i = kept_row(t), j = kept_col(t);
+    double U = 0.0;
+    for (int u = 0; u < 8; ++u) {
+        double T = (j == 0) ? dp[u * 8] : dmul(dp[u * 8], c_cos[j * 8]);
+#pragma unroll
+        for (int v = 1; v < 8; ++v) T = dadd(T, (j == 0) ? dp[u * 8 + v] : dmul(dp[u * 8 + v], c_cos[j * 8 + v]));
+        const double term = (i == 0) ? T : dmul(c_cos[i * 8 + u], T);
+        U = (u == 0) ? term : dadd(U, term);
+    }
+    const double aa = (i == 0 && j == 0) ? BLAZ_A00 : (i == 0 || j == 0) ? BLAZ_A0K : BLAZ_AKK;
+    return quantize_bits(dmul(dmul(aa, U), i64_to_double(phi)));
+}
+
+// D' = D * (1/s) of a block in d (input block on entry), as compress_block
+// forms it; s is the block's exact stored slope (> 0).
+__device__ __forceinline__ void exact_dprime(double (&d)[64], double s)
+{
+#pragma unroll
+    for (int i = 7; i >= 0; --i) {
+#pragma unroll
+        for (int j = 7; j >= 0; --j) {
+            if (i == 0 && j == 0) d[0] = 0.0;
+            else if (i == 0) d[j] = dsub(d[j], d[j - 1]);
+            else if (j == 0) d[i * 8] = dsub(d[i * 8], d[(i - 1) * 8]);
+            else d[i * 8 + j] = dhalf(dadd(dsub(d[i * 8 + j], d[(i - 1) * 8 + j]), dsub(d[i * 8 + j], d[i * 8 + j - 1])));
+        }
+    }
+    const double r = ddiv(1.0, s);
+#pragma unroll
+    for (int p = 0; p < 64; ++p) d[p] = dmul(d[p], r);
 }
 
 }  // namespace blaz

@@ -20,6 +20,7 @@
 #include "batch_internal.cuh"
 #include "block_codec.cuh"
 #include "block_ops.cuh"
+#include "compress_fast.cuh"
 #include "gemm_fp64.cuh"
 
 namespace blaz {
@@ -92,7 +93,20 @@ __global__ void __launch_bounds__(kThreads)
                 double sv;
                 uint8_t ph;
                 int8_t c[kKeep];
-                compress_block(d, sv, ph, c);
+                const uint32_t pending = compress_block_fast(d, sv, ph, c);
+                if (pending) {  // undecided codes (or phi): exact binary64, as the two-kernel path
+                    if (op.vec) load_block<true>(op.A, op.lda, bi, bj, d);
+                    else load_block<false>(op.A, op.lda, bi, bj, d);
+                    if (pending == kPendingAll) {
+                        compress_block(d, sv, ph, c);
+                    } else {
+                        exact_dprime(d, sv);
+                        for (uint32_t m = pending; m; m &= m - 1) {
+                            const int t = __ffs(m) - 1;
+                            c[t] = exact_code(d, t, ph);
+                        }
+                    }
+                }
                 op.so[b] = sv;
                 op.po[b] = ph;
                 store_codes(op.co + b * kKeep, c);

@@ -21,7 +21,7 @@ template <bool kVec>
 __global__ void __launch_bounds__(128)
     k_compress_fast(const double *__restrict__ A, int64_t lda, int64_t nbc, int64_t nb, double *__restrict__ f,
                     double *__restrict__ s, uint8_t *__restrict__ phi, int8_t *__restrict__ code,
-                    unsigned *__restrict__ fix_list, unsigned *__restrict__ fix_count)
+                    uint2 *__restrict__ fix_list, unsigned *__restrict__ fix_count)
 {
     for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x) {
         const int64_t bi = b / nbc, bj = b - (b / nbc) * nbc;
@@ -31,47 +31,58 @@ __global__ void __launch_bounds__(128)
         double sv;
         uint8_t ph;
         int8_t c[kKeep];
-        const bool ok = compress_block_fast(d, sv, ph, c);
+        const uint32_t pending = compress_block_fast(d, sv, ph, c);
         s[b] = sv;
-        if (ok) {
+        if (pending != kPendingAll) {
             phi[b] = ph;
             store_codes(code + b * kKeep, c);
         }
-        // Append the blocks left undecided, one atomic per warp.
+        // Append the blocks with undecided codes, one atomic per warp.
         const unsigned act = __activemask();
-        const unsigned need = __ballot_sync(act, !ok);
+        const unsigned need = __ballot_sync(act, pending != 0u);
         if (need) {
             const int lane = threadIdx.x & 31;
             const int leader = __ffs(need) - 1;
             unsigned base = 0;
             if (lane == leader) base = atomicAdd(fix_count, (unsigned)__popc(need));
             base = __shfl_sync(act, base, leader);
-            if (!ok) fix_list[base + __popc(need & ((1u << lane) - 1u))] = (unsigned)b;
+            if (pending) fix_list[base + __popc(need & ((1u << lane) - 1u))] = make_uint2((unsigned)b, pending);
         }
     }
 }
 
-// The exact binary64 compressor (compress_block) on the listed blocks.
+// The listed blocks: the whole exact compressor (compress_block) when phi was
+// not certified, else the exact binary64 value of each undecided code.
 template <bool kVec>
 __global__ void __launch_bounds__(128)
-    k_compress_fix(const double *__restrict__ A, int64_t lda, int64_t nbc, const unsigned *__restrict__ fix_list,
+    k_compress_fix(const double *__restrict__ A, int64_t lda, int64_t nbc, const uint2 *__restrict__ fix_list,
                    const unsigned *__restrict__ fix_count, double *__restrict__ f, double *__restrict__ s,
                    uint8_t *__restrict__ phi, int8_t *__restrict__ code)
 {
     const int64_t n = *fix_count;
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t b = fix_list[q];
+        const uint2 e = fix_list[q];
+        const int64_t b = e.x;
         const int64_t bi = b / nbc, bj = b - (b / nbc) * nbc;
         double d[64];
         load_block<kVec>(A, lda, bi, bj, d);
-        f[b] = d[0];
-        double sv;
-        uint8_t ph;
-        int8_t c[kKeep];
-        compress_block(d, sv, ph, c);
-        s[b] = sv;
-        phi[b] = ph;
-        store_codes(code + b * kKeep, c);
+        if (e.y == kPendingAll) {
+            f[b] = d[0];
+            double sv;
+            uint8_t ph;
+            int8_t c[kKeep];
+            compress_block(d, sv, ph, c);
+            s[b] = sv;
+            phi[b] = ph;
+            store_codes(code + b * kKeep, c);
+        } else {
+            exact_dprime(d, s[b]);
+            const int p = phi[b];
+            for (uint32_t m = e.y; m; m &= m - 1) {
+                const int t = __ffs(m) - 1;
+                code[b * kKeep + t] = exact_code(d, t, p);
+            }
+        }
     }
 }
 
@@ -226,14 +237,14 @@ static int grid_for(int64_t nb, int threads)
 
 static bool vec_ok(const void *p, int64_t ld) { return ((uintptr_t)p % 16 == 0) && (ld % 2 == 0); }
 
-size_t compress_scratch_bytes(int64_t nb) { return ((size_t)nb * 4 + 255) / 256 * 256 + 256; }
+size_t compress_scratch_bytes(int64_t nb) { return ((size_t)nb * 8 + 255) / 256 * 256 + 256; }
 
 int launch_compress(const double *A, int64_t lda, const blaz_cmat *out, void *scratch, cudaStream_t st)
 {
     const int64_t nbc = out->cols / 8, nb = (out->rows / 8) * nbc;
     if (nb == 0) return BLAZ_OK;
     if (nb > 0xFFFFFFFFll) return BLAZ_ERR_SHAPE;
-    unsigned *list = (unsigned *)scratch;
+    uint2 *list = (uint2 *)scratch;
     unsigned *count = (unsigned *)((char *)scratch + compress_scratch_bytes(nb) - 256);
     cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned), st);
     if (e != cudaSuccess) return set_cuda_error(e);
