@@ -18,6 +18,8 @@
 #include <cmath>
 #include <mutex>
 
+#include <cuda_fp16.h>
+
 #include "block_codec.cuh"
 #include "gmap.cuh"
 
@@ -116,6 +118,182 @@ __device__ __forceinline__ double block_dot_gram(const GramConsts &g, double fa,
     const double Q = combine(qh, ql, g.scaleH, 4096.0f);
     const double ta = sa * g.inv_phi[pa], tb = sb * g.inv_phi[pb];
     return 64.0 * fa * fb + fa * tb * Wb + fb * ta * Wa + ta * tb * Q;
+}
+
+// Tensor-core form of block_dot_gram, 16 blocks per warp.  Y_s = C_b H_s
+// (plus the column w_s) on mma.sync m16n8k16 with fp16 digits of H_s and w_s
+// (|digit| <= 2^10, exact in fp16) and fp16 codes; every product sum is an
+// integer below 2^22, exact in the fp32 accumulators.  Then, per row of the
+// accumulator fragment, sum_k ca_k Y_s[k] with Y split into exact 12-bit
+// halves, reduced over the four lanes that hold the row.
+struct GramTC {
+    uint2 bfrag[kSlices][2][4][32];  // [slice][k-step][n-tile][lane]: H_s (columns 0..27) and w_s (column 28)
+    float wl[kSlices][32][8];        // w_s digits at the 8 code positions a lane holds
+    double scaleH[kSlices], scaleW[kSlices];
+    double inv_phi[256];
+};
+
+__device__ __forceinline__ void mma_f16x(float (&c)[4], const uint32_t (&a)[4], uint2 b)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b.x), "r"(b.y));
+}
+
+__device__ __forceinline__ uint32_t code_pair_h(const int8_t *__restrict__ c, int k, bool valid)
+{
+    if (!valid || k >= kKeep) return 0u;
+    const uint16_t v = __ldg(reinterpret_cast<const uint16_t *>(c + k));
+    const __half lo = __short2half_rn((short)(int8_t)(uint8_t)(v & 0xFF));
+    const __half hi = __short2half_rn((short)(int8_t)(uint8_t)(v >> 8));
+    return (uint32_t)__half_as_ushort(lo) | ((uint32_t)__half_as_ushort(hi) << 16);
+}
+
+__device__ __forceinline__ float half_lo(uint32_t p) { return __half2float(__ushort_as_half((unsigned short)(p & 0xFFFF))); }
+__device__ __forceinline__ float half_hi(uint32_t p) { return __half2float(__ushort_as_half((unsigned short)(p >> 16))); }
+
+__global__ void __launch_bounds__(kDotThreads)
+    k_dot_tc(const __grid_constant__ GramTC g, int64_t nb, const double *__restrict__ fa, const double *__restrict__ sa,
+             const uint8_t *__restrict__ pa, const int8_t *__restrict__ ca, const double *__restrict__ fb,
+             const double *__restrict__ sb, const uint8_t *__restrict__ pb, const int8_t *__restrict__ cb,
+             double *__restrict__ partials, unsigned *__restrict__ counter, double *__restrict__ result)
+{
+    __shared__ uint2 sbf[kSlices][2][4][32];
+    __shared__ float swl[kSlices][32][8];
+    __shared__ double red[kDotThreads / 32];
+    __shared__ bool last;
+    for (int i = threadIdx.x; i < kSlices * 2 * 4 * 32; i += blockDim.x) (&sbf[0][0][0][0])[i] = (&g.bfrag[0][0][0][0])[i];
+    for (int i = threadIdx.x; i < kSlices * 32 * 8; i += blockDim.x) (&swl[0][0][0])[i] = (&g.wl[0][0][0])[i];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gq = lane >> 2, t = lane & 3;
+    const int wpc = blockDim.x >> 5;
+    const int64_t ngroups = (nb + 15) / 16;
+    double acc = 0.0;
+    for (int64_t grp = (int64_t)blockIdx.x * wpc + warp; grp < ngroups; grp += (int64_t)gridDim.x * wpc) {
+        const int64_t bA = grp * 16 + gq, bB = bA + 8;
+        const bool vA = bA < nb, vB = bB < nb;
+        // A fragments: codes of B-matrix blocks (rows gq and gq + 8).
+        const int8_t *cbA = cb + bA * kKeep, *cbB = cb + bB * kKeep;
+        uint32_t a0[4], a1[4];
+        a0[0] = code_pair_h(cbA, 2 * t, vA);
+        a0[1] = code_pair_h(cbB, 2 * t, vB);
+        a0[2] = code_pair_h(cbA, 2 * t + 8, vA);
+        a0[3] = code_pair_h(cbB, 2 * t + 8, vB);
+        a1[0] = code_pair_h(cbA, 16 + 2 * t, vA);
+        a1[1] = code_pair_h(cbB, 16 + 2 * t, vB);
+        a1[2] = code_pair_h(cbA, 24 + 2 * t, vA);
+        a1[3] = code_pair_h(cbB, 24 + 2 * t, vB);
+        // ca at the 8 code positions this lane holds (k = nt*8 + 2t + {0,1}), rows gq and gq+8.
+        float xa[2][8];
+        {
+            const int8_t *caA = ca + bA * kKeep, *caB = ca + bB * kKeep;
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+                const uint32_t pA = code_pair_h(caA, nt * 8 + 2 * t, vA), pB = code_pair_h(caB, nt * 8 + 2 * t, vB);
+                xa[0][2 * nt] = half_lo(pA);
+                xa[0][2 * nt + 1] = half_hi(pA);
+                xa[1][2 * nt] = half_lo(pB);
+                xa[1][2 * nt + 1] = half_hi(pB);
+            }
+        }
+        float qh[2][kSlices], ql[2][kSlices], wbs[2][kSlices], was[2][kSlices];
+#pragma unroll
+        for (int sl = 0; sl < kSlices; ++sl) {
+            float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f, w0 = 0.f, w1 = 0.f, wa0 = 0.f, wa1 = 0.f;
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+                float c[4] = {0.f, 0.f, 0.f, 0.f};
+                mma_f16x(c, a0, sbf[sl][0][nt][lane]);
+                mma_f16x(c, a1, sbf[sl][1][nt][lane]);
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int k = nt * 8 + 2 * t + q;
+                    if (k < kKeep) {
+                        const float y0 = c[q], y1 = c[2 + q];
+                        const float yh0 = rintf(y0 * (1.0f / 4096.0f)), yh1 = rintf(y1 * (1.0f / 4096.0f));
+                        h0 = fmaf(xa[0][2 * nt + q], yh0, h0);
+                        l0 = fmaf(xa[0][2 * nt + q], fmaf(-4096.0f, yh0, y0), l0);
+                        h1 = fmaf(xa[1][2 * nt + q], yh1, h1);
+                        l1 = fmaf(xa[1][2 * nt + q], fmaf(-4096.0f, yh1, y1), l1);
+                        const float wd = swl[sl][lane][2 * nt + q];
+                        wa0 = fmaf(xa[0][2 * nt + q], wd, wa0);
+                        wa1 = fmaf(xa[1][2 * nt + q], wd, wa1);
+                    } else if (k == kKeep) {  // column 28: w_s . cb
+                        w0 = c[q];
+                        w1 = c[2 + q];
+                    }
+                }
+            }
+            // reduce over the four lanes of the row (exact integer sums)
+#pragma unroll
+            for (int o = 1; o < 4; o <<= 1) {
+                h0 += __shfl_xor_sync(0xffffffffu, h0, o);
+                l0 += __shfl_xor_sync(0xffffffffu, l0, o);
+                h1 += __shfl_xor_sync(0xffffffffu, h1, o);
+                l1 += __shfl_xor_sync(0xffffffffu, l1, o);
+                w0 += __shfl_xor_sync(0xffffffffu, w0, o);
+                w1 += __shfl_xor_sync(0xffffffffu, w1, o);
+                wa0 += __shfl_xor_sync(0xffffffffu, wa0, o);
+                wa1 += __shfl_xor_sync(0xffffffffu, wa1, o);
+            }
+            qh[0][sl] = h0;
+            ql[0][sl] = l0;
+            qh[1][sl] = h1;
+            ql[1][sl] = l1;
+            wbs[0][sl] = w0;
+            wbs[1][sl] = w1;
+            was[0][sl] = wa0;
+            was[1][sl] = wa1;
+        }
+        // Binary64 tail on 16 lanes: lane t = 0 takes row gq (block bA), t = 1 row gq + 8.
+        // The slices are assembled in int64 (slices 0-2 and 3-4), then two fp64 ops each.
+        if (t < 2) {
+            const int h = t;
+            const int64_t b = h ? bB : bA;
+            if (h ? vB : vA) {
+                long long qhi = 0, qlo = 0, ahi = 0, alo = 0, bhi = 0, blo = 0;
+#pragma unroll
+                for (int sl = 0; sl < kSlices; ++sl) {
+                    const float vqh = h ? qh[1][sl] : qh[0][sl], vql = h ? ql[1][sl] : ql[0][sl];
+                    const float vwa = h ? was[1][sl] : was[0][sl], vwb = h ? wbs[1][sl] : wbs[0][sl];
+                    const long long T = 4096ll * f2i_exact(vqh) + f2i_exact(vql);
+                    const long long A = f2i_exact(vwa), Bw = f2i_exact(vwb);
+                    if (sl < 3) {
+                        qhi = qhi * 2048 + T;
+                        ahi = ahi * 2048 + A;
+                        bhi = bhi * 2048 + Bw;
+                    } else {
+                        qlo = qlo * 2048 + T;
+                        alo = alo * 2048 + A;
+                        blo = blo * 2048 + Bw;
+                    }
+                }
+                const double Q = fma(g.scaleH[2], i64_to_double(qhi), g.scaleH[4] * i64_to_double(qlo));
+                const double Wa = fma(g.scaleW[2], i64_to_double(ahi), g.scaleW[4] * i64_to_double(alo));
+                const double Wb = fma(g.scaleW[2], i64_to_double(bhi), g.scaleW[4] * i64_to_double(blo));
+                const double ta = sa[b] * g.inv_phi[pa[b]], tb = sb[b] * g.inv_phi[pb[b]];
+                const double f_a = fa[b], f_b = fb[b];
+                acc += 64.0 * f_a * f_b + f_a * tb * Wb + f_b * ta * Wa + ta * tb * Q;
+            }
+        }
+    }
+    const double tot = cta_sum(acc, red);
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = tot;
+        __threadfence();
+        last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double v = 0.0;
+    for (int q = threadIdx.x; q < (int)gridDim.x; q += blockDim.x) v += __ldcg(partials + q);
+    const double r = cta_sum(v, red);
+    if (threadIdx.x == 0) {
+        *result = r;
+        *counter = 0u;
+    }
 }
 
 // Flattened dot.  Every CTA writes its partial sum; the last CTA to finish
@@ -277,9 +455,50 @@ static const RowColConsts &rowcol_consts()
     return g;
 }
 
+static const GramTC &gram_tc()
+{
+    static GramTC tcc;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        const GramConsts &gc = gram_consts();
+        auto h2 = [](float lo, float hi) {
+            const __half a = __float2half_rn(lo), b = __float2half_rn(hi);
+            return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
+        };
+        // B[k = l (code of cb)][n]: n < 28 -> H_s[n][l]; n == 28 -> w_s[l]; else 0.
+        auto bval = [&](int s, int l, int n) -> float {
+            if (l >= kKeep) return 0.0f;
+            if (n < kKeep) return gc.H[s][n][l];
+            if (n == kKeep) return gc.w[s][l];
+            return 0.0f;
+        };
+        for (int s = 0; s < kSlices; ++s)
+            for (int ks = 0; ks < 2; ++ks)
+                for (int nt = 0; nt < 4; ++nt)
+                    for (int lane = 0; lane < 32; ++lane) {
+                        const int gg = lane >> 2, t = lane & 3, n = nt * 8 + gg, k = ks * 16 + 2 * t;
+                        tcc.bfrag[s][ks][nt][lane].x = h2(bval(s, k, n), bval(s, k + 1, n));
+                        tcc.bfrag[s][ks][nt][lane].y = h2(bval(s, k + 8, n), bval(s, k + 9, n));
+                    }
+        for (int s = 0; s < kSlices; ++s)
+            for (int lane = 0; lane < 32; ++lane)
+                for (int nt = 0; nt < 4; ++nt)
+                    for (int q = 0; q < 2; ++q) {
+                        const int k = nt * 8 + 2 * (lane & 3) + q;
+                        tcc.wl[s][lane][2 * nt + q] = k < kKeep ? gc.w[s][k] : 0.0f;
+                    }
+        for (int s = 0; s < kSlices; ++s) {
+            tcc.scaleH[s] = gc.scaleH[s];
+            tcc.scaleW[s] = gc.scaleW[s];
+        }
+        for (int p = 0; p < 256; ++p) tcc.inv_phi[p] = gc.inv_phi[p];
+    });
+    return tcc;
+}
+
 int dot_grid(int64_t nb)
 {
-    int64_t want = (nb + kDotThreads - 1) / kDotThreads;
+    int64_t want = ((nb + 15) / 16 + (kDotThreads / 32) - 1) / (kDotThreads / 32);
     int64_t cap = (int64_t)num_sms() * 4;
     if (want > cap) want = cap;
     return (int)(want < 1 ? 1 : want);
@@ -291,8 +510,8 @@ int launch_dot(const blaz_cmat *a, const blaz_cmat *b, double *result, double *p
     const int64_t nb = (a->rows / 8) * (a->cols / 8);
     int grid = dot_grid(nb);
     if (grid > max_ctas) grid = (int)max_ctas;
-    k_dot<<<grid, kDotThreads, 0, st>>>(gram_consts(), nb, a->f, a->s, a->phi, a->code, b->f, b->s, b->phi,
-                                        b->code, partials, counter, result);
+    k_dot_tc<<<grid, kDotThreads, 0, st>>>(gram_tc(), nb, a->f, a->s, a->phi, a->code, b->f, b->s, b->phi,
+                                           b->code, partials, counter, result);
     return launch_status();
 }
 
