@@ -101,7 +101,7 @@ void blaz_constants(double cos_out[64], double aa_out[64], int32_t kept_out[56])
 int blaz_compress(const double *A, int64_t lda, blaz_cmat *out, void *stream);
 /* (blaz_compress decides most of the DCT in fp32 under a proven error bound
  * and recomputes the blocks it cannot certify in binary64, so the result is
- * the same bits; it uses 8 bytes per block of stream-ordered scratch.) */
+ * the same bits; it uses 12 bytes per block of stream-ordered scratch.) */
 
 /* Decompression (inverse of Sec. II; Eq. eqbbb read as the exact inverse of
  * Eq. eqnorm): X = code/phi on the kept positions, 0 elsewhere;

@@ -22,7 +22,10 @@
 //     |D_f - X| <= (2u + u + 8u + u + 8u + 2u + O(u^2)) aa_ij S2_ij + 2^-100
 // against the binary64 coefficient X of the specification, whose own error
 // (17 roundings of 2^-53) is far below u; S2_ij = sum_uv |c_iu c_jv D'_uv|
-// <= sum |D'| < K + 1.  The kernel uses E_ij = 32u aa_ij (K+1) + 2^-100.
+// <= sum |D'| < K + 1, and also S2_ij <= max|D'| C1_i C1_j <= 8 max|D'|
+// with C1_k = sum_x |cos_kx| (C1_0 = C1_4 = 2 sqrt 2 is the largest).  The
+// kernel uses
+//     E_ij = 24u aa_ij min(K + 1, 8.0001 max|D'|) + 2^-100.
 #pragma once
 
 #include "block_codec.cuh"
@@ -162,6 +165,10 @@ __device__ __forceinline__ uint32_t compress_block_fast(double (&d)[64], double 
     // chain, cos(0) = 1) and fp32 inner sums T[u][j] for j >= 1.
     float T[8][8];
     double U00 = 0.0;
+    // max |D'| <= smaxf (1 + 2^-23) + 2^-126 (truncated fp32 rows); since
+    // max |D'| >= 1 (s is the mean of the nonzero |D|) the 8.0001 factor
+    // below covers both terms.
+    float smaxf = 0.0f;
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
         double row[8];
@@ -173,7 +180,10 @@ __device__ __forceinline__ uint32_t compress_block_fast(double (&d)[64], double 
         U00 = (u == 0) ? t0 : dadd(U00, t0);
         float rf[8];
 #pragma unroll
-        for (int v = 0; v < 8; ++v) rf[v] = trunc_f32(row[v]);
+        for (int v = 0; v < 8; ++v) {
+            rf[v] = trunc_f32(row[v]);
+            smaxf = fmaxf(smaxf, fabsf(rf[v]));
+        }
         T[u][0] = trunc_f32(t0);
 #pragma unroll
         for (int j = 1; j < 8; ++j) {
@@ -186,7 +196,8 @@ __device__ __forceinline__ uint32_t compress_block_fast(double (&d)[64], double 
     const double X00 = dmul(BLAZ_A00, U00);
 
     // Outer sums in fp32; bounds on max |X| over the other 63 coefficients.
-    const float base = 32.0f * 0x1p-24f * (float)(K + 1);
+    // E_ij / aa_ij, one factor for the block.
+    const float base = 24.0f * 0x1p-24f * fminf((float)(K + 1), smaxf * 8.0001f);
     float Dk[kKeep];
     float mlo = 0.0f, mhi = 0.0f;
 #pragma unroll

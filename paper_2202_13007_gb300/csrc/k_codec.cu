@@ -4,10 +4,10 @@
 // Compression is bit-exact binary64: every operation is an explicit
 // round-to-nearest intrinsic in the order fixed in include/blaz.h, so the
 // result does not depend on -fmad or on the compiler's scheduling.  The
-// compressor runs in two kernels: k_compress_fast decides every block it can
-// certify (compress_fast.cuh) and lists the others; k_compress_fix
-// recompresses the listed blocks with the exact binary64 path, densely (one
-// listed block per thread), so the rare exact blocks cost no warp divergence.
+// compressor runs in three kernels: k_compress_fast decides every block it
+// can certify (compress_fast.cuh) and lists the codes (or whole blocks) it
+// cannot; k_compress_fix_codes and k_compress_fix_blocks evaluate those
+// exactly in binary64, densely, so the rare exact work costs no divergence.
 #include <mutex>
 
 #include <cuda_fp16.h>
@@ -17,11 +17,27 @@
 
 namespace blaz {
 
+// Warp-aggregated append of `value` for the lanes where `want` holds.
+template <typename T>
+__device__ __forceinline__ void append(bool want, T value, T *__restrict__ list, unsigned *__restrict__ count)
+{
+    const unsigned act = __activemask();
+    const unsigned need = __ballot_sync(act, want);
+    if (!need) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(need) - 1;
+    unsigned base = 0;
+    if (lane == leader) base = atomicAdd(count, (unsigned)__popc(need));
+    base = __shfl_sync(act, base, leader);
+    if (want) list[base + __popc(need & ((1u << lane) - 1u))] = value;
+}
+
 template <bool kVec>
 __global__ void __launch_bounds__(128)
     k_compress_fast(const double *__restrict__ A, int64_t lda, int64_t nbc, int64_t nb, double *__restrict__ f,
                     double *__restrict__ s, uint8_t *__restrict__ phi, int8_t *__restrict__ code,
-                    uint2 *__restrict__ fix_list, unsigned *__restrict__ fix_count)
+                    uint2 *__restrict__ code_list, unsigned *__restrict__ code_count,
+                    unsigned *__restrict__ block_list, unsigned *__restrict__ block_count)
 {
     for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x) {
         const int64_t bi = b / nbc, bj = b - (b / nbc) * nbc;
@@ -37,50 +53,135 @@ __global__ void __launch_bounds__(128)
             phi[b] = ph;
             store_codes(code + b * kKeep, c);
         }
-        // Append the blocks with undecided codes, one atomic per warp.
-        const unsigned act = __activemask();
-        const unsigned need = __ballot_sync(act, pending != 0u);
-        if (need) {
-            const int lane = threadIdx.x & 31;
-            const int leader = __ffs(need) - 1;
-            unsigned base = 0;
-            if (lane == leader) base = atomicAdd(fix_count, (unsigned)__popc(need));
-            base = __shfl_sync(act, base, leader);
-            if (pending) fix_list[base + __popc(need & ((1u << lane) - 1u))] = make_uint2((unsigned)b, pending);
+        // Undecided codes and whole blocks go to separate lists, so that the
+        // fix-up kernels run without divergence between the two cases.
+        append(pending != 0u && pending != kPendingAll, make_uint2((unsigned)b, pending), code_list, code_count);
+        append(pending == kPendingAll, (unsigned)b, block_list, block_count);
+    }
+}
+
+// Row u of D' for block b, exactly as compress_block forms it: Eq. eqnorm
+// from rows u and u-1 of the input, then times r = 1/s (s as stored).
+template <bool kVec>
+__device__ __forceinline__ void team_dprime_row(const double *__restrict__ A, int64_t lda, int64_t nbc, int64_t b,
+                                                int u, double s, double (&dp)[8])
+{
+    const int64_t bi = b / nbc, bj = b - (b / nbc) * nbc;
+    const double *p = A + (bi * 8) * lda + bj * 8;
+    double cur[8], prev[8];
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+        cur[v] = __ldg(p + u * lda + v);
+        prev[v] = u > 0 ? __ldg(p + (u - 1) * lda + v) : 0.0;
+    }
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+        if (u == 0) dp[v] = v == 0 ? 0.0 : dsub(cur[v], cur[v - 1]);
+        else if (v == 0) dp[v] = dsub(cur[0], prev[0]);
+        else dp[v] = dhalf(dadd(dsub(cur[v], prev[v]), dsub(cur[v], cur[v - 1])));
+    }
+    const double r = ddiv(1.0, s);
+#pragma unroll
+    for (int v = 0; v < 8; ++v) dp[v] = dmul(dp[v], r);
+}
+
+// Whole blocks whose phi was not certified (or with non-finite values): the
+// exact binary64 compressor by a team of 8 lanes per listed block.  s is
+// already exact (k_compress_fast stores it for every block).  Lane u forms
+// row u of D' and the inner sums T_j[u] of all eight columns; lane i then
+// forms U[i][j] = sum_u cos_iu T_j[u] in the specified order from the
+// team's shuffles, X[i][j], and its share of m = max |X| (NaN ignored, as in
+// compress_block: the maximum of non-NaN values is order-free).
+template <bool kVec>
+__global__ void __launch_bounds__(128)
+    k_compress_fix_blocks(const double *__restrict__ A, int64_t lda, int64_t nbc, const unsigned *__restrict__ list,
+                          const unsigned *__restrict__ count, const double *__restrict__ s,
+                          uint8_t *__restrict__ phi, int8_t *__restrict__ code)
+{
+    const int lane = threadIdx.x & 31, u = lane & 7, tbase = lane & ~7;
+    const unsigned tmask = 0xFFu << tbase;
+    double ci[8];  // cos_{u,x}: this lane's row of the cosine table as output row i = u
+#pragma unroll
+    for (int x = 0; x < 8; ++x) ci[x] = c_cos[u * 8 + x];
+    const int64_t n = *count;
+    const int64_t teams = (int64_t)gridDim.x * blockDim.x / 8;
+    for (int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 8; q < n; q += teams) {
+        const int64_t b = list[q];
+        double dp[8];
+        team_dprime_row<kVec>(A, lda, nbc, b, u, s[b], dp);
+        double T[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            double acc = (j == 0) ? dp[0] : dmul(dp[0], cos_tab(j, 0));
+#pragma unroll
+            for (int v = 1; v < 8; ++v) acc = dadd(acc, (j == 0) ? dp[v] : dmul(dp[v], cos_tab(j, v)));
+            T[j] = acc;
+        }
+        double U[8];
+#pragma unroll
+        for (int uu = 0; uu < 8; ++uu) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const double Tu = __shfl_sync(tmask, T[j], tbase + uu);
+                const double term = (u == 0) ? Tu : dmul(ci[uu], Tu);
+                U[j] = (uu == 0) ? term : dadd(U[j], term);
+            }
+        }
+        double m = 0.0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            U[j] = dmul((u == 0 && j == 0) ? BLAZ_A00 : (u == 0 || j == 0) ? BLAZ_A0K : BLAZ_AKK, U[j]);
+            const double ax = fabs(U[j]);
+            m = (ax > m) ? ax : m;
+        }
+#pragma unroll
+        for (int off = 4; off; off >>= 1) {
+            const double o = __shfl_xor_sync(tmask, m, off);
+            m = (o > m) ? o : m;
+        }
+        const int ph = phi_of(m);
+        const double phd = i64_to_double(ph);
+        if (u == 0) phi[b] = (uint8_t)ph;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int t = kept_index(u, j);
+            if (t >= 0) code[b * kKeep + t] = quantize_bits(dmul(U[j], phd));
         }
     }
 }
 
-// The listed blocks: the whole exact compressor (compress_block) when phi was
-// not certified, else the exact binary64 value of each undecided code.
 template <bool kVec>
 __global__ void __launch_bounds__(128)
-    k_compress_fix(const double *__restrict__ A, int64_t lda, int64_t nbc, const uint2 *__restrict__ fix_list,
-                   const unsigned *__restrict__ fix_count, double *__restrict__ f, double *__restrict__ s,
-                   uint8_t *__restrict__ phi, int8_t *__restrict__ code)
+    k_compress_fix_codes(const double *__restrict__ A, int64_t lda, int64_t nbc, const uint2 *__restrict__ list,
+                         const unsigned *__restrict__ count, const double *__restrict__ s,
+                         const uint8_t *__restrict__ phi, int8_t *__restrict__ code)
 {
-    const int64_t n = *fix_count;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
-        const uint2 e = fix_list[q];
+    const int lane = threadIdx.x & 31, u = lane & 7, tbase = lane & ~7;
+    const unsigned tmask = 0xFFu << tbase;
+    const int64_t n = *count;
+    const int64_t teams = (int64_t)gridDim.x * blockDim.x / 8;
+    for (int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 8; q < n; q += teams) {
+        const uint2 e = list[q];
         const int64_t b = e.x;
-        const int64_t bi = b / nbc, bj = b - (b / nbc) * nbc;
-        double d[64];
-        load_block<kVec>(A, lda, bi, bj, d);
-        if (e.y == kPendingAll) {
-            f[b] = d[0];
-            double sv;
-            uint8_t ph;
-            int8_t c[kKeep];
-            compress_block(d, sv, ph, c);
-            s[b] = sv;
-            phi[b] = ph;
-            store_codes(code + b * kKeep, c);
-        } else {
-            exact_dprime(d, s[b]);
-            const int p = phi[b];
-            for (uint32_t m = e.y; m; m &= m - 1) {
-                const int t = __ffs(m) - 1;
-                code[b * kKeep + t] = exact_code(d, t, p);
+        double dp[8];
+        team_dprime_row<kVec>(A, lda, nbc, b, u, s[b], dp);
+        const int ph = phi[b];
+        for (uint32_t m = e.y; m; m &= m - 1) {
+            const int t = __ffs(m) - 1;
+            const int i = kept_row(t), j = kept_col(t);
+            double T = (j == 0) ? dp[0] : dmul(dp[0], c_cos[j * 8]);
+#pragma unroll
+            for (int v = 1; v < 8; ++v) T = dadd(T, (j == 0) ? dp[v] : dmul(dp[v], c_cos[j * 8 + v]));
+            double U = 0.0;
+#pragma unroll
+            for (int uu = 0; uu < 8; ++uu) {
+                const double Tu = __shfl_sync(tmask, T, tbase + uu);
+                const double term = (i == 0) ? Tu : dmul(c_cos[i * 8 + uu], Tu);
+                U = (uu == 0) ? term : dadd(U, term);
+            }
+            if (u == 0) {
+                const double aa = (i == 0 && j == 0) ? BLAZ_A00 : (i == 0 || j == 0) ? BLAZ_A0K : BLAZ_AKK;
+                code[b * kKeep + t] = quantize_bits(dmul(dmul(aa, U), i64_to_double(ph)));
             }
         }
     }
@@ -237,26 +338,40 @@ static int grid_for(int64_t nb, int threads)
 
 static bool vec_ok(const void *p, int64_t ld) { return ((uintptr_t)p % 16 == 0) && (ld % 2 == 0); }
 
-size_t compress_scratch_bytes(int64_t nb) { return ((size_t)nb * 8 + 255) / 256 * 256 + 256; }
+size_t compress_scratch_bytes(int64_t nb)
+{
+    auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+    return up((size_t)nb * 8) + up((size_t)nb * 4) + 256;
+}
 
 int launch_compress(const double *A, int64_t lda, const blaz_cmat *out, void *scratch, cudaStream_t st)
 {
     const int64_t nbc = out->cols / 8, nb = (out->rows / 8) * nbc;
     if (nb == 0) return BLAZ_OK;
     if (nb > 0xFFFFFFFFll) return BLAZ_ERR_SHAPE;
-    uint2 *list = (uint2 *)scratch;
-    unsigned *count = (unsigned *)((char *)scratch + compress_scratch_bytes(nb) - 256);
-    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned), st);
+    auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+    uint2 *code_list = (uint2 *)scratch;
+    unsigned *block_list = (unsigned *)((char *)scratch + up((size_t)nb * 8));
+    unsigned *counts = (unsigned *)((char *)scratch + up((size_t)nb * 8) + up((size_t)nb * 4));
+    cudaError_t e = cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned), st);
     if (e != cudaSuccess) return set_cuda_error(e);
     const int threads = 128;
     const int grid = grid_for(nb, threads);
-    const int fix_grid = num_sms() * 4;
+    const int fix_grid = num_sms() * 8;
     if (vec_ok(A, lda)) {
-        k_compress_fast<true><<<grid, threads, 0, st>>>(A, lda, nbc, nb, out->f, out->s, out->phi, out->code, list, count);
-        k_compress_fix<true><<<fix_grid, threads, 0, st>>>(A, lda, nbc, list, count, out->f, out->s, out->phi, out->code);
+        k_compress_fast<true><<<grid, threads, 0, st>>>(A, lda, nbc, nb, out->f, out->s, out->phi, out->code,
+                                                         code_list, counts, block_list, counts + 1);
+        k_compress_fix_blocks<true><<<fix_grid, threads, 0, st>>>(A, lda, nbc, block_list, counts + 1, out->s,
+                                                                   out->phi, out->code);
+        k_compress_fix_codes<true><<<fix_grid, threads, 0, st>>>(A, lda, nbc, code_list, counts, out->s, out->phi,
+                                                                  out->code);
     } else {
-        k_compress_fast<false><<<grid, threads, 0, st>>>(A, lda, nbc, nb, out->f, out->s, out->phi, out->code, list, count);
-        k_compress_fix<false><<<fix_grid, threads, 0, st>>>(A, lda, nbc, list, count, out->f, out->s, out->phi, out->code);
+        k_compress_fast<false><<<grid, threads, 0, st>>>(A, lda, nbc, nb, out->f, out->s, out->phi, out->code,
+                                                          code_list, counts, block_list, counts + 1);
+        k_compress_fix_blocks<false><<<fix_grid, threads, 0, st>>>(A, lda, nbc, block_list, counts + 1, out->s,
+                                                                    out->phi, out->code);
+        k_compress_fix_codes<false><<<fix_grid, threads, 0, st>>>(A, lda, nbc, code_list, counts, out->s, out->phi,
+                                                                   out->code);
     }
     return launch_status();
 }

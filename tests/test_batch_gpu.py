@@ -147,6 +147,30 @@ def test_small_batch_against_oracle(B):
     plan.free()
 
 
+def test_batch_compress_at_certification_boundaries(B, boundary_blocks):
+    """The batch kernel's compressor (certified fp32 decisions, exact
+    binary64 fix-up inside the item) on the blocks closest to a phi or code
+    rounding boundary, against the oracle bit for bit."""
+    blk = boundary_blocks[0]
+    X = np.ascontiguousarray(blk.transpose(1, 0, 2).reshape(8, -1))
+    Y = np.concatenate([X, X[:, ::-1]], axis=0)
+    ops, outs = [], []
+    for M in (X, Y):
+        out = B.CMat.empty(*M.shape)
+        ops.append({"op": "compress", "A": torch.from_numpy(M).cuda(), "out": out})
+        outs.append((M, out))
+    plan = B.Batch(ops, blocks_per_item=16)
+    plan.run()
+    torch.cuda.synchronize()
+    for M, out in outs:
+        oc = O.compress(M)
+        f, s, phi, code = out.to_host()
+        assert np.array_equal(phi, oc.phi) and np.array_equal(code, oc.code)
+        assert np.array_equal(s.view(np.uint64), oc.s.view(np.uint64))
+        assert np.array_equal(f.view(np.uint64), oc.f.view(np.uint64))
+    plan.free()
+
+
 def test_autotuned_batch_and_aliasing_rule(B):
     specs = W.batch_ops(count=30, seed=8, lo=64, hi=512)
     ops, meta = make_batch(B, specs)

@@ -117,6 +117,19 @@ def test_compress_special_values(B):
     assert_cmat_equal(B.compress(dev(X)), O.compress(X))
 
 
+def test_compress_certification_boundaries(B, boundary_blocks):
+    blk, dphi, dcode = boundary_blocks
+    # the selection does reach the region where fp32 certification fails
+    assert np.min(dphi) < 1e-6 and np.min(dcode) < 1e-7
+    X = np.ascontiguousarray(blk.transpose(1, 0, 2).reshape(8, -1))
+    assert_cmat_equal(B.compress(dev(X)), O.compress(X))
+    # the same blocks with a ragged second block row and a strided view
+    Y = np.concatenate([X, X[:, ::-1]], axis=0)
+    tb = torch.zeros((16, Y.shape[1] + 8), dtype=torch.float64, device="cuda")
+    tb[:, 8:] = dev(Y)
+    assert_cmat_equal(B.compress(tb[:, 8:]), O.compress(Y))
+
+
 @pytest.mark.parametrize("shape", [(0, 0), (0, 16), (16, 0)])
 def test_empty_matrices(B, shape):
     X = torch.zeros(shape, dtype=torch.float64, device="cuda")
