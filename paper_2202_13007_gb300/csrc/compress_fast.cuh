@@ -112,6 +112,51 @@ __device__ __forceinline__ double dmax_nonneg(double a, double b)
     return __double_as_longlong(a) >= __double_as_longlong(b) ? a : b;
 }
 
+// 1 when x != 0 (NaN included), 0 for +-0, on the integer pipe: the OR of
+// the magnitude bits goes through inline PTX so that the compiler cannot
+// fold the test back into a binary64 comparison.
+__device__ __forceinline__ int nonzero_bits(double x)
+{
+    unsigned m;
+    asm("or.b32 %0, %1, %2;" : "=r"(m) : "r"((unsigned)__double2hiint(x) << 1), "r"((unsigned)__double2loint(x)));
+    return m != 0u;
+}
+
+// RN(1/k) for k = 1..64 (entry k-1), exact hex literals.
+__device__ __align__(16) double c_rcp_k[64] = {
+    0x1.0000000000000p+0, 0x1.0000000000000p-1, 0x1.5555555555555p-2, 0x1.0000000000000p-2,
+    0x1.999999999999ap-3, 0x1.5555555555555p-3, 0x1.2492492492492p-3, 0x1.0000000000000p-3,
+    0x1.c71c71c71c71cp-4, 0x1.999999999999ap-4, 0x1.745d1745d1746p-4, 0x1.5555555555555p-4,
+    0x1.3b13b13b13b14p-4, 0x1.2492492492492p-4, 0x1.1111111111111p-4, 0x1.0000000000000p-4,
+    0x1.e1e1e1e1e1e1ep-5, 0x1.c71c71c71c71cp-5, 0x1.af286bca1af28p-5, 0x1.999999999999ap-5,
+    0x1.8618618618618p-5, 0x1.745d1745d1746p-5, 0x1.642c8590b2164p-5, 0x1.5555555555555p-5,
+    0x1.47ae147ae147bp-5, 0x1.3b13b13b13b14p-5, 0x1.2f684bda12f68p-5, 0x1.2492492492492p-5,
+    0x1.1a7b9611a7b96p-5, 0x1.1111111111111p-5, 0x1.0842108421084p-5, 0x1.0000000000000p-5,
+    0x1.f07c1f07c1f08p-6, 0x1.e1e1e1e1e1e1ep-6, 0x1.d41d41d41d41dp-6, 0x1.c71c71c71c71cp-6,
+    0x1.bacf914c1bad0p-6, 0x1.af286bca1af28p-6, 0x1.a41a41a41a41ap-6, 0x1.999999999999ap-6,
+    0x1.8f9c18f9c18fap-6, 0x1.8618618618618p-6, 0x1.7d05f417d05f4p-6, 0x1.745d1745d1746p-6,
+    0x1.6c16c16c16c17p-6, 0x1.642c8590b2164p-6, 0x1.5c9882b931057p-6, 0x1.5555555555555p-6,
+    0x1.4e5e0a72f0539p-6, 0x1.47ae147ae147bp-6, 0x1.4141414141414p-6, 0x1.3b13b13b13b14p-6,
+    0x1.3521cfb2b78c1p-6, 0x1.2f684bda12f68p-6, 0x1.29e4129e4129ep-6, 0x1.2492492492492p-6,
+    0x1.1f7047dc11f70p-6, 0x1.1a7b9611a7b96p-6, 0x1.15b1e5f75270dp-6, 0x1.1111111111111p-6,
+    0x1.0c9714fbcda3bp-6, 0x1.0842108421084p-6, 0x1.0410410410410p-6, 0x1.0000000000000p-6};
+
+// s = RN(S/K) for an integer count 1 <= K <= 64 by one product and two fused
+// corrections (Markstein's theorem: with y = RN(1/K), q a faithful quotient
+// and the exact remainder r = S - K q, RN(q + r y) is the correctly rounded
+// quotient); used for 2^-900 <= S < Inf, where neither step can leave the
+// normal range.  Other S take the general division.
+__device__ __forceinline__ double div_by_count(double S, int K)
+{
+    const unsigned es = (unsigned)__double2hiint(S) >> 20;  // S >= 0
+    const double Kd = i64_to_double(K);
+    if (es < 1023 - 900 || es >= 0x7FF) return ddiv(S, Kd);
+    const double y = __ldg(&c_rcp_k[K - 1]);
+    const double q = dmul(S, y);
+    const double r = __fma_rn(-q, Kd, S);
+    return __fma_rn(r, y, q);
+}
+
 constexpr uint32_t kPendingAll = 0x80000000u;  // phi not certified / non-finite: whole block exact
 
 // Compress one block held in d (overwritten).  Returns 0 when every decision
@@ -144,7 +189,7 @@ __device__ __forceinline__ uint32_t compress_block_fast(double (&d)[64], double 
     double S = 0.0;
 #pragma unroll
     for (int p = 0; p < 64; ++p) {
-        K += (__double_as_longlong(d[p]) << 1) != 0;
+        K += nonzero_bits(d[p]);
         S = dadd(S, fabs(d[p]));
     }
     if (K == 0) {
@@ -154,7 +199,7 @@ __device__ __forceinline__ uint32_t compress_block_fast(double (&d)[64], double 
         for (int t = 0; t < kKeep; ++t) code[t] = 0;
         return 0u;
     }
-    const double s = ddiv(S, i64_to_double(K));
+    const double s = div_by_count(S, K);
     const double r = ddiv(1.0, s);
     s_out = s;
     // Inf / NaN / overflow (S >= 0, r >= 0): exact path
@@ -220,18 +265,25 @@ __device__ __forceinline__ uint32_t compress_block_fast(double (&d)[64], double 
     }
     // Eq. eqphi.  m = max(|X00|, max over the others), certified when phi is
     // the same at both ends of the interval of possible m.
+    // phi = trunc(RN(127/m)) in [1, 255] is decided in fp32 from bounds
+    // m_lo <= m <= m_hi: the quotients 127/m_hi, 127/m_lo (correctly rounded,
+    // widened by 2^-20) bound the real 127/m, whose binary64 rounding moves
+    // it by 2^-53 relative, so equal clamped truncations at both ends fix
+    // phi.  When the other coefficients are certainly below |X00|, m = |X00|
+    // exactly and an undecided phi takes the exact division.
     const double ax00 = fabs(X00);
-    // mhi, mlo widened by 2^-20 (relative) in fp32 before the exact conversion
-    const double mhi_d = f2d_bits(mhi * (1.0f + 0x1p-20f));
-    const double mlo_d = f2d_bits(mlo * (1.0f - 0x1p-20f));
-    int phi;
-    if (__double_as_longlong(mhi_d) < __double_as_longlong(ax00)) {
-        phi = phi_of(ax00);  // the DC coefficient is the maximum: m is exact
-    } else {
-        const int p_lo_m = phi_of(dmax_nonneg(ax00, mlo_d));
-        const int p_hi_m = phi_of(dmax_nonneg(ax00, mhi_d));
-        if (p_lo_m != p_hi_m) return kPendingAll;
-        phi = p_hi_m;
+    const float a00 = trunc_f32(ax00);                  // a00 <= |X00| < a00 (1 + 2^-23)
+    const bool m_exact = __double_as_longlong(f2d_bits(mhi * (1.0f + 0x1p-20f))) < __double_as_longlong(ax00);
+    const float m_lo = m_exact ? a00 : fmaxf(a00, mlo * (1.0f - 0x1p-20f));
+    const float m_hi = m_exact ? a00 * (1.0f + 0x1p-22f) : fmaxf(a00 * (1.0f + 0x1p-22f), mhi * (1.0f + 0x1p-20f));
+    const float q_lo = __fdiv_rn(127.0f, m_hi) * (1.0f - 0x1p-20f);
+    const float q_hi = __fdiv_rn(127.0f, m_lo) * (1.0f + 0x1p-20f);
+    const int p_lo = q_lo >= 255.0f ? 255 : (q_lo < 1.0f ? 1 : (int)q_lo);
+    const int p_hi = q_hi >= 255.0f ? 255 : (q_hi < 1.0f ? 1 : (int)q_hi);
+    int phi = p_lo;
+    if (p_lo != p_hi) {
+        if (!m_exact) return kPendingAll;
+        phi = phi_of(ax00);
     }
     phi_out = (uint8_t)phi;
     const float phif = (float)phi;

@@ -32,8 +32,13 @@ __device__ __forceinline__ void append(bool want, T value, T *__restrict__ list,
     if (want) list[base + __popc(need & ((1u << lane) - 1u))] = value;
 }
 
+// CTA size of the fast compressor.  At ~180 registers per thread, small CTAs
+// let more warps share an SM (registers are granted per warp, an SM takes
+// only whole CTAs).
+constexpr int kFastThreads = 64;
+
 template <bool kVec>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(kFastThreads)
     k_compress_fast(const double *__restrict__ A, int64_t lda, int64_t nbc, int64_t nb, double *__restrict__ f,
                     double *__restrict__ s, uint8_t *__restrict__ phi, int8_t *__restrict__ code,
                     uint2 *__restrict__ code_list, unsigned *__restrict__ code_count,
@@ -328,15 +333,17 @@ __global__ void __launch_bounds__(128)
     }
 }
 
-static int grid_for(int64_t nb, int threads)
-{
-    int64_t want = (nb + threads - 1) / threads;
-    int64_t cap = (int64_t)num_sms() * 64;
-    if (want > cap) want = cap;
-    return (int)(want < 1 ? 1 : want);
-}
-
 static bool vec_ok(const void *p, int64_t ld) { return ((uintptr_t)p % 16 == 0) && (ld % 2 == 0); }
+
+// One block per thread: short-lived CTAs keep the warps of an SM at different
+// phases of the block (binary64 normalization, fp32 DCT, integer codes), so
+// the FP64 pipe overlaps the others; a single resident wave of long-lived
+// CTAs runs ~10% slower at 16384^2.
+static int fast_grid(int64_t nb)
+{
+    const int64_t want = (nb + kFastThreads - 1) / kFastThreads;
+    return (int)(want < 1 ? 1 : (want > 0x7FFFFFFF ? 0x7FFFFFFF : want));
+}
 
 size_t compress_scratch_bytes(int64_t nb)
 {
@@ -356,18 +363,19 @@ int launch_compress(const double *A, int64_t lda, const blaz_cmat *out, void *sc
     cudaError_t e = cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned), st);
     if (e != cudaSuccess) return set_cuda_error(e);
     const int threads = 128;
-    const int grid = grid_for(nb, threads);
     const int fix_grid = num_sms() * 8;
     if (vec_ok(A, lda)) {
-        k_compress_fast<true><<<grid, threads, 0, st>>>(A, lda, nbc, nb, out->f, out->s, out->phi, out->code,
-                                                         code_list, counts, block_list, counts + 1);
+        k_compress_fast<true><<<fast_grid(nb), kFastThreads, 0, st>>>(A, lda, nbc, nb, out->f, out->s,
+                                                                      out->phi, out->code, code_list, counts,
+                                                                      block_list, counts + 1);
         k_compress_fix_blocks<true><<<fix_grid, threads, 0, st>>>(A, lda, nbc, block_list, counts + 1, out->s,
                                                                    out->phi, out->code);
         k_compress_fix_codes<true><<<fix_grid, threads, 0, st>>>(A, lda, nbc, code_list, counts, out->s, out->phi,
                                                                   out->code);
     } else {
-        k_compress_fast<false><<<grid, threads, 0, st>>>(A, lda, nbc, nb, out->f, out->s, out->phi, out->code,
-                                                          code_list, counts, block_list, counts + 1);
+        k_compress_fast<false><<<fast_grid(nb), kFastThreads, 0, st>>>(A, lda, nbc, nb, out->f, out->s,
+                                                                       out->phi, out->code, code_list, counts,
+                                                                       block_list, counts + 1);
         k_compress_fix_blocks<false><<<fix_grid, threads, 0, st>>>(A, lda, nbc, block_list, counts + 1, out->s,
                                                                     out->phi, out->code);
         k_compress_fix_codes<false><<<fix_grid, threads, 0, st>>>(A, lda, nbc, code_list, counts, out->s, out->phi,
