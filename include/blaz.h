@@ -93,7 +93,9 @@ void blaz_constants(double cos_out[64], double aa_out[64], int32_t kept_out[56])
  * out: rows/cols set by the caller, arrays preallocated (device).
  * Codes, phi and s are bit-identical to the binary64 operation order
  *   D(i,j) per Eq. eqnorm, interior ((Mij - Mi-1,j) + (Mij - Mi,j-1)) * 0.5;
- *   K = #{D != 0}; S = sum |D| row-major left to right; s = S / K (0 if K = 0);
+ *   K = #{D != 0}; S = sum |D| as a fixed pairwise tree over the row-major
+ *   index p (q[k] = |D_k| + |D_k+32|, k < 32, then q[k] += q[k+h] for
+ *   h = 16, 8, 4, 2, 1; S = q[0]); s = S / K (0 if K = 0);
  *   D' = D * (1/s); T[u][j] = sum_v D'[u][v] cos_jv (v ascending);
  *   U[i][j] = sum_u cos_iu T[u][j] (u ascending); X = RN(alpha_i alpha_j) * U;
  *   m = max |X|; phi = trunc(127/m) clamped to [1,255];

@@ -114,7 +114,7 @@ static int8_t quantize_code(double v)
 typedef struct {
     double delta[64];      /* Eq. eqnorm                                  */
     int32_t K;             /* Eq. eqslope2: number of nonzero deltas      */
-    double sum_abs;        /* sum |delta|, row-major left to right        */
+    double sum_abs;        /* sum |delta|, fixed pairwise tree            */
     double s;              /* Eq. eqslope                                 */
     double dprime[64];     /* (1/s) * delta                               */
     double s_max;          /* max |dprime| (prediction stage)             */
@@ -149,13 +149,18 @@ void blazo_block_stages(const double *M, blazo_stages *st)
         }
     }
 
-    /* Eqs. eqslope, eqslope2 */
+    /* Eqs. eqslope, eqslope2.  The paper leaves the order of the sum open;
+     * it is a fixed pairwise tree over the row-major index p: first
+     * tree[k] = |d[k]| + |d[k+32]| for k < 32, then tree[k] += tree[k+h]
+     * for h = 16, 8, 4, 2, 1 (k < h); S = tree[0]. */
     int K = 0;
-    double S = 0.0;
-    for (int p = 0; p < 64; ++p) {
+    for (int p = 0; p < 64; ++p)
         if (d[p] != 0.0) ++K;
-        S = S + fabs(d[p]);
-    }
+    double tree[32];
+    for (int k = 0; k < 32; ++k) tree[k] = fabs(d[k]) + fabs(d[k + 32]);
+    for (int h = 16; h >= 1; h /= 2)
+        for (int k = 0; k < h; ++k) tree[k] = tree[k] + tree[k + h];
+    double S = tree[0];
     st->K = K;
     st->sum_abs = S;
     double s = 0.0;

@@ -64,6 +64,21 @@ __device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a,
 __device__ __forceinline__ double ddiv(double a, double b) { return __ddiv_rn(a, b); }
 
 // trunc toward zero, saturated to [-127, 127], NaN -> 0.
+// S = sum |D| of Eqs. eqslope / eqslope2 as the fixed pairwise tree over the
+// row-major index: q[k] = |D_k| + |D_k+32| (k < 32), then q[k] += q[k+h] for
+// h = 16, 8, 4, 2, 1; S = q[0].  Depth 6.
+__device__ __forceinline__ double tree_sum_abs(const double (&d)[64])
+{
+    double q[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) q[k] = dadd(fabs(d[k]), fabs(d[k + 32]));
+#pragma unroll
+    for (int h = 16; h >= 1; h >>= 1)
+#pragma unroll
+        for (int k = 0; k < h; ++k) q[k] = dadd(q[k], q[k + h]);
+    return q[0];
+}
+
 __device__ __forceinline__ int8_t quantize(double v)
 {
     if (v != v) return 0;

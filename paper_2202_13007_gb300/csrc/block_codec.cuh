@@ -55,14 +55,11 @@ __device__ __forceinline__ void compress_block(double (&d)[64], double &s_out, u
             }
         }
     }
-    // Eqs. eqslope / eqslope2: K nonzero entries, S = sum |D| row-major.
+    // Eqs. eqslope / eqslope2: K nonzero entries, S = sum |D| (pairwise tree).
     int K = 0;
-    double S = 0.0;
 #pragma unroll
-    for (int p = 0; p < 64; ++p) {
-        K += (d[p] != 0.0);
-        S = dadd(S, fabs(d[p]));
-    }
+    for (int p = 0; p < 64; ++p) K += (d[p] != 0.0);
+    const double S = tree_sum_abs(d);
     if (K == 0) {  // constant block: s = 0, all coefficients 0, phi = 127/0 -> 255
         s_out = 0.0;
         phi_out = 255;

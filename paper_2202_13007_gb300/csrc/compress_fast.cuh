@@ -184,14 +184,12 @@ __device__ __forceinline__ uint32_t compress_block_fast(double (&d)[64], double 
             }
         }
     }
-    // Eqs. eqslope, eqslope2 (K counted on the bit patterns: x != 0).
+    // Eqs. eqslope, eqslope2 (K counted on the bit patterns: x != 0; S as the
+    // pairwise tree).
     int K = 0;
-    double S = 0.0;
 #pragma unroll
-    for (int p = 0; p < 64; ++p) {
-        K += nonzero_bits(d[p]);
-        S = dadd(S, fabs(d[p]));
-    }
+    for (int p = 0; p < 64; ++p) K += nonzero_bits(d[p]);
+    const double S = tree_sum_abs(d);
     if (K == 0) {
         s_out = 0.0;
         phi_out = 255;

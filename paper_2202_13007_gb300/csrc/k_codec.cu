@@ -38,7 +38,7 @@ __device__ __forceinline__ void append(bool want, T value, T *__restrict__ list,
 constexpr int kFastThreads = 64;
 
 template <bool kVec>
-__global__ void __launch_bounds__(kFastThreads)
+__global__ void __launch_bounds__(kFastThreads, 6)
     k_compress_fast(const double *__restrict__ A, int64_t lda, int64_t nbc, int64_t nb, double *__restrict__ f,
                     double *__restrict__ s, uint8_t *__restrict__ phi, int8_t *__restrict__ code,
                     uint2 *__restrict__ code_list, unsigned *__restrict__ code_count,

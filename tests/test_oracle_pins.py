@@ -145,6 +145,34 @@ def _dyadic_blocks():
         yield np.cumsum(rng.integers(-8, 9, (8, 8)), axis=1) / 16.0
 
 
+def test_slope_sum_meets_the_pairwise_tree_error_bound():
+    """S = sum |D| (Eqs. eqslope, eqslope2) is taken as a fixed pairwise tree
+    of depth 6 over the row-major index, so every |D| passes through six
+    additions: |S - sum|D|| <= gamma_6 sum|D| (gamma_6 = 6u/(1-6u)).  The
+    first block puts three large |D| early in row-major order (a spike at
+    M01) and ~60 values |D| ~ 1.6e-16 elsewhere: a left-to-right sum drops
+    every small term (error ~35u), so this bound fails for that order."""
+    from fractions import Fraction
+
+    u = Fraction(1, 2 ** 53)
+    gamma6 = 6 * u / (1 - 6 * u)
+    c = 1.6e-16
+    spike = np.fromfunction(lambda i, j: c * (i + j), (8, 8))
+    spike[0, 1] = 1.0
+    rng = np.random.default_rng(21)
+    blocks = [spike] + [rng.standard_normal((8, 8)) * 10.0 ** rng.integers(-5, 5) for _ in range(100)]
+    for n, M in enumerate(blocks):
+        st = O.block_stages(M)
+        d = st["delta"].ravel()
+        exact = sum(Fraction(abs(float(x))) for x in d)
+        assert abs(Fraction(st["sum_abs"]) - exact) <= gamma6 * exact
+        if n == 0:
+            seq = 0.0
+            for x in d:
+                seq += abs(float(x))
+            assert abs(Fraction(seq) - exact) > 6 * u * exact   # the input separates the orders
+
+
 def test_brute_force_against_real_arithmetic():
     kept = O.kept_positions()
     n_checked = n_near = 0
