@@ -32,11 +32,11 @@ METRIC = "compressed add/scale/dot GB/s (% HBM peak), matmul TFLOP/s, serve p50/
 BYTES_PER_BLOCK = {"compress": 557, "decompress": 557, "add": 135, "scale": 90, "dot": 90}
 STEP_OPS = ["compress", "compress", "decompress", "add", "scale", "dot"]
 # binary64 operations per block that the certified compressor must evaluate
-# exactly (the rest of the DCT runs in fp32 under a proven bound):
-# normalization 161 (the 49 halvings are exact exponent decrements),
-# |D| sum 64, s and 1/s 2, D' = D * (1/s) 64, DC chain 63 + 1, 127/m 1,
-# DC code 1.
-COMPRESS_FLOPS_PER_BLOCK = 357
+# exactly (the rest of the DCT and the decision phi = trunc(127/m) run in fp32
+# under proven bounds): normalization 161 (the 49 halvings are exact exponent
+# decrements), |D| pairwise tree 63, s and 1/s 2, D' = D * (1/s) 64, DC chain
+# 63 + 1, DC code 1.
+COMPRESS_FLOPS_PER_BLOCK = 355
 FP64_PEAK_DERIVED = 2 * 152 * 2070e6  # 2 FP64 lanes/clk/SM x 152 SMs x 2070 MHz (1.25 TFLOP/s nominal, FMA=2)
 
 
@@ -488,7 +488,7 @@ def main():
         B.dot(ca, cb, out=res[0])
         B.dot_rowcol(ca, cb, 17, 200, out=res[1])
 
-    launches_per_step = 7   # compress x2, decompress, add, scale, dot, dot_rowcol
+    launches_per_step = 9   # compress x2 (k_compress_fast + k_compress_fix), decompress, add, scale, dot, dot_rowcol
 
     for _ in range(args.warmup):
         step()

@@ -4,10 +4,10 @@
 // Compression is bit-exact binary64: every operation is an explicit
 // round-to-nearest intrinsic in the order fixed in include/blaz.h, so the
 // result does not depend on -fmad or on the compiler's scheduling.  The
-// compressor runs in three kernels: k_compress_fast decides every block it
-// can certify (compress_fast.cuh) and lists the codes (or whole blocks) it
-// cannot; k_compress_fix_codes and k_compress_fix_blocks evaluate those
-// exactly in binary64, densely, so the rare exact work costs no divergence.
+// compressor runs in two kernels: k_compress_fast decides every block it can
+// certify (compress_fast.cuh) and lists the codes (or whole blocks) it
+// cannot; k_compress_fix evaluates those exactly in binary64, densely, by
+// teams of 8 lanes, so the rare exact work costs no divergence.
 #include <mutex>
 
 #include <cuda_fp16.h>
@@ -91,103 +91,113 @@ __device__ __forceinline__ void team_dprime_row(const double *__restrict__ A, in
 }
 
 // Whole blocks whose phi was not certified (or with non-finite values): the
-// exact binary64 compressor by a team of 8 lanes per listed block.  s is
-// already exact (k_compress_fast stores it for every block).  Lane u forms
-// row u of D' and the inner sums T_j[u] of all eight columns; lane i then
-// forms U[i][j] = sum_u cos_iu T_j[u] in the specified order from the
-// team's shuffles, X[i][j], and its share of m = max |X| (NaN ignored, as in
+// exact binary64 compressor by the team of 8 lanes.  s is already exact
+// (k_compress_fast stores it for every block).  Lane u forms row u of D' and
+// the inner sums T_j[u] of all eight columns; lane i then forms
+// U[i][j] = sum_u cos_iu T_j[u] in the specified order from the team's
+// shuffles, X[i][j], and its share of m = max |X| (NaN ignored, as in
 // compress_block: the maximum of non-NaN values is order-free).
 template <bool kVec>
-__global__ void __launch_bounds__(128)
-    k_compress_fix_blocks(const double *__restrict__ A, int64_t lda, int64_t nbc, const unsigned *__restrict__ list,
-                          const unsigned *__restrict__ count, const double *__restrict__ s,
-                          uint8_t *__restrict__ phi, int8_t *__restrict__ code)
+__device__ __forceinline__ void fix_whole_block(const double *__restrict__ A, int64_t lda, int64_t nbc, int64_t b,
+                                                const double *__restrict__ s, uint8_t *__restrict__ phi,
+                                                int8_t *__restrict__ code, int u, int tbase, unsigned tmask)
 {
-    const int lane = threadIdx.x & 31, u = lane & 7, tbase = lane & ~7;
-    const unsigned tmask = 0xFFu << tbase;
     double ci[8];  // cos_{u,x}: this lane's row of the cosine table as output row i = u
 #pragma unroll
     for (int x = 0; x < 8; ++x) ci[x] = c_cos[u * 8 + x];
-    const int64_t n = *count;
-    const int64_t teams = (int64_t)gridDim.x * blockDim.x / 8;
-    for (int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 8; q < n; q += teams) {
-        const int64_t b = list[q];
-        double dp[8];
-        team_dprime_row<kVec>(A, lda, nbc, b, u, s[b], dp);
-        double T[8];
+    double dp[8];
+    team_dprime_row<kVec>(A, lda, nbc, b, u, s[b], dp);
+    double T[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        double acc = (j == 0) ? dp[0] : dmul(dp[0], cos_tab(j, 0));
+#pragma unroll
+        for (int v = 1; v < 8; ++v) acc = dadd(acc, (j == 0) ? dp[v] : dmul(dp[v], cos_tab(j, v)));
+        T[j] = acc;
+    }
+    double U[8];
+#pragma unroll
+    for (int uu = 0; uu < 8; ++uu) {
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-            double acc = (j == 0) ? dp[0] : dmul(dp[0], cos_tab(j, 0));
-#pragma unroll
-            for (int v = 1; v < 8; ++v) acc = dadd(acc, (j == 0) ? dp[v] : dmul(dp[v], cos_tab(j, v)));
-            T[j] = acc;
+            const double Tu = __shfl_sync(tmask, T[j], tbase + uu);
+            const double term = (u == 0) ? Tu : dmul(ci[uu], Tu);
+            U[j] = (uu == 0) ? term : dadd(U[j], term);
         }
-        double U[8];
+    }
+    double m = 0.0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        U[j] = dmul((u == 0 && j == 0) ? BLAZ_A00 : (u == 0 || j == 0) ? BLAZ_A0K : BLAZ_AKK, U[j]);
+        const double ax = fabs(U[j]);
+        m = (ax > m) ? ax : m;
+    }
+#pragma unroll
+    for (int off = 4; off; off >>= 1) {
+        const double o = __shfl_xor_sync(tmask, m, off);
+        m = (o > m) ? o : m;
+    }
+    const int ph = phi_of(m);
+    const double phd = i64_to_double(ph);
+    if (u == 0) phi[b] = (uint8_t)ph;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int t = kept_index(u, j);
+        if (t >= 0) code[b * kKeep + t] = quantize_bits(dmul(U[j], phd));
+    }
+}
+
+// Undecided codes of block b (bit t of `pending` for code t), phi already
+// set: for each, the team forms the inner sums T[u] (lane u) and the outer
+// sum over u in the specified order from the shuffles.
+template <bool kVec>
+__device__ __forceinline__ void fix_codes_of_block(const double *__restrict__ A, int64_t lda, int64_t nbc, int64_t b,
+                                                   uint32_t pending, const double *__restrict__ s,
+                                                   const uint8_t *__restrict__ phi, int8_t *__restrict__ code, int u,
+                                                   int tbase, unsigned tmask)
+{
+    double dp[8];
+    team_dprime_row<kVec>(A, lda, nbc, b, u, s[b], dp);
+    const int ph = phi[b];
+    for (uint32_t m = pending; m; m &= m - 1) {
+        const int t = __ffs(m) - 1;
+        const int i = kept_row(t), j = kept_col(t);
+        double T = (j == 0) ? dp[0] : dmul(dp[0], c_cos[j * 8]);
+#pragma unroll
+        for (int v = 1; v < 8; ++v) T = dadd(T, (j == 0) ? dp[v] : dmul(dp[v], c_cos[j * 8 + v]));
+        double U = 0.0;
 #pragma unroll
         for (int uu = 0; uu < 8; ++uu) {
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const double Tu = __shfl_sync(tmask, T[j], tbase + uu);
-                const double term = (u == 0) ? Tu : dmul(ci[uu], Tu);
-                U[j] = (uu == 0) ? term : dadd(U[j], term);
-            }
+            const double Tu = __shfl_sync(tmask, T, tbase + uu);
+            const double term = (i == 0) ? Tu : dmul(c_cos[i * 8 + uu], Tu);
+            U = (uu == 0) ? term : dadd(U, term);
         }
-        double m = 0.0;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            U[j] = dmul((u == 0 && j == 0) ? BLAZ_A00 : (u == 0 || j == 0) ? BLAZ_A0K : BLAZ_AKK, U[j]);
-            const double ax = fabs(U[j]);
-            m = (ax > m) ? ax : m;
-        }
-#pragma unroll
-        for (int off = 4; off; off >>= 1) {
-            const double o = __shfl_xor_sync(tmask, m, off);
-            m = (o > m) ? o : m;
-        }
-        const int ph = phi_of(m);
-        const double phd = i64_to_double(ph);
-        if (u == 0) phi[b] = (uint8_t)ph;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int t = kept_index(u, j);
-            if (t >= 0) code[b * kKeep + t] = quantize_bits(dmul(U[j], phd));
+        if (u == 0) {
+            const double aa = (i == 0 && j == 0) ? BLAZ_A00 : (i == 0 || j == 0) ? BLAZ_A0K : BLAZ_AKK;
+            code[b * kKeep + t] = quantize_bits(dmul(dmul(aa, U), i64_to_double(ph)));
         }
     }
 }
 
+// The exact fix-up of both lists in one launch, a team of 8 lanes per entry:
+// entries [0, #blocks) of the whole-block list, then the code list.  The two
+// lists hold different blocks, so the entries are independent.
 template <bool kVec>
 __global__ void __launch_bounds__(128)
-    k_compress_fix_codes(const double *__restrict__ A, int64_t lda, int64_t nbc, const uint2 *__restrict__ list,
-                         const unsigned *__restrict__ count, const double *__restrict__ s,
-                         const uint8_t *__restrict__ phi, int8_t *__restrict__ code)
+    k_compress_fix(const double *__restrict__ A, int64_t lda, int64_t nbc, const unsigned *__restrict__ block_list,
+                   const uint2 *__restrict__ code_list, const unsigned *__restrict__ counts,
+                   const double *__restrict__ s, uint8_t *__restrict__ phi, int8_t *__restrict__ code)
 {
     const int lane = threadIdx.x & 31, u = lane & 7, tbase = lane & ~7;
     const unsigned tmask = 0xFFu << tbase;
-    const int64_t n = *count;
+    const int64_t ncodes = counts[0], nblocks = counts[1];
     const int64_t teams = (int64_t)gridDim.x * blockDim.x / 8;
-    for (int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 8; q < n; q += teams) {
-        const uint2 e = list[q];
-        const int64_t b = e.x;
-        double dp[8];
-        team_dprime_row<kVec>(A, lda, nbc, b, u, s[b], dp);
-        const int ph = phi[b];
-        for (uint32_t m = e.y; m; m &= m - 1) {
-            const int t = __ffs(m) - 1;
-            const int i = kept_row(t), j = kept_col(t);
-            double T = (j == 0) ? dp[0] : dmul(dp[0], c_cos[j * 8]);
-#pragma unroll
-            for (int v = 1; v < 8; ++v) T = dadd(T, (j == 0) ? dp[v] : dmul(dp[v], c_cos[j * 8 + v]));
-            double U = 0.0;
-#pragma unroll
-            for (int uu = 0; uu < 8; ++uu) {
-                const double Tu = __shfl_sync(tmask, T, tbase + uu);
-                const double term = (i == 0) ? Tu : dmul(c_cos[i * 8 + uu], Tu);
-                U = (uu == 0) ? term : dadd(U, term);
-            }
-            if (u == 0) {
-                const double aa = (i == 0 && j == 0) ? BLAZ_A00 : (i == 0 || j == 0) ? BLAZ_A0K : BLAZ_AKK;
-                code[b * kKeep + t] = quantize_bits(dmul(dmul(aa, U), i64_to_double(ph)));
-            }
+    for (int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 8; q < nblocks + ncodes; q += teams) {
+        if (q < nblocks) {
+            fix_whole_block<kVec>(A, lda, nbc, block_list[q], s, phi, code, u, tbase, tmask);
+        } else {
+            const uint2 e = code_list[q - nblocks];
+            fix_codes_of_block<kVec>(A, lda, nbc, e.x, e.y, s, phi, code, u, tbase, tmask);
         }
     }
 }
@@ -363,23 +373,19 @@ int launch_compress(const double *A, int64_t lda, const blaz_cmat *out, void *sc
     cudaError_t e = cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned), st);
     if (e != cudaSuccess) return set_cuda_error(e);
     const int threads = 128;
-    const int fix_grid = num_sms() * 8;
+    const int fix_grid = num_sms() * 4;  // one resident wave (72 registers per thread)
     if (vec_ok(A, lda)) {
         k_compress_fast<true><<<fast_grid(nb), kFastThreads, 0, st>>>(A, lda, nbc, nb, out->f, out->s,
                                                                       out->phi, out->code, code_list, counts,
                                                                       block_list, counts + 1);
-        k_compress_fix_blocks<true><<<fix_grid, threads, 0, st>>>(A, lda, nbc, block_list, counts + 1, out->s,
-                                                                   out->phi, out->code);
-        k_compress_fix_codes<true><<<fix_grid, threads, 0, st>>>(A, lda, nbc, code_list, counts, out->s, out->phi,
-                                                                  out->code);
+        k_compress_fix<true><<<fix_grid, threads, 0, st>>>(A, lda, nbc, block_list, code_list, counts, out->s,
+                                                            out->phi, out->code);
     } else {
         k_compress_fast<false><<<fast_grid(nb), kFastThreads, 0, st>>>(A, lda, nbc, nb, out->f, out->s,
                                                                        out->phi, out->code, code_list, counts,
                                                                        block_list, counts + 1);
-        k_compress_fix_blocks<false><<<fix_grid, threads, 0, st>>>(A, lda, nbc, block_list, counts + 1, out->s,
-                                                                    out->phi, out->code);
-        k_compress_fix_codes<false><<<fix_grid, threads, 0, st>>>(A, lda, nbc, code_list, counts, out->s, out->phi,
-                                                                   out->code);
+        k_compress_fix<false><<<fix_grid, threads, 0, st>>>(A, lda, nbc, block_list, code_list, counts, out->s,
+                                                             out->phi, out->code);
     }
     return launch_status();
 }
