@@ -51,7 +51,9 @@ enum {
     BLAZ_ERR_TIMEOUT = -7,  /* a bounded device wait ran out                               */
     BLAZ_ERR_BUDGET = -8,   /* server: request exceeds the admission budget                */
     BLAZ_ERR_ARG = -9,      /* any other invalid argument (mode, index, count)             */
-    BLAZ_ERR_RANGE = -10    /* an index is outside the matrix                              */
+    BLAZ_ERR_RANGE = -10,   /* an index is outside the matrix                              */
+    BLAZ_ERR_IO = -11,      /* a file could not be opened, read or written                 */
+    BLAZ_ERR_FORMAT = -12   /* a file is not a compressed matrix of this format            */
 };
 
 /* A compressed matrix: structure of arrays in device memory, nb = (rows/8)*(cols/8).
@@ -174,6 +176,38 @@ int blaz_dot_rowcol(const blaz_cmat *a, const blaz_cmat *b, int64_t i, int64_t j
 enum { BLAZ_MM_FP64 = 0, BLAZ_MM_SPLIT_BF16 = 1 };
 int blaz_matmul(const blaz_cmat *a, const double *B, int64_t ldb, int64_t m, double *C, int64_t ldc,
                 int mode, void *stream);
+
+/* Matrix product C = A_hat * B_hat of two compressed matrices (Sec. III,
+ * "Matrix multiplication": B = B1 x B2 of compressed blocks, each
+ * decompressed block computed once).  a: n x k, b: k x m (a->cols must equal
+ * b->rows, else BLAZ_ERR_SHAPE); C: device, n x m binary64, ldc >= m.  Both
+ * operands are decompressed once into stream-ordered scratch (8nk + 8km
+ * bytes, plus 12k(n+m) bytes of slices in split mode), then multiplied as in
+ * blaz_matmul with the same modes and accuracy (relative to |A_hat||B_hat|). */
+int blaz_matmul_cc(const blaz_cmat *a, const blaz_cmat *b, double *C, int64_t ldc, int mode, void *stream);
+
+/* ---- Files: save and load compressed matrices ------------------------------
+ * The 360-bit payload of Sec. II per block, stored as a little-endian file:
+ *   bytes  0..7   magic "BLAZCMAT"
+ *          8..11  uint32 version (1)      12..15 uint32 header size (64)
+ *         16..23  int64 rows              24..31 int64 cols
+ *         32..39  int64 nb = (rows/8)(cols/8)
+ *         40..47  uint64 payload bytes = 45 nb
+ *         48..55  uint64 FNV-1a 64-bit hash of the payload
+ *         56..63  zero
+ *   payload: f[nb] (binary64), s[nb] (binary64), phi[nb] (uint8),
+ *            code[nb][28] (int8), in block order.
+ * These calls are host-side and blocking: save waits for `stream` to finish
+ * the device-to-host copies, load waits for its host-to-device copies.  A
+ * file is written to `path`.tmp and renamed, so a reader never sees half a
+ * file.  BLAZ_ERR_IO for a failed open/read/write, BLAZ_ERR_FORMAT for a bad
+ * magic, version, size or hash (checked before any device copy). */
+int blaz_cmat_save(const blaz_cmat *a, const char *path, void *stream);
+/* Shape stored in a file (host only; no device access). */
+int blaz_cmat_file_info(const char *path, int64_t *rows, int64_t *cols);
+/* Fills `out`, allocated by the caller with the file's rows and cols
+ * (BLAZ_ERR_SHAPE otherwise). */
+int blaz_cmat_load(const char *path, blaz_cmat *out, void *stream);
 
 /* ---- Batched mixed operations: one persistent, graph-captured launch ----------
  * Many compressed-matrix operations of different kinds and sizes (the

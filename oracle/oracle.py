@@ -270,3 +270,13 @@ def matmul(a: CMat, B):
     _chk(lib().blazo_matmul(_p(a.f, _D), _p(a.s, _D), _p(a.phi, _U8), _p(a.code, _I8), a.rows, a.cols,
                             _p(B, _D), m, m, _p(C, _D), m), "matmul")
     return C
+
+
+def matmul_cc(a: CMat, b: CMat):
+    """A_hat @ B_hat of two compressed matrices (Sec. III, "Matrix
+    multiplication": the product of the decompressed blocks, each
+    decompressed once): B is decompressed by the oracle, then the plain
+    i-j-k product of `matmul`."""
+    assert a.cols == b.rows
+    return matmul(a, decompress(b))
+

@@ -103,6 +103,11 @@ SIGNATURES = {
     "blaz_dot_noalloc": (ctypes.c_int, [_DESC, _DESC, _P, _P]),
     "blaz_dot_rowcol": (ctypes.c_int, [_DESC, _DESC, _I64, _I64, _P, _P]),
     "blaz_matmul": (ctypes.c_int, [_DESC, _P, _I64, _I64, _P, _I64, ctypes.c_int, _P]),
+    "blaz_matmul_cc": (ctypes.c_int, [_DESC, _DESC, _P, _I64, ctypes.c_int, _P]),
+    "blaz_cmat_save": (ctypes.c_int, [_DESC, ctypes.c_char_p, _P]),
+    "blaz_cmat_file_info": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_int64),
+                                           ctypes.POINTER(ctypes.c_int64)]),
+    "blaz_cmat_load": (ctypes.c_int, [ctypes.c_char_p, _DESC, _P]),
     "blaz_batch_plan": (ctypes.c_int, [ctypes.POINTER(_Op), _I64, ctypes.POINTER(_BatchCfg),
                                        ctypes.POINTER(ctypes.c_void_p), _P]),
     "blaz_batch_run": (ctypes.c_int, [_P, _P]),
@@ -152,8 +157,14 @@ def _check(rc: int, what: str):
 def _dev_f64(t: torch.Tensor, name: str):
     if not (t.is_cuda and t.dtype == torch.float64 and t.dim() == 2):
         raise TypeError(f"{name} must be a 2-D float64 CUDA tensor")
-    if t.stride(1) != 1:
+    if t.numel() and t.stride(1) != 1:
         raise TypeError(f"{name} must have unit column stride")
+
+
+def _ld(t: torch.Tensor) -> int:
+    """Leading dimension of a row-major matrix view (the row length when empty,
+    where torch may report any stride)."""
+    return t.stride(0) if t.numel() else t.shape[1]
 
 
 @dataclass
@@ -218,7 +229,7 @@ def blaz_compress(A: torch.Tensor, out: CMat | None = None, stream=None) -> CMat
     if (out.rows, out.cols) != (rows, cols):
         raise ValueError("out shape mismatch")
     d = out.desc()
-    _check(lib().blaz_compress(A.data_ptr(), A.stride(0), ctypes.byref(d), _stream(stream)), "blaz_compress")
+    _check(lib().blaz_compress(A.data_ptr(), _ld(A), ctypes.byref(d), _stream(stream)), "blaz_compress")
     return out
 
 
@@ -227,7 +238,7 @@ def blaz_decompress(a: CMat, out: torch.Tensor | None = None, stream=None) -> to
         out = torch.empty((a.rows, a.cols), dtype=torch.float64, device=a.f.device)
     _dev_f64(out, "out")
     d = a.desc()
-    _check(lib().blaz_decompress(ctypes.byref(d), out.data_ptr(), out.stride(0), _stream(stream)),
+    _check(lib().blaz_decompress(ctypes.byref(d), out.data_ptr(), _ld(out), _stream(stream)),
            "blaz_decompress")
     return out
 
@@ -289,8 +300,44 @@ def blaz_matmul(a: CMat, B: torch.Tensor, mode: str = "fp64", out: torch.Tensor 
         out = torch.empty((a.rows, m), dtype=torch.float64, device=B.device)
     _dev_f64(out, "out")
     da = a.desc()
-    _check(lib().blaz_matmul(ctypes.byref(da), B.data_ptr(), B.stride(0), m, out.data_ptr(), out.stride(0),
+    _check(lib().blaz_matmul(ctypes.byref(da), B.data_ptr(), _ld(B), m, out.data_ptr(), _ld(out),
                              _MODES[mode], _stream(stream)), "blaz_matmul")
+    return out
+
+
+def blaz_matmul_cc(a: CMat, b: CMat, mode: str = "fp64", out: torch.Tensor | None = None,
+                   stream=None) -> torch.Tensor:
+    """C = A_hat * B_hat of two compressed matrices (dense binary64 n x m)."""
+    if a.cols != b.rows:
+        raise ValueError("inner dimensions differ")
+    if out is None:
+        out = torch.empty((a.rows, b.cols), dtype=torch.float64, device=a.f.device)
+    _dev_f64(out, "out")
+    da, db = a.desc(), b.desc()
+    _check(lib().blaz_matmul_cc(ctypes.byref(da), ctypes.byref(db), out.data_ptr(), _ld(out),
+                                _MODES[mode], _stream(stream)), "blaz_matmul_cc")
+    return out
+
+
+def blaz_cmat_save(a: CMat, path, stream=None) -> None:
+    """Write `a` to `path` (format in include/blaz.h); blocks until written."""
+    da = a.desc()
+    _check(lib().blaz_cmat_save(ctypes.byref(da), os.fsencode(path), _stream(stream)), "blaz_cmat_save")
+
+
+def blaz_cmat_file_info(path) -> tuple[int, int]:
+    """(rows, cols) stored in a compressed-matrix file (host only)."""
+    r, c = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().blaz_cmat_file_info(os.fsencode(path), ctypes.byref(r), ctypes.byref(c)), "blaz_cmat_file_info")
+    return r.value, c.value
+
+
+def blaz_cmat_load(path, out: CMat | None = None, stream=None) -> CMat:
+    """Read a compressed matrix from `path` into `out` (allocated here if None)."""
+    if out is None:
+        out = CMat.empty(*blaz_cmat_file_info(path))
+    do = out.desc()
+    _check(lib().blaz_cmat_load(os.fsencode(path), ctypes.byref(do), _stream(stream)), "blaz_cmat_load")
     return out
 
 
@@ -317,17 +364,17 @@ class Batch:
                     setattr(o, key, d[key].desc())
             if "A" in d:
                 _dev_f64(d["A"], "A")
-                o.A, o.lda = d["A"].data_ptr(), d["A"].stride(0)
+                o.A, o.lda = d["A"].data_ptr(), _ld(d["A"])
             if "c" in d:
                 o.c = float(d["c"])
             if "result" in d:
                 o.result = d["result"].data_ptr()
             if "B" in d:
                 _dev_f64(d["B"], "B")
-                o.B, o.ldb, o.m = d["B"].data_ptr(), d["B"].stride(0), d["B"].shape[1]
+                o.B, o.ldb, o.m = d["B"].data_ptr(), _ld(d["B"]), d["B"].shape[1]
             if "C" in d:
                 _dev_f64(d["C"], "C")
-                o.C, o.ldc = d["C"].data_ptr(), d["C"].stride(0)
+                o.C, o.ldc = d["C"].data_ptr(), _ld(d["C"])
             self._keep.append(d)
         cfg = _BatchCfg(blocks_per_item, ctas_per_sm, 1 if autotune else 0)
         h = ctypes.c_void_p()
@@ -459,4 +506,5 @@ def _from_ptr(ptr: int, nbytes: int, dtype, shape, dev):
 
 # short aliases
 compress, decompress, add, sub, scale = blaz_compress, blaz_decompress, blaz_add, blaz_sub, blaz_scale
-dot, dot_rowcol, matmul = blaz_dot, blaz_dot_rowcol, blaz_matmul
+dot, dot_rowcol, matmul, matmul_cc = blaz_dot, blaz_dot_rowcol, blaz_matmul, blaz_matmul_cc
+save, load, file_info = blaz_cmat_save, blaz_cmat_load, blaz_cmat_file_info

@@ -105,6 +105,8 @@ const char *blaz_strerror(int status)
     case BLAZ_ERR_BUDGET: return "request exceeds the admission budget";
     case BLAZ_ERR_ARG: return "invalid argument";
     case BLAZ_ERR_RANGE: return "index out of range";
+    case BLAZ_ERR_IO: return "file open, read or write failed";
+    case BLAZ_ERR_FORMAT: return "not a compressed-matrix file of this format";
     default: return "unknown status";
     }
 }
@@ -281,6 +283,30 @@ int blaz_matmul(const blaz_cmat *a, const double *B, int64_t ldb, int64_t m, dou
     if (mode == BLAZ_MM_SPLIT_BF16)
         return launch_matmul_split_bf16(Ah, k, B, ldb, C, ldc, n, k, m, (char *)ws.p + ah_bytes, st);
     return launch_gemm_fp64(Ah, k, B, ldb, C, ldc, n, k, m, st);
+}
+
+int blaz_matmul_cc(const blaz_cmat *a, const blaz_cmat *b, double *C, int64_t ldc, int mode, void *stream)
+{
+    int rc;
+    if ((rc = validate_cmat(a)) || (rc = validate_cmat(b))) return rc;
+    if (a->cols != b->rows) return BLAZ_ERR_SHAPE;
+    if (mode != BLAZ_MM_FP64 && mode != BLAZ_MM_SPLIT_BF16) return BLAZ_ERR_ARG;
+    const int64_t n = a->rows, k = a->cols, m = b->cols;
+    if (n == 0 || m == 0) return BLAZ_OK;
+    if (!C) return BLAZ_ERR_NULL;
+    if (ldc < m) return BLAZ_ERR_LD;
+    cudaStream_t st = (cudaStream_t)stream;
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t ah_bytes = up(sizeof(double) * (size_t)(n * k)), bh_bytes = up(sizeof(double) * (size_t)(k * m));
+    const size_t extra = mode == BLAZ_MM_SPLIT_BF16 ? split_bf16_scratch_bytes(n, k, m) : 0;
+    Scratch ws(st);
+    if ((rc = ws.alloc(ah_bytes + bh_bytes + extra))) return rc;
+    double *Ah = (double *)ws.p, *Bh = (double *)((char *)ws.p + ah_bytes);
+    if (k > 0 && (rc = launch_decompress(a, Ah, k, st))) return rc;
+    if (k > 0 && (rc = launch_decompress(b, Bh, m, st))) return rc;
+    if (mode == BLAZ_MM_SPLIT_BF16)
+        return launch_matmul_split_bf16(Ah, k, Bh, m, C, ldc, n, k, m, (char *)ws.p + ah_bytes + bh_bytes, st);
+    return launch_gemm_fp64(Ah, k, Bh, m, C, ldc, n, k, m, st);
 }
 
 }  // extern "C"

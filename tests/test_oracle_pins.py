@@ -317,6 +317,14 @@ def test_dot_products_and_matmul_match_library():
     ii = np.array([0, 5, 5, 255]); jj = np.array([0, 1, 47, 13])
     e, ae = O.matmul_entries(ca, Bd, ii, jj)
     assert np.allclose(e, C[ii, jj], rtol=1e-14, atol=1e-14)
+    # compressed x compressed: the product of the two decompressions, and
+    # entry by entry Algorithm 3's line . column
+    Ccc = O.matmul_cc(ca, cb)
+    bound = np.abs(Ah) @ np.abs(Bh)
+    assert np.all(np.abs(Ccc - P) <= 1e-13 * bound)
+    for i, j in [(17, 200), (0, 0), (255, 255), (100, 3)]:
+        r, ar = O.dot_rowcol(ca, cb, i, j)
+        assert abs(Ccc[i, j] - r) <= 1e-13 * ar
 
 
 def test_dot_rowcol_is_an_entry_of_the_product():

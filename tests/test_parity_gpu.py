@@ -362,6 +362,51 @@ def test_matmul_split_bf16_empty_inner_dimension(B):
 
 
 @pytest.mark.parametrize("mode", ["fp64", "split_bf16"])
+@pytest.mark.parametrize("n,k,m", [(8, 8, 8), (72, 136, 64), (264, 256, 520)])
+def test_matmul_compressed_by_compressed(B, mode, n, k, m):
+    """A_hat @ B_hat (both compressed) against the oracle's product of the two
+    decompressions, with the tolerance of the matching dense-B mode."""
+    A = W.random_block_matrix(n, k, seed=n + k)
+    Bm = W.random_block_matrix(k, m, seed=k + m + 1)
+    ga, gb = B.compress(dev(A)), B.compress(dev(Bm))
+    C = B.matmul_cc(ga, gb, mode=mode).cpu().numpy()
+    assert B.device_status() == 0
+    oa, ob = O.compress(A), O.compress(Bm)
+    ref = O.matmul_cc(oa, ob)
+    bound = np.abs(O.decompress(oa)) @ np.abs(O.decompress(ob))
+    tol = 1e-12 if mode == "fp64" else split_bf16_tol(k)
+    err = np.abs(C - ref)
+    assert np.all(err <= tol * bound + 1e-300), np.max(err / (bound + 1e-300))
+
+
+def test_matmul_compressed_by_compressed_edges(B):
+    import ctypes
+
+    a = B.compress(dev(W.random_block_matrix(16, 24, seed=3)))
+    b = B.compress(dev(W.random_block_matrix(16, 8, seed=4)))
+    out = torch.zeros((16, 8), dtype=torch.float64, device="cuda")
+    da, db = a.desc(), b.desc()
+    rc = B.lib().blaz_matmul_cc(ctypes.byref(da), ctypes.byref(db), out.data_ptr(), 8, 0,
+                                ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == -1                                       # inner dimensions differ: BLAZ_ERR_SHAPE
+    e0 = B.compress(torch.zeros((16, 0), dtype=torch.float64, device="cuda"))
+    e1 = B.compress(torch.zeros((0, 24), dtype=torch.float64, device="cuda"))
+    C = B.matmul_cc(e0, e1)
+    assert C.shape == (16, 24) and float(C.abs().max()) == 0.0
+    # output into a strided view (ldc > m)
+    A = W.random_block_matrix(40, 32, seed=5)
+    Bm = W.random_block_matrix(32, 48, seed=6)
+    big = torch.full((40, 72), 7.0, dtype=torch.float64, device="cuda")
+    B.matmul_cc(B.compress(dev(A)), B.compress(dev(Bm)), out=big[:, 8:56])
+    oa, ob = O.compress(A), O.compress(Bm)
+    ref = O.matmul_cc(oa, ob)
+    bound = np.abs(O.decompress(oa)) @ np.abs(O.decompress(ob))
+    got = big.cpu().numpy()
+    assert np.all(np.abs(got[:, 8:56] - ref) <= 1e-12 * bound + 1e-300)
+    assert np.all(got[:, :8] == 7.0) and np.all(got[:, 56:] == 7.0)
+
+
+@pytest.mark.parametrize("mode", ["fp64", "split_bf16"])
 def test_precision_config_max_relative_error(B, mode, record_property):
     """Precision workload: compressed 4096^2 bump field times a smoothed N(0,1)
     4096^2 matrix; sampled entries against the oracle (which compresses the
