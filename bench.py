@@ -260,6 +260,53 @@ def matmul_extras(B, W, torch, dev):
     return out
 
 
+def shape_and_file_extras(B, W, torch, dev):
+    """Any-shape matrices and files: compress and dot of a 4095 x 4093 bump
+    field (edge-replicated to 4096 x 4096) against the 4096 x 4096 field, and
+    save / load of its compressed form (11.8 MB) through a local file."""
+    import os
+    import tempfile
+
+    def timed(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    n = 4096
+    ta = W.bump_field_torch(n, n, dev)
+    tb = W.bump_field_torch(n, n + 1, dev)
+    pa, pb = ta[:n - 1, :n - 3], tb[:n - 1, :n - 3]
+    ga, gb = B.compress(ta), B.compress(tb)
+    qa, qb = B.compress_padded(pa), B.compress_padded(pb)
+    res = torch.empty((), dtype=torch.float64, device=dev)
+    out = {
+        "compress_ms": timed(lambda: B.compress(ta, out=ga)),
+        "compress_padded_ms": timed(lambda: B.compress_padded(pa, out=qa)),
+        "dot_ms": timed(lambda: B.dot(ga, gb, out=res)),
+        "dot_padded_ms": timed(lambda: B.dot_padded(qa, qb, out=res)),
+    }
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "a.blaz")
+        import time
+
+        t0 = time.perf_counter()
+        B.save(ga, path)
+        t1 = time.perf_counter()
+        B.load(path, out=gb)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        out.update({"save_ms": (t1 - t0) * 1e3, "load_ms": (t2 - t1) * 1e3, "file_bytes": os.path.getsize(path)})
+    out["config"] = ("4095x4093 padded vs 4096x4096 bump fields (CUDA events); save/load of a 4096x4096 "
+                     "compressed matrix through a local file (host wall clock)")
+    return out
+
+
 def run_serve(args, B, W, torch, dev, seconds, max_batch, streams, mode="fp64", seed=13, rate=5000.0):
     """Poisson stream (5k req/s, sides log-uniform over multiples of 8 in
     [64, 4096], op mix 40/30/15/10/5 %) against a server with a 40 GB budget.
@@ -570,7 +617,7 @@ def main():
     if rank == 0 and not args.no_extras:
         del dec
         torch.cuda.empty_cache()
-        extras = {"matmul": matmul_extras(B, W, torch, dev)}
+        extras = {"matmul": matmul_extras(B, W, torch, dev), "shapes_files": shape_and_file_extras(B, W, torch, dev)}
         srv = run_serve(args, B, W, torch, dev, 1.0, max_batch=0, streams=4, mode="split_bf16")
         extras["serve"] = {k: srv[k] for k in ("p50_ms", "p99_ms", "throughput_rps", "offered_rps", "mean_batch")}
         extras["serve"]["config"] = "1 s of the served Poisson stream (5k req/s); full line: --workload serve"
@@ -598,6 +645,7 @@ def main():
             "cpu_baseline": cpu,
             "matmul_tflops": extras["matmul"] if extras else None,
             "serve": extras["serve"] if extras else None,
+            "shapes_files": extras["shapes_files"] if extras else None,
         }
         print(json.dumps(line), flush=True)
     if dist:

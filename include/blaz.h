@@ -186,6 +186,33 @@ int blaz_matmul(const blaz_cmat *a, const double *B, int64_t ldb, int64_t m, dou
  * blaz_matmul with the same modes and accuracy (relative to |A_hat||B_hat|). */
 int blaz_matmul_cc(const blaz_cmat *a, const blaz_cmat *b, double *C, int64_t ldc, int mode, void *stream);
 
+/* ---- Matrices of any shape (padding) ----------------------------------------
+ * The paper states that the method works for matrices of any dimensions
+ * (Sec. IV, experimental setup) without fixing the partial blocks.  Here a
+ * rows x cols matrix is compressed as its extension to ceil8(rows) x
+ * ceil8(cols) that repeats the last row and the last column (edge
+ * replication, which keeps the boundary blocks as smooth as the data); the
+ * blaz_cmat holds that block grid, and the caller keeps the logical shape
+ * (BLAZ_ERR_SHAPE unless ceil8(rows) == a->rows and ceil8(cols) == a->cols).
+ * add, sub and scale apply unchanged (block-wise); the calls below restrict
+ * decompression, the flattened dot and the products to the logical entries. */
+int blaz_compress_padded(const double *A, int64_t lda, int64_t rows, int64_t cols, blaz_cmat *out, void *stream);
+/* Writes the logical rows x cols entries only (lda >= cols). */
+int blaz_decompress_padded(const blaz_cmat *a, int64_t rows, int64_t cols, double *A, int64_t lda, void *stream);
+/* <vec A_hat, vec B_hat> over the logical entries: full blocks in the Gram
+ * form, the partial blocks of the last block row and column decompressed in
+ * binary64 and summed over their logical entries. */
+int blaz_dot_padded(const blaz_cmat *a, const blaz_cmat *b, int64_t rows, int64_t cols, double *result,
+                    void *stream);
+/* C (n x m) = A_hat (logical n x k) * B (k x m, ldb >= m): A_hat is decoded
+ * with zeros outside the logical entries, B copied into a zero-padded
+ * ceil8(k)-row scratch when k is not a multiple of 8. */
+int blaz_matmul_padded(const blaz_cmat *a, int64_t n, int64_t k, const double *B, int64_t ldb, int64_t m, double *C,
+                       int64_t ldc, int mode, void *stream);
+/* C (n x m) = A_hat (logical n x k) * B_hat (logical k x m). */
+int blaz_matmul_cc_padded(const blaz_cmat *a, const blaz_cmat *b, int64_t n, int64_t k, int64_t m, double *C,
+                          int64_t ldc, int mode, void *stream);
+
 /* ---- Files: save and load compressed matrices ------------------------------
  * The 360-bit payload of Sec. II per block, stored as a little-endian file:
  *   bytes  0..7   magic "BLAZCMAT"

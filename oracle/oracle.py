@@ -280,3 +280,51 @@ def matmul_cc(a: CMat, b: CMat):
     assert a.cols == b.rows
     return matmul(a, decompress(b))
 
+
+
+# --- matrices of any shape (padding) ------------------------------------------
+# The paper states that the method works for matrices of any dimensions
+# without saying how the last partial blocks are formed.  Reading: the matrix
+# is extended to the next multiple of 8 in each direction by repeating its
+# last row and its last column (edge replication, so the boundary blocks stay
+# as smooth as the data); the compressed matrix is that of the extension, and
+# every result refers to the logical rows x cols entries only.
+
+def ceil8(n: int) -> int:
+    return (n + 7) // 8 * 8
+
+
+def pad_edge(A):
+    """The edge-replicated extension of A to multiples of 8."""
+    A = np.asarray(A, dtype=np.float64)
+    rows, cols = A.shape
+    r8, c8 = ceil8(rows), ceil8(cols)
+    if rows == 0 or cols == 0:
+        return np.zeros((r8, c8))
+    return np.pad(A, ((0, r8 - rows), (0, c8 - cols)), mode="edge")
+
+
+def compress_padded(A) -> CMat:
+    return compress(pad_edge(A))
+
+
+def decompress_padded(c: CMat, rows: int, cols: int):
+    assert (ceil8(rows), ceil8(cols)) == (c.rows, c.cols)
+    return decompress(c)[:rows, :cols]
+
+
+def dot_padded(a: CMat, b: CMat, rows: int, cols: int):
+    """<vec A_hat, vec B_hat> over the logical entries; (value, sum |A_hat B_hat|)."""
+    import math
+
+    p = decompress_padded(a, rows, cols) * decompress_padded(b, rows, cols)
+    return math.fsum(p.ravel().tolist()), math.fsum(np.abs(p).ravel().tolist())
+
+
+def matmul_padded(a: CMat, B, n: int, k: int):
+    """A_hat (logical n x k) @ B (k x m)."""
+    return decompress_padded(a, n, k) @ np.asarray(B, dtype=np.float64)
+
+
+def matmul_cc_padded(a: CMat, b: CMat, n: int, k: int, m: int):
+    return decompress_padded(a, n, k) @ decompress_padded(b, k, m)

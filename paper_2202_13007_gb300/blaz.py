@@ -104,6 +104,11 @@ SIGNATURES = {
     "blaz_dot_rowcol": (ctypes.c_int, [_DESC, _DESC, _I64, _I64, _P, _P]),
     "blaz_matmul": (ctypes.c_int, [_DESC, _P, _I64, _I64, _P, _I64, ctypes.c_int, _P]),
     "blaz_matmul_cc": (ctypes.c_int, [_DESC, _DESC, _P, _I64, ctypes.c_int, _P]),
+    "blaz_compress_padded": (ctypes.c_int, [_P, _I64, _I64, _I64, _DESC, _P]),
+    "blaz_decompress_padded": (ctypes.c_int, [_DESC, _I64, _I64, _P, _I64, _P]),
+    "blaz_dot_padded": (ctypes.c_int, [_DESC, _DESC, _I64, _I64, _P, _P]),
+    "blaz_matmul_padded": (ctypes.c_int, [_DESC, _I64, _I64, _P, _I64, _I64, _P, _I64, ctypes.c_int, _P]),
+    "blaz_matmul_cc_padded": (ctypes.c_int, [_DESC, _DESC, _I64, _I64, _I64, _P, _I64, ctypes.c_int, _P]),
     "blaz_cmat_save": (ctypes.c_int, [_DESC, ctypes.c_char_p, _P]),
     "blaz_cmat_file_info": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_int64),
                                            ctypes.POINTER(ctypes.c_int64)]),
@@ -177,6 +182,7 @@ class CMat:
     s: torch.Tensor      # float64 [nb]
     phi: torch.Tensor    # uint8   [nb]
     code: torch.Tensor   # int8    [nb, 28]
+    shape: tuple | None = None  # logical (rows, cols) when compressed by blaz_compress_padded
 
     @property
     def nb(self) -> int:
@@ -316,6 +322,80 @@ def blaz_matmul_cc(a: CMat, b: CMat, mode: str = "fp64", out: torch.Tensor | Non
     da, db = a.desc(), b.desc()
     _check(lib().blaz_matmul_cc(ctypes.byref(da), ctypes.byref(db), out.data_ptr(), _ld(out),
                                 _MODES[mode], _stream(stream)), "blaz_matmul_cc")
+    return out
+
+
+def _ceil8(n: int) -> int:
+    return (n + 7) // 8 * 8
+
+
+def blaz_compress_padded(A: torch.Tensor, out: CMat | None = None, stream=None) -> CMat:
+    """Compress a matrix of any shape (edge-replicated to multiples of 8);
+    the result's ``shape`` attribute keeps the logical (rows, cols)."""
+    _dev_f64(A, "A")
+    rows, cols = A.shape
+    if out is None:
+        out = CMat.empty(_ceil8(rows), _ceil8(cols), device=A.device)
+    d = out.desc()
+    _check(lib().blaz_compress_padded(A.data_ptr(), _ld(A), rows, cols, ctypes.byref(d), _stream(stream)),
+           "blaz_compress_padded")
+    out.shape = (rows, cols)
+    return out
+
+
+def _logical(a: CMat, shape):
+    return tuple(shape) if shape is not None else (a.shape or (a.rows, a.cols))
+
+
+def blaz_decompress_padded(a: CMat, shape=None, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    rows, cols = _logical(a, shape)
+    if out is None:
+        out = torch.empty((rows, cols), dtype=torch.float64, device=a.f.device)
+    _dev_f64(out, "out")
+    d = a.desc()
+    _check(lib().blaz_decompress_padded(ctypes.byref(d), rows, cols, out.data_ptr(), _ld(out), _stream(stream)),
+           "blaz_decompress_padded")
+    return out
+
+
+def blaz_dot_padded(a: CMat, b: CMat, shape=None, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    rows, cols = _logical(a, shape)
+    if out is None:
+        out = torch.empty((), dtype=torch.float64, device=a.f.device)
+    da, db = a.desc(), b.desc()
+    _check(lib().blaz_dot_padded(ctypes.byref(da), ctypes.byref(db), rows, cols, out.data_ptr(), _stream(stream)),
+           "blaz_dot_padded")
+    return out
+
+
+def blaz_matmul_padded(a: CMat, B: torch.Tensor, shape=None, mode: str = "fp64", out: torch.Tensor | None = None,
+                       stream=None) -> torch.Tensor:
+    n, k = _logical(a, shape)
+    _dev_f64(B, "B")
+    if B.shape[0] != k:
+        raise ValueError("inner dimensions differ")
+    m = B.shape[1]
+    if out is None:
+        out = torch.empty((n, m), dtype=torch.float64, device=B.device)
+    _dev_f64(out, "out")
+    da = a.desc()
+    _check(lib().blaz_matmul_padded(ctypes.byref(da), n, k, B.data_ptr(), _ld(B), m, out.data_ptr(), _ld(out),
+                                    _MODES[mode], _stream(stream)), "blaz_matmul_padded")
+    return out
+
+
+def blaz_matmul_cc_padded(a: CMat, b: CMat, a_shape=None, b_shape=None, mode: str = "fp64",
+                          out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    n, k = _logical(a, a_shape)
+    k2, m = _logical(b, b_shape)
+    if k != k2:
+        raise ValueError("inner dimensions differ")
+    if out is None:
+        out = torch.empty((n, m), dtype=torch.float64, device=a.f.device)
+    _dev_f64(out, "out")
+    da, db = a.desc(), b.desc()
+    _check(lib().blaz_matmul_cc_padded(ctypes.byref(da), ctypes.byref(db), n, k, m, out.data_ptr(), _ld(out),
+                                       _MODES[mode], _stream(stream)), "blaz_matmul_cc_padded")
     return out
 
 
@@ -508,3 +588,5 @@ def _from_ptr(ptr: int, nbytes: int, dtype, shape, dev):
 compress, decompress, add, sub, scale = blaz_compress, blaz_decompress, blaz_add, blaz_sub, blaz_scale
 dot, dot_rowcol, matmul, matmul_cc = blaz_dot, blaz_dot_rowcol, blaz_matmul, blaz_matmul_cc
 save, load, file_info = blaz_cmat_save, blaz_cmat_load, blaz_cmat_file_info
+compress_padded, decompress_padded, dot_padded = blaz_compress_padded, blaz_decompress_padded, blaz_dot_padded
+matmul_padded, matmul_cc_padded = blaz_matmul_padded, blaz_matmul_cc_padded

@@ -188,7 +188,39 @@ int blaz_compress(const double *A, int64_t lda, blaz_cmat *out, void *stream)
     cudaStream_t st = (cudaStream_t)stream;
     Scratch ws(st);
     if ((rc = ws.alloc(compress_scratch_bytes(nblocks(out))))) return rc;
-    return launch_compress(A, lda, out, ws.p, st);
+    return launch_compress(A, lda, out->rows, out->cols, out, ws.p, st);
+}
+
+static int64_t ceil8(int64_t n) { return (n + 7) / 8 * 8; }
+
+// A logical rows x cols shape whose edge-replicated extension is a's block grid.
+static int check_logical(const blaz_cmat *a, int64_t rows, int64_t cols)
+{
+    if (rows < 0 || cols < 0 || ceil8(rows) != a->rows || ceil8(cols) != a->cols) return BLAZ_ERR_SHAPE;
+    return BLAZ_OK;
+}
+
+int blaz_compress_padded(const double *A, int64_t lda, int64_t rows, int64_t cols, blaz_cmat *out, void *stream)
+{
+    int rc;
+    if ((rc = validate_cmat(out)) || (rc = check_logical(out, rows, cols))) return rc;
+    if (nblocks(out) == 0) return BLAZ_OK;
+    if (!A) return BLAZ_ERR_NULL;
+    if (lda < cols) return BLAZ_ERR_LD;
+    cudaStream_t st = (cudaStream_t)stream;
+    Scratch ws(st);
+    if ((rc = ws.alloc(compress_scratch_bytes(nblocks(out))))) return rc;
+    return launch_compress(A, lda, rows, cols, out, ws.p, st);
+}
+
+int blaz_decompress_padded(const blaz_cmat *a, int64_t rows, int64_t cols, double *A, int64_t lda, void *stream)
+{
+    int rc;
+    if ((rc = validate_cmat(a)) || (rc = check_logical(a, rows, cols))) return rc;
+    if (nblocks(a) == 0) return BLAZ_OK;
+    if (!A) return BLAZ_ERR_NULL;
+    if (lda < cols) return BLAZ_ERR_LD;
+    return launch_decompress(a, A, lda, (cudaStream_t)stream, rows, cols, false);
 }
 
 int blaz_decompress(const blaz_cmat *a, double *A, int64_t lda, void *stream)
@@ -242,6 +274,24 @@ int blaz_dot(const blaz_cmat *a, const blaz_cmat *b, double *result, void *strea
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), st);
     if (e != cudaSuccess) return set_cuda_error(e);
     return launch_dot(a, b, result, partials, counter, grid, st);
+}
+
+int blaz_dot_padded(const blaz_cmat *a, const blaz_cmat *b, int64_t rows, int64_t cols, double *result,
+                    void *stream)
+{
+    int rc;
+    if ((rc = validate_cmat(a)) || (rc = validate_cmat(b))) return rc;
+    if ((rc = same_shape(a, b)) || (rc = check_logical(a, rows, cols))) return rc;
+    if (!result) return BLAZ_ERR_NULL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int grid = dot_grid(nblocks(a));
+    Scratch ws(st);
+    if ((rc = ws.alloc(sizeof(double) * grid + 256))) return rc;
+    double *partials = (double *)ws.p;
+    unsigned *counter = (unsigned *)((char *)ws.p + ((sizeof(double) * grid + 255) & ~(size_t)255));
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    return launch_dot(a, b, result, partials, counter, grid, st, rows, cols);
 }
 
 int blaz_dot_rowcol(const blaz_cmat *a, const blaz_cmat *b, int64_t i, int64_t j, double *result, void *stream)
@@ -307,6 +357,104 @@ int blaz_matmul_cc(const blaz_cmat *a, const blaz_cmat *b, double *C, int64_t ld
     if (mode == BLAZ_MM_SPLIT_BF16)
         return launch_matmul_split_bf16(Ah, k, Bh, m, C, ldc, n, k, m, (char *)ws.p + ah_bytes + bh_bytes, st);
     return launch_gemm_fp64(Ah, k, Bh, m, C, ldc, n, k, m, st);
+}
+
+// Dense product of a zero-filled decoded Ah (n8 x k8) by B, for logical
+// n x k x m: B is copied into a zero-padded k8 x m scratch when k8 != k, and
+// the n8 x m result is cropped into C when n8 != n.
+static int padded_gemm(const double *Ah, int64_t n, int64_t k, int64_t n8, int64_t k8, const double *B, int64_t ldb,
+                       int64_t m, double *C, int64_t ldc, int mode, char *scratch, cudaStream_t st)
+{
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const double *Bu = B;
+    int64_t ldbu = ldb;
+    cudaError_t e = cudaSuccess;
+    if (k8 != k) {
+        double *Bp = (double *)scratch;
+        scratch += up(sizeof(double) * (size_t)(k8 * m));
+        if (k > 0)
+            e = cudaMemcpy2DAsync(Bp, sizeof(double) * m, B, sizeof(double) * ldb, sizeof(double) * m, k,
+                                  cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(Bp + k * m, 0, sizeof(double) * (size_t)((k8 - k) * m), st);
+        if (e != cudaSuccess) return set_cuda_error(e);
+        Bu = Bp;
+        ldbu = m;
+    }
+    double *Cu = C;
+    int64_t ldcu = ldc;
+    if (n8 != n) {
+        Cu = (double *)scratch;
+        scratch += up(sizeof(double) * (size_t)(n8 * m));
+        ldcu = m;
+    }
+    int rc = mode == BLAZ_MM_SPLIT_BF16 ? launch_matmul_split_bf16(Ah, k8, Bu, ldbu, Cu, ldcu, n8, k8, m, scratch, st)
+                                        : launch_gemm_fp64(Ah, k8, Bu, ldbu, Cu, ldcu, n8, k8, m, st);
+    if (rc || n8 == n) return rc;
+    e = cudaMemcpy2DAsync(C, sizeof(double) * ldc, Cu, sizeof(double) * m, sizeof(double) * m, n,
+                          cudaMemcpyDeviceToDevice, st);
+    return e == cudaSuccess ? BLAZ_OK : set_cuda_error(e);
+}
+
+static size_t padded_gemm_bytes(int64_t n, int64_t k, int64_t n8, int64_t k8, int64_t m, int mode)
+{
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    return (k8 != k ? up(sizeof(double) * (size_t)(k8 * m)) : 0) + (n8 != n ? up(sizeof(double) * (size_t)(n8 * m)) : 0) +
+           (mode == BLAZ_MM_SPLIT_BF16 ? split_bf16_scratch_bytes(n8, k8, m) : 0);
+}
+
+int blaz_matmul_padded(const blaz_cmat *a, int64_t n, int64_t k, const double *B, int64_t ldb, int64_t m, double *C,
+                       int64_t ldc, int mode, void *stream)
+{
+    int rc;
+    if ((rc = validate_cmat(a)) || (rc = check_logical(a, n, k))) return rc;
+    if (m < 0) return BLAZ_ERR_SHAPE;
+    if (mode != BLAZ_MM_FP64 && mode != BLAZ_MM_SPLIT_BF16) return BLAZ_ERR_ARG;
+    if (n == 0 || m == 0) return BLAZ_OK;
+    if (!C || (k > 0 && !B)) return BLAZ_ERR_NULL;
+    if (ldc < m || (k > 0 && ldb < m)) return BLAZ_ERR_LD;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n8 = a->rows, k8 = a->cols;
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t ah = up(sizeof(double) * (size_t)(n8 * k8));
+    Scratch ws(st);
+    if ((rc = ws.alloc(ah + padded_gemm_bytes(n, k, n8, k8, m, mode)))) return rc;
+    double *Ah = (double *)ws.p;
+    if (k8 > 0 && (rc = launch_decompress(a, Ah, k8, st, n, k, true))) return rc;
+    return padded_gemm(Ah, n, k, n8, k8, B, ldb, m, C, ldc, mode, (char *)ws.p + ah, st);
+}
+
+int blaz_matmul_cc_padded(const blaz_cmat *a, const blaz_cmat *b, int64_t n, int64_t k, int64_t m, double *C,
+                          int64_t ldc, int mode, void *stream)
+{
+    int rc;
+    if ((rc = validate_cmat(a)) || (rc = validate_cmat(b))) return rc;
+    if ((rc = check_logical(a, n, k)) || (rc = check_logical(b, k, m))) return rc;
+    if (mode != BLAZ_MM_FP64 && mode != BLAZ_MM_SPLIT_BF16) return BLAZ_ERR_ARG;
+    if (n == 0 || m == 0) return BLAZ_OK;
+    if (!C) return BLAZ_ERR_NULL;
+    if (ldc < m) return BLAZ_ERR_LD;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n8 = a->rows, k8 = a->cols, m8 = b->cols;
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t ah = up(sizeof(double) * (size_t)(n8 * k8)), bh = up(sizeof(double) * (size_t)(k8 * m8));
+    // B_hat is decoded zero-filled at its full k8 x m8 grid, so the product
+    // runs on k8 x m8 and only the n x m corner is kept.
+    const size_t cbytes = (n8 != n || m8 != m) ? up(sizeof(double) * (size_t)(n8 * m8)) : 0;
+    const size_t extra = mode == BLAZ_MM_SPLIT_BF16 ? split_bf16_scratch_bytes(n8, k8, m8) : 0;
+    Scratch ws(st);
+    if ((rc = ws.alloc(ah + bh + cbytes + extra))) return rc;
+    double *Ah = (double *)ws.p, *Bh = (double *)((char *)ws.p + ah);
+    if (k8 > 0 && (rc = launch_decompress(a, Ah, k8, st, n, k, true))) return rc;
+    if (k8 > 0 && (rc = launch_decompress(b, Bh, m8, st, k, m, true))) return rc;
+    double *Cu = cbytes ? (double *)((char *)ws.p + ah + bh) : C;
+    const int64_t ldcu = cbytes ? m8 : ldc;
+    char *sx = (char *)ws.p + ah + bh + cbytes;
+    rc = mode == BLAZ_MM_SPLIT_BF16 ? launch_matmul_split_bf16(Ah, k8, Bh, m8, Cu, ldcu, n8, k8, m8, sx, st)
+                                    : launch_gemm_fp64(Ah, k8, Bh, m8, Cu, ldcu, n8, k8, m8, st);
+    if (rc || !cbytes) return rc;
+    cudaError_t e = cudaMemcpy2DAsync(C, sizeof(double) * ldc, Cu, sizeof(double) * m8, sizeof(double) * m, n,
+                                      cudaMemcpyDeviceToDevice, st);
+    return e == cudaSuccess ? BLAZ_OK : set_cuda_error(e);
 }
 
 }  // extern "C"

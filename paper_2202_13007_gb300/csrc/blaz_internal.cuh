@@ -96,12 +96,20 @@ int batch_device_status();           // reads and clears the batch kernel's stat
 
 // ---- launchers (one per kernel family) ------------------------------------------
 size_t compress_scratch_bytes(int64_t nb);
-int launch_compress(const double *A, int64_t lda, const blaz_cmat *out, void *scratch, cudaStream_t st);
-int launch_decompress(const blaz_cmat *a, double *A, int64_t lda, cudaStream_t st);
+// rows x cols: the logical shape (rows, cols >= 1 when out has blocks); blocks
+// beyond it read the edge-replicated extension.
+int launch_compress(const double *A, int64_t lda, int64_t rows, int64_t cols, const blaz_cmat *out, void *scratch,
+                    cudaStream_t st);
+// rows x cols: the logical shape (-1: the block grid's); entries of partial
+// blocks beyond it are skipped, or written as 0 when zero_fill is set.
+int launch_decompress(const blaz_cmat *a, double *A, int64_t lda, cudaStream_t st, int64_t rows = -1,
+                      int64_t cols = -1, bool zero_fill = false);
 int launch_add(const blaz_cmat *a, const blaz_cmat *b, const blaz_cmat *out, bool subtract, cudaStream_t st);
 int launch_scale(const blaz_cmat *a, double c, const blaz_cmat *out, cudaStream_t st);
+// rows x cols: the logical shape (-1: the block grid's); for a padded pair the
+// partial blocks are summed over their logical entries by a second kernel.
 int launch_dot(const blaz_cmat *a, const blaz_cmat *b, double *result, double *partials, unsigned *counter,
-               int64_t max_ctas, cudaStream_t st);
+               int64_t max_ctas, cudaStream_t st, int64_t rows = -1, int64_t cols = -1);
 int dot_grid(int64_t nb);
 int rowcol_grid(int64_t nkb);
 int launch_dot_rowcol(const blaz_cmat *a, const blaz_cmat *b, int64_t i, int64_t j, double *result,

@@ -32,6 +32,22 @@ __device__ __forceinline__ void load_block(const double *__restrict__ A, int64_t
     }
 }
 
+// Block (bi, bj) of the edge-replicated extension of a rows x cols matrix
+// (rows, cols >= 1): entry (r, c) reads A at (min(r, rows-1), min(c, cols-1)).
+__device__ __forceinline__ void load_block_clamped(const double *__restrict__ A, int64_t lda, int64_t bi,
+                                                   int64_t bj, int64_t rows, int64_t cols, double (&d)[64])
+{
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int64_t r = bi * 8 + i < rows ? bi * 8 + i : rows - 1;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int64_t c = bj * 8 + j < cols ? bj * 8 + j : cols - 1;
+            d[i * 8 + j] = __ldg(A + r * lda + c);
+        }
+    }
+}
+
 // Compress one block held in d (overwritten).  Writes s, phi and the 28 codes.
 __device__ __forceinline__ void compress_block(double (&d)[64], double &s_out, uint8_t &phi_out,
                                                int8_t (&code)[kKeep])

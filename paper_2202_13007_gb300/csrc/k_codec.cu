@@ -39,7 +39,8 @@ constexpr int kFastThreads = 64;
 
 template <bool kVec>
 __global__ void __launch_bounds__(kFastThreads, 6)
-    k_compress_fast(const double *__restrict__ A, int64_t lda, int64_t nbc, int64_t nb, double *__restrict__ f,
+    k_compress_fast(const double *__restrict__ A, int64_t lda, int64_t rows, int64_t cols, int64_t nbc, int64_t nb,
+                    double *__restrict__ f,
                     double *__restrict__ s, uint8_t *__restrict__ phi, int8_t *__restrict__ code,
                     uint2 *__restrict__ code_list, unsigned *__restrict__ code_count,
                     unsigned *__restrict__ block_list, unsigned *__restrict__ block_count)
@@ -47,7 +48,8 @@ __global__ void __launch_bounds__(kFastThreads, 6)
     for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x) {
         const int64_t bi = b / nbc, bj = b - (b / nbc) * nbc;
         double d[64];
-        load_block<kVec>(A, lda, bi, bj, d);
+        if (bi * 8 + 8 <= rows && bj * 8 + 8 <= cols) load_block<kVec>(A, lda, bi, bj, d);
+        else load_block_clamped(A, lda, bi, bj, rows, cols, d);  // partial block of a padded matrix
         f[b] = d[0];
         double sv;
         uint8_t ph;
@@ -66,18 +68,21 @@ __global__ void __launch_bounds__(kFastThreads, 6)
 }
 
 // Row u of D' for block b, exactly as compress_block forms it: Eq. eqnorm
-// from rows u and u-1 of the input, then times r = 1/s (s as stored).
+// from rows u and u-1 of the input, then times r = 1/s (s as stored).  Rows
+// and columns beyond the logical rows x cols repeat the last one (padding).
 template <bool kVec>
-__device__ __forceinline__ void team_dprime_row(const double *__restrict__ A, int64_t lda, int64_t nbc, int64_t b,
-                                                int u, double s, double (&dp)[8])
+__device__ __forceinline__ void team_dprime_row(const double *__restrict__ A, int64_t lda, int64_t rows, int64_t cols,
+                                                int64_t nbc, int64_t b, int u, double s, double (&dp)[8])
 {
     const int64_t bi = b / nbc, bj = b - (b / nbc) * nbc;
-    const double *p = A + (bi * 8) * lda + bj * 8;
+    const int64_t r = bi * 8 + u < rows ? bi * 8 + u : rows - 1;
+    const int64_t rp = bi * 8 + u - 1 < rows ? bi * 8 + u - 1 : rows - 1;
     double cur[8], prev[8];
 #pragma unroll
     for (int v = 0; v < 8; ++v) {
-        cur[v] = __ldg(p + u * lda + v);
-        prev[v] = u > 0 ? __ldg(p + (u - 1) * lda + v) : 0.0;
+        const int64_t c = bj * 8 + v < cols ? bj * 8 + v : cols - 1;
+        cur[v] = __ldg(A + r * lda + c);
+        prev[v] = u > 0 ? __ldg(A + rp * lda + c) : 0.0;
     }
 #pragma unroll
     for (int v = 0; v < 8; ++v) {
@@ -85,9 +90,9 @@ __device__ __forceinline__ void team_dprime_row(const double *__restrict__ A, in
         else if (v == 0) dp[v] = dsub(cur[0], prev[0]);
         else dp[v] = dhalf(dadd(dsub(cur[v], prev[v]), dsub(cur[v], cur[v - 1])));
     }
-    const double r = ddiv(1.0, s);
+    const double rs = ddiv(1.0, s);
 #pragma unroll
-    for (int v = 0; v < 8; ++v) dp[v] = dmul(dp[v], r);
+    for (int v = 0; v < 8; ++v) dp[v] = dmul(dp[v], rs);
 }
 
 // Whole blocks whose phi was not certified (or with non-finite values): the
@@ -98,7 +103,8 @@ __device__ __forceinline__ void team_dprime_row(const double *__restrict__ A, in
 // shuffles, X[i][j], and its share of m = max |X| (NaN ignored, as in
 // compress_block: the maximum of non-NaN values is order-free).
 template <bool kVec>
-__device__ __forceinline__ void fix_whole_block(const double *__restrict__ A, int64_t lda, int64_t nbc, int64_t b,
+__device__ __forceinline__ void fix_whole_block(const double *__restrict__ A, int64_t lda, int64_t rows, int64_t cols,
+                                                int64_t nbc, int64_t b,
                                                 const double *__restrict__ s, uint8_t *__restrict__ phi,
                                                 int8_t *__restrict__ code, int u, int tbase, unsigned tmask)
 {
@@ -106,7 +112,7 @@ __device__ __forceinline__ void fix_whole_block(const double *__restrict__ A, in
 #pragma unroll
     for (int x = 0; x < 8; ++x) ci[x] = c_cos[u * 8 + x];
     double dp[8];
-    team_dprime_row<kVec>(A, lda, nbc, b, u, s[b], dp);
+    team_dprime_row<kVec>(A, lda, rows, cols, nbc, b, u, s[b], dp);
     double T[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
@@ -151,13 +157,14 @@ __device__ __forceinline__ void fix_whole_block(const double *__restrict__ A, in
 // set: for each, the team forms the inner sums T[u] (lane u) and the outer
 // sum over u in the specified order from the shuffles.
 template <bool kVec>
-__device__ __forceinline__ void fix_codes_of_block(const double *__restrict__ A, int64_t lda, int64_t nbc, int64_t b,
+__device__ __forceinline__ void fix_codes_of_block(const double *__restrict__ A, int64_t lda, int64_t rows,
+                                                   int64_t cols, int64_t nbc, int64_t b,
                                                    uint32_t pending, const double *__restrict__ s,
                                                    const uint8_t *__restrict__ phi, int8_t *__restrict__ code, int u,
                                                    int tbase, unsigned tmask)
 {
     double dp[8];
-    team_dprime_row<kVec>(A, lda, nbc, b, u, s[b], dp);
+    team_dprime_row<kVec>(A, lda, rows, cols, nbc, b, u, s[b], dp);
     const int ph = phi[b];
     for (uint32_t m = pending; m; m &= m - 1) {
         const int t = __ffs(m) - 1;
@@ -184,7 +191,8 @@ __device__ __forceinline__ void fix_codes_of_block(const double *__restrict__ A,
 // lists hold different blocks, so the entries are independent.
 template <bool kVec>
 __global__ void __launch_bounds__(128)
-    k_compress_fix(const double *__restrict__ A, int64_t lda, int64_t nbc, const unsigned *__restrict__ block_list,
+    k_compress_fix(const double *__restrict__ A, int64_t lda, int64_t rows, int64_t cols, int64_t nbc,
+                   const unsigned *__restrict__ block_list,
                    const uint2 *__restrict__ code_list, const unsigned *__restrict__ counts,
                    const double *__restrict__ s, uint8_t *__restrict__ phi, int8_t *__restrict__ code)
 {
@@ -194,10 +202,10 @@ __global__ void __launch_bounds__(128)
     const int64_t teams = (int64_t)gridDim.x * blockDim.x / 8;
     for (int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 8; q < nblocks + ncodes; q += teams) {
         if (q < nblocks) {
-            fix_whole_block<kVec>(A, lda, nbc, block_list[q], s, phi, code, u, tbase, tmask);
+            fix_whole_block<kVec>(A, lda, rows, cols, nbc, block_list[q], s, phi, code, u, tbase, tmask);
         } else {
             const uint2 e = code_list[q - nblocks];
-            fix_codes_of_block<kVec>(A, lda, nbc, e.x, e.y, s, phi, code, u, tbase, tmask);
+            fix_codes_of_block<kVec>(A, lda, rows, cols, nbc, e.x, e.y, s, phi, code, u, tbase, tmask);
         }
     }
 }
@@ -282,7 +290,7 @@ template <bool kVec>
 __global__ void __launch_bounds__(128)
     k_decompress(const __grid_constant__ DecConsts dc, const double *__restrict__ f, const double *__restrict__ s,
                  const uint8_t *__restrict__ phi, const int8_t *__restrict__ code, int64_t nbc, int64_t nb,
-                 double *__restrict__ A, int64_t lda)
+                 double *__restrict__ A, int64_t lda, int64_t rows, int64_t cols, bool zero_fill)
 {
     __shared__ uint2 sb[kDecSlices][2][8][32];
     for (int i = threadIdx.x; i < kDecSlices * 2 * 8 * 32; i += blockDim.x)
@@ -328,15 +336,30 @@ __global__ void __launch_bounds__(128)
             const double ts = __ldg(s + b) * dc.inv_phi[__ldg(phi + b)] * dc.scale;
             const int64_t bi = b / nbc, bj = b - bi * nbc;
             double *p = A + (bi * 8) * lda + bj * 8 + 2 * t;
+            // A partial block of a padded matrix: entries outside the logical
+            // rows x cols are skipped (cropped output) or written as 0.
+            const bool inside = bi * 8 + 8 <= rows && bj * 8 + 8 <= cols;
+            const bool c0in = bj * 8 + 2 * t < cols, c1in = bj * 8 + 2 * t + 1 < cols;
 #pragma unroll
             for (int nt = 0; nt < 8; ++nt) {
                 const double o0 = fma(ts, i64_to_double(acc[nt][2 * h]), fb);
                 const double o1 = fma(ts, i64_to_double(acc[nt][2 * h + 1]), fb);
-                if (kVec) {
-                    *reinterpret_cast<double2 *>(p + nt * lda) = make_double2(o0, o1);
+                if (inside) {
+                    if (kVec) {
+                        *reinterpret_cast<double2 *>(p + nt * lda) = make_double2(o0, o1);
+                    } else {
+                        p[nt * lda] = o0;
+                        p[nt * lda + 1] = o1;
+                    }
                 } else {
-                    p[nt * lda] = o0;
-                    p[nt * lda + 1] = o1;
+                    const bool rin = bi * 8 + nt < rows;
+                    if (zero_fill) {
+                        p[nt * lda] = rin && c0in ? o0 : 0.0;
+                        p[nt * lda + 1] = rin && c1in ? o1 : 0.0;
+                    } else {
+                        if (rin && c0in) p[nt * lda] = o0;
+                        if (rin && c1in) p[nt * lda + 1] = o1;
+                    }
                 }
             }
         }
@@ -361,7 +384,8 @@ size_t compress_scratch_bytes(int64_t nb)
     return up((size_t)nb * 8) + up((size_t)nb * 4) + 256;
 }
 
-int launch_compress(const double *A, int64_t lda, const blaz_cmat *out, void *scratch, cudaStream_t st)
+int launch_compress(const double *A, int64_t lda, int64_t rows, int64_t cols, const blaz_cmat *out, void *scratch,
+                    cudaStream_t st)
 {
     const int64_t nbc = out->cols / 8, nb = (out->rows / 8) * nbc;
     if (nb == 0) return BLAZ_OK;
@@ -375,33 +399,38 @@ int launch_compress(const double *A, int64_t lda, const blaz_cmat *out, void *sc
     const int threads = 128;
     const int fix_grid = num_sms() * 4;  // one resident wave (72 registers per thread)
     if (vec_ok(A, lda)) {
-        k_compress_fast<true><<<fast_grid(nb), kFastThreads, 0, st>>>(A, lda, nbc, nb, out->f, out->s,
-                                                                      out->phi, out->code, code_list, counts,
-                                                                      block_list, counts + 1);
-        k_compress_fix<true><<<fix_grid, threads, 0, st>>>(A, lda, nbc, block_list, code_list, counts, out->s,
-                                                            out->phi, out->code);
+        k_compress_fast<true><<<fast_grid(nb), kFastThreads, 0, st>>>(A, lda, rows, cols, nbc, nb, out->f,
+                                                                      out->s, out->phi, out->code, code_list,
+                                                                      counts, block_list, counts + 1);
+        k_compress_fix<true><<<fix_grid, threads, 0, st>>>(A, lda, rows, cols, nbc, block_list, code_list, counts,
+                                                            out->s, out->phi, out->code);
     } else {
-        k_compress_fast<false><<<fast_grid(nb), kFastThreads, 0, st>>>(A, lda, nbc, nb, out->f, out->s,
-                                                                       out->phi, out->code, code_list, counts,
-                                                                       block_list, counts + 1);
-        k_compress_fix<false><<<fix_grid, threads, 0, st>>>(A, lda, nbc, block_list, code_list, counts, out->s,
-                                                             out->phi, out->code);
+        k_compress_fast<false><<<fast_grid(nb), kFastThreads, 0, st>>>(A, lda, rows, cols, nbc, nb, out->f,
+                                                                       out->s, out->phi, out->code, code_list,
+                                                                       counts, block_list, counts + 1);
+        k_compress_fix<false><<<fix_grid, threads, 0, st>>>(A, lda, rows, cols, nbc, block_list, code_list, counts,
+                                                             out->s, out->phi, out->code);
     }
     return launch_status();
 }
 
-int launch_decompress(const blaz_cmat *a, double *A, int64_t lda, cudaStream_t st)
+int launch_decompress(const blaz_cmat *a, double *A, int64_t lda, cudaStream_t st, int64_t rows, int64_t cols,
+                      bool zero_fill)
 {
     const int64_t nbc = a->cols / 8, nb = (a->rows / 8) * nbc;
     if (nb == 0) return BLAZ_OK;
+    if (rows < 0) rows = a->rows;
+    if (cols < 0) cols = a->cols;
     const int threads = 128;
     int64_t want = ((nb + 15) / 16 + 3) / 4;
     const int64_t cap = (int64_t)num_sms() * 16;
     const int grid = (int)std::max<int64_t>(1, std::min(want, cap));
     if (vec_ok(A, lda))
-        k_decompress<true><<<grid, threads, 0, st>>>(dec_consts(), a->f, a->s, a->phi, a->code, nbc, nb, A, lda);
+        k_decompress<true><<<grid, threads, 0, st>>>(dec_consts(), a->f, a->s, a->phi, a->code, nbc, nb, A, lda,
+                                                     rows, cols, zero_fill);
     else
-        k_decompress<false><<<grid, threads, 0, st>>>(dec_consts(), a->f, a->s, a->phi, a->code, nbc, nb, A, lda);
+        k_decompress<false><<<grid, threads, 0, st>>>(dec_consts(), a->f, a->s, a->phi, a->code, nbc, nb, A, lda,
+                                                      rows, cols, zero_fill);
     return launch_status();
 }
 

@@ -157,7 +157,8 @@ __global__ void __launch_bounds__(kDotThreads)
     k_dot_tc(const __grid_constant__ GramTC g, int64_t nb, const double *__restrict__ fa, const double *__restrict__ sa,
              const uint8_t *__restrict__ pa, const int8_t *__restrict__ ca, const double *__restrict__ fb,
              const double *__restrict__ sb, const uint8_t *__restrict__ pb, const int8_t *__restrict__ cb,
-             double *__restrict__ partials, unsigned *__restrict__ counter, double *__restrict__ result)
+             double *__restrict__ partials, unsigned *__restrict__ counter, double *__restrict__ result,
+             int64_t nbc, int64_t rows, int64_t cols, bool padded)
 {
     __shared__ uint2 sbf[kSlices][2][4][32];
     __shared__ float swl[kSlices][32][8];
@@ -251,7 +252,12 @@ __global__ void __launch_bounds__(kDotThreads)
         if (t < 2) {
             const int h = t;
             const int64_t b = h ? bB : bA;
-            if (h ? vB : vA) {
+            bool full = true;  // partial blocks of a padded matrix are left to k_dot_boundary
+            if (padded) {
+                const int64_t bi = b / nbc, bj = b - bi * nbc;
+                full = bi * 8 + 8 <= rows && bj * 8 + 8 <= cols;
+            }
+            if ((h ? vB : vA) && full) {
                 long long qhi = 0, qlo = 0, ahi = 0, alo = 0, bhi = 0, blo = 0;
 #pragma unroll
                 for (int sl = 0; sl < kSlices; ++sl) {
@@ -504,14 +510,74 @@ int dot_grid(int64_t nb)
     return (int)(want < 1 ? 1 : want);
 }
 
-int launch_dot(const blaz_cmat *a, const blaz_cmat *b, double *result, double *partials, unsigned *counter,
-               int64_t max_ctas, cudaStream_t st)
+// The partial blocks of a padded matrix pair (the last block row when rows is
+// not a multiple of 8, then the last block column when cols is not, without
+// the corner twice): each thread decompresses one block of each operand in
+// binary64 and sums the products of its logical entries, row-major.  CTA
+// partials are added in CTA order by the last CTA, which adds the sum of the
+// full blocks already in *result.
+__global__ void __launch_bounds__(kDotThreads)
+    k_dot_boundary(const double *__restrict__ fa, const double *__restrict__ sa, const uint8_t *__restrict__ pa,
+                   const int8_t *__restrict__ ca, const double *__restrict__ fb, const double *__restrict__ sb,
+                   const uint8_t *__restrict__ pb, const int8_t *__restrict__ cb, int64_t nbr, int64_t nbc,
+                   int64_t rows, int64_t cols, int64_t nbd, double *__restrict__ partials,
+                   unsigned *__restrict__ counter, double *__restrict__ result)
 {
-    const int64_t nb = (a->rows / 8) * (a->cols / 8);
+    __shared__ double red[kDotThreads / 32];
+    __shared__ bool last;
+    const int64_t nrow = rows % 8 ? nbc : 0;
+    double acc = 0.0;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nbd; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t bi = q < nrow ? nbr - 1 : q - nrow, bj = q < nrow ? q : nbc - 1;
+        const int64_t b = bi * nbc + bj;
+        double x[64], y[64];
+        decompress_block_at(fa[b], sa[b], pa[b], ca + b * kKeep, x);
+        decompress_block_at(fb[b], sb[b], pb[b], cb + b * kKeep, y);
+        const int64_t ri = rows - bi * 8 < 8 ? rows - bi * 8 : 8, cj = cols - bj * 8 < 8 ? cols - bj * 8 : 8;
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (i < ri && j < cj) acc = fma(x[i * 8 + j], y[i * 8 + j], acc);
+    }
+    const double tot = cta_sum(acc, red);
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = tot;
+        __threadfence();
+        last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double v = 0.0;
+    for (int q = threadIdx.x; q < (int)gridDim.x; q += blockDim.x) v += __ldcg(partials + q);
+    const double r = cta_sum(v, red);
+    if (threadIdx.x == 0) {
+        *result = __ldcg(result) + r;
+        *counter = 0u;
+    }
+}
+
+int launch_dot(const blaz_cmat *a, const blaz_cmat *b, double *result, double *partials, unsigned *counter,
+               int64_t max_ctas, cudaStream_t st, int64_t rows, int64_t cols)
+{
+    const int64_t nbc = a->cols / 8, nb = (a->rows / 8) * nbc;
+    if (rows < 0) rows = a->rows;
+    if (cols < 0) cols = a->cols;
+    const bool padded = rows != a->rows || cols != a->cols;
     int grid = dot_grid(nb);
     if (grid > max_ctas) grid = (int)max_ctas;
     k_dot_tc<<<grid, kDotThreads, 0, st>>>(gram_tc(), nb, a->f, a->s, a->phi, a->code, b->f, b->s, b->phi,
-                                           b->code, partials, counter, result);
+                                           b->code, partials, counter, result, nbc, rows, cols, padded);
+    int rc = launch_status();
+    if (rc || !padded) return rc;
+    // The partial blocks: the last block row and/or the last block column.
+    const int64_t nbr = a->rows / 8;
+    const int64_t nbd = (rows % 8 ? nbc : 0) + (cols % 8 ? nbr - (rows % 8 ? 1 : 0) : 0);
+    int64_t want = (nbd + kDotThreads - 1) / kDotThreads;
+    const int bgrid = (int)std::max<int64_t>(1, std::min<int64_t>(want, std::min<int64_t>(max_ctas, num_sms())));
+    k_dot_boundary<<<bgrid, kDotThreads, 0, st>>>(a->f, a->s, a->phi, a->code, b->f, b->s, b->phi, b->code, nbr,
+                                                  nbc, rows, cols, nbd, partials, counter, result);
     return launch_status();
 }
 

@@ -13,6 +13,13 @@ def pytest_configure(config):
     config.addinivalue_line("markers", "slow: long-running CPU test")
 
 
+def split_bf16_tol(k):
+    """(|A_hat||B|)_ij multiplier of the split-bf16 product: fp32 accumulation
+    over the 6k slice products plus the three-slice representation error
+    (about 2^-24 of each operand)."""
+    return (6 * k + 8) * 2.0 ** -24
+
+
 def load_golden(name):
     """Parse a tests/golden/*.txt fixture into {section: [rows of tokens]}."""
     path = os.path.join(ROOT, "tests", "golden", name)

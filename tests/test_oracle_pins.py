@@ -246,6 +246,46 @@ def test_round_trip_within_quantization_bound():
         assert np.all(np.abs(back[8 * bi:8 * bi + 8, 8 * bj:8 * bj + 8] - M) <= bound)
 
 
+@pytest.mark.parametrize("shape", [(13, 21), (8, 3), (5, 8), (1, 1), (29, 16)])
+def test_padded_shapes_round_trip_and_logical_results(shape):
+    """Any shape (padding reading: edge replication to multiples of 8).  The
+    logical entries come back within each block's quantization bound; the
+    extension repeats the last row and column; on multiples of 8 nothing
+    changes; dot and products over the logical entries equal numpy's on the
+    cropped decompressions."""
+    rows, cols = shape
+    rng = np.random.default_rng(rows * 31 + cols)
+    A = np.sin(np.arange(rows)[:, None] / 3.0) * np.cos(np.arange(cols)[None, :] / 5.0) + 0.01 * rng.standard_normal(shape)
+    Bm = rng.standard_normal(shape)
+    P = O.pad_edge(A)
+    assert P.shape == (O.ceil8(rows), O.ceil8(cols))
+    assert np.array_equal(P[:rows, :cols], A)
+    assert np.all(P[rows:, :cols] == A[-1, :]) and np.all(P[:, cols:] == P[:, cols - 1:cols])
+    c = O.compress_padded(A)
+    back = O.decompress_padded(c, rows, cols)
+    full = O.decompress(c)
+    for b in range(c.nb):
+        bi, bj = divmod(b, c.cols // 8)
+        st = O.block_stages(P[8 * bi:8 * bi + 8, 8 * bj:8 * bj + 8])
+        bound = _roundtrip_bound(st) + 1e-12 * (1 + np.abs(P).max())
+        err = np.abs(full[8 * bi:8 * bi + 8, 8 * bj:8 * bj + 8] - P[8 * bi:8 * bi + 8, 8 * bj:8 * bj + 8])
+        assert np.all(err <= bound)
+    assert np.array_equal(back, full[:rows, :cols])
+    cb = O.compress_padded(Bm)
+    v, av = O.dot_padded(c, cb, rows, cols)
+    Bh = O.decompress_padded(cb, rows, cols)
+    assert abs(v - float(np.dot(back.ravel(), Bh.ravel()))) <= 1e-13 * av
+    D = rng.standard_normal((cols, 7))
+    assert np.allclose(O.matmul_padded(c, D, rows, cols), back @ D, rtol=0, atol=1e-13 * (np.abs(back) @ np.abs(D)).max())
+    E = rng.standard_normal((cols, 11))
+    ce = O.compress_padded(E)
+    Ccc = O.matmul_cc_padded(c, ce, rows, cols, 11)
+    assert np.allclose(Ccc, back @ O.decompress_padded(ce, cols, 11), rtol=0, atol=1e-13)
+    A8 = rng.standard_normal((16, 24))
+    c8, d8 = O.compress_padded(A8), O.compress(A8)
+    assert np.array_equal(c8.code, d8.code) and np.array_equal(c8.f, d8.f) and np.array_equal(c8.s, d8.s)
+
+
 # --- Algorithms 1 and 2 -------------------------------------------------------------
 def _blocks(X):
     r, cc = X.shape

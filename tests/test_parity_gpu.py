@@ -18,6 +18,7 @@ import torch
 
 import oracle as O
 import workloads as W
+from conftest import split_bf16_tol
 
 pytestmark = pytest.mark.gpu
 
@@ -335,12 +336,6 @@ def test_precision_config_matmul_fp64_sampled(B):
 
 
 # --- split-precision tensor-core product -----------------------------------------------------
-def split_bf16_tol(k):
-    """(|A_hat||B|)_ij multiplier: fp32 accumulation over the 6k slice products
-    plus the three-slice representation error (about 2^-24 of each operand)."""
-    return (6 * k + 8) * 2.0 ** -24
-
-
 @pytest.mark.parametrize("n,k,m", [(256, 256, 256), (72, 136, 50), (8, 8, 1), (64, 1024, 129), (384, 64, 520)])
 def test_matmul_split_bf16(B, n, k, m):
     A = W.random_block_matrix(n, k, seed=n + k)
