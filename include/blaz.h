@@ -220,7 +220,8 @@ int blaz_matmul_cc_padded(const blaz_cmat *a, const blaz_cmat *b, int64_t n, int
  *         16..23  int64 rows              24..31 int64 cols
  *         32..39  int64 nb = (rows/8)(cols/8)
  *         40..47  uint64 payload bytes = 45 nb
- *         48..55  uint64 FNV-1a 64-bit hash of the payload
+ *         48..55  uint64 FNV-1a 64-bit hash of the payload taken over
+ *                 little-endian 64-bit words (last word zero-padded)
  *         56..63  zero
  *   payload: f[nb] (binary64), s[nb] (binary64), phi[nb] (uint8),
  *            code[nb][28] (int8), in block order.

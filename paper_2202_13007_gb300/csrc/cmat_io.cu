@@ -24,11 +24,23 @@ struct Header {
 };
 static_assert(sizeof(Header) == kHeaderBytes, "header layout");
 
-// FNV-1a, 64-bit (offset basis 14695981039346656037, prime 1099511628211).
-uint64_t fnv1a(const unsigned char *p, size_t n, uint64_t h = 14695981039346656037ull)
+// FNV-1a, 64-bit (offset basis 14695981039346656037, prime 1099511628211),
+// taken over the payload as little-endian 64-bit words (the last word padded
+// with zero bytes) rather than bytes: eight times fewer steps.
+uint64_t fnv1a64(const unsigned char *p, size_t n)
 {
-    for (size_t i = 0; i < n; ++i) {
-        h ^= p[i];
+    uint64_t h = 14695981039346656037ull;
+    size_t i = 0;
+    for (; i + 8 <= n; i += 8) {
+        uint64_t w;
+        std::memcpy(&w, p + i, 8);
+        h ^= w;
+        h *= 1099511628211ull;
+    }
+    if (i < n) {
+        uint64_t w = 0;
+        std::memcpy(&w, p + i, n - i);
+        h ^= w;
         h *= 1099511628211ull;
     }
     return h;
@@ -102,7 +114,7 @@ int blaz_cmat_save(const blaz_cmat *a, const char *path, void *stream)
     h.cols = a->cols;
     h.nb = nb;
     h.payload_bytes = payload.size();
-    h.hash = fnv1a(payload.data(), payload.size());
+    h.hash = fnv1a64(payload.data(), payload.size());
     h.zero = 0;
     const std::string tmp = std::string(path) + ".tmp";
     {
@@ -147,7 +159,7 @@ int blaz_cmat_load(const char *path, blaz_cmat *out, void *stream)
     std::vector<unsigned char> payload((size_t)h.payload_bytes);
     if (!payload.empty() && std::fread(payload.data(), payload.size(), 1, f.f) != 1) return BLAZ_ERR_FORMAT;
     if (std::fgetc(f.f) != EOF) return BLAZ_ERR_FORMAT;  // trailing bytes
-    if (fnv1a(payload.data(), payload.size()) != h.hash) return BLAZ_ERR_FORMAT;
+    if (fnv1a64(payload.data(), payload.size()) != h.hash) return BLAZ_ERR_FORMAT;
     if (out->rows != h.rows || out->cols != h.cols) return BLAZ_ERR_SHAPE;
     if ((rc = validate_cmat(out))) return rc;
     const int64_t nb = h.nb;

@@ -574,9 +574,11 @@ int launch_dot(const blaz_cmat *a, const blaz_cmat *b, double *result, double *p
     // The partial blocks: the last block row and/or the last block column.
     const int64_t nbr = a->rows / 8;
     const int64_t nbd = (rows % 8 ? nbc : 0) + (cols % 8 ? nbr - (rows % 8 ? 1 : 0) : 0);
-    int64_t want = (nbd + kDotThreads - 1) / kDotThreads;
-    const int bgrid = (int)std::max<int64_t>(1, std::min<int64_t>(want, std::min<int64_t>(max_ctas, num_sms())));
-    k_dot_boundary<<<bgrid, kDotThreads, 0, st>>>(a->f, a->s, a->phi, a->code, b->f, b->s, b->phi, b->code, nbr,
+    // One warp per CTA: each thread decodes two blocks in binary64, so the
+    // O(n) partial blocks are spread over as many SMs as possible.
+    const int64_t want = (nbd + 31) / 32;
+    const int bgrid = (int)std::max<int64_t>(1, std::min<int64_t>(want, max_ctas));
+    k_dot_boundary<<<bgrid, 32, 0, st>>>(a->f, a->s, a->phi, a->code, b->f, b->s, b->phi, b->code, nbr,
                                                   nbc, rows, cols, nbd, partials, counter, result);
     return launch_status();
 }

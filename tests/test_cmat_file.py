@@ -19,9 +19,11 @@ NKEEP = 28
 
 
 def fnv1a(data: bytes) -> int:
+    """FNV-1a 64 over little-endian 64-bit words, the last one zero-padded."""
     h = 14695981039346656037
-    for b in data:
-        h ^= b
+    data = data + b"\0" * (-len(data) % 8)
+    for (w,) in struct.iter_unpack("<Q", data):
+        h ^= w
         h = (h * 1099511628211) & 0xFFFFFFFFFFFFFFFF
     return h
 
