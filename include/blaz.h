@@ -237,6 +237,23 @@ int blaz_cmat_file_info(const char *path, int64_t *rows, int64_t *cols);
  * (BLAZ_ERR_SHAPE otherwise). */
 int blaz_cmat_load(const char *path, blaz_cmat *out, void *stream);
 
+/* ---- Host buffers ----------------------------------------------------------
+ * blaz_compress of a matrix in HOST memory (A: host pointer, lda >= cols;
+ * page-locked memory runs at the link rate).  The matrix moves in slabs of
+ * block rows (~48 MB) into a ring of three device staging buffers on a copy
+ * stream owned by the library (one per device; transfers of successive calls
+ * run in issue order), and `stream` compresses every slab as it lands, so
+ * the compression hides behind the transfer.  Asynchronous: A must stay valid
+ * and unchanged until `stream` has passed the call.  Same bits as
+ * blaz_compress.  Device memory: the ring plus 12 bytes per block of a slab,
+ * stream-ordered. */
+int blaz_compress_host(const double *A, int64_t lda, blaz_cmat *out, void *stream);
+/* The packed payload of a compressed matrix (the file payload layout:
+ * f[nb], s[nb], phi[nb], code[nb][28]; 45 nb bytes) to / from host memory,
+ * stream-ordered (asynchronous for page-locked host memory). */
+int blaz_cmat_download(const blaz_cmat *a, void *host, void *stream);
+int blaz_cmat_upload(const void *host, blaz_cmat *a, void *stream);
+
 /* ---- Batched mixed operations: one persistent, graph-captured launch ----------
  * Many compressed-matrix operations of different kinds and sizes (the
  * block-wise algorithms of Sec. III applied to whole matrices) run as one

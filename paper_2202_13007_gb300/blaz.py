@@ -109,6 +109,9 @@ SIGNATURES = {
     "blaz_dot_padded": (ctypes.c_int, [_DESC, _DESC, _I64, _I64, _P, _P]),
     "blaz_matmul_padded": (ctypes.c_int, [_DESC, _I64, _I64, _P, _I64, _I64, _P, _I64, ctypes.c_int, _P]),
     "blaz_matmul_cc_padded": (ctypes.c_int, [_DESC, _DESC, _I64, _I64, _I64, _P, _I64, ctypes.c_int, _P]),
+    "blaz_compress_host": (ctypes.c_int, [_P, _I64, _DESC, _P]),
+    "blaz_cmat_download": (ctypes.c_int, [_DESC, _P, _P]),
+    "blaz_cmat_upload": (ctypes.c_int, [_P, _DESC, _P]),
     "blaz_cmat_save": (ctypes.c_int, [_DESC, ctypes.c_char_p, _P]),
     "blaz_cmat_file_info": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_int64),
                                            ctypes.POINTER(ctypes.c_int64)]),
@@ -399,6 +402,41 @@ def blaz_matmul_cc_padded(a: CMat, b: CMat, a_shape=None, b_shape=None, mode: st
     return out
 
 
+def blaz_compress_host(A: torch.Tensor, out: CMat | None = None, stream=None) -> CMat:
+    """Compress a float64 matrix held in host memory (page-locked for full
+    speed); transfer and compression are pipelined by the library.  `A` must
+    not change until the stream has passed the call."""
+    if A.is_cuda or A.dtype != torch.float64 or A.dim() != 2:
+        raise TypeError("A must be a 2-D float64 host tensor")
+    if A.numel() and A.stride(1) != 1:
+        raise TypeError("A must have unit column stride")
+    rows, cols = A.shape
+    out = out or CMat.empty(rows, cols)
+    if (out.rows, out.cols) != (rows, cols):
+        raise ValueError("out shape mismatch")
+    d = out.desc()
+    _check(lib().blaz_compress_host(A.data_ptr(), _ld(A), ctypes.byref(d), _stream(stream)), "blaz_compress_host")
+    return out
+
+
+def blaz_cmat_download(a: CMat, host: torch.Tensor, stream=None) -> torch.Tensor:
+    """Copy the packed payload (45 bytes per block) into a uint8 host tensor."""
+    if host.is_cuda or host.dtype != torch.uint8 or host.numel() < a.nbytes or not host.is_contiguous():
+        raise TypeError("host must be a contiguous uint8 host tensor of at least a.nbytes bytes")
+    d = a.desc()
+    _check(lib().blaz_cmat_download(ctypes.byref(d), host.data_ptr(), _stream(stream)), "blaz_cmat_download")
+    return host
+
+
+def blaz_cmat_upload(host: torch.Tensor, a: CMat, stream=None) -> CMat:
+    """Fill `a` from a packed payload in a uint8 host tensor."""
+    if host.is_cuda or host.dtype != torch.uint8 or host.numel() < a.nbytes or not host.is_contiguous():
+        raise TypeError("host must be a contiguous uint8 host tensor of at least a.nbytes bytes")
+    d = a.desc()
+    _check(lib().blaz_cmat_upload(host.data_ptr(), ctypes.byref(d), _stream(stream)), "blaz_cmat_upload")
+    return a
+
+
 def blaz_cmat_save(a: CMat, path, stream=None) -> None:
     """Write `a` to `path` (format in include/blaz.h); blocks until written."""
     da = a.desc()
@@ -590,3 +628,4 @@ dot, dot_rowcol, matmul, matmul_cc = blaz_dot, blaz_dot_rowcol, blaz_matmul, bla
 save, load, file_info = blaz_cmat_save, blaz_cmat_load, blaz_cmat_file_info
 compress_padded, decompress_padded, dot_padded = blaz_compress_padded, blaz_decompress_padded, blaz_dot_padded
 matmul_padded, matmul_cc_padded = blaz_matmul_padded, blaz_matmul_cc_padded
+compress_host, download, upload = blaz_compress_host, blaz_cmat_download, blaz_cmat_upload

@@ -64,27 +64,6 @@ static int same_shape(const blaz_cmat *a, const blaz_cmat *b)
     return (a->rows == b->rows && a->cols == b->cols) ? BLAZ_OK : BLAZ_ERR_SHAPE;
 }
 
-// Stream-ordered scratch that is released on the same stream.
-struct Scratch {
-    void *p = nullptr;
-    cudaStream_t st;
-    explicit Scratch(cudaStream_t s) : st(s) {}
-    int alloc(size_t bytes)
-    {
-        cudaError_t e = cudaMallocAsync(&p, bytes ? bytes : 16, st);
-        if (e != cudaSuccess) {
-            p = nullptr;
-            cudaGetLastError();
-            return e == cudaErrorMemoryAllocation ? BLAZ_ERR_OOM : set_cuda_error(e);
-        }
-        return BLAZ_OK;
-    }
-    ~Scratch()
-    {
-        if (p) cudaFreeAsync(p, st);
-    }
-};
-
 }  // namespace blaz
 
 using namespace blaz;

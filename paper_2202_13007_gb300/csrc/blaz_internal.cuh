@@ -92,6 +92,27 @@ int set_cuda_error(cudaError_t e);   // records e, returns BLAZ_ERR_CUDA
 int launch_status();                 // cudaGetLastError -> BLAZ_OK / BLAZ_ERR_CUDA
 int num_sms();                       // SM count of the current device (cached)
 int validate_cmat(const blaz_cmat *m);   // shape, NULL and alignment checks of a descriptor
+
+// Stream-ordered scratch that is released on the same stream.
+struct Scratch {
+    void *p = nullptr;
+    cudaStream_t st;
+    explicit Scratch(cudaStream_t s) : st(s) {}
+    int alloc(size_t bytes)
+    {
+        cudaError_t e = cudaMallocAsync(&p, bytes ? bytes : 16, st);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            cudaGetLastError();
+            return e == cudaErrorMemoryAllocation ? BLAZ_ERR_OOM : set_cuda_error(e);
+        }
+        return BLAZ_OK;
+    }
+    ~Scratch()
+    {
+        if (p) cudaFreeAsync(p, st);
+    }
+};
 int batch_device_status();           // reads and clears the batch kernel's status word
 
 // ---- launchers (one per kernel family) ------------------------------------------

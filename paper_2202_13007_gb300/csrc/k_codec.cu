@@ -311,54 +311,63 @@ __global__ void __launch_bounds__(128)
         a1[1] = code_pair(cB, 16 + 2 * t, vB);
         a1[2] = code_pair(cA, 24 + 2 * t, vA);
         a1[3] = code_pair(cB, 24 + 2 * t, vB);
-        long long acc[8][4];
+        // Per block (h = 0: bA, 1: bB): base f, scale (s/phi) 2^E, output row
+        // pointer and the logical-shape flags of a partial block.
+        double fb[2], ts[2];
+        double *pb[2];
+        bool inside[2], c0in[2], c1in[2];
+        int64_t r0[2];
 #pragma unroll
-        for (int nt = 0; nt < 8; ++nt)
+        for (int h = 0; h < 2; ++h) {
+            const int64_t b = h ? bB : bA;
+            const bool v = h ? vB : vA;
+            const int64_t bi = v ? b / nbc : 0, bj = v ? b - bi * nbc : 0;
+            fb[h] = v ? __ldg(f + b) : 0.0;
+            ts[h] = v ? __ldg(s + b) * dc.inv_phi[__ldg(phi + b)] * dc.scale : 0.0;
+            pb[h] = A + (bi * 8) * lda + bj * 8 + 2 * t;
+            r0[h] = bi * 8;
+            inside[h] = bi * 8 + 8 <= rows && bj * 8 + 8 <= cols;
+            c0in[h] = bj * 8 + 2 * t < cols;
+            c1in[h] = bj * 8 + 2 * t + 1 < cols;
+        }
+        // One output row nt of every block at a time: the four slice products
+        // (exact fp32 integers) are assembled in int64 and stored at once, so
+        // only four accumulators are live.
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc[nt][q] = 0;
+        for (int nt = 0; nt < 8; ++nt) {
+            long long acc[4] = {0, 0, 0, 0};
 #pragma unroll
-        for (int sl = 0; sl < kDecSlices; ++sl) {
-#pragma unroll
-            for (int nt = 0; nt < 8; ++nt) {
+            for (int sl = 0; sl < kDecSlices; ++sl) {
                 float c[4] = {0.f, 0.f, 0.f, 0.f};
                 mma_f16(c, a0, sb[sl][0][nt][lane]);
                 mma_f16(c, a1, sb[sl][1][nt][lane]);
 #pragma unroll
-                for (int q = 0; q < 4; ++q) acc[nt][q] = acc[nt][q] * 2048 + f2i_small(c[q]);
+                for (int q = 0; q < 4; ++q) acc[q] = acc[q] * 2048 + f2i_small(c[q]);
             }
-        }
-        // c0, c1: block bA, row nt, columns 2t, 2t+1; c2, c3: block bB.
+            // c0, c1: block bA, row nt, columns 2t, 2t+1; c2, c3: block bB.
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int64_t b = h ? bB : bA;
-            if (!(h ? vB : vA)) continue;
-            const double fb = __ldg(f + b);
-            const double ts = __ldg(s + b) * dc.inv_phi[__ldg(phi + b)] * dc.scale;
-            const int64_t bi = b / nbc, bj = b - bi * nbc;
-            double *p = A + (bi * 8) * lda + bj * 8 + 2 * t;
-            // A partial block of a padded matrix: entries outside the logical
-            // rows x cols are skipped (cropped output) or written as 0.
-            const bool inside = bi * 8 + 8 <= rows && bj * 8 + 8 <= cols;
-            const bool c0in = bj * 8 + 2 * t < cols, c1in = bj * 8 + 2 * t + 1 < cols;
-#pragma unroll
-            for (int nt = 0; nt < 8; ++nt) {
-                const double o0 = fma(ts, i64_to_double(acc[nt][2 * h]), fb);
-                const double o1 = fma(ts, i64_to_double(acc[nt][2 * h + 1]), fb);
-                if (inside) {
+            for (int h = 0; h < 2; ++h) {
+                if (!(h ? vB : vA)) continue;
+                const double o0 = fma(ts[h], i64_to_double(acc[2 * h]), fb[h]);
+                const double o1 = fma(ts[h], i64_to_double(acc[2 * h + 1]), fb[h]);
+                double *p = pb[h] + nt * lda;
+                if (inside[h]) {
                     if (kVec) {
-                        *reinterpret_cast<double2 *>(p + nt * lda) = make_double2(o0, o1);
+                        *reinterpret_cast<double2 *>(p) = make_double2(o0, o1);
                     } else {
-                        p[nt * lda] = o0;
-                        p[nt * lda + 1] = o1;
+                        p[0] = o0;
+                        p[1] = o1;
                     }
                 } else {
-                    const bool rin = bi * 8 + nt < rows;
+                    // A partial block of a padded matrix: entries outside the
+                    // logical rows x cols are skipped (cropped output) or 0.
+                    const bool rin = r0[h] + nt < rows;
                     if (zero_fill) {
-                        p[nt * lda] = rin && c0in ? o0 : 0.0;
-                        p[nt * lda + 1] = rin && c1in ? o1 : 0.0;
+                        p[0] = rin && c0in[h] ? o0 : 0.0;
+                        p[1] = rin && c1in[h] ? o1 : 0.0;
                     } else {
-                        if (rin && c0in) p[nt * lda] = o0;
-                        if (rin && c1in) p[nt * lda + 1] = o1;
+                        if (rin && c0in[h]) p[0] = o0;
+                        if (rin && c1in[h]) p[1] = o1;
                     }
                 }
             }
@@ -422,8 +431,18 @@ int launch_decompress(const blaz_cmat *a, double *A, int64_t lda, cudaStream_t s
     if (rows < 0) rows = a->rows;
     if (cols < 0) cols = a->cols;
     const int threads = 128;
+    // One resident wave of CTAs (each first stages 16 KB of B fragments in
+    // shared memory), striding over groups of 16 blocks.
+    static const int occ = [] {
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_decompress<true>, 128, 0) != cudaSuccess) {
+            (void)cudaGetLastError();
+            n = 4;
+        }
+        return n > 0 ? n : 1;
+    }();
     int64_t want = ((nb + 15) / 16 + 3) / 4;
-    const int64_t cap = (int64_t)num_sms() * 16;
+    const int64_t cap = (int64_t)num_sms() * occ;
     const int grid = (int)std::max<int64_t>(1, std::min(want, cap));
     if (vec_ok(A, lda))
         k_decompress<true><<<grid, threads, 0, st>>>(dec_consts(), a->f, a->s, a->phi, a->code, nbc, nb, A, lda,
