@@ -7,7 +7,7 @@
 // The host-to-device link is the bound of compressing a host matrix (about
 // 210 GB/s on this machine against ~700 GB/s of compression throughput), so
 // the matrix is moved in slabs of block rows on a copy stream into a ring of
-// device staging buffers while the caller's stream compresses the slabs
+// device staging buffers (up to 512 MB) while the caller's stream compresses the slabs
 // already landed; every slab's blocks form a contiguous range of the output.
 #include <mutex>
 #include <vector>
@@ -17,8 +17,12 @@
 namespace blaz {
 namespace {
 
-constexpr int kRing = 3;                          // staging buffers in flight
 constexpr size_t kSlabBytes = (size_t)48 << 20;   // target bytes per slab
+// Staging in flight: up to 512 MB (ten slabs), so that the transfer can run
+// ~2.4 ms ahead of compressions queued behind other work on the caller's
+// stream.
+constexpr size_t kRingBytes = (size_t)512 << 20;
+constexpr int kRingMax = 16;
 
 // One non-blocking copy stream per device, shared by all calls so that the
 // transfers of successive calls queue behind each other in issue order.
@@ -34,15 +38,15 @@ cudaStream_t copy_stream(int dev)
 }
 
 struct Events {
-    cudaEvent_t e[2 * kRing + 1] = {};  // the last one marks the copy stream on an early exit
+    cudaEvent_t e[2 * kRingMax + 1] = {};
     int n = 0;
     ~Events()
     {
         for (int i = 0; i < n; ++i) cudaEventDestroy(e[i]);  // released once the recorded work completes
     }
-    cudaError_t create()
+    cudaError_t create(int count)
     {
-        for (; n < 2 * kRing + 1; ++n) {
+        for (; n < count; ++n) {
             cudaError_t r = cudaEventCreateWithFlags(&e[n], cudaEventDisableTiming);
             if (r != cudaSuccess) return r;
         }
@@ -77,11 +81,13 @@ int blaz_compress_host(const double *A, int64_t lda, blaz_cmat *out, void *strea
     if (slab < 8) slab = 8;
     if (slab > rows) slab = rows;
     const int64_t nslab = (rows + slab - 1) / slab;
-    const int nbuf = nslab < kRing ? (int)nslab : kRing;
     auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t buf_bytes = up(row_bytes * (size_t)slab);
-    Events ev;  // [0, kRing): slab landed in buffer b; [kRing, 2 kRing): buffer b free again
-    if ((e = ev.create()) != cudaSuccess) return set_cuda_error(e);
+    int64_t ring = (int64_t)(kRingBytes / buf_bytes);
+    ring = ring < 2 ? 2 : (ring > kRingMax ? kRingMax : ring);
+    const int nbuf = (int)(nslab < ring ? nslab : ring);
+    Events ev;  // [0, nbuf): slab landed in buffer b; [nbuf, 2 nbuf): buffer b free again; last: early exit
+    if ((e = ev.create(2 * nbuf + 1)) != cudaSuccess) return set_cuda_error(e);
     Scratch ws(st);  // compress lists, reused slab after slab on `st`
     if ((rc = ws.alloc(compress_scratch_bytes((slab / 8) * nbc)))) return rc;
     // The staging ring is allocated on the copy stream (so the transfers do
@@ -94,7 +100,7 @@ int blaz_compress_host(const double *A, int64_t lda, blaz_cmat *out, void *strea
     }
     auto finish = [&](int status) {
         // on an early exit, `st` first waits for whatever the copy stream holds
-        cudaEvent_t last = ev.e[2 * kRing];
+        cudaEvent_t last = ev.e[2 * nbuf];
         if (status != BLAZ_OK && cudaEventRecord(last, cs) == cudaSuccess) cudaStreamWaitEvent(st, last, 0);
         cudaFreeAsync(stage, st);
         return status;
@@ -103,7 +109,7 @@ int blaz_compress_host(const double *A, int64_t lda, blaz_cmat *out, void *strea
         const int b = (int)(k % nbuf);
         const int64_t r0 = k * slab, nr = rows - r0 < slab ? rows - r0 : slab;
         double *buf = (double *)((char *)stage + b * buf_bytes);
-        if (k >= nbuf && (e = cudaStreamWaitEvent(cs, ev.e[kRing + b], 0)) != cudaSuccess)
+        if (k >= nbuf && (e = cudaStreamWaitEvent(cs, ev.e[nbuf + b], 0)) != cudaSuccess)
             return finish(set_cuda_error(e));
         e = cudaMemcpy2DAsync(buf, row_bytes, A + r0 * lda, sizeof(double) * (size_t)lda, row_bytes, (size_t)nr,
                               cudaMemcpyHostToDevice, cs);
@@ -113,7 +119,7 @@ int blaz_compress_host(const double *A, int64_t lda, blaz_cmat *out, void *strea
         const int64_t b0 = (r0 / 8) * nbc;
         blaz_cmat sub{nr, cols, out->f + b0, out->s + b0, out->phi + b0, out->code + b0 * kKeep};
         if ((rc = launch_compress(buf, cols, nr, cols, &sub, ws.p, st))) return finish(rc);
-        if ((e = cudaEventRecord(ev.e[kRing + b], st)) != cudaSuccess) return finish(set_cuda_error(e));
+        if ((e = cudaEventRecord(ev.e[nbuf + b], st)) != cudaSuccess) return finish(set_cuda_error(e));
     }
     return finish(BLAZ_OK);
 }
