@@ -6,6 +6,7 @@
 #pragma once
 
 #include "blaz_internal.cuh"
+#include "exact_div.cuh"
 
 namespace blaz {
 
@@ -37,8 +38,11 @@ __device__ __forceinline__ void add_block(int64_t b, const double *f1, const dou
     } else {
         const double a1 = ddiv(sa, ss);
         const double a2 = ddiv(sb, ss);
-        const double b1 = dmul(ddiv(a1, (double)pa), (double)ph);
-        const double b2 = dmul(ddiv(a2, (double)pb), (double)ph);
+        // beta_k = (alpha_k / phi_k) phi: division by the integer phi_k without
+        // a division sequence, integers converted on the integer pipe
+        const double phd = i64_to_double(ph);
+        const double b1 = dmul(div_small_int(a1, pa), phd);
+        const double b2 = dmul(div_small_int(a2, pb), phd);
 #pragma unroll
         for (int q = 0; q < 7; ++q) {
             uint32_t v = 0;
@@ -123,8 +127,11 @@ __device__ __forceinline__ void add_block_fast(int64_t b, const double *f1, cons
     } else {
         const double a1 = ddiv(sa, ss);
         const double a2 = ddiv(sb, ss);
-        const double b1 = dmul(ddiv(a1, (double)pa), (double)ph);
-        const double b2 = dmul(ddiv(a2, (double)pb), (double)ph);
+        // beta_k = (alpha_k / phi_k) phi: division by the integer phi_k without
+        // a division sequence, integers converted on the integer pipe
+        const double phd = i64_to_double(ph);
+        const double b1 = dmul(div_small_int(a1, pa), phd);
+        const double b2 = dmul(div_small_int(a2, pb), phd);
         const unsigned e1 = ((unsigned)__double2hiint(b1) >> 20) & 0x7FF, e2 = ((unsigned)__double2hiint(b2) >> 20) & 0x7FF;
         // fp32 path for finite |b| < 2^100 (no Inf / NaN / overflow in fp32)
         const bool fast = e1 < 1023 + 100 && e2 < 1023 + 100;

@@ -29,6 +29,7 @@
 #pragma once
 
 #include "block_codec.cuh"
+#include "exact_div.cuh"
 #include "gmap.cuh"
 
 namespace blaz {
@@ -122,40 +123,8 @@ __device__ __forceinline__ int nonzero_bits(double x)
     return m != 0u;
 }
 
-// RN(1/k) for k = 1..64 (entry k-1), exact hex literals.
-__device__ __align__(16) double c_rcp_k[64] = {
-    0x1.0000000000000p+0, 0x1.0000000000000p-1, 0x1.5555555555555p-2, 0x1.0000000000000p-2,
-    0x1.999999999999ap-3, 0x1.5555555555555p-3, 0x1.2492492492492p-3, 0x1.0000000000000p-3,
-    0x1.c71c71c71c71cp-4, 0x1.999999999999ap-4, 0x1.745d1745d1746p-4, 0x1.5555555555555p-4,
-    0x1.3b13b13b13b14p-4, 0x1.2492492492492p-4, 0x1.1111111111111p-4, 0x1.0000000000000p-4,
-    0x1.e1e1e1e1e1e1ep-5, 0x1.c71c71c71c71cp-5, 0x1.af286bca1af28p-5, 0x1.999999999999ap-5,
-    0x1.8618618618618p-5, 0x1.745d1745d1746p-5, 0x1.642c8590b2164p-5, 0x1.5555555555555p-5,
-    0x1.47ae147ae147bp-5, 0x1.3b13b13b13b14p-5, 0x1.2f684bda12f68p-5, 0x1.2492492492492p-5,
-    0x1.1a7b9611a7b96p-5, 0x1.1111111111111p-5, 0x1.0842108421084p-5, 0x1.0000000000000p-5,
-    0x1.f07c1f07c1f08p-6, 0x1.e1e1e1e1e1e1ep-6, 0x1.d41d41d41d41dp-6, 0x1.c71c71c71c71cp-6,
-    0x1.bacf914c1bad0p-6, 0x1.af286bca1af28p-6, 0x1.a41a41a41a41ap-6, 0x1.999999999999ap-6,
-    0x1.8f9c18f9c18fap-6, 0x1.8618618618618p-6, 0x1.7d05f417d05f4p-6, 0x1.745d1745d1746p-6,
-    0x1.6c16c16c16c17p-6, 0x1.642c8590b2164p-6, 0x1.5c9882b931057p-6, 0x1.5555555555555p-6,
-    0x1.4e5e0a72f0539p-6, 0x1.47ae147ae147bp-6, 0x1.4141414141414p-6, 0x1.3b13b13b13b14p-6,
-    0x1.3521cfb2b78c1p-6, 0x1.2f684bda12f68p-6, 0x1.29e4129e4129ep-6, 0x1.2492492492492p-6,
-    0x1.1f7047dc11f70p-6, 0x1.1a7b9611a7b96p-6, 0x1.15b1e5f75270dp-6, 0x1.1111111111111p-6,
-    0x1.0c9714fbcda3bp-6, 0x1.0842108421084p-6, 0x1.0410410410410p-6, 0x1.0000000000000p-6};
-
-// s = RN(S/K) for an integer count 1 <= K <= 64 by one product and two fused
-// corrections (Markstein's theorem: with y = RN(1/K), q a faithful quotient
-// and the exact remainder r = S - K q, RN(q + r y) is the correctly rounded
-// quotient); used for 2^-900 <= S < Inf, where neither step can leave the
-// normal range.  Other S take the general division.
-__device__ __forceinline__ double div_by_count(double S, int K)
-{
-    const unsigned es = (unsigned)__double2hiint(S) >> 20;  // S >= 0
-    const double Kd = i64_to_double(K);
-    if (es < 1023 - 900 || es >= 0x7FF) return ddiv(S, Kd);
-    const double y = __ldg(&c_rcp_k[K - 1]);
-    const double q = dmul(S, y);
-    const double r = __fma_rn(-q, Kd, S);
-    return __fma_rn(r, y, q);
-}
+// s = RN(S/K) for the nonzero count 1 <= K <= 64 (exact_div.cuh).
+__device__ __forceinline__ double div_by_count(double S, int K) { return div_small_int(S, K); }
 
 constexpr uint32_t kPendingAll = 0x80000000u;  // phi not certified / non-finite: whole block exact
 

@@ -54,73 +54,7 @@ struct GramConsts {
 // Exact conversion of an integer-valued float with |x| < 2^24 to int.
 __device__ __forceinline__ int f2i_exact(float x) { return __float2int_rn(x); }
 
-// sum_s scale[s] * (hi_s * 4096 + lo_s), the slices combined in binary64.
-__device__ __forceinline__ double combine(const float (&hi)[kSlices], const float (&lo)[kSlices],
-                                          const double (&scale)[kSlices], float hi_mult)
-{
-    double r = 0.0;
-#pragma unroll
-    for (int s = 0; s < kSlices; ++s) {
-        const long long v = (long long)f2i_exact(hi[s]) * (long long)hi_mult + (long long)f2i_exact(lo[s]);
-        r = fma(scale[s], i64_to_double(v), r);
-    }
-    return r;
-}
-
-__device__ __forceinline__ void codes_to_float(const int8_t *__restrict__ src, float (&x)[kKeep])
-{
-    const uint32_t *w = reinterpret_cast<const uint32_t *>(src);
-#pragma unroll
-    for (int q = 0; q < 7; ++q) {
-        const uint32_t v = __ldg(w + q);
-#pragma unroll
-        for (int b = 0; b < 4; ++b) x[4 * q + b] = (float)(int)(int8_t)(uint8_t)(v >> (8 * b));
-    }
-}
-
-// <A_hat_b, B_hat_b> of block b from the codes (see the file comment).
-__device__ __forceinline__ double block_dot_gram(const GramConsts &g, double fa, double sa, int pa,
-                                                 const int8_t *__restrict__ ca, double fb, double sb, int pb,
-                                                 const int8_t *__restrict__ cb)
-{
-    float xa[kKeep], xb[kKeep];
-    codes_to_float(ca, xa);
-    codes_to_float(cb, xb);
-    float wa[kSlices], wb[kSlices], zero[kSlices];
-    float qh[kSlices], ql[kSlices];
-#pragma unroll
-    for (int s = 0; s < kSlices; ++s) {
-        float pa_ = 0.0f, pb_ = 0.0f;
-#pragma unroll
-        for (int t = 0; t < kKeep; ++t) {
-            pa_ = fmaf(g.w[s][t], xa[t], pa_);
-            pb_ = fmaf(g.w[s][t], xb[t], pb_);
-        }
-        wa[s] = pa_;
-        wb[s] = pb_;
-        zero[s] = 0.0f;
-        float h = 0.0f, l = 0.0f;
-#pragma unroll
-        for (int k = 0; k < kKeep; ++k) {
-            float y = 0.0f;
-#pragma unroll
-            for (int j = 0; j < kKeep; ++j) y = fmaf(g.H[s][k][j], xb[j], y);
-            const float yh = rintf(y * (1.0f / 4096.0f));
-            const float yl = fmaf(-4096.0f, yh, y);
-            h = fmaf(xa[k], yh, h);
-            l = fmaf(xa[k], yl, l);
-        }
-        qh[s] = h;
-        ql[s] = l;
-    }
-    const double Wa = combine(zero, wa, g.scaleW, 0.0f);
-    const double Wb = combine(zero, wb, g.scaleW, 0.0f);
-    const double Q = combine(qh, ql, g.scaleH, 4096.0f);
-    const double ta = sa * g.inv_phi[pa], tb = sb * g.inv_phi[pb];
-    return 64.0 * fa * fb + fa * tb * Wb + fb * ta * Wa + ta * tb * Q;
-}
-
-// Tensor-core form of block_dot_gram, 16 blocks per warp.  Y_s = C_b H_s
+// Tensor-core form of the Gram dot, 16 blocks per warp.  Y_s = C_b H_s
 // (plus the column w_s) on mma.sync m16n8k16 with fp16 digits of H_s and w_s
 // (|digit| <= 2^10, exact in fp16) and fp16 codes; every product sum is an
 // integer below 2^22, exact in the fp32 accumulators.  Then, per row of the
@@ -153,7 +87,7 @@ __device__ __forceinline__ uint32_t code_pair_h(const int8_t *__restrict__ c, in
 __device__ __forceinline__ float half_lo(uint32_t p) { return __half2float(__ushort_as_half((unsigned short)(p & 0xFFFF))); }
 __device__ __forceinline__ float half_hi(uint32_t p) { return __half2float(__ushort_as_half((unsigned short)(p >> 16))); }
 
-__global__ void __launch_bounds__(kDotThreads)
+__global__ void __launch_bounds__(kDotThreads, 3)
     k_dot_tc(const __grid_constant__ GramTC g, int64_t nb, const double *__restrict__ fa, const double *__restrict__ sa,
              const uint8_t *__restrict__ pa, const int8_t *__restrict__ ca, const double *__restrict__ fb,
              const double *__restrict__ sb, const uint8_t *__restrict__ pb, const int8_t *__restrict__ cb,
@@ -289,39 +223,6 @@ __global__ void __launch_bounds__(kDotThreads)
         partials[blockIdx.x] = tot;
         __threadfence();
         last = (atomicAdd(counter, 1u) == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    double v = 0.0;
-    for (int q = threadIdx.x; q < (int)gridDim.x; q += blockDim.x) v += __ldcg(partials + q);
-    const double r = cta_sum(v, red);
-    if (threadIdx.x == 0) {
-        *result = r;
-        *counter = 0u;
-    }
-}
-
-// Flattened dot.  Every CTA writes its partial sum; the last CTA to finish
-// adds the partials in CTA order and resets the arrival counter.
-__global__ void __launch_bounds__(kDotThreads)
-    k_dot(const __grid_constant__ GramConsts g, int64_t nb, const double *__restrict__ fa,
-          const double *__restrict__ sa, const uint8_t *__restrict__ pa, const int8_t *__restrict__ ca,
-          const double *__restrict__ fb, const double *__restrict__ sb, const uint8_t *__restrict__ pb,
-          const int8_t *__restrict__ cb, double *__restrict__ partials, unsigned *__restrict__ counter,
-          double *__restrict__ result)
-{
-    __shared__ double red[kDotThreads / 32];
-    __shared__ bool last;
-    double acc = 0.0;
-    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x)
-        acc += block_dot_gram(g, fa[b], sa[b], pa[b], ca + b * kKeep, fb[b], sb[b], pb[b], cb + b * kKeep);
-    const double tot = cta_sum(acc, red);
-    if (threadIdx.x == 0) {
-        partials[blockIdx.x] = tot;
-        __threadfence();
-        const unsigned arrived = atomicAdd(counter, 1u);
-        last = (arrived == gridDim.x - 1);
     }
     __syncthreads();
     if (!last) return;
@@ -505,7 +406,9 @@ static const GramTC &gram_tc()
 int dot_grid(int64_t nb)
 {
     int64_t want = ((nb + 15) / 16 + (kDotThreads / 32) - 1) / (kDotThreads / 32);
-    int64_t cap = (int64_t)num_sms() * 4;
+    // two resident waves (3 CTAs of 256 threads per SM), never more than the
+    // 1024 partial sums of the no-allocation entry point
+    int64_t cap = std::min<int64_t>((int64_t)num_sms() * 6, 1024);
     if (want > cap) want = cap;
     return (int)(want < 1 ? 1 : want);
 }

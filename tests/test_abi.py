@@ -73,14 +73,14 @@ def test_strerror_and_argument_errors_without_gpu(libblaz):
     assert libblaz.blaz_matmul(ctypes.byref(empty), None, 0, 4, None, 4, 7, None) == -9   # bad mode
 
 
-def test_count_reciprocal_table_is_correctly_rounded():
-    """The compressor divides the slope sum S by the count K through a table
-    of RN(1/K) (Eq. eqslope2 evaluated by Markstein's correction): each entry
-    must be the correctly rounded reciprocal, which Python's IEEE division
-    gives."""
-    src = open(os.path.join(ROOT, "paper_2202_13007_gb300", "csrc", "compress_fast.cuh")).read()
-    body = src[src.index("c_rcp_k[64] = {"):]
+def test_integer_reciprocal_table_is_correctly_rounded():
+    """Divisions by an integer (S/K of Eq. eqslope2, alpha_k/phi_k of
+    Algorithm 1) use a table of RN(1/k) and Markstein's correction: each
+    entry must be the correctly rounded reciprocal, which Python's IEEE
+    division gives."""
+    src = open(os.path.join(ROOT, "paper_2202_13007_gb300", "csrc", "exact_div.cuh")).read()
+    body = src[src.index("c_rcp_k[256] = {"):]
     body = body[body.index("{") + 1:body.index("}")]
     vals = [float.fromhex(t) for t in body.replace("\n", " ").split(",") if t.strip()]
-    assert len(vals) == 64
-    assert all(v == 1.0 / k for k, v in zip(range(1, 65), vals))
+    assert len(vals) == 256
+    assert all(v == 1.0 / k for k, v in zip(range(1, 257), vals))
