@@ -194,6 +194,105 @@ def cpu_baseline(side: int, rows: int = 8192):
                       f"({nb} blocks, {secs:.1f} s)"}
 
 
+def cpu_parallel(side: int, rows: int = 8192):
+    """The same oracle step block-parallel over the host cores: the sample is
+    cut into block-row slabs, one oracle call chain per slab, on a thread pool
+    (the C oracle runs without the GIL)."""
+    import concurrent.futures as cf
+
+    import oracle as O
+
+    O.build()
+    O.dct_tables()                      # initialise the oracle's tables before threading
+    A, Bm = oracle_sample(side, rows)
+    cores = os.cpu_count() or 1
+    step = max(8, (rows // cores) // 8 * 8)
+    spans = [(r, min(rows, r + step)) for r in range(0, rows, step)]
+    t = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+        list(ex.map(lambda sp: run_oracle_step(O, A[sp[0]:sp[1]], Bm[sp[0]:sp[1]]), spans))
+    secs = time.perf_counter() - t
+    nb = (rows // 8) * (side // 8)
+    byts = nb * sum(BYTES_PER_BLOCK[o] for o in STEP_OPS)
+    return {"value": byts / secs / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle, block-parallel",
+            "sample": f"the oracle step on the first {rows} rows of both {side}x{side} fields in "
+                      f"{len(spans)} block-row slabs on {cores} threads ({secs:.2f} s)"}
+
+
+def plain_way(B, torch, ca, cb, dev):
+    """The same operations done the plain way on the same GPU: decompress,
+    operate in binary64 (torch), recompress; against the compressed-domain
+    operations.  Accuracy: each result against the exact operation on the
+    decompressed operands (max |error| / max |exact|)."""
+    n = ca.rows
+    Ah = torch.empty((n, n), dtype=torch.float64, device=dev)
+    Bh = torch.empty_like(Ah)
+    Xh = torch.empty_like(Ah)
+    cx = B.CMat.empty(n, n, dev)
+    res = torch.empty((), dtype=torch.float64, device=dev)
+
+    def timed(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    def plain_add():
+        B.decompress(ca, out=Ah)
+        B.decompress(cb, out=Bh)
+        torch.add(Ah, Bh, out=Xh)
+        B.compress(Xh, out=cx)
+
+    def plain_scale():
+        B.decompress(ca, out=Ah)
+        torch.mul(Ah, 3.5, out=Xh)
+        B.compress(Xh, out=cx)
+
+    def plain_dot():
+        B.decompress(ca, out=Ah)
+        B.decompress(cb, out=Bh)
+        torch.dot(Ah.view(-1), Bh.view(-1), out=res)
+
+    out = {"add": {"compressed_ms": timed(lambda: B.add(ca, cb, out=cx)), "plain_ms": timed(plain_add)},
+           "scale": {"compressed_ms": timed(lambda: B.scale(ca, 3.5, out=cx)), "plain_ms": timed(plain_scale)},
+           "dot": {"compressed_ms": timed(lambda: B.dot(ca, cb, out=res)), "plain_ms": timed(plain_dot)}}
+    # accuracy against the exact operation on the decompressed operands
+    B.decompress(ca, out=Ah)
+    B.decompress(cb, out=Bh)
+    exact = Ah + Bh
+    scale_ = float(exact.abs().max())
+    B.add(ca, cb, out=cx)
+    B.decompress(cx, out=Xh)
+    out["add"]["compressed_err"] = float((Xh - exact).abs().max()) / scale_
+    B.compress(exact, out=cx)
+    B.decompress(cx, out=Xh)
+    out["add"]["plain_err"] = float((Xh - exact).abs().max()) / scale_
+    exact = Ah * 3.5
+    scale_ = float(exact.abs().max())
+    B.scale(ca, 3.5, out=cx)
+    B.decompress(cx, out=Xh)
+    out["scale"]["compressed_err"] = float((Xh - exact).abs().max()) / scale_
+    B.compress(exact, out=cx)
+    B.decompress(cx, out=Xh)
+    out["scale"]["plain_err"] = float((Xh - exact).abs().max()) / scale_
+    ref = float(torch.dot(Ah.view(-1), Bh.view(-1)))
+    absref = float(torch.dot(Ah.abs().view(-1), Bh.abs().view(-1)))
+    out["dot"]["compressed_err"] = abs(float(B.dot(ca, cb, out=res)) - ref) / absref
+    out["dot"]["plain_err"] = 0.0
+    for v in out.values():
+        v["speedup"] = v["plain_ms"] / v["compressed_ms"]
+    out["config"] = (f"{n}x{n} bump fields: plain = decompress (blaz), binary64 op (torch), recompress (blaz); "
+                     "err = max|result - exact op on the decompressed operands| / max|exact| "
+                     "(dot: |error| / sum|A_hat B_hat|)")
+    del Ah, Bh, Xh
+    return out
+
+
 def reference_arm(args, rank: int, world: int):
     """--impl reference: the oracle as it stands, timed on the host cores."""
     if rank != 0:
@@ -634,14 +733,17 @@ def main():
     if rank == 0 and not args.no_extras:
         del dec
         torch.cuda.empty_cache()
-        extras = {"matmul": matmul_extras(B, W, torch, dev), "shapes_files": shape_and_file_extras(B, W, torch, dev)}
+        extras = {"matmul": matmul_extras(B, W, torch, dev), "shapes_files": shape_and_file_extras(B, W, torch, dev),
+                  "plain_way": plain_way(B, torch, ca, cb, dev)}
         srv = run_serve(args, B, W, torch, dev, 1.0, max_batch=0, streams=4, mode="split_bf16")
         extras["serve"] = {k: srv[k] for k in ("p50_ms", "p99_ms", "throughput_rps", "offered_rps", "mean_batch")}
         extras["serve"]["config"] = "1 s of the served Poisson stream (5k req/s); full line: --workload serve"
 
     cpu = None
+    cpu_par = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(n)
+        cpu_par = cpu_parallel(n)
 
     if rank == 0:
         line = {
@@ -663,6 +765,8 @@ def main():
             "matmul_tflops": extras["matmul"] if extras else None,
             "serve": extras["serve"] if extras else None,
             "shapes_files": extras["shapes_files"] if extras else None,
+            "plain_way": extras["plain_way"] if extras else None,
+            "cpu_parallel": cpu_par,
         }
         print(json.dumps(line), flush=True)
     if dist:

@@ -2,6 +2,8 @@
 // addition / subtraction (Algorithm 1, Eq. eq55) and multiplication by a
 // constant (Algorithm 2) of "Compressed Matrix Computations" (arXiv 2202.13007).
 // Bit-exact binary64 (explicit round-to-nearest intrinsics).
+#include <algorithm>
+
 #include "block_ops.cuh"
 
 namespace blaz {
@@ -38,6 +40,42 @@ __global__ void __launch_bounds__(256) k_scale(int64_t nb, const double *f1, con
     }
 }
 
+// Algorithm 2 with 16-byte accesses (all four arrays of both matrices 16-byte
+// aligned): f and s as pairs of binary64 products, phi and the codes copied
+// as 16-byte words, the ragged tails of each array byte by byte.  Same bits
+// as k_scale.
+template <bool kCopy>
+__global__ void __launch_bounds__(256)
+    k_scale_vec(int64_t nb, const double *f1, const double *s1, const uint8_t *p1, const int8_t *c1, double cst,
+                double *f, double *s, uint8_t *p, int8_t *c)  // f1 == f and s1 == s in place
+{
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t n2 = nb / 2;
+    const double2 *f1v = reinterpret_cast<const double2 *>(f1), *s1v = reinterpret_cast<const double2 *>(s1);
+    double2 *fv = reinterpret_cast<double2 *>(f), *sv = reinterpret_cast<double2 *>(s);
+    for (int64_t i = tid; i < n2; i += stride) {
+        double2 a = f1v[i], b = s1v[i];
+        a.x = dmul(a.x, cst);
+        a.y = dmul(a.y, cst);
+        b.x = dmul(b.x, cst);
+        b.y = dmul(b.y, cst);
+        fv[i] = a;
+        sv[i] = b;
+    }
+    if (tid == 0 && (nb & 1)) {
+        f[nb - 1] = dmul(f1[nb - 1], cst);
+        s[nb - 1] = dmul(s1[nb - 1], cst);
+    }
+    if (!kCopy) return;
+    const int64_t np = nb / 16, nc = nb * kKeep / 16;
+    const uint4 *p1v = reinterpret_cast<const uint4 *>(p1), *c1v = reinterpret_cast<const uint4 *>(c1);
+    uint4 *pv = reinterpret_cast<uint4 *>(p), *cv = reinterpret_cast<uint4 *>(c);
+    for (int64_t i = tid; i < np; i += stride) __stcs(pv + i, __ldcs(p1v + i));
+    for (int64_t i = tid; i < nc; i += stride) __stcs(cv + i, __ldcs(c1v + i));
+    for (int64_t i = np * 16 + tid; i < nb; i += stride) p[i] = p1[i];
+    for (int64_t i = nc * 16 + tid; i < nb * kKeep; i += stride) c[i] = c1[i];
+}
+
 static int grid_for(int64_t n, int threads)
 {
     int64_t want = (n + threads - 1) / threads;
@@ -64,12 +102,24 @@ int launch_scale(const blaz_cmat *a, double c, const blaz_cmat *o, cudaStream_t 
 {
     const int64_t nb = (a->rows / 8) * (a->cols / 8);
     if (nb == 0) return BLAZ_OK;
-    if (o->code != a->code || o->phi != a->phi)
+    const bool copy = o->code != a->code || o->phi != a->phi;
+    auto a16 = [](const void *q) { return ((uintptr_t)q & 15) == 0; };
+    const bool vec = a16(a->f) && a16(a->s) && a16(o->f) && a16(o->s) &&
+                     (!copy || (a16(a->phi) && a16(a->code) && a16(o->phi) && a16(o->code)));
+    if (vec) {
+        // one 16-byte word per thread and pass: 4 resident CTAs of 256 threads per SM, two waves
+        const int grid = (int)std::min<int64_t>((int64_t)num_sms() * 8, std::max<int64_t>(1, (nb * 7 / 4 + 255) / 256));
+        if (copy)
+            k_scale_vec<true><<<grid, 256, 0, st>>>(nb, a->f, a->s, a->phi, a->code, c, o->f, o->s, o->phi, o->code);
+        else
+            k_scale_vec<false><<<grid, 256, 0, st>>>(nb, a->f, a->s, a->phi, a->code, c, o->f, o->s, o->phi, o->code);
+    } else if (copy) {
         k_scale<true><<<grid_for(nb * 7, 256), 256, 0, st>>>(nb, a->f, a->s, a->phi, a->code, c, o->f, o->s, o->phi,
                                                            o->code);
-    else
+    } else {
         k_scale<false><<<grid_for(nb, 256), 256, 0, st>>>(nb, a->f, a->s, a->phi, a->code, c, o->f, o->s, o->phi,
                                                             o->code);
+    }
     return launch_status();
 }
 

@@ -188,6 +188,22 @@ def test_add_sub_scale_plain_pair(B):
         assert_cmat_equal(gs, os_)
 
 
+def test_scale_of_unaligned_arrays(B):
+    """Arrays that start 8 bytes (f, s) or 1 byte (phi) or 4 bytes (codes) off
+    a 16-byte boundary take the scalar kernel; same bits as the oracle."""
+    A = W.random_block_matrix(64, 72, seed=21)
+    g = B.compress(dev(A))
+    nb = g.nb
+    store = [torch.empty(nb + 2, dtype=torch.float64, device="cuda") for _ in range(2)] + \
+            [torch.empty(nb + 16, dtype=torch.uint8, device="cuda"), torch.empty((nb + 1, 28), dtype=torch.int8, device="cuda")]
+    a = B.CMat(64, 72, store[0][1:nb + 1], store[1][1:nb + 1], store[2][1:nb + 1], store[3][1:nb + 1])
+    a.f.copy_(g.f), a.s.copy_(g.s), a.phi.copy_(g.phi), a.code.copy_(g.code)
+    oa = O.compress(A)
+    assert_cmat_equal(B.scale(a, -2.25), O.scale(oa, -2.25))
+    B.scale(a, 0.75, out=a)                                 # in place
+    assert_cmat_equal(a, O.scale(oa, 0.75))
+
+
 @pytest.mark.parametrize("cst", [-0.97, -1.0, 2.0, 0.0, 1e-300])
 def test_add_with_scaled_partner(B, cst):
     X = W.random_block_matrix(64, 64, seed=3)
