@@ -22,6 +22,26 @@ int launch_status()
     return e == cudaSuccess ? BLAZ_OK : set_cuda_error(e);
 }
 
+void keep_pool_cached()
+{
+    static std::mutex mu;
+    static std::vector<char> done;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    std::lock_guard<std::mutex> lk(mu);
+    if ((int)done.size() <= dev) done.resize(dev + 1, 0);
+    if (done[dev]) return;
+    done[dev] = 1;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t keep = UINT64_MAX;
+        if (cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess)
+            (void)cudaGetLastError();
+    } else {
+        (void)cudaGetLastError();
+    }
+}
+
 int num_sms()
 {
     static std::mutex mu;

@@ -93,6 +93,12 @@ int launch_status();                 // cudaGetLastError -> BLAZ_OK / BLAZ_ERR_C
 int num_sms();                       // SM count of the current device (cached)
 int validate_cmat(const blaz_cmat *m);   // shape, NULL and alignment checks of a descriptor
 
+// Keeps the current device's default memory pool (this process's
+// stream-ordered allocations) cached across synchronizations instead of
+// returning it to the system, so that scratch and staging are re-used rather
+// than re-mapped call after call.  Once per device.
+void keep_pool_cached();
+
 // Stream-ordered scratch that is released on the same stream.
 struct Scratch {
     void *p = nullptr;
@@ -100,6 +106,7 @@ struct Scratch {
     explicit Scratch(cudaStream_t s) : st(s) {}
     int alloc(size_t bytes)
     {
+        keep_pool_cached();
         cudaError_t e = cudaMallocAsync(&p, bytes ? bytes : 16, st);
         if (e != cudaSuccess) {
             p = nullptr;

@@ -94,6 +94,7 @@ int blaz_compress_host(const double *A, int64_t lda, blaz_cmat *out, void *strea
     // not wait for earlier work on `st`) and freed on `st` after the last
     // slab, which has waited for every transfer.
     void *stage = nullptr;
+    keep_pool_cached();
     if ((e = cudaMallocAsync(&stage, nbuf * buf_bytes, cs)) != cudaSuccess) {
         (void)cudaGetLastError();
         return e == cudaErrorMemoryAllocation ? BLAZ_ERR_OOM : set_cuda_error(e);
