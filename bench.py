@@ -49,9 +49,11 @@ def parse():
     p.add_argument("--side", type=int, default=16384)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--workload", default="sweep", choices=["sweep", "batch", "serve"],
-                   help="sweep: the bandwidth-sweep step (default line); batch / serve: the batched and "
-                        "served configurations, each printed as its own line")
+    p.add_argument("--workload", default="sweep", choices=["sweep", "batch", "serve", "matmul"],
+                   help="sweep: the bandwidth-sweep step (default line); batch / serve / matmul: the batched, "
+                        "served and precision (matrix product) configurations, each printed as its own line")
+    p.add_argument("--mm-side", type=int, default=4096, help="matmul workload: n = k = m")
+    p.add_argument("--mm-mode", default="both", choices=["fp64", "split_bf16", "both"])
     p.add_argument("--serve-seconds", type=float, default=2.0)
     p.add_argument("--no-extras", action="store_true", help="skip the matmul and serve fields of the sweep line")
     return p.parse_args()
@@ -502,6 +504,47 @@ def serve_line(args):
     print(json.dumps(line), flush=True)
 
 
+def matmul_line(args):
+    """Precision configuration alone: compressed n x n bump field A (seed n)
+    times a dense N(0,1) n x n matrix smoothed by a 5x5 box filter (seed 7),
+    timed over --steps calls after --warmup, per mode; TFLOP/s = 2 n^3 / time."""
+    import torch
+
+    import workloads as W
+    from paper_2202_13007_gb300 import blaz as B
+
+    n = args.mm_side
+    dev = torch.device("cuda", 0)
+    ta = W.bump_field_torch(n, n, dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(7)
+    z = torch.randn((n, n), generator=g, dtype=torch.float64, device=dev)
+    Bd = sum(torch.roll(z, (di, dj), (0, 1)) for di in range(-2, 3) for dj in range(-2, 3)) / 25.0
+    ga = B.compress(ta)
+    C = torch.empty((n, n), dtype=torch.float64, device=dev)
+    modes = ["fp64", "split_bf16"] if args.mm_mode == "both" else [args.mm_mode]
+    res = {}
+    for mode in modes:
+        for _ in range(args.warmup):
+            B.matmul(ga, Bd, mode=mode, out=C)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            B.matmul(ga, Bd, mode=mode, out=C)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        res[mode] = {"ms": ms, "tflops": 2 * n ** 3 / (ms * 1e-3) / 1e12}
+    first = res[modes[0]]
+    print(json.dumps({"metric": METRIC + " [matmul]", "value": first["tflops"], "unit": "TFLOP/s", "n_gpus": 1,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": first["ms"],
+                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                      "data": "synthetic",
+                      "config": {"workload": f"matmul {n}^3: compressed bump field times smoothed N(0,1)",
+                                 "modes": res, "status": B.device_status()}}), flush=True)
+
+
 def batch_line(args):
     """2000 mixed ops (sides log-uniform over multiples of 8 in [64, 2048]) as
     one autotuned, graph-captured persistent launch, against the same ops
@@ -599,6 +642,9 @@ def main():
         return
     if args.workload == "batch":
         batch_line(args)
+        return
+    if args.workload == "matmul":
+        matmul_line(args)
         return
 
     import torch

@@ -20,7 +20,7 @@
 #include "batch_internal.cuh"
 #include "block_codec.cuh"
 #include "block_ops.cuh"
-#include "compress_fast.cuh"
+#include "compress_fix.cuh"
 #include "gemm_fp64.cuh"
 
 namespace blaz {
@@ -43,6 +43,19 @@ __device__ __forceinline__ double cta_sum128(double v, double *red)
         for (int q = 0; q < kThreads / 32; ++q) r += red[q];
     __syncthreads();
     return r;
+}
+
+// The exact fix-up of one block by a team of 8 lanes (compress_fix.cuh),
+// kept out of line: it is rare, and inlined it would raise the register
+// pressure of every path of the batch kernel.
+__device__ __noinline__ void batch_fix(const double *A, int64_t lda, int64_t rows, int64_t cols, int64_t nbc,
+                                       int64_t b, uint32_t pending, double *s, uint8_t *phi, int8_t *code, int u,
+                                       int tbase, unsigned tmask)
+{
+    if (pending == kPendingAll)
+        fix_whole_block<false>(A, lda, rows, cols, nbc, b, s, phi, code, u, tbase, tmask);
+    else
+        fix_codes_of_block<false>(A, lda, rows, cols, nbc, b, pending, s, phi, code, u, tbase, tmask);
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -83,35 +96,49 @@ __global__ void __launch_bounds__(kThreads)
             continue;
         }
         switch (op.kind) {
-        case BLAZ_OP_COMPRESS:
-            for (int64_t b = w.b0 + tid; b < w.b1; b += kThreads) {
-                const int64_t bi = b / op.nbc, bj = b - bi * op.nbc;
-                double d[64];
-                if (op.vec) load_block<true>(op.A, op.lda, bi, bj, d);
-                else load_block<false>(op.A, op.lda, bi, bj, d);
-                op.fo[b] = d[0];
-                double sv;
-                uint8_t ph;
-                int8_t c[kKeep];
-                const uint32_t pending = compress_block_fast(d, sv, ph, c);
-                if (pending) {  // undecided codes (or phi): exact binary64, as the two-kernel path
+        case BLAZ_OP_COMPRESS: {
+            // One block per lane with a warp-uniform trip count, then the
+            // blocks the certified pass left undecided are evaluated exactly by
+            // teams of 8 lanes (four blocks per round), as in k_compress_fix.
+            const int lane = tid & 31, u = lane & 7, tbase = lane & ~7, team = lane >> 3;
+            const unsigned tmask = 0xFFu << tbase;
+            const int64_t cols = op.nbc * 8, rows = INT64_MAX / 16;  // no partial blocks in a batch
+            for (int64_t bb = w.b0 + (tid & ~31); bb < w.b1; bb += kThreads) {
+                const int64_t b = bb + lane;
+                uint32_t pending = 0;
+                if (b < w.b1) {
+                    const int64_t bi = b / op.nbc, bj = b - bi * op.nbc;
+                    double d[64];
                     if (op.vec) load_block<true>(op.A, op.lda, bi, bj, d);
                     else load_block<false>(op.A, op.lda, bi, bj, d);
-                    if (pending == kPendingAll) {
-                        compress_block(d, sv, ph, c);
-                    } else {
-                        exact_dprime(d, sv);
-                        for (uint32_t m = pending; m; m &= m - 1) {
-                            const int t = __ffs(m) - 1;
-                            c[t] = exact_code(d, t, ph);
-                        }
+                    op.fo[b] = d[0];
+                    double sv;
+                    uint8_t ph;
+                    int8_t c[kKeep];
+                    pending = compress_block_fast(d, sv, ph, c);
+                    op.so[b] = sv;
+                    if (pending != kPendingAll) {
+                        op.po[b] = ph;
+                        store_codes(op.co + b * kKeep, c);
                     }
                 }
-                op.so[b] = sv;
-                op.po[b] = ph;
-                store_codes(op.co + b * kKeep, c);
+                unsigned need = __ballot_sync(0xffffffffu, pending != 0u);
+                if (!need) continue;
+                __syncwarp();  // s, phi and the decided codes are visible to the whole warp
+                while (need) {
+                    unsigned m = need;
+                    for (int k = 0; k < team; ++k) m &= m - 1;
+                    const int target = m ? __ffs(m) - 1 : -1;
+                    const uint32_t pend = __shfl_sync(0xffffffffu, pending, target < 0 ? 0 : target);
+                    if (target >= 0)
+                        batch_fix(op.A, op.lda, rows, cols, op.nbc, bb + target, pend, op.so, op.po, op.co, u, tbase,
+                                  tmask);
+                    for (int k = 0; k < 4; ++k) need &= need - 1;
+                    __syncwarp();
+                }
             }
             break;
+        }
         case BLAZ_OP_DECOMPRESS:
         case BLAZ_OP_MATMUL: {
             double *dst = op.kind == BLAZ_OP_MATMUL ? op.scratch : op.C;
