@@ -22,10 +22,8 @@
 //     |D_f - X| <= (2u + u + 8u + u + 8u + 2u + O(u^2)) aa_ij S2_ij + 2^-100
 // against the binary64 coefficient X of the specification, whose own error
 // (17 roundings of 2^-53) is far below u; S2_ij = sum_uv |c_iu c_jv D'_uv|
-// <= sum |D'| < K + 1, and also S2_ij <= max|D'| C1_i C1_j <= 8 max|D'|
-// with C1_k = sum_x |cos_kx| (C1_0 = C1_4 = 2 sqrt 2 is the largest).  The
-// kernel uses
-//     E_ij = 24u aa_ij min(K + 1, 8.0001 max|D'|) + 2^-100.
+// <= sum |D'| < K + 1 (every |cos_kx| <= 1).  The kernel uses
+//     E_ij = 24u aa_ij (K + 1) + 2^-100.
 #pragma once
 
 #include "block_codec.cuh"
@@ -177,10 +175,6 @@ __device__ __forceinline__ uint32_t compress_block_fast(double (&d)[64], double 
     // chain, cos(0) = 1) and fp32 inner sums T[u][j] for j >= 1.
     float T[8][8];
     double U00 = 0.0;
-    // max |D'| <= smaxf (1 + 2^-23) + 2^-126 (truncated fp32 rows); since
-    // max |D'| >= 1 (s is the mean of the nonzero |D|) the 8.0001 factor
-    // below covers both terms.
-    float smaxf = 0.0f;
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
         double row[8];
@@ -192,10 +186,7 @@ __device__ __forceinline__ uint32_t compress_block_fast(double (&d)[64], double 
         U00 = (u == 0) ? t0 : dadd(U00, t0);
         float rf[8];
 #pragma unroll
-        for (int v = 0; v < 8; ++v) {
-            rf[v] = trunc_f32(row[v]);
-            smaxf = fmaxf(smaxf, fabsf(rf[v]));
-        }
+        for (int v = 0; v < 8; ++v) rf[v] = trunc_f32(row[v]);
         T[u][0] = trunc_f32(t0);
 #pragma unroll
         for (int j = 1; j < 8; ++j) {
@@ -209,7 +200,7 @@ __device__ __forceinline__ uint32_t compress_block_fast(double (&d)[64], double 
 
     // Outer sums in fp32; bounds on max |X| over the other 63 coefficients.
     // E_ij / aa_ij, one factor for the block.
-    const float base = 24.0f * 0x1p-24f * fminf((float)(K + 1), smaxf * 8.0001f);
+    const float base = 24.0f * 0x1p-24f * (float)(K + 1);
     float Dk[kKeep];
     float mlo = 0.0f, mhi = 0.0f;
 #pragma unroll
@@ -271,6 +262,224 @@ __device__ __forceinline__ uint32_t compress_block_fast(double (&d)[64], double 
             else c = tl;
         }
         code[t] = (int8_t)c;
+    }
+    return pending;
+}
+
+// ---------------------------------------------------------------------------
+// Two-phase form of the certified compressor, for the two-kernel path, where
+// the exact DC chain runs only for the blocks that need it.
+//
+// The DC code is X00 phi truncated, X00 = RN(aa00 * U00) with U00 the
+// binary64 sums of D' in the specified order.  For a sign-coherent block (all
+// nonzero D of one sign) sum D' = +-K exactly, so X00 phi sits on an integer
+// whenever 8 | K phi and only the exact binary64 value decides it: such
+// blocks get the exact chain.  For the others the DC is one more fp32
+// coefficient under the bound below, and an undecided DC code goes to the
+// fix-up like any other code.
+//
+// Rows in fp32 from D and r directly: with e the exponent of s, D 2^-e and
+// r 2^e are exact (power-of-two scaling) and of order 1; both are truncated
+// to fp32 (relative error < 2u each, u = 2^-24) and multiplied in fp32 (u):
+// |D'_f - D'| <= 5u |D'| + 2^-126 against D' = RN64(D r), so the first term
+// of the bound in the header becomes 5u and E_ij = 28u aa_ij (K + 1) + 2^-100
+// covers the total of 25u + O(u^2).
+
+// binary64 -> binary32 of x 2^-e by truncating the significand (x 2^-e < 2^127);
+// values below 2^-126 (after scaling) and subnormal x become 0.
+__device__ __forceinline__ float trunc_f32_scaled(double x, int e)
+{
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const int ex = (int)((hi >> 20) & 0x7FF);
+    const int ef = ex - 1023 - e + 127;
+    if (ex == 0 || ef <= 0) return 0.0f;
+    const unsigned mant = __funnelshift_l(lo, hi, 3) & 0x7FFFFFu;
+    return __uint_as_float((hi & 0x80000000u) | ((unsigned)ef << 23) | mant);
+}
+
+// What the first phase leaves for the second.
+struct FastCtx {
+    uint32_t state;     // 0: decide in cf_finish; kPendingAll: whole block exact; 1: done (K == 0)
+    bool coherent;      // sign-coherent: the exact X00 comes from the dense DC pass
+    float base;         // E_ij / aa_ij
+    float mlo, mhi;     // bounds on max |X| over the 63 coefficients other than the DC
+    float Dk[kKeep];    // fp32 kept coefficients (Dk[0]: the DC estimate)
+};
+
+// Phase 1: normalization, slope (both exact), fp32 DCT of all 64
+// coefficients.  d holds D afterwards (the dense DC pass reads it).
+__device__ __forceinline__ void cf_prepare(double (&d)[64], double &s_out, double &r_out, FastCtx &c)
+{
+#pragma unroll
+    for (int i = 7; i >= 0; --i) {
+#pragma unroll
+        for (int j = 7; j >= 0; --j) {
+            if (i == 0 && j == 0) {
+                d[0] = 0.0;
+            } else if (i == 0) {
+                d[j] = dsub(d[j], d[j - 1]);
+            } else if (j == 0) {
+                d[i * 8] = dsub(d[i * 8], d[(i - 1) * 8]);
+            } else {
+                const double a = dsub(d[i * 8 + j], d[(i - 1) * 8 + j]);
+                const double b = dsub(d[i * 8 + j], d[i * 8 + j - 1]);
+                d[i * 8 + j] = dhalf(dadd(a, b));
+            }
+        }
+    }
+    int K = 0;
+    unsigned pos = 0u, neg = 0u;  // any nonzero D of each sign
+#pragma unroll
+    for (int p = 0; p < 64; ++p) {
+        const int nz = nonzero_bits(d[p]);
+        K += nz;
+        const unsigned sg = (unsigned)__double2hiint(d[p]) >> 31;
+        pos |= (unsigned)nz & (sg ^ 1u);
+        neg |= (unsigned)nz & sg;
+    }
+    c.coherent = false;
+    r_out = 0.0;
+    if (K == 0) {
+        s_out = 0.0;
+        c.state = 1u;
+        return;
+    }
+    const double S = tree_sum_abs(d);
+    const double s = div_by_count(S, K);
+    const double r = ddiv(1.0, s);
+    s_out = s;
+    r_out = r;
+    const int es_field = (int)((__double_as_longlong(s) >> 52) & 0x7FF);
+    // Inf / NaN / overflow, or a subnormal s: exact path
+    if (((__double_as_longlong(S) >> 52) & 0x7FF) >= 0x7FE || ((__double_as_longlong(r) >> 52) & 0x7FF) >= 0x7FE ||
+        es_field == 0) {
+        c.state = kPendingAll;
+        return;
+    }
+    c.state = 0u;
+    c.coherent = (pos ^ neg) != 0u;
+    const int e = es_field - 1023;
+    const float rr = trunc_f32_scaled(r, -e);
+    float T[8][8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        float rf[8];
+#pragma unroll
+        for (int v = 0; v < 8; ++v) rf[v] = trunc_f32_scaled(d[u * 8 + v], e) * rr;
+        float t0 = rf[0];
+#pragma unroll
+        for (int v = 1; v < 8; ++v) t0 += rf[v];
+        T[u][0] = t0;
+#pragma unroll
+        for (int j = 1; j < 8; ++j) {
+            float acc = rf[0] * cos_f(j, 0);
+#pragma unroll
+            for (int v = 1; v < 8; ++v) acc = fmaf(rf[v], cos_f(j, v), acc);
+            T[u][j] = acc;
+        }
+    }
+    c.base = 28.0f * 0x1p-24f * (float)(K + 1);
+    float mlo = 0.0f, mhi = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            float acc = cos_f(i, 0) * T[0][j];
+#pragma unroll
+            for (int u = 1; u < 8; ++u) acc = fmaf(cos_f(i, u), T[u][j], acc);
+            const float aa = (float)aa_tab(i, j);
+            const float Df = aa * acc;
+            if (!(i == 0 && j == 0)) {
+                const float E = c.base * aa + 1e-30f;
+                const float a = fabsf(Df);
+                mhi = fmaxf(mhi, a + E);
+                mlo = fmaxf(mlo, a - E);
+            }
+            const int t = kept_index(i, j);
+            if (t >= 0) c.Dk[t] = Df;
+        }
+    }
+    c.mlo = mlo;
+    c.mhi = mhi;
+}
+
+// The exact DC coefficient X00 = RN(aa00 U00) from D and r (the dense pass).
+__device__ __forceinline__ double cf_exact_dc(const double *D, double r)
+{
+    double U00 = 0.0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        double t0 = dmul(D[u * 8], r);
+#pragma unroll
+        for (int v = 1; v < 8; ++v) t0 = dadd(t0, dmul(D[u * 8 + v], r));
+        U00 = (u == 0) ? t0 : dadd(U00, t0);
+    }
+    return dmul(BLAZ_A00, U00);
+}
+
+// Phase 2: phi and the codes, with the exact X00 of a coherent block.
+// Returns 0, kPendingAll or the mask of undecided codes (as
+// compress_block_fast).
+__device__ __forceinline__ uint32_t cf_finish(const FastCtx &c, double X00, uint8_t &phi_out, int8_t (&code)[kKeep])
+{
+    if (c.state == 1u) {
+        phi_out = 255;
+#pragma unroll
+        for (int t = 0; t < kKeep; ++t) code[t] = 0;
+        return 0u;
+    }
+    if (c.state == kPendingAll) return kPendingAll;
+    // bounds on m = max(|X00|, the others), as in compress_block_fast; for a
+    // non-coherent block |X00| is itself known to within E00
+    const float aa00 = (float)BLAZ_A00;
+    const float E00 = c.base * aa00 + 1e-30f;
+    bool m_exact = false;
+    double ax00 = 0.0;
+    float dc_lo, dc_hi;
+    if (c.coherent) {
+        ax00 = fabs(X00);
+        const float a00 = trunc_f32(ax00);
+        m_exact = __double_as_longlong(f2d_bits(c.mhi * (1.0f + 0x1p-20f))) < __double_as_longlong(ax00);
+        dc_lo = a00;
+        dc_hi = a00 * (1.0f + 0x1p-22f);
+    } else {
+        const float a = fabsf(c.Dk[0]);
+        dc_lo = fmaxf(0.0f, (a - E00) * (1.0f - 0x1p-20f));
+        dc_hi = (a + E00) * (1.0f + 0x1p-20f);
+    }
+    const float m_lo = m_exact ? dc_lo : fmaxf(dc_lo, c.mlo * (1.0f - 0x1p-20f));
+    const float m_hi = m_exact ? dc_hi : fmaxf(dc_hi, c.mhi * (1.0f + 0x1p-20f));
+    const float q_lo = __fdiv_rn(127.0f, m_hi) * (1.0f - 0x1p-20f);
+    const float q_hi = __fdiv_rn(127.0f, m_lo) * (1.0f + 0x1p-20f);
+    const int p_lo = q_lo >= 255.0f ? 255 : (q_lo < 1.0f ? 1 : (int)q_lo);
+    const int p_hi = q_hi >= 255.0f ? 255 : (q_hi < 1.0f ? 1 : (int)q_hi);
+    int phi = p_lo;
+    if (p_lo != p_hi) {
+        if (!m_exact) return kPendingAll;
+        phi = phi_of(ax00);
+    }
+    phi_out = (uint8_t)phi;
+    const float phif = (float)phi;
+    uint32_t pending = 0u;
+#pragma unroll
+    for (int t = 0; t < kKeep; ++t) {
+        if (t == 0 && c.coherent) {
+            code[0] = quantize_bits(dmul(X00, i64_to_double(phi)));
+            continue;
+        }
+        const float aa = (float)aa_tab(kept_row(t), kept_col(t));
+        const float v = c.Dk[t] * phif;
+        const float Ev = (c.base * aa * phif) * (1.0f + 0x1p-20f) + 0x1p-22f * (fabsf(v) + 1.0f) + 0x1p-16f;
+        const float lo = v - Ev, hi = v + Ev;
+        int cc = 0;
+        if (lo >= 127.0f) cc = 127;
+        else if (hi <= -127.0f) cc = -127;
+        else {
+            const int tl = (int)truncf(lo), th = (int)truncf(hi);
+            if (tl != th || tl >= 127 || tl <= -127) pending |= 1u << t;
+            else cc = tl;
+        }
+        code[t] = (int8_t)cc;
     }
     return pending;
 }

@@ -33,39 +33,71 @@ __device__ __forceinline__ void append(bool want, T value, T *__restrict__ list,
     if (want) list[base + __popc(need & ((1u << lane) - 1u))] = value;
 }
 
-// CTA size of the fast compressor.  At ~180 registers per thread, small CTAs
-// let more warps share an SM (registers are granted per warp, an SM takes
-// only whole CTAs).
-constexpr int kFastThreads = 64;
+// CTA size of the fast compressor: 128 threads (one block each), 3 CTAs per
+// SM (168 registers).  The sign-coherent blocks of a CTA share one dense
+// pass of exact DC chains, which larger CTAs fill better; CTAs stay
+// short-lived so that the warps of an SM are at different phases.
+constexpr int kFastThreads = 128;
+
+// Dynamic shared memory of the fast compressor: D and r of every thread's
+// block, and the exact X00 of every slot.
+constexpr size_t kFastSmem = sizeof(double) * (size_t)kFastThreads * 66;
 
 template <bool kVec>
-__global__ void __launch_bounds__(kFastThreads, 6)
+__global__ void __launch_bounds__(kFastThreads, 3)
     k_compress_fast(const double *__restrict__ A, int64_t lda, int64_t rows, int64_t cols, int64_t nbc, int64_t nb,
-                    double *__restrict__ f,
-                    double *__restrict__ s, uint8_t *__restrict__ phi, int8_t *__restrict__ code,
-                    uint2 *__restrict__ code_list, unsigned *__restrict__ code_count,
+                    double *__restrict__ f, double *__restrict__ s, uint8_t *__restrict__ phi,
+                    int8_t *__restrict__ code, uint2 *__restrict__ code_list, unsigned *__restrict__ code_count,
                     unsigned *__restrict__ block_list, unsigned *__restrict__ block_count)
 {
-    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x) {
+    // Sign-coherent blocks of the CTA leave D and r here; after the barrier
+    // the CTA's threads evaluate their exact DC chains densely (one per
+    // thread) and leave X00 in sX.  Dynamic shared memory (kFastSmem bytes):
+    // 64 D + r per slot, an odd row length keeping the row reads
+    // conflict-free.
+    extern __shared__ double fast_smem[];
+    double(*sD)[65] = reinterpret_cast<double(*)[65]>(fast_smem);
+    double *sX = fast_smem + kFastThreads * 65;
+    __shared__ unsigned sCount;
+    if (threadIdx.x == 0) sCount = 0u;
+    __syncthreads();
+    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const bool valid = b < nb;
+    double d[64];
+    double sv = 0.0, rv = 0.0;
+    FastCtx ctx;
+    ctx.state = 1u;
+    ctx.coherent = false;
+    int slot = -1;
+    if (valid) {
         const int64_t bi = b / nbc, bj = b - (b / nbc) * nbc;
-        double d[64];
         if (bi * 8 + 8 <= rows && bj * 8 + 8 <= cols) load_block<kVec>(A, lda, bi, bj, d);
         else load_block_clamped(A, lda, bi, bj, rows, cols, d);  // partial block of a padded matrix
         f[b] = d[0];
-        double sv;
-        uint8_t ph;
-        int8_t c[kKeep];
-        const uint32_t pending = compress_block_fast(d, sv, ph, c);
+        cf_prepare(d, sv, rv, ctx);
         s[b] = sv;
-        if (pending != kPendingAll) {
-            phi[b] = ph;
-            store_codes(code + b * kKeep, c);
+        if (ctx.coherent) {
+            slot = (int)atomicAdd(&sCount, 1u);
+#pragma unroll
+            for (int p = 0; p < 64; ++p) sD[slot][p] = d[p];
+            sD[slot][64] = rv;
         }
-        // Undecided codes and whole blocks go to separate lists, so that the
-        // fix-up kernels run without divergence between the two cases.
-        append(pending != 0u && pending != kPendingAll, make_uint2((unsigned)b, pending), code_list, code_count);
-        append(pending == kPendingAll, (unsigned)b, block_list, block_count);
     }
+    __syncthreads();
+    if (threadIdx.x < sCount) sX[threadIdx.x] = cf_exact_dc(sD[threadIdx.x], sD[threadIdx.x][64]);
+    __syncthreads();
+    if (!valid) return;
+    uint8_t ph = 255;
+    int8_t c[kKeep];
+    const uint32_t pending = cf_finish(ctx, slot >= 0 ? sX[slot] : 0.0, ph, c);
+    if (pending != kPendingAll) {
+        phi[b] = ph;
+        store_codes(code + b * kKeep, c);
+    }
+    // Undecided codes and whole blocks go to separate lists, so that the
+    // fix-up kernel runs without divergence between the two cases.
+    append(pending != 0u && pending != kPendingAll, make_uint2((unsigned)b, pending), code_list, code_count);
+    append(pending == kPendingAll, (unsigned)b, block_list, block_count);
 }
 
 // The exact fix-up of both lists in one launch, a team of 8 lanes per entry:
@@ -289,14 +321,21 @@ int launch_compress(const double *A, int64_t lda, int64_t rows, int64_t cols, co
     if (e != cudaSuccess) return set_cuda_error(e);
     const int threads = 128;
     const int fix_grid = num_sms() * 4;  // one resident wave (72 registers per thread)
+    static const bool smem_ok = [] {
+        return cudaFuncSetAttribute(k_compress_fast<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kFastSmem) == cudaSuccess &&
+               cudaFuncSetAttribute(k_compress_fast<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kFastSmem) == cudaSuccess;
+    }();
+    if (!smem_ok) return set_cuda_error(cudaGetLastError());
     if (vec_ok(A, lda)) {
-        k_compress_fast<true><<<fast_grid(nb), kFastThreads, 0, st>>>(A, lda, rows, cols, nbc, nb, out->f,
+        k_compress_fast<true><<<fast_grid(nb), kFastThreads, kFastSmem, st>>>(A, lda, rows, cols, nbc, nb, out->f,
                                                                       out->s, out->phi, out->code, code_list,
                                                                       counts, block_list, counts + 1);
         k_compress_fix<true><<<fix_grid, threads, 0, st>>>(A, lda, rows, cols, nbc, block_list, code_list, counts,
                                                             out->s, out->phi, out->code);
     } else {
-        k_compress_fast<false><<<fast_grid(nb), kFastThreads, 0, st>>>(A, lda, rows, cols, nbc, nb, out->f,
+        k_compress_fast<false><<<fast_grid(nb), kFastThreads, kFastSmem, st>>>(A, lda, rows, cols, nbc, nb, out->f,
                                                                        out->s, out->phi, out->code, code_list,
                                                                        counts, block_list, counts + 1);
         k_compress_fix<false><<<fix_grid, threads, 0, st>>>(A, lda, rows, cols, nbc, block_list, code_list, counts,
