@@ -143,7 +143,7 @@ int blaz_dot(const blaz_cmat *a, const blaz_cmat *b, double *result, void *strea
  * Same arguments, result and determinism as blaz_dot.  Its scratch is a fixed
  * 8448-byte array in the library's device memory (every GPU that loads the
  * library holds it until the process exits): 1024 per-CTA partial sums and a
- * counter.  A call needs one partial per CTA it launches, min(ceil(nb/128),
+ * counter.  A call needs one partial per CTA it launches, min(ceil(nb/256),
  * 6 x SM count, 1024), i.e. at most 912 on a 152-SM GB300, so every matrix
  * size fits there (the BLAZ_ERR_RANGE check before anything is enqueued
  * cannot trigger).  The first call on a device

@@ -87,6 +87,93 @@ __device__ __forceinline__ uint32_t code_pair_h(const int8_t *__restrict__ c, in
 __device__ __forceinline__ float half_lo(uint32_t p) { return __half2float(__ushort_as_half((unsigned short)(p & 0xFFFF))); }
 __device__ __forceinline__ float half_hi(uint32_t p) { return __half2float(__ushort_as_half((unsigned short)(p >> 16))); }
 
+// One group of 16 blocks (rows gq and gq + 8 of the fragments): the slice
+// products C_b H_s and w_s.c_b on the tensor cores, the exact contraction
+// with c_a and w_s.c_a in the fragments, reduced over the 4 lanes of a row.
+// Every lane of a quad ends with the sums of both of its rows; the lane keeps
+// those of row `row` when `keep` holds.
+__device__ __forceinline__ void gram_group(const uint2 (*sbf)[2][4][32], const float (*swl)[32][8], int64_t grp,
+                                           int64_t nb, const int8_t *__restrict__ ca, const int8_t *__restrict__ cb,
+                                           int lane, int gq, int t, int row, bool keep, float (&qh)[kSlices],
+                                           float (&ql)[kSlices], float (&wbs)[kSlices], float (&was)[kSlices])
+{
+    const int64_t bA = grp * 16 + gq, bB = bA + 8;
+    const bool vA = bA < nb, vB = bB < nb;
+    // A fragments: codes of B-matrix blocks (rows gq and gq + 8).
+    const int8_t *cbA = cb + bA * kKeep, *cbB = cb + bB * kKeep;
+    uint32_t a0[4], a1[4];
+    a0[0] = code_pair_h(cbA, 2 * t, vA);
+    a0[1] = code_pair_h(cbB, 2 * t, vB);
+    a0[2] = code_pair_h(cbA, 2 * t + 8, vA);
+    a0[3] = code_pair_h(cbB, 2 * t + 8, vB);
+    a1[0] = code_pair_h(cbA, 16 + 2 * t, vA);
+    a1[1] = code_pair_h(cbB, 16 + 2 * t, vB);
+    a1[2] = code_pair_h(cbA, 24 + 2 * t, vA);
+    a1[3] = code_pair_h(cbB, 24 + 2 * t, vB);
+    // ca at the 8 code positions this lane holds (k = nt*8 + 2t + {0,1}), rows gq and gq+8.
+    float xa[2][8];
+    {
+        const int8_t *caA = ca + bA * kKeep, *caB = ca + bB * kKeep;
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+            const uint32_t pA = code_pair_h(caA, nt * 8 + 2 * t, vA), pB = code_pair_h(caB, nt * 8 + 2 * t, vB);
+            xa[0][2 * nt] = half_lo(pA);
+            xa[0][2 * nt + 1] = half_hi(pA);
+            xa[1][2 * nt] = half_lo(pB);
+            xa[1][2 * nt + 1] = half_hi(pB);
+        }
+    }
+#pragma unroll
+    for (int sl = 0; sl < kSlices; ++sl) {
+        float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f, w0 = 0.f, w1 = 0.f, wa0 = 0.f, wa1 = 0.f;
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+            float c[4] = {0.f, 0.f, 0.f, 0.f};
+            mma_f16x(c, a0, sbf[sl][0][nt][lane]);
+            mma_f16x(c, a1, sbf[sl][1][nt][lane]);
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int k = nt * 8 + 2 * t + q;
+                if (k < kKeep) {
+                    const float y0 = c[q], y1 = c[2 + q];
+                    const float yh0 = rintf(y0 * (1.0f / 4096.0f)), yh1 = rintf(y1 * (1.0f / 4096.0f));
+                    h0 = fmaf(xa[0][2 * nt + q], yh0, h0);
+                    l0 = fmaf(xa[0][2 * nt + q], fmaf(-4096.0f, yh0, y0), l0);
+                    h1 = fmaf(xa[1][2 * nt + q], yh1, h1);
+                    l1 = fmaf(xa[1][2 * nt + q], fmaf(-4096.0f, yh1, y1), l1);
+                    const float wd = swl[sl][lane][2 * nt + q];
+                    wa0 = fmaf(xa[0][2 * nt + q], wd, wa0);
+                    wa1 = fmaf(xa[1][2 * nt + q], wd, wa1);
+                } else if (k == kKeep) {  // column 28: w_s . cb
+                    w0 = c[q];
+                    w1 = c[2 + q];
+                }
+            }
+        }
+        // reduce over the four lanes of the row (exact integer sums)
+#pragma unroll
+        for (int o = 1; o < 4; o <<= 1) {
+            h0 += __shfl_xor_sync(0xffffffffu, h0, o);
+            l0 += __shfl_xor_sync(0xffffffffu, l0, o);
+            h1 += __shfl_xor_sync(0xffffffffu, h1, o);
+            l1 += __shfl_xor_sync(0xffffffffu, l1, o);
+            w0 += __shfl_xor_sync(0xffffffffu, w0, o);
+            w1 += __shfl_xor_sync(0xffffffffu, w1, o);
+            wa0 += __shfl_xor_sync(0xffffffffu, wa0, o);
+            wa1 += __shfl_xor_sync(0xffffffffu, wa1, o);
+        }
+        if (keep) {
+            qh[sl] = row ? h1 : h0;
+            ql[sl] = row ? l1 : l0;
+            wbs[sl] = row ? w1 : w0;
+            was[sl] = row ? wa1 : wa0;
+        }
+    }
+}
+
+// Two groups of 16 blocks per warp step: lanes t = 0, 1 keep the sums of
+// rows gq and gq + 8 of the first group, lanes t = 2, 3 those of the second,
+// so the binary64 tail runs on all 32 lanes, one block each.
 __global__ void __launch_bounds__(kDotThreads, 3)
     k_dot_tc(const __grid_constant__ GramTC g, int64_t nb, const double *__restrict__ fa, const double *__restrict__ sa,
              const uint8_t *__restrict__ pa, const int8_t *__restrict__ ca, const double *__restrict__ fb,
@@ -103,119 +190,46 @@ __global__ void __launch_bounds__(kDotThreads, 3)
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gq = lane >> 2, t = lane & 3;
     const int wpc = blockDim.x >> 5;
-    const int64_t ngroups = (nb + 15) / 16;
+    const int64_t npairs = (nb + 31) / 32;
     double acc = 0.0;
-    for (int64_t grp = (int64_t)blockIdx.x * wpc + warp; grp < ngroups; grp += (int64_t)gridDim.x * wpc) {
-        const int64_t bA = grp * 16 + gq, bB = bA + 8;
-        const bool vA = bA < nb, vB = bB < nb;
-        // A fragments: codes of B-matrix blocks (rows gq and gq + 8).
-        const int8_t *cbA = cb + bA * kKeep, *cbB = cb + bB * kKeep;
-        uint32_t a0[4], a1[4];
-        a0[0] = code_pair_h(cbA, 2 * t, vA);
-        a0[1] = code_pair_h(cbB, 2 * t, vB);
-        a0[2] = code_pair_h(cbA, 2 * t + 8, vA);
-        a0[3] = code_pair_h(cbB, 2 * t + 8, vB);
-        a1[0] = code_pair_h(cbA, 16 + 2 * t, vA);
-        a1[1] = code_pair_h(cbB, 16 + 2 * t, vB);
-        a1[2] = code_pair_h(cbA, 24 + 2 * t, vA);
-        a1[3] = code_pair_h(cbB, 24 + 2 * t, vB);
-        // ca at the 8 code positions this lane holds (k = nt*8 + 2t + {0,1}), rows gq and gq+8.
-        float xa[2][8];
-        {
-            const int8_t *caA = ca + bA * kKeep, *caB = ca + bB * kKeep;
-#pragma unroll
-            for (int nt = 0; nt < 4; ++nt) {
-                const uint32_t pA = code_pair_h(caA, nt * 8 + 2 * t, vA), pB = code_pair_h(caB, nt * 8 + 2 * t, vB);
-                xa[0][2 * nt] = half_lo(pA);
-                xa[0][2 * nt + 1] = half_hi(pA);
-                xa[1][2 * nt] = half_lo(pB);
-                xa[1][2 * nt + 1] = half_hi(pB);
-            }
+    for (int64_t pr = (int64_t)blockIdx.x * wpc + warp; pr < npairs; pr += (int64_t)gridDim.x * wpc) {
+        float qh[kSlices], ql[kSlices], wbs[kSlices], was[kSlices];
+#pragma unroll 1
+        for (int half = 0; half < 2; ++half)  // not unrolled: one group's registers at a time
+            gram_group(sbf, swl, 2 * pr + half, nb, ca, cb, lane, gq, t, t & 1, (t >> 1) == half, qh, ql, wbs, was);
+        // This lane's block: group 2 pr + (t >> 1), row gq + 8 (t & 1).
+        const int64_t b = (2 * pr + (t >> 1)) * 16 + gq + 8 * (t & 1);
+        bool use = b < nb;
+        if (use && padded) {  // partial blocks of a padded matrix are left to k_dot_boundary
+            const int64_t bi = b / nbc, bj = b - bi * nbc;
+            use = bi * 8 + 8 <= rows && bj * 8 + 8 <= cols;
         }
-        float qh[2][kSlices], ql[2][kSlices], wbs[2][kSlices], was[2][kSlices];
+        if (use) {
+            // slices assembled in int64 (0-2 and 3-4), then
+            // fa (64 fb + tb Wb) + ta (fb Wa + tb Q)
+            long long qhi = 0, qlo = 0, ahi = 0, alo = 0, bhi = 0, blo = 0;
 #pragma unroll
-        for (int sl = 0; sl < kSlices; ++sl) {
-            float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f, w0 = 0.f, w1 = 0.f, wa0 = 0.f, wa1 = 0.f;
-#pragma unroll
-            for (int nt = 0; nt < 4; ++nt) {
-                float c[4] = {0.f, 0.f, 0.f, 0.f};
-                mma_f16x(c, a0, sbf[sl][0][nt][lane]);
-                mma_f16x(c, a1, sbf[sl][1][nt][lane]);
-#pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    const int k = nt * 8 + 2 * t + q;
-                    if (k < kKeep) {
-                        const float y0 = c[q], y1 = c[2 + q];
-                        const float yh0 = rintf(y0 * (1.0f / 4096.0f)), yh1 = rintf(y1 * (1.0f / 4096.0f));
-                        h0 = fmaf(xa[0][2 * nt + q], yh0, h0);
-                        l0 = fmaf(xa[0][2 * nt + q], fmaf(-4096.0f, yh0, y0), l0);
-                        h1 = fmaf(xa[1][2 * nt + q], yh1, h1);
-                        l1 = fmaf(xa[1][2 * nt + q], fmaf(-4096.0f, yh1, y1), l1);
-                        const float wd = swl[sl][lane][2 * nt + q];
-                        wa0 = fmaf(xa[0][2 * nt + q], wd, wa0);
-                        wa1 = fmaf(xa[1][2 * nt + q], wd, wa1);
-                    } else if (k == kKeep) {  // column 28: w_s . cb
-                        w0 = c[q];
-                        w1 = c[2 + q];
-                    }
+            for (int sl = 0; sl < kSlices; ++sl) {
+                const long long T = 4096ll * f2i_exact(qh[sl]) + f2i_exact(ql[sl]);
+                const long long A = f2i_exact(was[sl]), Bw = f2i_exact(wbs[sl]);
+                if (sl < 3) {
+                    qhi = qhi * 2048 + T;
+                    ahi = ahi * 2048 + A;
+                    bhi = bhi * 2048 + Bw;
+                } else {
+                    qlo = qlo * 2048 + T;
+                    alo = alo * 2048 + A;
+                    blo = blo * 2048 + Bw;
                 }
             }
-            // reduce over the four lanes of the row (exact integer sums)
-#pragma unroll
-            for (int o = 1; o < 4; o <<= 1) {
-                h0 += __shfl_xor_sync(0xffffffffu, h0, o);
-                l0 += __shfl_xor_sync(0xffffffffu, l0, o);
-                h1 += __shfl_xor_sync(0xffffffffu, h1, o);
-                l1 += __shfl_xor_sync(0xffffffffu, l1, o);
-                w0 += __shfl_xor_sync(0xffffffffu, w0, o);
-                w1 += __shfl_xor_sync(0xffffffffu, w1, o);
-                wa0 += __shfl_xor_sync(0xffffffffu, wa0, o);
-                wa1 += __shfl_xor_sync(0xffffffffu, wa1, o);
-            }
-            qh[0][sl] = h0;
-            ql[0][sl] = l0;
-            qh[1][sl] = h1;
-            ql[1][sl] = l1;
-            wbs[0][sl] = w0;
-            wbs[1][sl] = w1;
-            was[0][sl] = wa0;
-            was[1][sl] = wa1;
-        }
-        // Binary64 tail on 16 lanes: lane t = 0 takes row gq (block bA), t = 1 row gq + 8.
-        // The slices are assembled in int64 (slices 0-2 and 3-4), then two fp64 ops each.
-        if (t < 2) {
-            const int h = t;
-            const int64_t b = h ? bB : bA;
-            bool full = true;  // partial blocks of a padded matrix are left to k_dot_boundary
-            if (padded) {
-                const int64_t bi = b / nbc, bj = b - bi * nbc;
-                full = bi * 8 + 8 <= rows && bj * 8 + 8 <= cols;
-            }
-            if ((h ? vB : vA) && full) {
-                long long qhi = 0, qlo = 0, ahi = 0, alo = 0, bhi = 0, blo = 0;
-#pragma unroll
-                for (int sl = 0; sl < kSlices; ++sl) {
-                    const float vqh = h ? qh[1][sl] : qh[0][sl], vql = h ? ql[1][sl] : ql[0][sl];
-                    const float vwa = h ? was[1][sl] : was[0][sl], vwb = h ? wbs[1][sl] : wbs[0][sl];
-                    const long long T = 4096ll * f2i_exact(vqh) + f2i_exact(vql);
-                    const long long A = f2i_exact(vwa), Bw = f2i_exact(vwb);
-                    if (sl < 3) {
-                        qhi = qhi * 2048 + T;
-                        ahi = ahi * 2048 + A;
-                        bhi = bhi * 2048 + Bw;
-                    } else {
-                        qlo = qlo * 2048 + T;
-                        alo = alo * 2048 + A;
-                        blo = blo * 2048 + Bw;
-                    }
-                }
-                const double Q = fma(g.scaleH[2], i64_to_double(qhi), g.scaleH[4] * i64_to_double(qlo));
-                const double Wa = fma(g.scaleW[2], i64_to_double(ahi), g.scaleW[4] * i64_to_double(alo));
-                const double Wb = fma(g.scaleW[2], i64_to_double(bhi), g.scaleW[4] * i64_to_double(blo));
-                const double ta = sa[b] * g.inv_phi[pa[b]], tb = sb[b] * g.inv_phi[pb[b]];
-                const double f_a = fa[b], f_b = fb[b];
-                acc += 64.0 * f_a * f_b + f_a * tb * Wb + f_b * ta * Wa + ta * tb * Q;
-            }
+            const double Q = fma(g.scaleH[2], i64_to_double(qhi), g.scaleH[4] * i64_to_double(qlo));
+            const double Wa = fma(g.scaleW[2], i64_to_double(ahi), g.scaleW[4] * i64_to_double(alo));
+            const double Wb = fma(g.scaleW[2], i64_to_double(bhi), g.scaleW[4] * i64_to_double(blo));
+            const double ta = sa[b] * g.inv_phi[pa[b]], tb = sb[b] * g.inv_phi[pb[b]];
+            const double f_a = fa[b], f_b = fb[b];
+            const double t1 = fma(tb, Wb, 64.0 * f_b);
+            const double t2 = fma(tb, Q, f_b * Wa);
+            acc += fma(f_a, t1, ta * t2);
         }
     }
     const double tot = cta_sum(acc, red);
@@ -405,7 +419,7 @@ static const GramTC &gram_tc()
 
 int dot_grid(int64_t nb)
 {
-    int64_t want = ((nb + 15) / 16 + (kDotThreads / 32) - 1) / (kDotThreads / 32);
+    int64_t want = ((nb + 31) / 32 + (kDotThreads / 32) - 1) / (kDotThreads / 32);  // 32 blocks per warp step
     // two resident waves (3 CTAs of 256 threads per SM), never more than the
     // 1024 partial sums of the no-allocation entry point
     int64_t cap = std::min<int64_t>((int64_t)num_sms() * 6, 1024);
