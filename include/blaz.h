@@ -77,6 +77,12 @@ int blaz_last_cuda_error(void);
  * on barriers (the tensor-core product) give up after about two seconds
  * instead of hanging, record the timeout here and return. */
 int blaz_device_status(void *stream);
+/* Self-test of the device-side timeout path: one GPU thread waits on
+ * `stream` for a device flag that nothing sets, for at most max_cycles SM
+ * clock cycles (0 .. 4e9, else BLAZ_ERR_ARG), then records BLAZ_ERR_TIMEOUT in
+ * the device status word (read and cleared by blaz_device_status) and
+ * returns.  Every wait in the library's kernels is bounded the same way. */
+int blaz_probe_bounded_wait(int64_t max_cycles, void *stream);
 
 /* Library-owned storage for a compressed matrix (stream-ordered allocation
  * on `stream`).  rows, cols >= 0 and multiples of 8.  The arrays are not

@@ -110,6 +110,7 @@ SIGNATURES = {
     "blaz_matmul_padded": (ctypes.c_int, [_DESC, _I64, _I64, _P, _I64, _I64, _P, _I64, ctypes.c_int, _P]),
     "blaz_matmul_cc_padded": (ctypes.c_int, [_DESC, _DESC, _I64, _I64, _I64, _P, _I64, ctypes.c_int, _P]),
     "blaz_compress_host": (ctypes.c_int, [_P, _I64, _DESC, _P]),
+    "blaz_probe_bounded_wait": (ctypes.c_int, [_I64, _P]),
     "blaz_cmat_download": (ctypes.c_int, [_DESC, _P, _P]),
     "blaz_cmat_upload": (ctypes.c_int, [_P, _DESC, _P]),
     "blaz_cmat_save": (ctypes.c_int, [_DESC, ctypes.c_char_p, _P]),

@@ -61,6 +61,10 @@ int num_sms()
 static int check_dims(int64_t rows, int64_t cols)
 {
     if (rows < 0 || cols < 0 || rows % 8 || cols % 8) return BLAZ_ERR_SHAPE;
+    // sides up to 2^34 and up to 2^40 blocks (45 TB): the block count and the
+    // byte sizes stay far from int64 overflow
+    if (rows > ((int64_t)1 << 34) || cols > ((int64_t)1 << 34) || (rows / 8) * (cols / 8) > ((int64_t)1 << 40))
+        return BLAZ_ERR_SHAPE;
     return BLAZ_OK;
 }
 
@@ -111,6 +115,11 @@ const char *blaz_strerror(int status)
 }
 
 int blaz_last_cuda_error(void) { return g_last_cuda; }
+
+int blaz_probe_bounded_wait(int64_t max_cycles, void *stream)
+{
+    return launch_probe_wait(max_cycles, (cudaStream_t)stream);
+}
 
 int blaz_device_status(void *stream)
 {
@@ -179,6 +188,7 @@ int blaz_cmat_free(blaz_cmat *m, void *stream)
 
 int blaz_compress(const double *A, int64_t lda, blaz_cmat *out, void *stream)
 {
+    BLAZ_NVTX();
     int rc = validate_cmat(out);
     if (rc) return rc;
     if (nblocks(out) == 0) return BLAZ_OK;
@@ -201,6 +211,7 @@ static int check_logical(const blaz_cmat *a, int64_t rows, int64_t cols)
 
 int blaz_compress_padded(const double *A, int64_t lda, int64_t rows, int64_t cols, blaz_cmat *out, void *stream)
 {
+    BLAZ_NVTX();
     int rc;
     if ((rc = validate_cmat(out)) || (rc = check_logical(out, rows, cols))) return rc;
     if (nblocks(out) == 0) return BLAZ_OK;
@@ -214,6 +225,7 @@ int blaz_compress_padded(const double *A, int64_t lda, int64_t rows, int64_t col
 
 int blaz_decompress_padded(const blaz_cmat *a, int64_t rows, int64_t cols, double *A, int64_t lda, void *stream)
 {
+    BLAZ_NVTX();
     int rc;
     if ((rc = validate_cmat(a)) || (rc = check_logical(a, rows, cols))) return rc;
     if (nblocks(a) == 0) return BLAZ_OK;
@@ -224,6 +236,7 @@ int blaz_decompress_padded(const blaz_cmat *a, int64_t rows, int64_t cols, doubl
 
 int blaz_decompress(const blaz_cmat *a, double *A, int64_t lda, void *stream)
 {
+    BLAZ_NVTX();
     int rc = validate_cmat(a);
     if (rc) return rc;
     if (nblocks(a) == 0) return BLAZ_OK;
@@ -242,16 +255,19 @@ static int add_or_sub(const blaz_cmat *a, const blaz_cmat *b, blaz_cmat *out, bo
 
 int blaz_add(const blaz_cmat *a, const blaz_cmat *b, blaz_cmat *out, void *stream)
 {
+    BLAZ_NVTX();
     return add_or_sub(a, b, out, false, stream);
 }
 
 int blaz_sub(const blaz_cmat *a, const blaz_cmat *b, blaz_cmat *out, void *stream)
 {
+    BLAZ_NVTX();
     return add_or_sub(a, b, out, true, stream);
 }
 
 int blaz_scale(const blaz_cmat *a, double c, blaz_cmat *out, void *stream)
 {
+    BLAZ_NVTX();
     int rc;
     if ((rc = validate_cmat(a)) || (rc = validate_cmat(out))) return rc;
     if ((rc = same_shape(a, out))) return rc;
@@ -260,6 +276,7 @@ int blaz_scale(const blaz_cmat *a, double c, blaz_cmat *out, void *stream)
 
 int blaz_dot(const blaz_cmat *a, const blaz_cmat *b, double *result, void *stream)
 {
+    BLAZ_NVTX();
     int rc;
     if ((rc = validate_cmat(a)) || (rc = validate_cmat(b))) return rc;
     if ((rc = same_shape(a, b))) return rc;
@@ -278,6 +295,7 @@ int blaz_dot(const blaz_cmat *a, const blaz_cmat *b, double *result, void *strea
 int blaz_dot_padded(const blaz_cmat *a, const blaz_cmat *b, int64_t rows, int64_t cols, double *result,
                     void *stream)
 {
+    BLAZ_NVTX();
     int rc;
     if ((rc = validate_cmat(a)) || (rc = validate_cmat(b))) return rc;
     if ((rc = same_shape(a, b)) || (rc = check_logical(a, rows, cols))) return rc;
@@ -295,6 +313,7 @@ int blaz_dot_padded(const blaz_cmat *a, const blaz_cmat *b, int64_t rows, int64_
 
 int blaz_dot_rowcol(const blaz_cmat *a, const blaz_cmat *b, int64_t i, int64_t j, double *result, void *stream)
 {
+    BLAZ_NVTX();
     int rc;
     if ((rc = validate_cmat(a)) || (rc = validate_cmat(b))) return rc;
     if (a->cols != b->rows) return BLAZ_ERR_SHAPE;
@@ -314,6 +333,7 @@ int blaz_dot_rowcol(const blaz_cmat *a, const blaz_cmat *b, int64_t i, int64_t j
 int blaz_matmul(const blaz_cmat *a, const double *B, int64_t ldb, int64_t m, double *C, int64_t ldc, int mode,
                 void *stream)
 {
+    BLAZ_NVTX();
     int rc;
     if ((rc = validate_cmat(a))) return rc;
     if (m < 0) return BLAZ_ERR_SHAPE;
@@ -336,6 +356,7 @@ int blaz_matmul(const blaz_cmat *a, const double *B, int64_t ldb, int64_t m, dou
 
 int blaz_matmul_cc(const blaz_cmat *a, const blaz_cmat *b, double *C, int64_t ldc, int mode, void *stream)
 {
+    BLAZ_NVTX();
     int rc;
     if ((rc = validate_cmat(a)) || (rc = validate_cmat(b))) return rc;
     if (a->cols != b->rows) return BLAZ_ERR_SHAPE;
@@ -404,6 +425,7 @@ static size_t padded_gemm_bytes(int64_t n, int64_t k, int64_t n8, int64_t k8, in
 int blaz_matmul_padded(const blaz_cmat *a, int64_t n, int64_t k, const double *B, int64_t ldb, int64_t m, double *C,
                        int64_t ldc, int mode, void *stream)
 {
+    BLAZ_NVTX();
     int rc;
     if ((rc = validate_cmat(a)) || (rc = check_logical(a, n, k))) return rc;
     if (m < 0) return BLAZ_ERR_SHAPE;
@@ -425,6 +447,7 @@ int blaz_matmul_padded(const blaz_cmat *a, int64_t n, int64_t k, const double *B
 int blaz_matmul_cc_padded(const blaz_cmat *a, const blaz_cmat *b, int64_t n, int64_t k, int64_t m, double *C,
                           int64_t ldc, int mode, void *stream)
 {
+    BLAZ_NVTX();
     int rc;
     if ((rc = validate_cmat(a)) || (rc = validate_cmat(b))) return rc;
     if ((rc = check_logical(a, n, k)) || (rc = check_logical(b, k, m))) return rc;

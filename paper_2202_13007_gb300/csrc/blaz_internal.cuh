@@ -3,6 +3,7 @@
 // "Compressed Matrix Computations" (arXiv 2202.13007).
 #pragma once
 
+#include <nvtx3/nvToolsExt.h>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -92,6 +93,28 @@ int set_cuda_error(cudaError_t e);   // records e, returns BLAZ_ERR_CUDA
 int launch_status();                 // cudaGetLastError -> BLAZ_OK / BLAZ_ERR_CUDA
 int num_sms();                       // SM count of the current device (cached)
 int validate_cmat(const blaz_cmat *m);   // shape, NULL and alignment checks of a descriptor
+
+// An NVTX range over a host call (visible in Nsight timelines; a few ns when
+// no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+#define BLAZ_NVTX() ::blaz::NvtxRange blaz_nvtx_range_(__func__)
+
+// Waits until *flag >= target for at most max_cycles SM clock cycles; false
+// when the limit ran out (the caller records BLAZ_ERR_TIMEOUT and returns).
+// Every spin-wait of the library goes through a bounded wait.
+__device__ __forceinline__ bool bounded_wait_geq(const volatile unsigned *flag, unsigned target, long long max_cycles)
+{
+    const long long t0 = clock64();
+    while (*flag < target)
+        if (clock64() - t0 > max_cycles) return false;
+    return true;
+}
+
+// Self-test of the device-side timeout path (k_mm_bf16.cu).
+int launch_probe_wait(int64_t max_cycles, cudaStream_t st);
 
 // Keeps the current device's default memory pool (this process's
 // stream-ordered allocations) cached across synchronizations instead of

@@ -89,6 +89,7 @@ extern "C" {
 
 int blaz_cmat_save(const blaz_cmat *a, const char *path, void *stream)
 {
+    BLAZ_NVTX();
     int rc;
     if (!path) return BLAZ_ERR_NULL;
     if ((rc = validate_cmat(a))) return rc;
@@ -150,6 +151,7 @@ int blaz_cmat_file_info(const char *path, int64_t *rows, int64_t *cols)
 
 int blaz_cmat_load(const char *path, blaz_cmat *out, void *stream)
 {
+    BLAZ_NVTX();
     if (!path || !out) return BLAZ_ERR_NULL;
     File f(path, "rb");
     if (!f.f) return BLAZ_ERR_IO;

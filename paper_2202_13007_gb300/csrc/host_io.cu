@@ -63,6 +63,7 @@ extern "C" {
 
 int blaz_compress_host(const double *A, int64_t lda, blaz_cmat *out, void *stream)
 {
+    BLAZ_NVTX();
     int rc = validate_cmat(out);
     if (rc) return rc;
     const int64_t rows = out->rows, cols = out->cols, nbc = cols / 8;
@@ -145,6 +146,7 @@ static int payload_copy(const blaz_cmat *a, unsigned char *host, bool to_host, c
 
 int blaz_cmat_download(const blaz_cmat *a, void *host, void *stream)
 {
+    BLAZ_NVTX();
     int rc = validate_cmat(a);
     if (rc) return rc;
     return payload_copy(a, (unsigned char *)host, true, (cudaStream_t)stream);
@@ -152,6 +154,7 @@ int blaz_cmat_download(const blaz_cmat *a, void *host, void *stream)
 
 int blaz_cmat_upload(const void *host, blaz_cmat *a, void *stream)
 {
+    BLAZ_NVTX();
     int rc = validate_cmat(a);
     if (rc) return rc;
     return payload_copy(a, (unsigned char *)const_cast<void *>(host), false, (cudaStream_t)stream);

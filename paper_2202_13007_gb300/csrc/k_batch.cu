@@ -77,15 +77,8 @@ __global__ void __launch_bounds__(kThreads)
         if (w.tile) {
             // 64 x 64 tile of a product: wait for the op's decompression items.
             if (tid == 0) {
-                const long long t0 = clock64();
-                int ok = 1;
-                while (*(volatile unsigned *)&done[w.op] < (unsigned)op.nitems) {
-                    if (clock64() - t0 > kWaitCycles) {
-                        ok = 0;
-                        atomicExch(&g_batch_status, BLAZ_ERR_TIMEOUT);
-                        break;
-                    }
-                }
+                const bool ok = bounded_wait_geq(&done[w.op], (unsigned)op.nitems, kWaitCycles);
+                if (!ok) atomicExch(&g_batch_status, BLAZ_ERR_TIMEOUT);
                 __threadfence();
                 s_ok = ok;
             }

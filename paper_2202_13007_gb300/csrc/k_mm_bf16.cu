@@ -330,6 +330,24 @@ static int make_map(CUtensorMap *map, const void *base, int64_t rows, int64_t co
 }
 
 // Reads and clears the device status word after synchronizing `st`.
+// Self-test of the timeout path: one thread waits for a flag that nothing
+// sets, for at most `max_cycles`, records BLAZ_ERR_TIMEOUT in the device
+// status word and returns; the context stays usable.
+__device__ unsigned g_probe_flag;  // never written
+
+__global__ void k_probe_wait(long long max_cycles)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0 && !bounded_wait_geq(&g_probe_flag, 1u, max_cycles))
+        atomicExch(&g_device_status, BLAZ_ERR_TIMEOUT);
+}
+
+int launch_probe_wait(int64_t max_cycles, cudaStream_t st)
+{
+    if (max_cycles < 0 || max_cycles > 4000000000LL) return BLAZ_ERR_ARG;
+    k_probe_wait<<<1, 32, 0, st>>>((long long)max_cycles);
+    return launch_status();
+}
+
 int device_status(cudaStream_t st)
 {
     cudaError_t e = cudaStreamSynchronize(st);

@@ -84,3 +84,10 @@ def test_integer_reciprocal_table_is_correctly_rounded():
     vals = [float.fromhex(t) for t in body.replace("\n", " ").split(",") if t.strip()]
     assert len(vals) == 256
     assert all(v == 1.0 / k for k, v in zip(range(1, 257), vals))
+
+
+def test_timeout_self_test_rejects_bad_limits_without_a_gpu(libblaz):
+    """blaz_probe_bounded_wait validates its limit before anything reaches a
+    device (BLAZ_ERR_ARG = -9)."""
+    assert libblaz.blaz_probe_bounded_wait(-1, None) == -9
+    assert libblaz.blaz_probe_bounded_wait(4000000001, None) == -9
