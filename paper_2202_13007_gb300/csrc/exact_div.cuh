@@ -83,12 +83,12 @@ __device__ __align__(16) double c_rcp_k[256] = {
     0x1.073260a47f7c6p-8, 0x1.0624dd2f1a9fcp-8, 0x1.05197f7d73404p-8, 0x1.0410410410410p-8,
     0x1.03091b51f5e1ap-8, 0x1.0204081020408p-8, 0x1.0101010101010p-8, 0x1.0000000000000p-8};
 
-// RN(x / k) for 1 <= k <= 256.
+// RN(x / k) for 1 <= k <= 256 (the general division for other k).
 __device__ __forceinline__ double div_small_int(double x, int k)
 {
     const unsigned ex = ((unsigned)__double2hiint(x) >> 20) & 0x7FF;
     const double kd = i64_to_double(k);
-    if (ex < 1023 - 900 || ex == 0x7FF) return ddiv(x, kd);
+    if (ex < 1023 - 900 || ex == 0x7FF || k < 1 || k > 256) return ddiv(x, kd);
     const double y = __ldg(&c_rcp_k[k - 1]);
     const double q = dmul(x, y);
     const double r = __fma_rn(-q, kd, x);

@@ -230,6 +230,30 @@ def test_add_special_values(B):
     assert_cmat_equal(B.add(gx, gy), O.add(O.compress(X), O.compress(Y)))
 
 
+def test_add_tiles_ragged_aliased_and_unaligned(B):
+    """The tiled kernel over 5 tiles of 256 blocks and a ragged one (25 x 41
+    blocks), with out aliasing b, and the per-block kernel for code arrays
+    4 bytes off a 16-byte boundary: same bits as the oracle."""
+    X = W.bump_field(328, 40, rows=200)
+    Y = W.bump_field(328, 41, rows=200)
+    gx, gy = B.compress(dev(X)), B.compress(dev(Y))
+    ox, oy = O.compress(X), O.compress(Y)
+    assert_cmat_equal(B.add(gx, gy), O.add(ox, oy))
+    assert_cmat_equal(B.sub(gx, gy), O.sub(ox, oy))
+    s, os_ = gx, ox
+    for _ in range(4):                                       # self-additions: y on integers
+        s, os_ = B.add(s, gx), O.add(os_, ox)
+        assert_cmat_equal(s, os_)
+    gy2 = B.compress(dev(Y))
+    B.sub(gx, gy2, out=gy2)                                  # out aliases b
+    assert_cmat_equal(gy2, O.sub(ox, oy))
+    nb = gx.nb
+    store = torch.empty((nb + 1, 28), dtype=torch.int8, device="cuda")
+    a = B.CMat(200, 328, gx.f, gx.s, gx.phi, store.view(-1)[4:4 + nb * 28].view(nb, 28))
+    a.code.copy_(gx.code)
+    assert_cmat_equal(B.add(a, gy), O.add(ox, oy))
+
+
 # --- dot products and matmul -----------------------------------------------------------------
 def test_dot_plain_pair(B):
     A, Bm = W.plain_pair()
