@@ -97,6 +97,29 @@ def profiled_traffic(name: str, blocks: int):
     return d["dram_bytes_per_block"] * blocks
 
 
+def probe_fp64(dev, st):
+    """Measured binary64 issue ceiling (G additions/s): the library's probe
+    (4 independent DADD chains per thread, 16 warps per SM), best of 3
+    launches timed with CUDA events on `st`."""
+    import torch
+
+    from paper_2202_13007_gb300 import blaz as B
+
+    out = torch.empty(torch.cuda.get_device_properties(dev).multi_processor_count * 512, dtype=torch.float64,
+                      device=dev)
+    B.probe_fp64_rate(64, out, st)
+    best = None
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        ops = B.probe_fp64_rate(4096, out, st)
+        e1.record(st)
+        torch.cuda.synchronize()
+        rate = ops / (e0.elapsed_time(e1) * 1e-3) / 1e9
+        best = rate if best is None else max(best, rate)
+    return best
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -718,6 +741,7 @@ def main():
     nb = (n // 8) ** 2
     achieved = COMPRESS_FLOPS_PER_BLOCK * nb / (comp_ms * 1e-3) / 1e9
     hbm, hbm_src = peaks()
+    fp64_probe = probe_fp64(dev, st)
 
     # End to end through the public API with host buffers, every step: A and B
     # compressed from page-locked host memory (blaz_compress_host pipelines the
@@ -805,7 +829,9 @@ def main():
                          "traffic_unit": "bytes per launch", "source_sha": kernel_sha("k_compress"),
                          "peak_source": "derived: 2 FP64 lanes/clk/SM x 152 SMs x 2070 MHz",
                          "ms_per_launch": comp_ms, "algorithmic_flops_per_launch": COMPRESS_FLOPS_PER_BLOCK * nb,
-                         "hbm_frac": 557 * nb / (comp_ms * 1e-3) / 1e9 / hbm, "hbm_peak_source": hbm_src},
+                         "hbm_frac": 557 * nb / (comp_ms * 1e-3) / 1e9 / hbm, "hbm_peak_source": hbm_src,
+                         "fp64_issue_probe_gops": fp64_probe,
+                         "frac_of_fp64_probe": achieved / fp64_probe if fp64_probe else None},
             "clocks": clk.summary(),
             "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps,

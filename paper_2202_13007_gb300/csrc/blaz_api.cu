@@ -125,7 +125,8 @@ int blaz_device_status(void *stream)
 {
     int a = device_status((cudaStream_t)stream);
     int b = batch_device_status();
-    return a != BLAZ_OK ? a : b;
+    int c = ops_device_status();
+    return a != BLAZ_OK ? a : b != BLAZ_OK ? b : c;
 }
 
 void blaz_constants(double cos_out[64], double aa_out[64], int32_t kept_out[56])

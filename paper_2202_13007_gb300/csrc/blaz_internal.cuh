@@ -144,6 +144,7 @@ struct Scratch {
     }
 };
 int batch_device_status();           // reads and clears the batch kernel's status word
+int ops_device_status();             // reads and clears the tiled addition's status word
 
 // ---- launchers (one per kernel family) ------------------------------------------
 size_t compress_scratch_bytes(int64_t nb);

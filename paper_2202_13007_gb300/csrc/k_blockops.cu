@@ -5,6 +5,7 @@
 #include <algorithm>
 
 #include "block_ops.cuh"
+#include "tcgen05.cuh"
 
 namespace blaz {
 
@@ -48,79 +49,228 @@ __device__ __forceinline__ bool beta_f32(double sk, double ss, float rho, float 
 }
 
 // Algorithm 1 over tiles of kAddTile blocks with the four binary64 divisions
-// taken out of the common path.  Each CTA stages the codes of both operands
-// with coalesced 16-byte loads into shared memory (a thread's 28 codes are
-// then 7 words at stride 7: conflict-free), forms beta_k in fp32 (beta_f32)
-// and decides each code from v = fl(beta_1 c_1 +- beta_2 c_2) and the bound
+// taken out of the common path.  Eight compute warps (one block per thread)
+// stage the codes of both operands with 16-byte asynchronous copies into
+// shared memory, two tiles deep (a thread's 28 codes are then 7 words at
+// stride 7: conflict-free), form beta_k in fp32 (beta_f32) and decide each
+// code from v = fl(beta_1 c_1 +- beta_2 c_2) and the bound
 //   |v - y| <= 2^-19 (|beta_1 c_1| + |beta_2 c_2|) + 2^-22 |v| + 2^-100
 // (2^-20 from beta, 2^-23 from the fp32 product and fma, the binary64
-// roundings of the specification far below), as add_block_fast does with
-// its tighter bound.  f and s are two binary64 additions per block.
+// roundings of the specification far below), evaluated per code as
+// E = 1.25 2^-19 (|beta_1| |c_1| + |beta_2| |c_2|) + 2^-100 (two fma).
+// f and s are two binary64 additions per block.
 //
-// A block with an undecided code, or whose beta_k has no fp32 estimate, is
-// appended to a per-tile list; after a barrier the CTA's threads evaluate
-// the listed blocks densely, one per thread, in binary64 (add_block's
-// arithmetic) for the undecided codes only.  Undecided codes are structural
-// rather than rare: equal phi and equal codes in both operands put y on an
-// integer (y = c phi / phi_k in real arithmetic), about one block in ten of
-// two smooth fields, so the dense list keeps the binary64 divisions to the
-// blocks that need them instead of to every warp that holds one.
+// A block with an undecided code, or whose beta_k has no fp32 estimate, goes
+// to a per-tile list with copies of its inputs.  Undecided codes are
+// structural rather than rare: equal phi and equal codes in both operands put
+// y on an integer (y = c phi / phi_k in real arithmetic), about one block in
+// ten of two smooth fields.  A ninth warp, the fixer, evaluates the listed
+// blocks in binary64 (add_block's arithmetic, undecided codes only; up to 32
+// blocks per pass of the warp, since a binary64 instruction costs a warp the
+// same for one lane as for 32), patches the tile's output codes in shared
+// memory and stores them with 16-byte writes, while the compute warps
+// already decide the next tile: the two share double-buffered output tiles
+// and lists through mbarriers (bounded waits; BLAZ_ERR_TIMEOUT in the status
+// word of these kernels).
 //
-// Output codes leave through shared memory as 16-byte stores.  Every input
-// of a tile is read before any output of it is written, so out may alias a
-// or b.  Requires 16-byte aligned code arrays (the launcher checks).
+// Every input of a tile is read before any output of it is written, so out
+// may alias a or b.  Requires 16-byte aligned code arrays (the launcher
+// checks).
 constexpr int kAddTile = 256;
+constexpr int kAddFixCap = 64;  // list entries per tile; beyond, the block's own thread fixes it
 
 struct AddFix {
     double sa, sb;
-    uint32_t undecided;  // bit 4q+k: code 4q+k
+    uint32_t wa[7], wb[7];  // the block's codes (the input stage is reused before the fixer runs)
+    uint32_t undecided;     // bit 4q+k: code 4q+k
     int t, pa, pb;
 };
 
+__device__ int g_ops_status;  // 0 or BLAZ_ERR_TIMEOUT (tiled addition)
+
+// two input stages of each operand, two output tiles, two lists
+constexpr size_t kAddSmem = 6 * kAddTile * 7 * 4 + 2 * kAddFixCap * sizeof(AddFix);
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// Starts the copies of the codes of both operands of one tile into a stage.
+__device__ __forceinline__ void add_stage_codes(int64_t tile, int64_t nb, const int8_t *c1, const int8_t *c2,
+                                                uint32_t *da, uint32_t *db, int t)
+{
+    const int64_t b0 = tile * kAddTile;
+    const int nt = (int)(nb - b0 < kAddTile ? nb - b0 : (int64_t)kAddTile);
+    const uint32_t *ga = reinterpret_cast<const uint32_t *>(c1 + b0 * kKeep);
+    const uint32_t *gb = reinterpret_cast<const uint32_t *>(c2 + b0 * kKeep);
+    if (nt == kAddTile) {
+        for (int i = t; i < kAddTile * 7 / 4; i += kAddTile) {
+            cp_async16(da + 4 * i, ga + 4 * i);
+            cp_async16(db + 4 * i, gb + 4 * i);
+        }
+    } else {
+        for (int i = t; i < nt * 7; i += kAddTile) {
+            cp_async4(da + i, ga + i);
+            cp_async4(db + i, gb + i);
+        }
+    }
+}
+
+// binary64 Algorithm 1 for the undecided codes of one block (bit 4q+k of
+// `undecided`: code k of word q), patched into its output words.
 template <bool kSub>
-__global__ void __launch_bounds__(kAddTile, 4)
+__device__ __forceinline__ void add_fix_block(double sa, double sb, int pa, int pb, const uint32_t *wa,
+                                              const uint32_t *wb, uint32_t undecided, uint32_t *wo)
+{
+    const double ss = dadd(sa, sb);
+    int ph = (pa * pb) / (pa + pb);
+    ph = ph < 1 ? 1 : ph;
+    const double a1 = ddiv(sa, ss);
+    const double a2 = ddiv(sb, ss);
+    const double phd = i64_to_double(ph);
+    const double b1 = dmul(div_small_int(a1, pa), phd);
+    const double b2 = dmul(div_small_int(a2, pb), phd);
+    // one pass per undecided code (the lane's set bits, lowest first)
+    for (uint32_t m = undecided; m; m &= m - 1u) {
+        const int bit = __ffs(m) - 1, q = bit >> 2, k = bit & 3;
+        const double x1 = (double)(int8_t)(uint8_t)(wa[q] >> (8 * k));
+        const double x2 = (double)(int8_t)(uint8_t)(wb[q] >> (8 * k));
+        const double y = kSub ? dsub(dmul(b1, x1), dmul(b2, x2)) : dadd(dmul(b1, x1), dmul(b2, x2));
+        reinterpret_cast<int8_t *>(wo + q)[k] = quantize(y);
+    }
+}
+
+__device__ __forceinline__ bool ops_wait(uint64_t *bar, uint32_t parity)
+{
+    const long long t0 = clock64();
+    while (!umma::mbar_try_wait(bar, parity))
+        if (clock64() - t0 > umma::kWaitCycles) {
+            atomicExch(&g_ops_status, BLAZ_ERR_TIMEOUT);
+            return false;
+        }
+    return true;
+}
+
+__device__ __forceinline__ void compute_bar() { asm volatile("bar.sync 1, %0;" ::"n"(kAddTile) : "memory"); }
+
+template <bool kSub>
+__global__ void __launch_bounds__(kAddTile + 32, 3)
     k_add_tile(int64_t nb, const double *f1, const double *s1, const uint8_t *p1, const int8_t *c1,
                const double *f2, const double *s2, const uint8_t *p2, const int8_t *c2, double *f, double *s,
                uint8_t *p, int8_t *c)
 {
-    __shared__ __align__(16) uint32_t sa_w[kAddTile * 7];
-    __shared__ __align__(16) uint32_t sb_w[kAddTile * 7];
-    __shared__ __align__(16) uint32_t so_w[kAddTile * 7];
-    __shared__ AddFix fix[kAddTile];
-    __shared__ int nfix;
+    // dynamic shared memory (kAddSmem bytes): input stages, output tiles, lists
+    extern __shared__ __align__(16) uint8_t add_smem[];
+    uint32_t(*sa_st)[kAddTile * 7] = reinterpret_cast<uint32_t(*)[kAddTile * 7]>(add_smem);
+    uint32_t(*sb_st)[kAddTile * 7] = sa_st + 2;
+    uint32_t(*so_st)[kAddTile * 7] = sa_st + 4;
+    AddFix(*fix)[kAddFixCap] = reinterpret_cast<AddFix(*)[kAddFixCap]>(add_smem + 6 * kAddTile * 7 * 4);
+    __shared__ int nfix[2];
+    __shared__ __align__(8) uint64_t work_ready[2], out_free[2];
+    __shared__ volatile int abort_flag;
     const int t = threadIdx.x;
     const int64_t ntiles = (nb + kAddTile - 1) / kAddTile;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    if (t == 0) {
+        for (int q = 0; q < 2; ++q) {
+            umma::mbar_init(&work_ready[q], kAddTile);
+            umma::mbar_init(&out_free[q], 1);
+            nfix[q] = 0;
+        }
+        abort_flag = 0;
+        umma::mbar_init_fence();
+    }
+    __syncthreads();
+
+    if (t >= kAddTile) {
+        // the fixer warp
+        const int lane = t - kAddTile;
+        for (int it = 0;; ++it) {
+            const int64_t tile = blockIdx.x + (int64_t)it * gridDim.x;
+            if (tile >= ntiles) break;
+            const int u = it & 1;
+            bool ok = true;
+            if (lane == 0) ok = ops_wait(&work_ready[u], (it >> 1) & 1);
+            if (!__shfl_sync(0xffffffffu, ok, 0)) {
+                abort_flag = 1;
+                break;
+            }
+            const int n = min(nfix[u], kAddFixCap);
+            for (int e = lane; e < n; e += 32) {
+                const AddFix &x = fix[u][e];
+                add_fix_block<kSub>(x.sa, x.sb, x.pa, x.pb, x.wa, x.wb, x.undecided, so_st[u] + x.t * 7);
+            }
+            __syncwarp();
+            const int64_t b0 = tile * kAddTile;
+            const int nt = (int)(nb - b0 < kAddTile ? nb - b0 : (int64_t)kAddTile);
+            uint32_t *go = reinterpret_cast<uint32_t *>(c + b0 * kKeep);
+            if (nt == kAddTile) {
+                uint4 *vo = reinterpret_cast<uint4 *>(go);
+                for (int i = lane; i < kAddTile * 7 / 4; i += 32)
+                    __stcs(vo + i, reinterpret_cast<const uint4 *>(so_st[u])[i]);
+            } else {
+                for (int i = lane; i < nt * 7; i += 32) __stcs(go + i, so_st[u][i]);
+            }
+            __syncwarp();
+            if (lane == 0) {
+                nfix[u] = 0;
+                umma::mbar_arrive(&out_free[u]);
+            }
+        }
+        return;
+    }
+
+    // the compute warps
+    int64_t tile = blockIdx.x;
+    if (tile < ntiles) add_stage_codes(tile, nb, c1, c2, sa_st[0], sb_st[0], t);
+    cp_async_commit();
+    // f, s and phi of the current tile, loaded one tile ahead
+    double nfa = 0.0, nfb = 0.0, nsa = 0.0, nsb = 0.0;
+    int npa = 1, npb = 1;
+    if (tile < ntiles && tile * kAddTile + t < nb) {
+        const int64_t b = tile * kAddTile + t;
+        nfa = __ldcs(f1 + b);
+        nfb = __ldcs(f2 + b);
+        nsa = __ldcs(s1 + b);
+        nsb = __ldcs(s2 + b);
+        npa = __ldcs(p1 + b);
+        npb = __ldcs(p2 + b);
+    }
+    for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
+        const int stg = it & 1, u = it & 1;
+        const uint32_t *sa_w = sa_st[stg], *sb_w = sb_st[stg];
+        uint32_t *so_w = so_st[u];
         const int64_t b0 = tile * kAddTile;
         const int nt = (int)(nb - b0 < kAddTile ? nb - b0 : (int64_t)kAddTile);
-        const int nw = nt * 7;  // 32-bit words of codes in this tile
-        const uint32_t *ga = reinterpret_cast<const uint32_t *>(c1 + b0 * kKeep);
-        const uint32_t *gb = reinterpret_cast<const uint32_t *>(c2 + b0 * kKeep);
-        if (t == 0) nfix = 0;
-        if (nt == kAddTile) {
-            const uint4 *va = reinterpret_cast<const uint4 *>(ga), *vb = reinterpret_cast<const uint4 *>(gb);
-            for (int i = t; i < kAddTile * 7 / 4; i += kAddTile) {
-                reinterpret_cast<uint4 *>(sa_w)[i] = __ldcs(va + i);
-                reinterpret_cast<uint4 *>(sb_w)[i] = __ldcs(vb + i);
-            }
-        } else {
-            for (int i = t; i < nw; i += kAddTile) {
-                sa_w[i] = __ldcs(ga + i);
-                sb_w[i] = __ldcs(gb + i);
-            }
+        const int64_t next = tile + gridDim.x;
+        if (next < ntiles) add_stage_codes(next, nb, c1, c2, sa_st[stg ^ 1], sb_st[stg ^ 1], t);
+        cp_async_commit();
+        const double fa = nfa, fb = nfb, sa = nsa, sb = nsb;
+        const int pa = npa, pb = npb;
+        if (next < ntiles && next * kAddTile + t < nb) {
+            const int64_t bn = next * kAddTile + t;
+            nfa = __ldcs(f1 + bn);
+            nfb = __ldcs(f2 + bn);
+            nsa = __ldcs(s1 + bn);
+            nsb = __ldcs(s2 + bn);
+            npa = __ldcs(p1 + bn);
+            npb = __ldcs(p2 + bn);
         }
         const int64_t b = b0 + t;
-        double fa = 0.0, fb = 0.0, sa = 0.0, sb = 0.0;
-        int pa = 1, pb = 1;
-        if (t < nt) {
-            fa = __ldcs(f1 + b);
-            fb = __ldcs(f2 + b);
-            sa = __ldcs(s1 + b);
-            sb = __ldcs(s2 + b);
-            pa = __ldcs(p1 + b);
-            pb = __ldcs(p2 + b);
-        }
-        __syncthreads();
+        // the output tile u is free once the fixer has stored tile it - 2
+        if (t == 0 && !ops_wait(&out_free[u], ((it >> 1) & 1) ^ 1)) abort_flag = 1;
+        cp_async_wait_prev();  // this thread's copies of the current stage have landed
+        compute_bar();
+        if (abort_flag) break;
         if (t < nt) {
             const double fs = kSub ? dsub(fa, fb) : dadd(fa, fb);
             const double ss = dadd(sa, sb);
@@ -136,19 +286,21 @@ __global__ void __launch_bounds__(kAddTile, 4)
                 float b1f = 0.0f, b2f = 0.0f;
                 const bool ok = beta_f32(sa, ss, __fdividef(phf, (float)pa), b1f) &
                                 beta_f32(sb, ss, __fdividef(phf, (float)pb), b2f);
-                const float ab1 = fabsf(b1f), ab2 = fabsf(b2f);
+                // |v| <= (|beta_1 c_1| + |beta_2 c_2|)(1 + 2^-20), so the bound is at most
+                // 1.125 2^-19 (|beta_1 c_1| + |beta_2 c_2|) + 2^-100; 1.25 covers the fp32
+                // roundings of E = e_1 |c_1| + e_2 |c_2| + 2^-100 with e_k = 1.25 2^-19 |beta_k|
+                const float e1 = 0x1.4p-19f * fabsf(b1f), e2 = 0x1.4p-19f * fabsf(b2f);
 #pragma unroll
                 for (int q = 0; q < 7; ++q) {
-                    const uint32_t wa = sa_w[t * 7 + q], wb = sb_w[t * 7 + q];
+                    // byte k of (w ^ 0x80808080) in the low byte of 1.5 2^23: the float 12583040 + c
+                    const uint32_t wa = sa_w[t * 7 + q] ^ 0x80808080u, wb = sb_w[t * 7 + q] ^ 0x80808080u;
                     uint32_t v32 = 0;
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
-                        const int i1 = (int)(int8_t)(uint8_t)(wa >> (8 * k));
-                        const int i2 = (int)(int8_t)(uint8_t)(wb >> (8 * k));
-                        const float x1 = small_int_to_float(i1), x2 = small_int_to_float(i2);
+                        const float x1 = __uint_as_float(__byte_perm(wa, 0x4B400000u, 0x7640 + k)) - 12583040.0f;
+                        const float x2 = __uint_as_float(__byte_perm(wb, 0x4B400000u, 0x7640 + k)) - 12583040.0f;
                         const float v = fmaf(b1f, x1, kSub ? -(b2f * x2) : b2f * x2);
-                        const float E = 0x1p-19f * fmaf(ab1, fabsf(x1), ab2 * fabsf(x2)) + 0x1p-22f * fabsf(v) +
-                                        0x1p-100f;
+                        const float E = fmaf(e1, fabsf(x1), fmaf(e2, fabsf(x2), 0x1p-100f));
                         const float lo = v - E, hi = v + E;
                         int code;
                         bool done;
@@ -171,55 +323,32 @@ __global__ void __launch_bounds__(kAddTile, 4)
                 if (!ok) undecided = 0x0FFFFFFFu;
             }
             if (undecided) {
-                const int i = atomicAdd(&nfix, 1);
-                fix[i].sa = sa;
-                fix[i].sb = sb;
-                fix[i].undecided = undecided;
-                fix[i].t = t;
-                fix[i].pa = pa;
-                fix[i].pb = pb;
+                const int i = atomicAdd(&nfix[u], 1);
+                if (i < kAddFixCap) {
+                    AddFix &x = fix[u][i];
+                    x.sa = sa;
+                    x.sb = sb;
+#pragma unroll
+                    for (int q = 0; q < 7; ++q) {
+                        x.wa[q] = sa_w[t * 7 + q];
+                        x.wb[q] = sb_w[t * 7 + q];
+                    }
+                    x.undecided = undecided;
+                    x.t = t;
+                    x.pa = pa;
+                    x.pb = pb;
+                } else {
+                    add_fix_block<kSub>(sa, sb, pa, pb, sa_w + t * 7, sb_w + t * 7, undecided, so_w + t * 7);
+                }
             }
             __stcs(f + b, fs);
             __stcs(s + b, ss);
             p[b] = (uint8_t)ph;
         }
-        __syncthreads();
-        // binary64 Algorithm 1 for the undecided codes of the listed blocks
-        for (int i = t; i < nfix; i += kAddTile) {
-            const AddFix e = fix[i];
-            const double ss = dadd(e.sa, e.sb);
-            int ph = (e.pa * e.pb) / (e.pa + e.pb);
-            ph = ph < 1 ? 1 : ph;
-            const double a1 = ddiv(e.sa, ss);
-            const double a2 = ddiv(e.sb, ss);
-            const double phd = i64_to_double(ph);
-            const double b1 = dmul(div_small_int(a1, e.pa), phd);
-            const double b2 = dmul(div_small_int(a2, e.pb), phd);
-            for (int q = 0; q < 7; ++q) {
-                const uint32_t m = (e.undecided >> (4 * q)) & 0xFu;
-                if (!m) continue;
-                const uint32_t wa = sa_w[e.t * 7 + q], wb = sb_w[e.t * 7 + q];
-                uint32_t w = so_w[e.t * 7 + q];
-                for (int k = 0; k < 4; ++k)
-                    if (m & (1u << k)) {
-                        const double x1 = (double)(int8_t)(uint8_t)(wa >> (8 * k));
-                        const double x2 = (double)(int8_t)(uint8_t)(wb >> (8 * k));
-                        const double y = kSub ? dsub(dmul(b1, x1), dmul(b2, x2)) : dadd(dmul(b1, x1), dmul(b2, x2));
-                        w = (w & ~(0xFFu << (8 * k))) | ((uint32_t)(uint8_t)quantize(y) << (8 * k));
-                    }
-                so_w[e.t * 7 + q] = w;
-            }
-        }
-        __syncthreads();
-        uint32_t *go = reinterpret_cast<uint32_t *>(c + b0 * kKeep);
-        if (nt == kAddTile) {
-            uint4 *vo = reinterpret_cast<uint4 *>(go);
-            for (int i = t; i < kAddTile * 7 / 4; i += kAddTile) __stcs(vo + i, reinterpret_cast<const uint4 *>(so_w)[i]);
-        } else {
-            for (int i = t; i < nw; i += kAddTile) __stcs(go + i, so_w[i]);
-        }
-        __syncthreads();
+        umma::mbar_arrive(&work_ready[u]);
+        compute_bar();  // every thread is done with this input stage before it is refilled
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");  // nothing in flight at exit (an aborted loop)
 }
 
 // Algorithm 2.  When out == a (in place) only f and s are touched; otherwise
@@ -287,20 +416,41 @@ static int grid_for(int64_t n, int threads)
     return (int)(want < 1 ? 1 : want);
 }
 
+int ops_device_status()
+{
+    int v = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(&v, g_ops_status, sizeof(int));
+    if (e != cudaSuccess) return set_cuda_error(e);
+    if (v != 0) {
+        const int zero = 0;
+        e = cudaMemcpyToSymbol(g_ops_status, &zero, sizeof(int));
+        if (e != cudaSuccess) return set_cuda_error(e);
+    }
+    return v;
+}
+
 int launch_add(const blaz_cmat *a, const blaz_cmat *b, const blaz_cmat *o, bool subtract, cudaStream_t st)
 {
     const int64_t nb = (a->rows / 8) * (a->cols / 8);
     if (nb == 0) return BLAZ_OK;
     auto a16 = [](const void *q) { return ((uintptr_t)q & 15) == 0; };
     if (a16(a->code) && a16(b->code) && a16(o->code)) {
-        // tiles of 256 blocks; 4 resident CTAs per SM, a few waves of tiles
+        // tiles of 256 blocks; one wave of 3 resident CTAs per SM, each
+        // looping over its tiles with the next tile's codes in flight
         const int64_t ntiles = (nb + kAddTile - 1) / kAddTile;
-        const int grid = (int)std::min<int64_t>(ntiles, (int64_t)num_sms() * 4 * 4);
+        const int grid = (int)std::min<int64_t>(ntiles, (int64_t)num_sms() * 3);
+        static const bool smem_ok = [] {
+            return cudaFuncSetAttribute(k_add_tile<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)kAddSmem) == cudaSuccess &&
+                   cudaFuncSetAttribute(k_add_tile<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)kAddSmem) == cudaSuccess;
+        }();
+        if (!smem_ok) return set_cuda_error(cudaGetLastError());
         if (subtract)
-            k_add_tile<true><<<grid, kAddTile, 0, st>>>(nb, a->f, a->s, a->phi, a->code, b->f, b->s, b->phi,
+            k_add_tile<true><<<grid, kAddTile + 32, kAddSmem, st>>>(nb, a->f, a->s, a->phi, a->code, b->f, b->s, b->phi,
                                                         b->code, o->f, o->s, o->phi, o->code);
         else
-            k_add_tile<false><<<grid, kAddTile, 0, st>>>(nb, a->f, a->s, a->phi, a->code, b->f, b->s, b->phi,
+            k_add_tile<false><<<grid, kAddTile + 32, kAddSmem, st>>>(nb, a->f, a->s, a->phi, a->code, b->f, b->s, b->phi,
                                                          b->code, o->f, o->s, o->phi, o->code);
         return launch_status();
     }

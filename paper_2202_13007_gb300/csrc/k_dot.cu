@@ -63,9 +63,30 @@ __device__ __forceinline__ int f2i_exact(float x) { return __float2int_rn(x); }
 struct GramTC {
     uint2 bfrag[kSlices][2][4][32];  // [slice][k-step][n-tile][lane]: H_s (columns 0..27) and w_s (column 28)
     float wl[kSlices][32][8];        // w_s digits at the 8 code positions a lane holds
-    double scaleH[kSlices], scaleW[kSlices];
+    int eH2, eH4, eW2, eW4;          // log2 of scaleH[2], scaleH[4], scaleW[2], scaleW[4]
     double inv_phi[256];
 };
+
+// v 2^e as binary64 on the integer pipe (v's low bits beyond 53 truncated);
+// e keeps the result a normal number for |v| < 2^63 (the slice scales).
+__device__ __forceinline__ double i64_ldexp(long long v, int e)
+{
+    if (v == 0) return 0.0;
+    const unsigned long long sign = v < 0 ? 0x8000000000000000ull : 0ull;
+    const unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
+    const int msb = 63 - __clzll((long long)a);
+    const unsigned long long m = msb <= 52 ? (a << (52 - msb)) : (a >> (msb - 52));
+    return __longlong_as_double(
+        (long long)(sign | ((unsigned long long)(msb + e + 1023) << 52) | (m & 0x000FFFFFFFFFFFFFull)));
+}
+
+// 64 x on the exponent for normal x well inside the range, else a product.
+__device__ __forceinline__ double times64(double x)
+{
+    const long long b = __double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7FF);
+    return (e >= 1 && e <= 2040) ? __longlong_as_double(b + (6ll << 52)) : 64.0 * x;
+}
 
 __device__ __forceinline__ void mma_f16x(float (&c)[4], const uint32_t (&a)[4], uint2 b)
 {
@@ -183,15 +204,17 @@ __global__ void __launch_bounds__(kDotThreads, 3)
 {
     __shared__ uint2 sbf[kSlices][2][4][32];
     __shared__ float swl[kSlices][32][8];
+    __shared__ double inv_phi[256];  // indexed per lane: shared, not the parameter bank
     __shared__ double red[kDotThreads / 32];
     __shared__ bool last;
     for (int i = threadIdx.x; i < kSlices * 2 * 4 * 32; i += blockDim.x) (&sbf[0][0][0][0])[i] = (&g.bfrag[0][0][0][0])[i];
     for (int i = threadIdx.x; i < kSlices * 32 * 8; i += blockDim.x) (&swl[0][0][0])[i] = (&g.wl[0][0][0])[i];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) inv_phi[i] = g.inv_phi[i];
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gq = lane >> 2, t = lane & 3;
     const int wpc = blockDim.x >> 5;
     const int64_t npairs = (nb + 31) / 32;
-    double acc = 0.0;
+    double acc1 = 0.0, acc2 = 0.0;
     for (int64_t pr = (int64_t)blockIdx.x * wpc + warp; pr < npairs; pr += (int64_t)gridDim.x * wpc) {
         float qh[kSlices], ql[kSlices], wbs[kSlices], was[kSlices];
 #pragma unroll 1
@@ -222,17 +245,20 @@ __global__ void __launch_bounds__(kDotThreads, 3)
                     blo = blo * 2048 + Bw;
                 }
             }
-            const double Q = fma(g.scaleH[2], i64_to_double(qhi), g.scaleH[4] * i64_to_double(qlo));
-            const double Wa = fma(g.scaleW[2], i64_to_double(ahi), g.scaleW[4] * i64_to_double(alo));
-            const double Wb = fma(g.scaleW[2], i64_to_double(bhi), g.scaleW[4] * i64_to_double(blo));
-            const double ta = sa[b] * g.inv_phi[pa[b]], tb = sb[b] * g.inv_phi[pb[b]];
+            // ten binary64 operations: the power-of-two slice scales and the
+            // factor 64 go to the exponent on the integer pipe
+            const double Q = i64_ldexp(qhi, g.eH2) + i64_ldexp(qlo, g.eH4);
+            const double Wa = i64_ldexp(ahi, g.eW2) + i64_ldexp(alo, g.eW4);
+            const double Wb = i64_ldexp(bhi, g.eW2) + i64_ldexp(blo, g.eW4);
+            const double ta = sa[b] * inv_phi[pa[b]], tb = sb[b] * inv_phi[pb[b]];
             const double f_a = fa[b], f_b = fb[b];
-            const double t1 = fma(tb, Wb, 64.0 * f_b);
+            const double t1 = fma(tb, Wb, times64(f_b));
             const double t2 = fma(tb, Q, f_b * Wa);
-            acc += fma(f_a, t1, ta * t2);
+            acc1 = fma(f_a, t1, acc1);
+            acc2 = fma(ta, t2, acc2);
         }
     }
-    const double tot = cta_sum(acc, red);
+    const double tot = cta_sum(acc1 + acc2, red);
     if (threadIdx.x == 0) {
         partials[blockIdx.x] = tot;
         __threadfence();
@@ -408,10 +434,10 @@ static const GramTC &gram_tc()
                         const int k = nt * 8 + 2 * (lane & 3) + q;
                         tcc.wl[s][lane][2 * nt + q] = k < kKeep ? gc.w[s][k] : 0.0f;
                     }
-        for (int s = 0; s < kSlices; ++s) {
-            tcc.scaleH[s] = gc.scaleH[s];
-            tcc.scaleW[s] = gc.scaleW[s];
-        }
+        tcc.eH2 = std::ilogb(gc.scaleH[2]);
+        tcc.eH4 = std::ilogb(gc.scaleH[4]);
+        tcc.eW2 = std::ilogb(gc.scaleW[2]);
+        tcc.eW4 = std::ilogb(gc.scaleW[4]);
         for (int p = 0; p < 256; ++p) tcc.inv_phi[p] = gc.inv_phi[p];
     });
     return tcc;

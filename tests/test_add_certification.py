@@ -1,6 +1,7 @@
 """The tiled addition kernel decides each code of Algorithm 1 from fp32
 estimates of beta_k = RN(RN(RN(s_k/s)/phi_k) phi) and the bound
     |v - y| <= 2^-19 (|beta_1 c_1| + |beta_2 c_2|) + 2^-22 |v| + 2^-100,
+evaluated as E = 1.25 2^-19 (|beta_1| |c_1| + |beta_2| |c_2|) + 2^-100 (two fma),
 falling back to binary64 when the interval [v - E, v + E] does not truncate
 to one code.  This test emulates the kernel's fp32 arithmetic in numpy (the
 scaled truncations of s_k and s, a quotient perturbed to both ends of the
@@ -59,11 +60,10 @@ def kernel_codes(a, b, pert1, pert2, sub=False):
     if sub:
         p2 = -p2
     v = (b1.astype(np.float64) * x1.astype(np.float64) + p2.astype(np.float64)).astype(F32)
-    ab2x2 = (np.abs(b2).astype(np.float64) * np.abs(x2).astype(np.float64)).astype(F32)
-    inner = (np.abs(b1).astype(np.float64) * np.abs(x1).astype(np.float64) + ab2x2.astype(np.float64)).astype(F32)
-    E = F32(2.0 ** -19) * inner
-    E = F32(E + F32(2.0 ** -22) * np.abs(v))
-    E = F32(E + F32(2.0 ** -100))
+    e1 = F32(F32(1.25 * 2.0 ** -19) * np.abs(b1))
+    e2 = F32(F32(1.25 * 2.0 ** -19) * np.abs(b2))
+    inner = (e2.astype(np.float64) * np.abs(x2).astype(np.float64) + 2.0 ** -100).astype(F32)
+    E = (e1.astype(np.float64) * np.abs(x1).astype(np.float64) + inner.astype(np.float64)).astype(F32)
     lo, hi = F32(v - E), F32(v + E)
     with np.errstate(invalid="ignore", over="ignore"):
         tl, th = np.trunc(lo), np.trunc(hi)

@@ -265,6 +265,31 @@ def test_dot_plain_pair(B):
     assert float(B.dot(ga, gb).item()) == v
 
 
+@pytest.mark.parametrize("shape", [(8, 8), (200, 328), (1032, 1000), (64, 8 * 129)])
+def test_dot_ragged_tiles_and_extreme_codes(B, shape):
+    """The tensor-core dot over tiles of 128 blocks: one block, a ragged last
+    tile, several tiles per CTA; then codes of +-127 everywhere (the largest
+    slice products) and mixed-sign slopes."""
+    r, c = shape
+    X = W.random_block_matrix(r, c, seed=r + c)
+    Y = W.random_block_matrix(r, c, seed=r + c + 1, kind="noise")
+    gx, gy = B.compress(dev(X)), B.compress(dev(Y))
+    ox, oy = O.compress(X), O.compress(Y)
+    v = float(B.dot(gx, gy).item())
+    ref, absref = O.dot(ox, oy)
+    assert abs(v - ref) <= 1e-12 * absref
+    rng = np.random.default_rng(r)
+    for m, om in ((gx, ox), (gy, oy)):
+        codes = rng.choice(np.array([-127, 127], np.int8), size=om.code.shape)
+        om.code[:] = codes
+        om.s[:] = om.s * rng.choice([-1.0, 1.0], size=om.s.shape)
+        m.code.copy_(torch.from_numpy(om.code))
+        m.s.copy_(torch.from_numpy(om.s))
+    v = float(B.dot(gx, gy).item())
+    ref, absref = O.dot(ox, oy)
+    assert abs(v - ref) <= 1e-12 * absref
+
+
 @pytest.mark.parametrize("ij", [(17, 200), (0, 0), (255, 255), (100, 3)])
 def test_dot_rowcol_plain_pair(B, ij):
     A, Bm = W.plain_pair()
