@@ -84,9 +84,9 @@ def kernel_sha(name: str) -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(name: str, blocks: int):
-    """DRAM bytes per launch from the committed ncu summary, scaled to `blocks`
-    blocks; None when the kernel source changed since the capture."""
+def profiled(name: str, key: str):
+    """A per-block figure of the committed ncu summary (profiles/traffic.json);
+    None when the kernel source changed since the capture."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
             d = json.load(fh)[name]
@@ -94,7 +94,14 @@ def profiled_traffic(name: str, blocks: int):
         return None
     if d.get("source_sha") != kernel_sha(name):
         return None
-    return d["dram_bytes_per_block"] * blocks
+    return d.get(key)
+
+
+def profiled_traffic(name: str, blocks: int):
+    """DRAM bytes per launch from the committed ncu summary, scaled to `blocks`
+    blocks; None when the kernel source changed since the capture."""
+    per_block = profiled(name, "dram_bytes_per_block")
+    return None if per_block is None else per_block * blocks
 
 
 def probe_fp64(dev, st):
@@ -831,7 +838,10 @@ def main():
                          "ms_per_launch": comp_ms, "algorithmic_flops_per_launch": COMPRESS_FLOPS_PER_BLOCK * nb,
                          "hbm_frac": 557 * nb / (comp_ms * 1e-3) / 1e9 / hbm, "hbm_peak_source": hbm_src,
                          "fp64_issue_probe_gops": fp64_probe,
-                         "frac_of_fp64_probe": achieved / fp64_probe if fp64_probe else None},
+                         "fp64_inst_per_block": profiled("k_compress", "fp64_inst_per_block"),
+                         "issued_frac_of_fp64_probe": (
+                             profiled("k_compress", "fp64_inst_per_block") * nb / (comp_ms * 1e-3) / 1e9 / fp64_probe
+                             if fp64_probe and profiled("k_compress", "fp64_inst_per_block") else None)},
             "clocks": clk.summary(),
             "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps,

@@ -190,14 +190,16 @@ __device__ __forceinline__ void mma_f16(float (&c)[4], const uint32_t (&a)[4], u
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b.x), "r"(b.y));
 }
 
-// Two consecutive int8 codes (k, k+1) of a block as an fp16 pair; zero beyond 28.
+// Two consecutive int8 codes (k, k+1) of a block as an fp16 pair; zero beyond
+// 28.  Off the conversion unit: byte x ^ 0x80 = x + 128 under the exponent of
+// 1024 is the fp16 number 1152 + x, and one exact subtraction leaves x.
 __device__ __forceinline__ uint32_t code_pair(const int8_t *__restrict__ c, int k, bool valid)
 {
     if (!valid || k >= kKeep) return 0u;
-    const uint16_t v = __ldg(reinterpret_cast<const uint16_t *>(c + k));
-    const __half lo = __short2half_rn((short)(int8_t)(uint8_t)(v & 0xFF));
-    const __half hi = __short2half_rn((short)(int8_t)(uint8_t)(v >> 8));
-    return (uint32_t)__half_as_ushort(lo) | ((uint32_t)__half_as_ushort(hi) << 16);
+    const uint32_t v = __ldg(reinterpret_cast<const uint16_t *>(c + k));
+    const uint32_t q = __byte_perm(v ^ 0x8080u, 0x64646464u, 0x4140);
+    const __half2 h = __hsub2(*reinterpret_cast<const __half2 *>(&q), __half2half2(__ushort_as_half((unsigned short)0x6480)));
+    return *reinterpret_cast<const uint32_t *>(&h);
 }
 
 template <bool kVec>
@@ -207,8 +209,10 @@ __global__ void __launch_bounds__(128)
                  double *__restrict__ A, int64_t lda, int64_t rows, int64_t cols, bool zero_fill)
 {
     __shared__ uint2 sb[kDecSlices][2][8][32];
+    __shared__ double inv_phi[256];  // indexed per lane: shared, not the parameter bank
     for (int i = threadIdx.x; i < kDecSlices * 2 * 8 * 32; i += blockDim.x)
         (&sb[0][0][0][0])[i] = (&dc.bfrag[0][0][0][0])[i];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) inv_phi[i] = dc.inv_phi[i];
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     const int64_t ngroups = (nb + 15) / 16;
@@ -237,7 +241,7 @@ __global__ void __launch_bounds__(128)
             const bool v = h ? vB : vA;
             const int64_t bi = v ? b / nbc : 0, bj = v ? b - bi * nbc : 0;
             fb[h] = v ? __ldg(f + b) : 0.0;
-            ts[h] = v ? __ldg(s + b) * dc.inv_phi[__ldg(phi + b)] * dc.scale : 0.0;
+            ts[h] = v ? __ldg(s + b) * inv_phi[__ldg(phi + b)] * dc.scale : 0.0;
             pb[h] = A + (bi * 8) * lda + bj * 8 + 2 * t;
             r0[h] = bi * 8;
             inside[h] = bi * 8 + 8 <= rows && bj * 8 + 8 <= cols;

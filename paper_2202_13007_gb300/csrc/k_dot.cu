@@ -51,8 +51,6 @@ struct GramConsts {
     double inv_phi[256];             // 1/phi
 };
 
-// Exact conversion of an integer-valued float with |x| < 2^24 to int.
-__device__ __forceinline__ int f2i_exact(float x) { return __float2int_rn(x); }
 
 // Tensor-core form of the Gram dot, 16 blocks per warp.  Y_s = C_b H_s
 // (plus the column w_s) on mma.sync m16n8k16 with fp16 digits of H_s and w_s
@@ -96,17 +94,42 @@ __device__ __forceinline__ void mma_f16x(float (&c)[4], const uint32_t (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b.x), "r"(b.y));
 }
 
-__device__ __forceinline__ uint32_t code_pair_h(const int8_t *__restrict__ c, int k, bool valid)
+// The conversions below stay off the conversion unit (a quarter-rate pipe
+// that the codes would otherwise saturate): a byte x ^ 0x80 = x + 128 placed
+// under the exponent of 1024 (fp16) or 1.5 2^23 (fp32) is the number
+// 1152 + x or 12583040 + x, and one exact subtraction leaves x.
+
+// Two consecutive raw int8 codes (k, k+1) of a block, as 16 bits; zero beyond 28.
+__device__ __forceinline__ uint32_t code_pair_raw(const int8_t *__restrict__ c, int k, bool valid)
 {
     if (!valid || k >= kKeep) return 0u;
-    const uint16_t v = __ldg(reinterpret_cast<const uint16_t *>(c + k));
-    const __half lo = __short2half_rn((short)(int8_t)(uint8_t)(v & 0xFF));
-    const __half hi = __short2half_rn((short)(int8_t)(uint8_t)(v >> 8));
-    return (uint32_t)__half_as_ushort(lo) | ((uint32_t)__half_as_ushort(hi) << 16);
+    return __ldg(reinterpret_cast<const uint16_t *>(c + k));
 }
 
-__device__ __forceinline__ float half_lo(uint32_t p) { return __half2float(__ushort_as_half((unsigned short)(p & 0xFFFF))); }
-__device__ __forceinline__ float half_hi(uint32_t p) { return __half2float(__ushort_as_half((unsigned short)(p >> 16))); }
+// A raw code pair as an fp16 pair (exact).
+__device__ __forceinline__ uint32_t pair_to_h2(uint32_t v)
+{
+    const uint32_t q = __byte_perm(v ^ 0x8080u, 0x64646464u, 0x4140);
+    const __half2 h = __hsub2(*reinterpret_cast<const __half2 *>(&q), __half2half2(__ushort_as_half((unsigned short)0x6480)));
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+__device__ __forceinline__ uint32_t code_pair_h(const int8_t *__restrict__ c, int k, bool valid)
+{
+    return pair_to_h2(code_pair_raw(c, k, valid));
+}
+
+// Code k (0 or 1) of a raw pair as fp32 (exact).
+__device__ __forceinline__ float pair_code_f(uint32_t v, int k)
+{
+    return __uint_as_float(__byte_perm(v ^ 0x8080u, 0x4B400000u, 0x7640 + k)) - 12583040.0f;
+}
+
+// rint of an integer-valued x / 4096 with |x| < 2^33 (so |x / 4096| < 2^21).
+__device__ __forceinline__ float rint_div4096(float x)
+{
+    return (x * (1.0f / 4096.0f) + 12582912.0f) - 12582912.0f;
+}
 
 // One group of 16 blocks (rows gq and gq + 8 of the fragments): the slice
 // products C_b H_s and w_s.c_b on the tensor cores, the exact contraction
@@ -137,11 +160,11 @@ __device__ __forceinline__ void gram_group(const uint2 (*sbf)[2][4][32], const f
         const int8_t *caA = ca + bA * kKeep, *caB = ca + bB * kKeep;
 #pragma unroll
         for (int nt = 0; nt < 4; ++nt) {
-            const uint32_t pA = code_pair_h(caA, nt * 8 + 2 * t, vA), pB = code_pair_h(caB, nt * 8 + 2 * t, vB);
-            xa[0][2 * nt] = half_lo(pA);
-            xa[0][2 * nt + 1] = half_hi(pA);
-            xa[1][2 * nt] = half_lo(pB);
-            xa[1][2 * nt + 1] = half_hi(pB);
+            const uint32_t pA = code_pair_raw(caA, nt * 8 + 2 * t, vA), pB = code_pair_raw(caB, nt * 8 + 2 * t, vB);
+            xa[0][2 * nt] = pair_code_f(pA, 0);
+            xa[0][2 * nt + 1] = pair_code_f(pA, 1);
+            xa[1][2 * nt] = pair_code_f(pB, 0);
+            xa[1][2 * nt + 1] = pair_code_f(pB, 1);
         }
     }
 #pragma unroll
@@ -157,7 +180,7 @@ __device__ __forceinline__ void gram_group(const uint2 (*sbf)[2][4][32], const f
                 const int k = nt * 8 + 2 * t + q;
                 if (k < kKeep) {
                     const float y0 = c[q], y1 = c[2 + q];
-                    const float yh0 = rintf(y0 * (1.0f / 4096.0f)), yh1 = rintf(y1 * (1.0f / 4096.0f));
+                    const float yh0 = rint_div4096(y0), yh1 = rint_div4096(y1);
                     h0 = fmaf(xa[0][2 * nt + q], yh0, h0);
                     l0 = fmaf(xa[0][2 * nt + q], fmaf(-4096.0f, yh0, y0), l0);
                     h1 = fmaf(xa[1][2 * nt + q], yh1, h1);
@@ -233,8 +256,8 @@ __global__ void __launch_bounds__(kDotThreads, 3)
             long long qhi = 0, qlo = 0, ahi = 0, alo = 0, bhi = 0, blo = 0;
 #pragma unroll
             for (int sl = 0; sl < kSlices; ++sl) {
-                const long long T = 4096ll * f2i_exact(qh[sl]) + f2i_exact(ql[sl]);
-                const long long A = f2i_exact(was[sl]), Bw = f2i_exact(wbs[sl]);
+                const long long T = 4096ll * f2i_small(qh[sl]) + f2i_small(ql[sl]);
+                const long long A = f2i_small(was[sl]), Bw = f2i_small(wbs[sl]);
                 if (sl < 3) {
                     qhi = qhi * 2048 + T;
                     ahi = ahi * 2048 + A;
