@@ -105,26 +105,30 @@ def profiled_traffic(name: str, blocks: int):
 
 
 def probe_fp64(dev, st):
-    """Measured binary64 issue ceiling (G additions/s): the library's probe
-    (4 independent DADD chains per thread, 16 warps per SM), best of 3
-    launches timed with CUDA events on `st`."""
+    """Measured binary64 issue rate (G additions/s) of the library's probe
+    (4 independent DADD chains per thread, one CTA per SM) at 1, 2, 4, 8 and
+    16 warps per SM, best of 3 launches each timed with CUDA events on `st`;
+    returns (the maximum, {warps per SM: rate})."""
     import torch
 
     from paper_2202_13007_gb300 import blaz as B
 
-    out = torch.empty(torch.cuda.get_device_properties(dev).multi_processor_count * 512, dtype=torch.float64,
+    out = torch.empty(torch.cuda.get_device_properties(dev).multi_processor_count * 16 * 32, dtype=torch.float64,
                       device=dev)
-    B.probe_fp64_rate(64, out, st)
-    best = None
-    for _ in range(3):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(st)
-        ops = B.probe_fp64_rate(4096, out, st)
-        e1.record(st)
-        torch.cuda.synchronize()
-        rate = ops / (e0.elapsed_time(e1) * 1e-3) / 1e9
-        best = rate if best is None else max(best, rate)
-    return best
+    rates = {}
+    for w in (1, 2, 4, 8, 16):
+        B.probe_fp64_rate(64, out, w, st)
+        best = None
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            ops = B.probe_fp64_rate(4096 if w >= 4 else 1024, out, w, st)
+            e1.record(st)
+            torch.cuda.synchronize()
+            rate = ops / (e0.elapsed_time(e1) * 1e-3) / 1e9
+            best = rate if best is None else max(best, rate)
+        rates[w] = best
+    return max(rates.values()), rates
 
 
 def peaks():
@@ -748,7 +752,7 @@ def main():
     nb = (n // 8) ** 2
     achieved = COMPRESS_FLOPS_PER_BLOCK * nb / (comp_ms * 1e-3) / 1e9
     hbm, hbm_src = peaks()
-    fp64_probe = probe_fp64(dev, st)
+    fp64_probe, fp64_by_warps = probe_fp64(dev, st)
 
     # End to end through the public API with host buffers, every step: A and B
     # compressed from page-locked host memory (blaz_compress_host pipelines the
@@ -838,6 +842,7 @@ def main():
                          "ms_per_launch": comp_ms, "algorithmic_flops_per_launch": COMPRESS_FLOPS_PER_BLOCK * nb,
                          "hbm_frac": 557 * nb / (comp_ms * 1e-3) / 1e9 / hbm, "hbm_peak_source": hbm_src,
                          "fp64_issue_probe_gops": fp64_probe,
+                         "fp64_issue_probe_by_warps_per_sm": fp64_by_warps,
                          "fp64_inst_per_block": profiled("k_compress", "fp64_inst_per_block"),
                          "issued_frac_of_fp64_probe": (
                              profiled("k_compress", "fp64_inst_per_block") * nb / (comp_ms * 1e-3) / 1e9 / fp64_probe

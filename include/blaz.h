@@ -83,14 +83,17 @@ int blaz_device_status(void *stream);
  * the device status word (read and cleared by blaz_device_status) and
  * returns.  Every wait in the library's kernels is bounded the same way. */
 int blaz_probe_bounded_wait(int64_t max_cycles, void *stream);
-/* Measurement probe (no counterpart in the paper): one CTA of 512 threads
- * per SM runs `iters` rounds of 4 independent binary64 additions per thread
- * on `stream`, writing one double per thread to out (device, out_len >=
- * 512 x SM count, else BLAZ_ERR_ARG; 1 <= iters <= 2^30).  *ops (host) gets
- * the number of binary64 additions launched; their count over the launch's
- * duration is the device's binary64 issue ceiling, the peak of the kernels
- * bound by binary64 arithmetic. */
-int blaz_probe_fp64_rate(int64_t iters, double *out, int64_t out_len, int64_t *ops, void *stream);
+/* Measurement probe (no counterpart in the paper): one CTA of
+ * 32 x warps_per_sm threads per SM (1 <= warps_per_sm <= 32, else
+ * BLAZ_ERR_ARG) runs `iters` rounds of 4 independent binary64 additions per
+ * thread on `stream`, writing one double per thread to out (device, out_len
+ * >= 32 x warps_per_sm x SM count, else BLAZ_ERR_ARG; 1 <= iters <= 2^30).
+ * *ops (host) gets the number of binary64 additions launched; their count
+ * over the launch's duration is the device's binary64 issue rate at that
+ * many warps per SM, whose maximum is the peak of the kernels bound by
+ * binary64 arithmetic. */
+int blaz_probe_fp64_rate(int64_t iters, int warps_per_sm, double *out, int64_t out_len, int64_t *ops,
+                         void *stream);
 
 /* Library-owned storage for a compressed matrix (stream-ordered allocation
  * on `stream`).  rows, cols >= 0 and multiples of 8.  The arrays are not

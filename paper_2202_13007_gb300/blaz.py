@@ -111,7 +111,7 @@ SIGNATURES = {
     "blaz_matmul_cc_padded": (ctypes.c_int, [_DESC, _DESC, _I64, _I64, _I64, _P, _I64, ctypes.c_int, _P]),
     "blaz_compress_host": (ctypes.c_int, [_P, _I64, _DESC, _P]),
     "blaz_probe_bounded_wait": (ctypes.c_int, [_I64, _P]),
-    "blaz_probe_fp64_rate": (ctypes.c_int, [_I64, _P, _I64, _P, _P]),
+    "blaz_probe_fp64_rate": (ctypes.c_int, [_I64, ctypes.c_int, _P, _I64, _P, _P]),
     "blaz_cmat_download": (ctypes.c_int, [_DESC, _P, _P]),
     "blaz_cmat_upload": (ctypes.c_int, [_P, _DESC, _P]),
     "blaz_cmat_save": (ctypes.c_int, [_DESC, ctypes.c_char_p, _P]),
@@ -222,13 +222,13 @@ def device_status(stream=None) -> int:
     return lib().blaz_device_status(_stream(stream))
 
 
-def probe_fp64_rate(iters: int, out, stream=None) -> int:
+def probe_fp64_rate(iters: int, out, warps_per_sm: int = 16, stream=None) -> int:
     """Launch the binary64 issue-rate probe on `stream` (out: float64 device
-    tensor of at least 512 x SM count elements); returns the number of
-    binary64 additions launched (time the launch with CUDA events)."""
+    tensor of at least 32 x warps_per_sm x SM count elements); returns the
+    number of binary64 additions launched (time the launch with CUDA events)."""
     ops = ctypes.c_int64(0)
-    _check(lib().blaz_probe_fp64_rate(int(iters), out.data_ptr(), out.numel(), ctypes.byref(ops), _stream(stream)),
-           "blaz_probe_fp64_rate")
+    _check(lib().blaz_probe_fp64_rate(int(iters), int(warps_per_sm), out.data_ptr(), out.numel(), ctypes.byref(ops),
+                                      _stream(stream)), "blaz_probe_fp64_rate")
     return ops.value
 
 

@@ -5,10 +5,10 @@
 
 namespace blaz {
 
-constexpr int kProbeThreads = 512;  // 16 warps per SM
+constexpr int kProbeMaxWarps = 32;  // warps per SM (one CTA per SM)
 constexpr int kProbeChains = 4;     // independent dependency chains per thread
 
-__global__ void __launch_bounds__(kProbeThreads) k_probe_fp64(double *out, int64_t iters, double c)
+__global__ void __launch_bounds__(kProbeMaxWarps * 32) k_probe_fp64(double *out, int64_t iters, double c)
 {
     double x[kProbeChains];
 #pragma unroll
@@ -26,13 +26,15 @@ __global__ void __launch_bounds__(kProbeThreads) k_probe_fp64(double *out, int64
 
 using namespace blaz;
 
-extern "C" int blaz_probe_fp64_rate(int64_t iters, double *out, int64_t out_len, int64_t *ops, void *stream)
+extern "C" int blaz_probe_fp64_rate(int64_t iters, int warps_per_sm, double *out, int64_t out_len, int64_t *ops,
+                                    void *stream)
 {
     BLAZ_NVTX();
     if (!out || !ops) return BLAZ_ERR_NULL;
-    const int64_t threads = (int64_t)num_sms() * kProbeThreads;
-    if (iters < 1 || iters > (1ll << 30) || out_len < threads) return BLAZ_ERR_ARG;
-    k_probe_fp64<<<num_sms(), kProbeThreads, 0, (cudaStream_t)stream>>>(out, iters, 1.0);
+    if (warps_per_sm < 1 || warps_per_sm > kProbeMaxWarps || iters < 1 || iters > (1ll << 30)) return BLAZ_ERR_ARG;
+    const int64_t threads = (int64_t)num_sms() * warps_per_sm * 32;
+    if (out_len < threads) return BLAZ_ERR_ARG;
+    k_probe_fp64<<<num_sms(), warps_per_sm * 32, 0, (cudaStream_t)stream>>>(out, iters, 1.0);
     *ops = threads * iters * kProbeChains;
     return launch_status();
 }

@@ -91,3 +91,21 @@ def test_timeout_self_test_rejects_bad_limits_without_a_gpu(libblaz):
     device (BLAZ_ERR_ARG = -9)."""
     assert libblaz.blaz_probe_bounded_wait(-1, None) == -9
     assert libblaz.blaz_probe_bounded_wait(4000000001, None) == -9
+
+
+def test_fp64_probe_rejects_bad_arguments_without_a_gpu(libblaz):
+    """blaz_probe_fp64_rate checks its pointers (BLAZ_ERR_NULL = -2), its warp
+    count and its round count (BLAZ_ERR_ARG = -9) before anything reaches a
+    device."""
+    import ctypes
+
+    ops = ctypes.c_int64(0)
+    fake = ctypes.c_void_p(16)  # never dereferenced: the checks fail first
+    f = libblaz.blaz_probe_fp64_rate
+    f.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
+    assert f(1, 16, None, 1 << 20, ctypes.byref(ops), None) == -2
+    assert f(1, 16, fake, 1 << 20, None, None) == -2
+    assert f(1, 0, fake, 1 << 20, ctypes.byref(ops), None) == -9
+    assert f(1, 33, fake, 1 << 20, ctypes.byref(ops), None) == -9
+    assert f(0, 16, fake, 1 << 20, ctypes.byref(ops), None) == -9
+    assert f((1 << 30) + 1, 16, fake, 1 << 20, ctypes.byref(ops), None) == -9

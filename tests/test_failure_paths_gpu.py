@@ -81,3 +81,23 @@ def test_outputs_stay_inside_their_arrays(B):
     guards_intact()
     ref = O.scale(O.add(O.compress(A), O.compress(Bm)), -3.0)
     assert np.array_equal(out.code.cpu().numpy(), ref.code)
+
+
+def test_fp64_probe_counts_its_additions(B):
+    """The binary64 issue-rate probe launches 4 additions per thread and round
+    on one CTA of 32 w threads per SM, and its rate is a positive number."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    out = torch.empty(sms * 16 * 32, dtype=torch.float64, device="cuda")
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    ops = B.probe_fp64_rate(256, out, 16, st)
+    e1.record(st)
+    torch.cuda.synchronize()
+    assert ops == sms * 16 * 32 * 256 * 4
+    assert ops / (e0.elapsed_time(e1) * 1e-3) > 1e9
+    # each thread's 4 chains start at tid * 1e-3 + i and add 256 ones each
+    t = torch.arange(16 * 32, dtype=torch.float64, device="cuda") * 1e-3
+    assert torch.allclose(out[: 16 * 32], 4 * t + (0 + 1 + 2 + 3) + 4 * 256.0, rtol=1e-12, atol=0)
+    with pytest.raises(B.BlazError):
+        B.probe_fp64_rate(256, out[:10], 16, st)
