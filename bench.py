@@ -68,6 +68,7 @@ def step_bytes(side: int) -> int:
 
 KERNEL_SOURCES = {"k_compress": ["paper_2202_13007_gb300/csrc/k_codec.cu",
                                   "paper_2202_13007_gb300/csrc/compress_fast.cuh",
+                                  "paper_2202_13007_gb300/csrc/compress_fix.cuh",
                                   "paper_2202_13007_gb300/csrc/exact_div.cuh",
                                   "paper_2202_13007_gb300/csrc/block_codec.cuh",
                                   "paper_2202_13007_gb300/csrc/gmap.cuh",
