@@ -107,6 +107,31 @@ int blaz_cmat_free(blaz_cmat *m, void *stream);
  * (row, col) of kept code t.  Host pointers; no GPU needed. */
 void blaz_constants(double cos_out[64], double aa_out[64], int32_t kept_out[56]);
 
+/* Every stage of the compression of one 8x8 block, for inspection (Sec. II,
+ * Fig. 1 pipeline and Examples 1-5).  Field by field: */
+typedef struct blaz_block_stages {
+    double delta[64];      /* Eq. eqnorm, row-major                                  */
+    int32_t K;             /* Eq. eqslope2: number of nonzero entries of delta       */
+    double sum_abs;        /* sum |delta| (the fixed pairwise tree of the specification) */
+    double s;              /* Eq. eqslope: sum_abs / K (0 when K = 0)                */
+    double dprime[64];     /* delta * (1/s) (0 when K = 0)                            */
+    double s_max;          /* max |dprime| (prediction stage)                        */
+    uint8_t psi[64];       /* Eq. eqpredict: index of the nearest of 256 reference
+                              slopes s - s_max + k 2 s_max / 256, ties up; not stored
+                              in the compressed block                                */
+    double dct[64];        /* Eq. eqdct of dprime, all 64 coefficients               */
+    double m;              /* max |dct|                                              */
+    uint8_t phi;           /* Eq. eqphi                                              */
+    double f;              /* the block's first element                              */
+    int8_t code[BLAZ_NKEEP]; /* the 28 kept codes                                    */
+} blaz_block_stages;
+
+/* The stages above for one block, computed on the GPU on `stream` in the
+ * binary64 operation order of blaz_compress (so f, s, phi and code equal the
+ * compressed block's).  M: device, 64 binary64 values (row-major 8x8); out:
+ * device, one blaz_block_stages.  BLAZ_ERR_NULL for a NULL pointer. */
+int blaz_debug_block_stages(const double *M, blaz_block_stages *out, void *stream);
+
 /* Compression, Sec. II (Fig. 1 pipeline; Eqs. eqnorm, eqslope, eqdct, eqphi):
  * A: device, rows x cols binary64, row-major with leading dimension lda >= cols.
  * out: rows/cols set by the caller, arrays preallocated (device).

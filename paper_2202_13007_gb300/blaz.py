@@ -11,6 +11,7 @@ import ctypes
 import os
 from dataclasses import dataclass
 
+import numpy as np
 import torch
 
 from . import _build
@@ -112,6 +113,7 @@ SIGNATURES = {
     "blaz_compress_host": (ctypes.c_int, [_P, _I64, _DESC, _P]),
     "blaz_probe_bounded_wait": (ctypes.c_int, [_I64, _P]),
     "blaz_probe_fp64_rate": (ctypes.c_int, [_I64, ctypes.c_int, _P, _I64, _P, _P]),
+    "blaz_debug_block_stages": (ctypes.c_int, [_P, _P, _P]),
     "blaz_cmat_download": (ctypes.c_int, [_DESC, _P, _P]),
     "blaz_cmat_upload": (ctypes.c_int, [_P, _DESC, _P]),
     "blaz_cmat_save": (ctypes.c_int, [_DESC, ctypes.c_char_p, _P]),
@@ -220,6 +222,51 @@ def device_status(stream=None) -> int:
     """Synchronize `stream` and return (and clear) the device status word:
     0, or -7 (BLAZ_ERR_TIMEOUT) if a kernel's bounded wait ran out."""
     return lib().blaz_device_status(_stream(stream))
+
+
+class BlockStages(ctypes.Structure):
+    """blaz_block_stages of include/blaz.h: the stages of compressing one block."""
+
+    _fields_ = [
+        ("delta", ctypes.c_double * 64),
+        ("K", ctypes.c_int32),
+        ("sum_abs", ctypes.c_double),
+        ("s", ctypes.c_double),
+        ("dprime", ctypes.c_double * 64),
+        ("s_max", ctypes.c_double),
+        ("psi", ctypes.c_uint8 * 64),
+        ("dct", ctypes.c_double * 64),
+        ("m", ctypes.c_double),
+        ("phi", ctypes.c_uint8),
+        ("f", ctypes.c_double),
+        ("code", ctypes.c_int8 * NKEEP),
+    ]
+
+
+def debug_block_stages(M, stream=None) -> dict:
+    """Every stage of compressing one 8x8 block (M: 64 binary64 values on the
+    GPU, row-major), computed by the library's kernel; numpy arrays back."""
+    M = M.contiguous()
+    if M.dtype != torch.float64 or M.numel() != 64 or not M.is_cuda:
+        raise ValueError("M must be 64 float64 values on a CUDA device")
+    buf = torch.zeros(ctypes.sizeof(BlockStages), dtype=torch.uint8, device=M.device)
+    _check(lib().blaz_debug_block_stages(M.data_ptr(), buf.data_ptr(), _stream(stream)), "blaz_debug_block_stages")
+    host = buf.cpu().numpy()
+    st = BlockStages.from_buffer_copy(host.tobytes())
+    return {
+        "delta": np.array(st.delta).reshape(8, 8),
+        "K": int(st.K),
+        "sum_abs": float(st.sum_abs),
+        "s": float(st.s),
+        "dprime": np.array(st.dprime).reshape(8, 8),
+        "s_max": float(st.s_max),
+        "psi": np.array(st.psi, dtype=np.uint8).reshape(8, 8),
+        "dct": np.array(st.dct).reshape(8, 8),
+        "m": float(st.m),
+        "phi": int(st.phi),
+        "f": float(st.f),
+        "code": np.array(st.code, dtype=np.int8),
+    }
 
 
 def probe_fp64_rate(iters: int, out, warps_per_sm: int = 16, stream=None) -> int:

@@ -494,3 +494,37 @@ def test_precision_config_max_relative_error(B, mode, record_property):
     record_property("max_componentwise_error", worst_comp)
     record_property("max_relative_error", worst_rel)
     assert worst_comp <= tol
+
+
+# --- the stages of one block (Examples 1-5 of Sec. II) ------------------------------------------
+def _stage_blocks():
+    from conftest import load_golden
+
+    g = load_golden("example_xy.txt")
+    ex = np.array([[float(x) for x in row] for row in g["A"]])
+    rng = np.random.default_rng(77)
+    blocks = [ex, np.full((8, 8), 3.25), W.random_block_matrix(8, 8, 4), W.random_block_matrix(8, 8, 5, "noise"),
+              W.random_block_matrix(8, 8, 6, "wide"), np.cumsum(np.cumsum(rng.random((8, 8)), 0), 1)]
+    return blocks
+
+
+@pytest.mark.parametrize("k", range(6))
+def test_debug_block_stages_match_the_oracle(B, k):
+    """Every stage (delta, K, the slope sum, s, dprime, s_max, the prediction
+    indexes, all 64 DCT coefficients, m, phi, f, codes) bit for bit against
+    the oracle, on the paper's worked example, a constant block and random
+    smooth, rough and wide-range blocks."""
+    M = _stage_blocks()[k]
+    g = B.debug_block_stages(dev(M.reshape(64)))
+    o = O.block_stages(M)
+    for key in ("delta", "dprime", "dct"):
+        same_bits(g[key].reshape(-1), o[key].reshape(-1))
+    for key in ("sum_abs", "s", "s_max", "m", "f"):
+        same_bits([g[key]], [o[key]])
+    assert g["K"] == o["K"] and g["phi"] == o["phi"]
+    assert np.array_equal(g["psi"], o["psi"])
+    assert np.array_equal(g["code"], o["code"])
+    # the stored block equals the compressor's
+    c = B.compress(dev(M)).to_host()
+    assert c[2][0] == g["phi"] and np.array_equal(c[3][0], g["code"])
+    same_bits(c[1][:1], [g["s"]])
