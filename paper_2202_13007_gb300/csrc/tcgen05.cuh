@@ -1,7 +1,7 @@
 // tcgen05.cuh -- inline-PTX helpers for the 5th-generation tensor cores of
 // sm_103a shared by the tensor-core kernels of this library: mbarriers with
 // bounded waits, shared-memory matrix descriptors (K-major, 128-byte
-// swizzle), tcgen05.mma / commit, tensor-memory loads and the proxy fences.
+// swizzle), tcgen05.mma / commit and tensor-memory allocation and loads.
 #pragma once
 
 #include <cstdint>
@@ -78,10 +78,6 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr)
     return d;
 }
 
-// Byte offset of 16-byte chunk c (0..7) of row r in a K-major tile of
-// 128-byte rows stored with the 128-byte swizzle (tile 1024-byte aligned).
-__host__ __device__ constexpr uint32_t sw128_offset(uint32_t r, uint32_t c) { return r * 128u + ((c ^ (r & 7u)) << 4); }
-
 // Instruction descriptor of kind::f16 with an fp32 accumulator, both
 // operands K-major; a_bf16 / b_bf16 select bf16 (else fp16) inputs.
 __host__ __device__ constexpr uint32_t idesc_f16(int M, int N, bool a_bf16, bool b_bf16)
@@ -111,9 +107,6 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar)
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// Generic-proxy writes to shared memory made visible to the tensor cores.
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 __device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t cols)
 {
