@@ -32,8 +32,7 @@ constexpr int kDecSlices = 5;
 constexpr int kDecDigitBits = 9;
 struct DecConsts {
     uint2 bfrag[kDecSlices][2][8][32];  // B fragments [slice][k-step][n-tile][lane]
-    double scale;                       // 2^E of the last slice
-    double inv_phi[256];
+    double inv_phi_scaled[256];         // RN(1/phi) 2^E (2^E: weight of the last slice; exact scaling)
 };
 
 static const DecConsts &dec_consts()
@@ -69,9 +68,9 @@ static const DecConsts &dec_consts()
                         dc.bfrag[s][ks][nt][lane].x = h2(digit[s][n][k], digit[s][n][k + 1]);
                         dc.bfrag[s][ks][nt][lane].y = h2(digit[s][n][k + 8], digit[s][n][k + 9]);
                     }
-        dc.scale = (double)ldexpl(1.0L, E - kDecDigitBits * (kDecSlices - 1));
-        dc.inv_phi[0] = 0.0;
-        for (int p = 1; p < 256; ++p) dc.inv_phi[p] = 1.0 / (double)p;
+        const double scale = (double)ldexpl(1.0L, E - kDecDigitBits * (kDecSlices - 1));
+        dc.inv_phi_scaled[0] = 0.0;
+        for (int p = 1; p < 256; ++p) dc.inv_phi_scaled[p] = (1.0 / (double)p) * scale;
     });
     return dc;
 }
@@ -103,10 +102,10 @@ __global__ void __launch_bounds__(128)
                  double *__restrict__ A, int64_t lda, int64_t rows, int64_t cols, bool zero_fill)
 {
     __shared__ uint2 sb[kDecSlices][2][8][32];
-    __shared__ double inv_phi[256];  // indexed per lane: shared, not the parameter bank
+    __shared__ double inv_phi_scaled[256];  // indexed per lane: shared, not the parameter bank
     for (int i = threadIdx.x; i < kDecSlices * 2 * 8 * 32; i += blockDim.x)
         (&sb[0][0][0][0])[i] = (&dc.bfrag[0][0][0][0])[i];
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) inv_phi[i] = dc.inv_phi[i];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) inv_phi_scaled[i] = dc.inv_phi_scaled[i];
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     const int64_t ngroups = (nb + 15) / 16;
@@ -135,7 +134,7 @@ __global__ void __launch_bounds__(128)
             const bool v = h ? vB : vA;
             const int64_t bi = v ? b / nbc : 0, bj = v ? b - bi * nbc : 0;
             fb[h] = v ? __ldg(f + b) : 0.0;
-            ts[h] = v ? __ldg(s + b) * inv_phi[__ldg(phi + b)] * dc.scale : 0.0;
+            ts[h] = v ? __ldg(s + b) * inv_phi_scaled[__ldg(phi + b)] : 0.0;  // (s / phi) 2^E
             pb[h] = A + (bi * 8) * lda + bj * 8 + 2 * t;
             r0[h] = bi * 8;
             inside[h] = bi * 8 + 8 <= rows && bj * 8 + 8 <= cols;
@@ -203,7 +202,7 @@ int launch_decompress(const blaz_cmat *a, double *A, int64_t lda, cudaStream_t s
     if (rows < 0) rows = a->rows;
     if (cols < 0) cols = a->cols;
     const int threads = 128;
-    // One resident wave of CTAs (each first stages 16 KB of B fragments in
+    // One resident wave of CTAs (each first stages 20 KB of B fragments in
     // shared memory), striding over groups of 16 blocks.
     static const int occ = [] {
         int n = 0;
