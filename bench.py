@@ -132,6 +132,28 @@ def probe_fp64(dev, st):
     return max(rates.values()), rates
 
 
+def max_over_ranks(ms: float, dist, device) -> float:
+    """The slowest rank's elapsed time: the job's time when every rank runs
+    its own replica of the step (weak scaling)."""
+    if dist is None:
+        return ms
+    import torch
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, side: int, steps: int, ms: float) -> float:
+    """Whole-job GB/s of algorithmic bytes: every rank's steps over the job's time."""
+    return world * step_bytes(side) * steps / (ms * 1e-3) / 1e9
+
+
+def replica_seeds(side: int, rank: int):
+    """Seeds of fields A and B on a rank: each replica draws its own pair."""
+    return side + 2 * rank, side + 1 + 2 * rank
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -699,8 +721,9 @@ def main():
     n = args.side
     dev = torch.device("cuda", local)
     st = torch.cuda.current_stream()
-    ta = W.bump_field_torch(n, n + 2 * rank, dev)
-    tb = W.bump_field_torch(n, n + 1 + 2 * rank, dev)
+    seed_a, seed_b = replica_seeds(n, rank)
+    ta = W.bump_field_torch(n, seed_a, dev)
+    tb = W.bump_field_torch(n, seed_b, dev)
     ca, cb, cs, cc = (B.CMat.empty(n, n, dev) for _ in range(4))
     dec = torch.empty((n, n), dtype=torch.float64, device=dev)
     res = torch.empty(2, dtype=torch.float64, device=dev)
@@ -740,14 +763,11 @@ def main():
             step(record=True)
         t1.record(st)
         torch.cuda.synchronize()
-    ms = t0.elapsed_time(t1)
+    ms = max_over_ranks(t0.elapsed_time(t1), dist, dev)
     if dist:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
         dist.barrier()
     ms_step = ms / args.steps
-    value = world * step_bytes(n) * args.steps / (ms * 1e-3) / 1e9
+    value = job_throughput(world, n, args.steps, ms)
 
     comp_ms = statistics.mean(a.elapsed_time(b) for a, b in ev_pairs)
     nb = (n // 8) ** 2
@@ -792,11 +812,7 @@ def main():
             e2e_step()
         e1.record(st)
         torch.cuda.synchronize()
-        ems = e0.elapsed_time(e1)
-        if dist:
-            tt = torch.tensor([ems], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ems = float(tt.item())
+        ems = max_over_ranks(e0.elapsed_time(e1), dist, dev)
         # the link floor: the same host-to-device bytes as plain page-locked copies
         floor = []
         for _ in range(3):
@@ -809,7 +825,7 @@ def main():
             floor.append(f0.elapsed_time(f1))
         h2d = 2 * n * n * 8
         d2h = cs.nbytes + 16
-        e2e = {"value": world * step_bytes(n) * args.steps / (ems * 1e-3) / 1e9, "unit": "GB/s",
+        e2e = {"value": job_throughput(world, n, args.steps, ems), "unit": "GB/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ems / args.steps,
                "h2d_copy_ms_per_step": min(floor)}
 
