@@ -290,33 +290,34 @@ __global__ void __launch_bounds__(kAddTile + 32, 3)
                 // 1.125 2^-19 (|beta_1 c_1| + |beta_2 c_2|) + 2^-100; 1.25 covers the fp32
                 // roundings of E = e_1 |c_1| + e_2 |c_2| + 2^-100 with e_k = 1.25 2^-19 |beta_k|
                 const float e1 = 0x1.4p-19f * fabsf(b1f), e2 = 0x1.4p-19f * fabsf(b2f);
+                // two codes at a time on the paired fp32 pipe (same per-lane roundings)
+                const float2 B1 = make_float2(b1f, b1f), B2 = make_float2(kSub ? -b2f : b2f, kSub ? -b2f : b2f);
+                const float2 E1 = make_float2(e1, e1), E2 = make_float2(e2, e2);
+                const float2 bias = make_float2(-12583040.0f, -12583040.0f), tiny = make_float2(0x1p-100f, 0x1p-100f);
+                const float2 neg1 = make_float2(-1.0f, -1.0f);
 #pragma unroll
                 for (int q = 0; q < 7; ++q) {
                     // byte k of (w ^ 0x80808080) in the low byte of 1.5 2^23: the float 12583040 + c
                     const uint32_t wa = sa_w[t * 7 + q] ^ 0x80808080u, wb = sb_w[t * 7 + q] ^ 0x80808080u;
                     uint32_t v32 = 0;
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const float x1 = __uint_as_float(__byte_perm(wa, 0x4B400000u, 0x7640 + k)) - 12583040.0f;
-                        const float x2 = __uint_as_float(__byte_perm(wb, 0x4B400000u, 0x7640 + k)) - 12583040.0f;
-                        const float v = fmaf(b1f, x1, kSub ? -(b2f * x2) : b2f * x2);
-                        const float E = fmaf(e1, fabsf(x1), fmaf(e2, fabsf(x2), 0x1p-100f));
-                        const float lo = v - E, hi = v + E;
-                        int code;
-                        bool done;
-                        if (lo >= 127.0f) {
-                            code = 127;
-                            done = true;
-                        } else if (hi <= -127.0f) {
-                            code = -127;
-                            done = true;
-                        } else {
-                            const int tl = (int)truncf(lo), th = (int)truncf(hi);
-                            code = tl;
-                            done = tl == th;
-                        }
-                        if (!done) undecided |= 1u << (4 * q + k);
-                        v32 |= (uint32_t)(uint8_t)(int8_t)code << (8 * k);
+                    for (int k = 0; k < 4; k += 2) {
+                        const float2 x1 = __fadd2_rn(make_float2(__uint_as_float(__byte_perm(wa, 0x4B400000u, 0x7640 + k)),
+                                                                 __uint_as_float(__byte_perm(wa, 0x4B400000u, 0x7641 + k))),
+                                                     bias);
+                        const float2 x2 = __fadd2_rn(make_float2(__uint_as_float(__byte_perm(wb, 0x4B400000u, 0x7640 + k)),
+                                                                 __uint_as_float(__byte_perm(wb, 0x4B400000u, 0x7641 + k))),
+                                                     bias);
+                        const float2 v = __ffma2_rn(B1, x1, __fmul2_rn(B2, x2));
+                        const float2 E = __ffma2_rn(E1, make_float2(fabsf(x1.x), fabsf(x1.y)),
+                                                    __ffma2_rn(E2, make_float2(fabsf(x2.x), fabsf(x2.y)), tiny));
+                        const float2 hi = __fadd2_rn(v, E), lo = __ffma2_rn(E, neg1, v);
+                        // trunc of both ends, saturated to +-127: one code when they agree
+                        const int l0 = min(127, max(-127, (int)truncf(lo.x))), h0 = min(127, max(-127, (int)truncf(hi.x)));
+                        const int l1 = min(127, max(-127, (int)truncf(lo.y))), h1 = min(127, max(-127, (int)truncf(hi.y)));
+                        undecided |= (uint32_t)(l0 != h0) << (4 * q + k);
+                        undecided |= (uint32_t)(l1 != h1) << (4 * q + k + 1);
+                        v32 |= ((uint32_t)(uint8_t)(int8_t)l0 << (8 * k)) | ((uint32_t)(uint8_t)(int8_t)l1 << (8 * k + 8));
                     }
                     so_w[t * 7 + q] = v32;
                 }

@@ -69,6 +69,14 @@ def kernel_codes(a, b, pert1, pert2, sub=False):
         tl, th = np.trunc(lo), np.trunc(hi)
     code = np.where(lo >= 127, 127, np.where(hi <= -127, -127, tl))
     decided = (lo >= 127) | (hi <= -127) | (tl == th)
+    # the same decisions as trunc of both ends saturated to +-127 (the
+    # kernels' branch-free form): decided when the two agree, code = that value
+    with np.errstate(invalid="ignore"):
+        cl = np.clip(np.nan_to_num(tl, nan=0.0), -127, 127)
+        ch = np.clip(np.nan_to_num(th, nan=0.0), -127, 127)
+    finite = np.isfinite(lo) & np.isfinite(hi)
+    assert np.array_equal((cl == ch)[finite], decided[finite])
+    assert np.array_equal(np.where(cl == ch, cl, 0)[finite], np.where(decided, code, 0)[finite])
     decided &= (ok1 & ok2)[:, None]
     zero_s = (ss == 0.0)[:, None]
     code = np.where(zero_s, 0, code)
