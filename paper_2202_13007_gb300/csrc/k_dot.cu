@@ -169,7 +169,13 @@ __device__ __forceinline__ void gram_group(const uint2 (*sbf)[2][4][32], const f
     }
 #pragma unroll
     for (int sl = 0; sl < kSlices; ++sl) {
-        float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f, w0 = 0.f, w1 = 0.f, wa0 = 0.f, wa1 = 0.f;
+        // rows gq and gq + 8 side by side on the paired fp32 instructions
+        // (the same per-lane roundings as scalar fmas; every value is an
+        // exact integer)
+        float2 H = make_float2(0.f, 0.f), L = H, WA = H;
+        float w0 = 0.f, w1 = 0.f;
+        const float2 inv4096 = make_float2(1.0f / 4096.0f, 1.0f / 4096.0f), m4096 = make_float2(-4096.0f, -4096.0f);
+        const float2 rnd = make_float2(12582912.0f, 12582912.0f), nrnd = make_float2(-12582912.0f, -12582912.0f);
 #pragma unroll
         for (int nt = 0; nt < 4; ++nt) {
             float c[4] = {0.f, 0.f, 0.f, 0.f};
@@ -179,21 +185,20 @@ __device__ __forceinline__ void gram_group(const uint2 (*sbf)[2][4][32], const f
             for (int q = 0; q < 2; ++q) {
                 const int k = nt * 8 + 2 * t + q;
                 if (k < kKeep) {
-                    const float y0 = c[q], y1 = c[2 + q];
-                    const float yh0 = rint_div4096(y0), yh1 = rint_div4096(y1);
-                    h0 = fmaf(xa[0][2 * nt + q], yh0, h0);
-                    l0 = fmaf(xa[0][2 * nt + q], fmaf(-4096.0f, yh0, y0), l0);
-                    h1 = fmaf(xa[1][2 * nt + q], yh1, h1);
-                    l1 = fmaf(xa[1][2 * nt + q], fmaf(-4096.0f, yh1, y1), l1);
+                    const float2 y = make_float2(c[q], c[2 + q]);
+                    const float2 yh = __fadd2_rn(__ffma2_rn(y, inv4096, rnd), nrnd);  // rint(y / 4096)
+                    const float2 x = make_float2(xa[0][2 * nt + q], xa[1][2 * nt + q]);
+                    H = __ffma2_rn(x, yh, H);
+                    L = __ffma2_rn(x, __ffma2_rn(m4096, yh, y), L);
                     const float wd = swl[sl][lane][2 * nt + q];
-                    wa0 = fmaf(xa[0][2 * nt + q], wd, wa0);
-                    wa1 = fmaf(xa[1][2 * nt + q], wd, wa1);
+                    WA = __ffma2_rn(x, make_float2(wd, wd), WA);
                 } else if (k == kKeep) {  // column 28: w_s . cb
                     w0 = c[q];
                     w1 = c[2 + q];
                 }
             }
         }
+        float h0 = H.x, h1 = H.y, l0 = L.x, l1 = L.y, wa0 = WA.x, wa1 = WA.y;
         // reduce over the four lanes of the row (exact integer sums)
 #pragma unroll
         for (int o = 1; o < 4; o <<= 1) {
