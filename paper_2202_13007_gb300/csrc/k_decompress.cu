@@ -151,8 +151,13 @@ __global__ void __launch_bounds__(128)
                 float c[4] = {0.f, 0.f, 0.f, 0.f};
                 mma_f16(c, a0, sb[sl][0][nt][lane]);
                 mma_f16(c, a1, sb[sl][1][nt][lane]);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) y[sl][q] = f2i_small(c[q]);
+                // c + 1.5 2^23 holds the integer c in its low bits (|c| < 2^22), two at a time
+                const float2 r01 = __fadd2_rn(make_float2(c[0], c[1]), make_float2(12582912.0f, 12582912.0f));
+                const float2 r23 = __fadd2_rn(make_float2(c[2], c[3]), make_float2(12582912.0f, 12582912.0f));
+                y[sl][0] = __float_as_int(r01.x) - 0x4B400000;
+                y[sl][1] = __float_as_int(r01.y) - 0x4B400000;
+                y[sl][2] = __float_as_int(r23.x) - 0x4B400000;
+                y[sl][3] = __float_as_int(r23.y) - 0x4B400000;
             }
             long long acc[4];
 #pragma unroll
