@@ -18,7 +18,8 @@
  *   compress (Sec. II, Eqs. eqnorm, eqslope, eqphi):
  *     f = M00
  *     D(i,j) per Eq. eqnorm; the interior case is ((Mij-Mi-1j)+(Mij-Mij-1))*0.5
- *     K = #{D != 0}; S = sum |D| in row-major order, left to right;
+ *     K = #{D != 0}; S = sum |D| as a fixed pairwise tree over the row-major
+ *     index (|D_k| + |D_k+32| for k < 32, then strides 16, 8, 4, 2, 1);
  *     s = S / K (s = 0 when K = 0: constant block)
  *     r = 1 / s ; D'(i,j) = D(i,j) * r           (D' = (1/s) D literally)
  *     DCT-II, Eq. eqdct with alpha_i alpha_j outside the double sum:
@@ -292,9 +293,9 @@ void blazo_decompress_block(double f, double s, uint8_t phi, const int8_t *code,
  * algorithm subtracts (Sec. III: subtraction works like addition): the first
  * elements are subtracted, the slopes still add (s = s1 + s2 keeps the
  * combined block's scale positive) and the rescaled codes are subtracted. */
-static void addsub_block(int sub, double f1, double s1, uint8_t phi1, const int8_t *c1,
-                         double f2, double s2, uint8_t phi2, const int8_t *c2,
-                         double *f, double *s, uint8_t *phi, int8_t *c)
+static void addsub_block_n(int sub, int ncodes, double f1, double s1, uint8_t phi1, const int8_t *c1,
+                           double f2, double s2, uint8_t phi2, const int8_t *c2,
+                           double *f, double *s, uint8_t *phi, int8_t *c)
 {
     double fs = sub ? f1 - f2 : f1 + f2;
     double ss = s1 + s2;
@@ -305,16 +306,23 @@ static void addsub_block(int sub, double f1, double s1, uint8_t phi1, const int8
     *s = ss;
     *phi = (uint8_t)ph;
     if (ss == 0.0) {
-        memset(c, 0, NKEEP);
+        memset(c, 0, (size_t)ncodes);
         return;
     }
     double a1 = s1 / ss;
     double a2 = s2 / ss;
     double b1 = (a1 / (double)p1) * (double)ph;
     double b2 = (a2 / (double)p2) * (double)ph;
-    for (int t = 0; t < NKEEP; ++t)
+    for (int t = 0; t < ncodes; ++t)
         c[t] = quantize_code(sub ? b1 * (double)c1[t] - b2 * (double)c2[t]
                                  : b1 * (double)c1[t] + b2 * (double)c2[t]);
+}
+
+static void addsub_block(int sub, double f1, double s1, uint8_t phi1, const int8_t *c1,
+                         double f2, double s2, uint8_t phi2, const int8_t *c2,
+                         double *f, double *s, uint8_t *phi, int8_t *c)
+{
+    addsub_block_n(sub, NKEEP, f1, s1, phi1, c1, f2, s2, phi2, c2, f, s, phi, c);
 }
 
 void blazo_add_block(double f1, double s1, uint8_t phi1, const int8_t *c1,
@@ -575,5 +583,132 @@ int blazo_matmul(const double *fa, const double *sa, const uint8_t *pa, const in
             C[i * ldc + j] = r.sum + r.comp;
         }
     free(Ah);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Tunable rate.  Sec. VI names a tunable compression rate as future work     */
+/* ("by skewing the quantization"); the reading taken here keeps the first r  */
+/* rows and the first r columns of the DCT, r = 1..8 (r = 2 is Sec. II's      */
+/* format): keep(r) = 8 r + (8 - r) r codes per block, in the order rows      */
+/* 0..r-1 (j = 0..7), then (i, 0..r-1) for i = r..7.  Every other stage is    */
+/* unchanged: f, s and phi (from the maximum over all 64 coefficients, so it  */
+/* does not depend on r), the truncation of X phi, Algorithms 1 and 2.        */
+/* ------------------------------------------------------------------------ */
+static int keep_count(int r) { return 8 * r + (8 - r) * r; }
+
+static void kept_pos_rate(int r, int t, int *i, int *j)
+{
+    if (t < 8 * r) { *i = t / 8; *j = t % 8; }
+    else { int q = t - 8 * r; *i = r + q / r; *j = q % r; }
+}
+
+int blazo_keep_count(int r) { return (r >= 1 && r <= 8) ? keep_count(r) : -1; }
+
+void blazo_compress_block_rate(const double *M, int r, double *f, double *s, uint8_t *phi, int8_t *code)
+{
+    blazo_stages st;
+    blazo_block_stages(M, &st);
+    *f = st.f;
+    *s = st.s;
+    *phi = st.phi;
+    double phid = (double)st.phi;
+    for (int t = 0; t < keep_count(r); ++t) {
+        int i, j;
+        kept_pos_rate(r, t, &i, &j);
+        code[t] = quantize_code(st.dct[i * BLK + j] * phid);
+    }
+}
+
+/* The same definition as blazo_decompress_block with the rate's kept set. */
+void blazo_decompress_block_rate(double f, double s, uint8_t phi, const int8_t *code, int r, double *M)
+{
+    cm_init();
+    double X[BLK][BLK];
+    memset(X, 0, sizeof(X));
+    for (int t = 0; t < keep_count(r); ++t) {
+        int i, j;
+        kept_pos_rate(r, t, &i, &j);
+        X[i][j] = (double)code[t] / (double)phi;
+    }
+    double Y[BLK][BLK];
+    for (int i = 0; i < BLK; ++i)
+        for (int j = 0; j < BLK; ++j) Y[i][j] = AA[i][j] * X[i][j];
+    double Q[BLK][BLK];
+    for (int i = 0; i < BLK; ++i)
+        for (int v = 0; v < BLK; ++v) {
+            double acc = Y[i][0] * COS[0][v];
+            for (int j = 1; j < BLK; ++j) acc = acc + Y[i][j] * COS[j][v];
+            Q[i][v] = acc;
+        }
+    double P[BLK][BLK];
+    for (int u = 0; u < BLK; ++u)
+        for (int v = 0; v < BLK; ++v) {
+            double acc = COS[0][u] * Q[0][v];
+            for (int i = 1; i < BLK; ++i) acc = acc + COS[i][u] * Q[i][v];
+            P[u][v] = acc;
+        }
+    for (int i = 0; i < BLK; ++i)
+        for (int j = 0; j < BLK; ++j) {
+            double dh = s * P[i][j];
+            double v;
+            if (i == 0 && j == 0) v = f;
+            else if (i == 0) v = M[j - 1] + dh;
+            else if (j == 0) v = M[(i - 1) * BLK] + dh;
+            else v = (M[(i - 1) * BLK + j] + M[i * BLK + j - 1]) * 0.5 + dh;
+            M[i * BLK + j] = v;
+        }
+}
+
+int blazo_compress_rate(const double *A, int64_t rows, int64_t cols, int64_t lda, int r,
+                        double *f, double *s, uint8_t *phi, int8_t *code)
+{
+    int e = check_shape(rows, cols);
+    if (e) return e;
+    if (lda < cols) return ORC_ERR_LD;
+    if (r < 1 || r > 8) return ORC_ERR_RANGE;
+    int64_t nbc = cols / BLK, nk = keep_count(r);
+    double M[64];
+    for (int64_t bi = 0; bi < rows / BLK; ++bi)
+        for (int64_t bj = 0; bj < nbc; ++bj) {
+            for (int i = 0; i < BLK; ++i)
+                for (int j = 0; j < BLK; ++j)
+                    M[i * BLK + j] = A[(bi * BLK + i) * lda + bj * BLK + j];
+            int64_t b = bi * nbc + bj;
+            blazo_compress_block_rate(M, r, &f[b], &s[b], &phi[b], &code[b * nk]);
+        }
+    return ORC_OK;
+}
+
+int blazo_decompress_rate(const double *f, const double *s, const uint8_t *phi, const int8_t *code, int r,
+                          int64_t rows, int64_t cols, double *A, int64_t lda)
+{
+    int e = check_shape(rows, cols);
+    if (e) return e;
+    if (lda < cols) return ORC_ERR_LD;
+    if (r < 1 || r > 8) return ORC_ERR_RANGE;
+    int64_t nbc = cols / BLK, nk = keep_count(r);
+    double M[64];
+    for (int64_t bi = 0; bi < rows / BLK; ++bi)
+        for (int64_t bj = 0; bj < nbc; ++bj) {
+            int64_t b = bi * nbc + bj;
+            blazo_decompress_block_rate(f[b], s[b], phi[b], &code[b * nk], r, M);
+            for (int i = 0; i < BLK; ++i)
+                for (int j = 0; j < BLK; ++j)
+                    A[(bi * BLK + i) * lda + bj * BLK + j] = M[i * BLK + j];
+        }
+    return ORC_OK;
+}
+
+int blazo_add_rate(int64_t nb, int r, int sub,
+                   const double *f1, const double *s1, const uint8_t *phi1, const int8_t *c1,
+                   const double *f2, const double *s2, const uint8_t *phi2, const int8_t *c2,
+                   double *f, double *s, uint8_t *phi, int8_t *c)
+{
+    if (r < 1 || r > 8) return ORC_ERR_RANGE;
+    int nk = keep_count(r);
+    for (int64_t b = 0; b < nb; ++b)
+        addsub_block_n(sub, nk, f1[b], s1[b], phi1[b], &c1[b * nk], f2[b], s2[b], phi2[b], &c2[b * nk],
+                       &f[b], &s[b], &phi[b], &c[b * nk]);
     return ORC_OK;
 }

@@ -95,6 +95,12 @@ def _declare(L):
     for name in ("blazo_dct_tables", "blazo_kept_positions", "blazo_block_stages", "blazo_compress_block",
                  "blazo_decompress_block"):
         getattr(L, name).restype = None
+    L.blazo_keep_count.argtypes = [ctypes.c_int]
+    L.blazo_keep_count.restype = ctypes.c_int
+    L.blazo_compress_rate.argtypes = [_D, _i64, _i64, _i64, ctypes.c_int, _D, _D, _U8, _I8]
+    L.blazo_decompress_rate.argtypes = [_D, _D, _U8, _I8, ctypes.c_int, _i64, _i64, _D, _i64]
+    L.blazo_add_rate.argtypes = [_i64, ctypes.c_int, ctypes.c_int, _D, _D, _U8, _I8, _D, _D, _U8, _I8,
+                                 _D, _D, _U8, _I8]
 
 
 def _p(a, t):
@@ -328,3 +334,49 @@ def matmul_padded(a: CMat, B, n: int, k: int):
 
 def matmul_cc_padded(a: CMat, b: CMat, n: int, k: int, m: int):
     return decompress_padded(a, n, k) @ decompress_padded(b, k, m)
+
+
+# --- tunable rate: the first r rows and r columns of the DCT kept -----------------
+def keep_count(r: int) -> int:
+    """Codes per block at rate r (8 r + (8 - r) r; 28 for r = 2)."""
+    n = lib().blazo_keep_count(int(r))
+    if n < 0:
+        raise ValueError("r must be 1..8")
+    return n
+
+
+def empty_rate(rows: int, cols: int, r: int) -> CMat:
+    nb = (rows // 8) * (cols // 8)
+    return CMat(rows, cols, np.zeros(nb), np.zeros(nb), np.zeros(nb, np.uint8),
+                np.zeros((nb, keep_count(r)), np.int8))
+
+
+def compress_rate(A, r: int) -> CMat:
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    rows, cols = A.shape
+    out = empty_rate(rows, cols, r)
+    _chk(lib().blazo_compress_rate(_p(A, _D), rows, cols, cols, int(r), _p(out.f, _D), _p(out.s, _D),
+                                   _p(out.phi, _U8), _p(out.code, _I8)), "compress_rate")
+    return out
+
+
+def decompress_rate(c: CMat, r: int):
+    out = np.zeros((c.rows, c.cols))
+    _chk(lib().blazo_decompress_rate(_p(c.f, _D), _p(c.s, _D), _p(c.phi, _U8), _p(c.code, _I8), int(r),
+                                     c.rows, c.cols, _p(out, _D), c.cols), "decompress_rate")
+    return out
+
+
+def add_rate(a: CMat, b: CMat, r: int, sub: bool = False) -> CMat:
+    """Algorithm 1 (sub: the subtraction) on rate-r blocks."""
+    assert (a.rows, a.cols) == (b.rows, b.cols)
+    out = empty_rate(a.rows, a.cols, r)
+    _chk(lib().blazo_add_rate(a.nb, int(r), int(bool(sub)), _p(a.f, _D), _p(a.s, _D), _p(a.phi, _U8),
+                              _p(a.code, _I8), _p(b.f, _D), _p(b.s, _D), _p(b.phi, _U8), _p(b.code, _I8),
+                              _p(out.f, _D), _p(out.s, _D), _p(out.phi, _U8), _p(out.code, _I8)), "add_rate")
+    return out
+
+
+def scale_rate(a: CMat, c: float) -> CMat:
+    """Algorithm 2 on rate-r blocks: f and s times c, phi and the codes kept."""
+    return CMat(a.rows, a.cols, a.f * float(c), a.s * float(c), a.phi.copy(), a.code.copy())
