@@ -468,6 +468,47 @@ def shape_and_file_extras(B, W, torch, dev):
     return out
 
 
+def rate_extras(B, W, torch, dev):
+    """Tunable rate (the first r DCT rows and columns kept): compress,
+    decompress and add of a 4096 x 4096 bump field at r = 1, 2, 4, 8, with the
+    compression ratio 512 / (17 + keep(r)) and the relative 2-norm error of the
+    round trip.  r = 2 is also timed on the 28-code kernels for comparison."""
+
+    def timed(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    n = 4096
+    ta = W.bump_field_torch(n, n, dev)
+    tb = W.bump_field_torch(n, n + 1, dev)
+    back = torch.empty_like(ta)
+    out = {}
+    for r in (1, 2, 4, 8):
+        ga, gb = B.compress_rate(ta, r), B.compress_rate(tb, r)
+        gs = B.CMat.empty(n, n, dev, rate=r)
+        B.decompress_rate(ga, out=back)
+        err = float(torch.linalg.vector_norm(back - ta) / torch.linalg.vector_norm(ta))
+        out[f"r{r}"] = {"keep": B.keep_count(r), "ratio": 512.0 / (17 + B.keep_count(r)), "rel_err": err,
+                        "compress_ms": timed(lambda: B.compress_rate(ta, r, out=ga)),
+                        "decompress_ms": timed(lambda: B.decompress_rate(ga, out=back)),
+                        "add_ms": timed(lambda: B.add_rate(ga, gb, out=gs))}
+        del ga, gb, gs
+    g2, h2 = B.compress(ta), B.compress(tb)
+    s2 = B.CMat.empty(n, n, dev)
+    out["r2_28code_kernels"] = {"compress_ms": timed(lambda: B.compress(ta, out=g2)),
+                                "decompress_ms": timed(lambda: B.decompress(g2, out=back)),
+                                "add_ms": timed(lambda: B.add(g2, h2, out=s2))}
+    out["config"] = "4096x4096 bump fields (CUDA events, 5 reps after one warm-up); rate kernels: binary64, one thread per block"
+    return out
+
+
 def run_serve(args, B, W, torch, dev, seconds, max_batch, streams, mode="fp64", seed=13, rate=5000.0):
     """Poisson stream (5k req/s, sides log-uniform over multiples of 8 in
     [64, 4096], op mix 40/30/15/10/5 %) against a server with a 40 GB budget.
@@ -834,7 +875,7 @@ def main():
         del dec
         torch.cuda.empty_cache()
         extras = {"matmul": matmul_extras(B, W, torch, dev), "shapes_files": shape_and_file_extras(B, W, torch, dev),
-                  "plain_way": plain_way(B, torch, ca, cb, dev)}
+                  "plain_way": plain_way(B, torch, ca, cb, dev), "rates": rate_extras(B, W, torch, dev)}
         srv = run_serve(args, B, W, torch, dev, 1.0, max_batch=0, streams=4, mode="split_bf16")
         extras["serve"] = {k: srv[k] for k in ("p50_ms", "p99_ms", "throughput_rps", "offered_rps", "mean_batch")}
         extras["serve"]["config"] = "1 s of the served Poisson stream (5k req/s); full line: --workload serve"
@@ -872,6 +913,7 @@ def main():
             "serve": extras["serve"] if extras else None,
             "shapes_files": extras["shapes_files"] if extras else None,
             "plain_way": extras["plain_way"] if extras else None,
+            "rates": extras["rates"] if extras else None,
             "cpu_parallel": cpu_par,
         }
         print(json.dumps(line), flush=True)

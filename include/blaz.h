@@ -170,6 +170,39 @@ int blaz_sub(const blaz_cmat *a, const blaz_cmat *b, blaz_cmat *out, void *strea
  * copied.  out may equal a (in place: only f and s are rewritten). */
 int blaz_scale(const blaz_cmat *a, double c, blaz_cmat *out, void *stream);
 
+/* ---- Tunable rate ------------------------------------------------------------
+ * Sec. VI names a tunable compression rate as future work (more or less
+ * compression "by skewing the quantization").  These entry points keep the
+ * first r rows and the first r columns of each block's DCT, r = 1..8:
+ * keep(r) = 8r + (8-r)r codes per block (15, 28, 39, 48, 55, 60, 63, 64),
+ * in the order rows 0..r-1 (columns 0..7), then (i, 0..r-1) for i = r..7.
+ * r = 2 is the 28-code format of the functions above.  Everything else is
+ * unchanged: f, s and phi (from the maximum over all 64 coefficients, so phi
+ * does not depend on r), the truncated codes, Algorithms 1 and 2.  A block
+ * takes 17 + keep(r) bytes: compression ratio 512 / (17 + keep(r)).
+ *
+ * A rate-r matrix uses the blaz_cmat descriptor with code holding
+ * nb x keep(r) bytes (row-major [nb][keep(r)]); the rate is not stored in the
+ * descriptor and every call names it.  r outside 1..8: BLAZ_ERR_ARG.  The
+ * kernels are plain binary64, one thread per block (compress, add, sub and
+ * scale bit-exact with the same binary64 operation order as above). */
+
+/* keep(r), or -1 when r is outside 1..8.  No GPU needed. */
+int blaz_keep_count(int r);
+/* blaz_cmat_alloc with nb x keep(r) code bytes. */
+int blaz_cmat_alloc_rate(blaz_cmat *m, int64_t rows, int64_t cols, int r, void *stream);
+/* Compression at rate r (A: device, lda >= cols). */
+int blaz_compress_rate(const double *A, int64_t lda, int r, blaz_cmat *out, void *stream);
+/* Decompression at rate r: the definition of blaz_decompress with the rate's
+ * kept positions.  A: device, lda >= cols.  Within 1e-12 of the block scale of
+ * the exact result. */
+int blaz_decompress_rate(const blaz_cmat *a, int r, double *A, int64_t lda, void *stream);
+/* Algorithm 1 / its subtraction / Algorithm 2 on rate-r matrices; operands of
+ * the same shape and rate; out may alias a or b. */
+int blaz_add_rate(const blaz_cmat *a, const blaz_cmat *b, int r, blaz_cmat *out, void *stream);
+int blaz_sub_rate(const blaz_cmat *a, const blaz_cmat *b, int r, blaz_cmat *out, void *stream);
+int blaz_scale_rate(const blaz_cmat *a, double c, int r, blaz_cmat *out, void *stream);
+
 /* Flattened dot product <vec A_hat, vec B_hat> = sum_ij A_hat_ij B_hat_ij of
  * two compressed matrices of the same shape (A_hat, B_hat the decompressed
  * matrices).  result: device, one binary64, written in stream order.

@@ -19,7 +19,7 @@ LIB = os.path.join(BUILD, "libblaz.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
           "--expt-relaxed-constexpr", "-ftz=false", "-prec-div=true", "-prec-sqrt=true"]
-EXACT_TUS = {"k_codec.cu", "k_decompress.cu", "k_blockops.cu", "k_stages.cu"}
+EXACT_TUS = {"k_codec.cu", "k_decompress.cu", "k_blockops.cu", "k_stages.cu", "k_rate.cu"}
 
 
 def nvcc() -> str:

@@ -114,6 +114,13 @@ SIGNATURES = {
     "blaz_probe_bounded_wait": (ctypes.c_int, [_I64, _P]),
     "blaz_probe_fp64_rate": (ctypes.c_int, [_I64, ctypes.c_int, _P, _I64, _P, _P]),
     "blaz_debug_block_stages": (ctypes.c_int, [_P, _P, _P]),
+    "blaz_keep_count": (ctypes.c_int, [ctypes.c_int]),
+    "blaz_cmat_alloc_rate": (ctypes.c_int, [_DESC, _I64, _I64, ctypes.c_int, _P]),
+    "blaz_compress_rate": (ctypes.c_int, [_P, _I64, ctypes.c_int, _DESC, _P]),
+    "blaz_decompress_rate": (ctypes.c_int, [_DESC, ctypes.c_int, _P, _I64, _P]),
+    "blaz_add_rate": (ctypes.c_int, [_DESC, _DESC, ctypes.c_int, _DESC, _P]),
+    "blaz_sub_rate": (ctypes.c_int, [_DESC, _DESC, ctypes.c_int, _DESC, _P]),
+    "blaz_scale_rate": (ctypes.c_int, [_DESC, ctypes.c_double, ctypes.c_int, _DESC, _P]),
     "blaz_cmat_download": (ctypes.c_int, [_DESC, _P, _P]),
     "blaz_cmat_upload": (ctypes.c_int, [_P, _DESC, _P]),
     "blaz_cmat_save": (ctypes.c_int, [_DESC, ctypes.c_char_p, _P]),
@@ -188,8 +195,9 @@ class CMat:
     f: torch.Tensor      # float64 [nb]
     s: torch.Tensor      # float64 [nb]
     phi: torch.Tensor    # uint8   [nb]
-    code: torch.Tensor   # int8    [nb, 28]
+    code: torch.Tensor   # int8    [nb, keep(rate)] (28 at the default rate 2)
     shape: tuple | None = None  # logical (rows, cols) when compressed by blaz_compress_padded
+    rate: int = 2        # first `rate` DCT rows and columns kept (the blaz_*_rate entry points)
 
     @property
     def nb(self) -> int:
@@ -197,10 +205,10 @@ class CMat:
 
     @property
     def nbytes(self) -> int:
-        return self.nb * (8 + 8 + 1 + NKEEP)
+        return self.nb * (8 + 8 + 1 + keep_count(self.rate))
 
     @staticmethod
-    def empty(rows: int, cols: int, device=None) -> "CMat":
+    def empty(rows: int, cols: int, device=None, rate: int = 2) -> "CMat":
         device = device or torch.device("cuda", torch.cuda.current_device())
         if rows % 8 or cols % 8 or rows < 0 or cols < 0:
             raise ValueError("sides must be non-negative multiples of 8")
@@ -208,7 +216,7 @@ class CMat:
         return CMat(rows, cols, torch.empty(nb, dtype=torch.float64, device=device),
                     torch.empty(nb, dtype=torch.float64, device=device),
                     torch.empty(nb, dtype=torch.uint8, device=device),
-                    torch.empty((nb, NKEEP), dtype=torch.int8, device=device))
+                    torch.empty((nb, keep_count(rate)), dtype=torch.int8, device=device), rate=rate)
 
     def desc(self) -> _CMatDesc:
         return _CMatDesc(self.rows, self.cols, self.f.data_ptr(), self.s.data_ptr(), self.phi.data_ptr(),
@@ -330,6 +338,71 @@ def blaz_scale(a: CMat, c: float, out: CMat | None = None, stream=None) -> CMat:
     out = out or CMat.empty(a.rows, a.cols, a.f.device)
     da, do = a.desc(), out.desc()
     _check(lib().blaz_scale(ctypes.byref(da), float(c), ctypes.byref(do), _stream(stream)), "blaz_scale")
+    return out
+
+
+def keep_count(r: int) -> int:
+    """Codes kept per block at rate r (8r + (8-r)r; ValueError outside 1..8)."""
+    if not 1 <= int(r) <= 8:
+        raise ValueError("rate must be in 1..8")
+    return 8 * int(r) + (8 - int(r)) * int(r)
+
+
+def _same_rate(*ms: CMat) -> int:
+    r = ms[0].rate
+    for m in ms:
+        if m.rate != r or m.code.shape != (m.nb, keep_count(r)):
+            raise ValueError("operands must have the same rate and [nb, keep(rate)] codes")
+    return r
+
+
+def blaz_compress_rate(A: torch.Tensor, r: int, out: CMat | None = None, stream=None) -> CMat:
+    """Compression keeping the first r rows and columns of each block's DCT."""
+    _dev_f64(A, "A")
+    rows, cols = A.shape
+    out = out or CMat.empty(rows, cols, A.device, rate=r)
+    if (out.rows, out.cols) != (rows, cols) or out.rate != r:
+        raise ValueError("out shape or rate mismatch")
+    _same_rate(out)
+    d = out.desc()
+    _check(lib().blaz_compress_rate(A.data_ptr(), _ld(A), int(r), ctypes.byref(d), _stream(stream)),
+           "blaz_compress_rate")
+    return out
+
+
+def blaz_decompress_rate(a: CMat, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    r = _same_rate(a)
+    if out is None:
+        out = torch.empty((a.rows, a.cols), dtype=torch.float64, device=a.f.device)
+    _dev_f64(out, "out")
+    d = a.desc()
+    _check(lib().blaz_decompress_rate(ctypes.byref(d), r, out.data_ptr(), _ld(out), _stream(stream)),
+           "blaz_decompress_rate")
+    return out
+
+
+def _binary_rate(name, a: CMat, b: CMat, out: CMat | None, stream):
+    out = out or CMat.empty(a.rows, a.cols, a.f.device, rate=a.rate)
+    r = _same_rate(a, b, out)
+    da, db, do = a.desc(), b.desc(), out.desc()
+    _check(getattr(lib(), name)(ctypes.byref(da), ctypes.byref(db), r, ctypes.byref(do), _stream(stream)), name)
+    return out
+
+
+def blaz_add_rate(a: CMat, b: CMat, out: CMat | None = None, stream=None) -> CMat:
+    return _binary_rate("blaz_add_rate", a, b, out, stream)
+
+
+def blaz_sub_rate(a: CMat, b: CMat, out: CMat | None = None, stream=None) -> CMat:
+    return _binary_rate("blaz_sub_rate", a, b, out, stream)
+
+
+def blaz_scale_rate(a: CMat, c: float, out: CMat | None = None, stream=None) -> CMat:
+    out = out or CMat.empty(a.rows, a.cols, a.f.device, rate=a.rate)
+    r = _same_rate(a, out)
+    da, do = a.desc(), out.desc()
+    _check(lib().blaz_scale_rate(ctypes.byref(da), float(c), r, ctypes.byref(do), _stream(stream)),
+           "blaz_scale_rate")
     return out
 
 
@@ -688,3 +761,5 @@ save, load, file_info = blaz_cmat_save, blaz_cmat_load, blaz_cmat_file_info
 compress_padded, decompress_padded, dot_padded = blaz_compress_padded, blaz_decompress_padded, blaz_dot_padded
 matmul_padded, matmul_cc_padded = blaz_matmul_padded, blaz_matmul_cc_padded
 compress_host, download, upload = blaz_compress_host, blaz_cmat_download, blaz_cmat_upload
+compress_rate, decompress_rate = blaz_compress_rate, blaz_decompress_rate
+add_rate, sub_rate, scale_rate = blaz_add_rate, blaz_sub_rate, blaz_scale_rate

@@ -143,7 +143,7 @@ void blaz_constants(double cos_out[64], double aa_out[64], int32_t kept_out[56])
         }
 }
 
-int blaz_cmat_alloc(blaz_cmat *m, int64_t rows, int64_t cols, void *stream)
+static int cmat_alloc(blaz_cmat *m, int64_t rows, int64_t cols, int nkeep, void *stream)
 {
     if (!m) return BLAZ_ERR_NULL;
     int rc = check_dims(rows, cols);
@@ -158,7 +158,7 @@ int blaz_cmat_alloc(blaz_cmat *m, int64_t rows, int64_t cols, void *stream)
     if (nb == 0) return BLAZ_OK;
     // One allocation: f | s | code | phi (each 256-byte aligned).
     auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    const size_t of = 0, os = up(of + 8 * nb), oc = up(os + 8 * nb), op = up(oc + (size_t)kKeep * nb);
+    const size_t of = 0, os = up(of + 8 * nb), oc = up(os + 8 * nb), op = up(oc + (size_t)nkeep * nb);
     const size_t total = up(op + nb);
     void *base = nullptr;
     cudaError_t e = cudaMallocAsync(&base, total, st);
@@ -172,6 +172,19 @@ int blaz_cmat_alloc(blaz_cmat *m, int64_t rows, int64_t cols, void *stream)
     m->code = (int8_t *)(b + oc);
     m->phi = (uint8_t *)(b + op);
     return BLAZ_OK;
+}
+
+int blaz_cmat_alloc(blaz_cmat *m, int64_t rows, int64_t cols, void *stream)
+{
+    return cmat_alloc(m, rows, cols, kKeep, stream);
+}
+
+int blaz_keep_count(int r) { return (r >= 1 && r <= 8) ? 8 * r + (8 - r) * r : -1; }
+
+int blaz_cmat_alloc_rate(blaz_cmat *m, int64_t rows, int64_t cols, int r, void *stream)
+{
+    if (blaz_keep_count(r) < 0) return BLAZ_ERR_ARG;
+    return cmat_alloc(m, rows, cols, blaz_keep_count(r), stream);
 }
 
 int blaz_cmat_free(blaz_cmat *m, void *stream)
@@ -273,6 +286,61 @@ int blaz_scale(const blaz_cmat *a, double c, blaz_cmat *out, void *stream)
     if ((rc = validate_cmat(a)) || (rc = validate_cmat(out))) return rc;
     if ((rc = same_shape(a, out))) return rc;
     return launch_scale(a, c, out, (cudaStream_t)stream);
+}
+
+int blaz_compress_rate(const double *A, int64_t lda, int r, blaz_cmat *out, void *stream)
+{
+    BLAZ_NVTX();
+    if (blaz_keep_count(r) < 0) return BLAZ_ERR_ARG;
+    int rc = validate_cmat(out);
+    if (rc) return rc;
+    if (nblocks(out) == 0) return BLAZ_OK;
+    if (!A) return BLAZ_ERR_NULL;
+    if (lda < out->cols) return BLAZ_ERR_LD;
+    return launch_compress_rate(A, lda, out, r, (cudaStream_t)stream);
+}
+
+int blaz_decompress_rate(const blaz_cmat *a, int r, double *A, int64_t lda, void *stream)
+{
+    BLAZ_NVTX();
+    if (blaz_keep_count(r) < 0) return BLAZ_ERR_ARG;
+    int rc = validate_cmat(a);
+    if (rc) return rc;
+    if (nblocks(a) == 0) return BLAZ_OK;
+    if (!A) return BLAZ_ERR_NULL;
+    if (lda < a->cols) return BLAZ_ERR_LD;
+    return launch_decompress_rate(a, r, A, lda, (cudaStream_t)stream);
+}
+
+static int add_or_sub_rate(const blaz_cmat *a, const blaz_cmat *b, int r, blaz_cmat *out, bool sub, void *stream)
+{
+    if (blaz_keep_count(r) < 0) return BLAZ_ERR_ARG;
+    int rc;
+    if ((rc = validate_cmat(a)) || (rc = validate_cmat(b)) || (rc = validate_cmat(out))) return rc;
+    if ((rc = same_shape(a, b)) || (rc = same_shape(a, out))) return rc;
+    return launch_add_rate(a, b, out, r, sub, (cudaStream_t)stream);
+}
+
+int blaz_add_rate(const blaz_cmat *a, const blaz_cmat *b, int r, blaz_cmat *out, void *stream)
+{
+    BLAZ_NVTX();
+    return add_or_sub_rate(a, b, r, out, false, stream);
+}
+
+int blaz_sub_rate(const blaz_cmat *a, const blaz_cmat *b, int r, blaz_cmat *out, void *stream)
+{
+    BLAZ_NVTX();
+    return add_or_sub_rate(a, b, r, out, true, stream);
+}
+
+int blaz_scale_rate(const blaz_cmat *a, double c, int r, blaz_cmat *out, void *stream)
+{
+    BLAZ_NVTX();
+    if (blaz_keep_count(r) < 0) return BLAZ_ERR_ARG;
+    int rc;
+    if ((rc = validate_cmat(a)) || (rc = validate_cmat(out))) return rc;
+    if ((rc = same_shape(a, out))) return rc;
+    return launch_scale_rate(a, c, out, r, (cudaStream_t)stream);
 }
 
 int blaz_dot(const blaz_cmat *a, const blaz_cmat *b, double *result, void *stream)

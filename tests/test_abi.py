@@ -109,3 +109,25 @@ def test_fp64_probe_rejects_bad_arguments_without_a_gpu(libblaz):
     assert f(1, 33, fake, 1 << 20, ctypes.byref(ops), None) == -9
     assert f(0, 16, fake, 1 << 20, ctypes.byref(ops), None) == -9
     assert f((1 << 30) + 1, 16, fake, 1 << 20, ctypes.byref(ops), None) == -9
+
+
+def test_rate_entry_points_check_the_rate_without_a_gpu(libblaz):
+    """The tunable-rate entry points reject r outside 1..8 (BLAZ_ERR_ARG = -9)
+    before any descriptor or device check; keep(r) = 8r + (8-r)r."""
+    import ctypes
+
+    from paper_2202_13007_gb300 import blaz
+
+    assert [libblaz.blaz_keep_count(r) for r in range(0, 10)] == [-1, 15, 28, 39, 48, 55, 60, 63, 64, -1]
+    empty = blaz._CMatDesc(0, 16, None, None, None, None)
+    e = ctypes.byref(empty)
+    for r in (0, 9):
+        assert libblaz.blaz_compress_rate(None, 16, r, e, None) == -9
+        assert libblaz.blaz_decompress_rate(e, r, None, 16, None) == -9
+        assert libblaz.blaz_add_rate(e, e, r, e, None) == -9
+        assert libblaz.blaz_sub_rate(e, e, r, e, None) == -9
+        assert libblaz.blaz_scale_rate(e, ctypes.c_double(2.0), r, e, None) == -9
+        assert libblaz.blaz_cmat_alloc_rate(e, 8, 8, r, None) == -9
+    for r in (1, 8):   # empty operands need no device
+        assert libblaz.blaz_compress_rate(None, 16, r, e, None) == 0
+        assert libblaz.blaz_add_rate(e, e, r, e, None) == 0

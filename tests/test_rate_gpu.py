@@ -1,0 +1,155 @@
+"""GPU parity of the tunable-rate entry points (the first r DCT rows and
+columns kept, r = 1..8) against the oracle: codes, phi, f and s of compress,
+add, sub and scale bit for bit; decompression within
+1e-12 (|f| + 14 |s| sum|c| / phi) per block, the bound of the 28-code path
+(the recurrence adds at most 14 inverse-DCT terms of size <= |s| sum|c|/phi)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+RATES = list(range(1, 9))
+
+
+@pytest.fixture(scope="session")
+def B():
+    from paper_2202_13007_gb300 import _build, blaz
+
+    _build.build()
+    blaz.lib()
+    torch.cuda.init()
+    return blaz
+
+
+def dev(A):
+    return torch.from_numpy(np.ascontiguousarray(A)).cuda()
+
+
+def same_bits(x, y):
+    x = np.asarray(x, np.float64)
+    y = np.asarray(y, np.float64)
+    nan = np.isnan(x)
+    assert np.array_equal(nan, np.isnan(y))
+    assert np.array_equal(x[~nan].view(np.uint64), y[~nan].view(np.uint64))
+
+
+def assert_same(g, o):
+    f, s, phi, code = g.to_host()
+    assert np.array_equal(phi, o.phi)
+    assert np.array_equal(code, o.code)
+    same_bits(f, o.f)
+    same_bits(s, o.s)
+
+
+def mixed_matrix(seed=3):
+    """72 x 136 (153 blocks: a ragged last CTA): smooth, rough and
+    wide-range rows plus special blocks (constant, zero, NaN, infinities,
+    subnormal, Sec. II's Example 1)."""
+    rng = np.random.default_rng(seed)
+    X = np.concatenate([W.random_block_matrix(24, 136, seed=seed + k, kind=kind)
+                        for k, kind in enumerate(["smooth", "noise", "wide"])], axis=0)
+    X[0:8, 0:8] = np.fromfunction(lambda i, j: (0.1 * i) * (0.1 * j), (8, 8))
+    X[0:8, 8:16] = 2.5
+    X[0:8, 16:24] = 0.0
+    X[8:16, 8:16] = rng.standard_normal((8, 8)) * 1e-310
+    X[8, 20] = np.nan
+    X[16, 30] = np.inf
+    X[16:24, 40:48] = -np.inf
+    X[24:32, 48:56] = rng.standard_normal((8, 8)) * 1e300
+    return X
+
+
+@pytest.mark.parametrize("r", RATES)
+def test_compress_rate_bit_exact(B, r):
+    X = mixed_matrix()
+    assert_same(B.compress_rate(dev(X), r), O.compress_rate(X, r))
+
+
+def test_rate_two_matches_the_28_code_kernels(B):
+    A, Bm = W.plain_pair()
+    a2, a = B.compress_rate(dev(A), 2), B.compress(dev(A))
+    for x, y in zip(a2.to_host(), a.to_host()):
+        assert np.array_equal(np.asarray(x).view(np.uint8), np.asarray(y).view(np.uint8))
+
+
+@pytest.mark.parametrize("r", RATES)
+def test_decompress_rate(B, r):
+    X = mixed_matrix(5)
+    oc = O.compress_rate(X, r)
+    got = B.decompress_rate(B.compress_rate(dev(X), r)).cpu().numpy()
+    ref = O.decompress_rate(oc, r)
+    scale = np.abs(oc.f) + 14 * np.abs(oc.s) * np.abs(oc.code.astype(np.float64)).sum(1) / oc.phi
+    tol = (1e-12 * scale).reshape(oc.rows // 8, 1, oc.cols // 8, 1)
+    err = np.abs(got - ref).reshape(oc.rows // 8, 8, oc.cols // 8, 8)
+    # blocks with a NaN slope (NaN or infinite inputs) are NaN past M00 on both sides
+    assert np.array_equal(np.isnan(got), np.isnan(ref))
+    ok = (err <= tol) | np.isnan(ref.reshape(err.shape)) | (got == ref).reshape(err.shape)
+    assert np.all(ok), np.argwhere(~ok)[:5]
+
+
+@pytest.mark.parametrize("r", RATES)
+def test_add_sub_scale_rate_bit_exact(B, r):
+    X, Y = mixed_matrix(7), mixed_matrix(11)[:, ::-1]
+    ga, gb = B.compress_rate(dev(X), r), B.compress_rate(dev(Y), r)
+    oa, ob = O.compress_rate(X, r), O.compress_rate(Y, r)
+    assert_same(B.add_rate(ga, gb), O.add_rate(oa, ob, r))
+    assert_same(B.sub_rate(ga, gb), O.add_rate(oa, ob, r, sub=True))
+    for c in (-0.97, 3.5, 0.0):
+        assert_same(B.scale_rate(ga, c), O.scale_rate(oa, c))
+
+
+@pytest.mark.parametrize("r", [1, 3, 8])
+def test_rate_ops_in_place_and_aliased(B, r):
+    X, Y = mixed_matrix(2), mixed_matrix(4)
+    oa, ob = O.compress_rate(X, r), O.compress_rate(Y, r)
+    ga, gb = B.compress_rate(dev(X), r), B.compress_rate(dev(Y), r)
+    B.add_rate(ga, gb, out=ga)                     # out aliases a
+    want = O.add_rate(oa, ob, r)
+    assert_same(ga, want)
+    B.sub_rate(gb, ga, out=ga)                     # out aliases b
+    want = O.add_rate(ob, want, r, sub=True)
+    assert_same(ga, want)
+    B.scale_rate(ga, -2.0, out=ga)                 # in place
+    assert_same(ga, O.scale_rate(want, -2.0))
+
+
+@pytest.mark.parametrize("r", [1, 4])
+def test_rate_strided_view_and_large_sampled(B, r):
+    big = W.random_block_matrix(64, 200, seed=9)
+    tb = dev(big)
+    view = tb[:, 1:137]                            # lda = 200, base not 16-byte aligned
+    assert_same(B.compress_rate(view, r), O.compress_rate(big[:, 1:137], r))
+    # 2048 x 2048 (65536 blocks, a full grid of CTAs): sampled blocks
+    n = 2048
+    A = W.bump_field(n, seed=21)
+    g = B.compress_rate(dev(A), r)
+    f, s, phi, code = g.to_host()
+    rng = np.random.default_rng(1)
+    nbc = n // 8
+    idx = np.unique(np.concatenate([rng.integers(0, nbc * nbc, 200), [0, nbc - 1, nbc * nbc - 1]]))
+    sub = np.concatenate([A[8 * (b // nbc):8 * (b // nbc) + 8, 8 * (b % nbc):8 * (b % nbc) + 8] for b in idx],
+                         axis=1)
+    oc = O.compress_rate(sub, r)
+    assert np.array_equal(phi[idx], oc.phi) and np.array_equal(code[idx], oc.code)
+    same_bits(f[idx], oc.f)
+    same_bits(s[idx], oc.s)
+
+
+def test_rate_argument_errors(B):
+    X = dev(mixed_matrix())
+    for r in (0, 9, -3):
+        with pytest.raises(ValueError):
+            B.keep_count(r)
+    a = B.compress_rate(X, 3)
+    b = B.compress_rate(X, 5)
+    with pytest.raises(ValueError):
+        B.add_rate(a, b)
+    d = a.desc()
+    assert B.lib().blaz_compress_rate(X.data_ptr(), 136, 9, d, None) == -9
+    assert B.lib().blaz_decompress_rate(d, 0, X.data_ptr(), 136, None) == -9
+    e = B.CMat.empty(0, 16, rate=4)
+    assert B.decompress_rate(e).shape == (0, 16)
