@@ -5,6 +5,7 @@
 #include <vector>
 
 #include "blaz_internal.cuh"
+#include "rate.cuh"
 
 namespace blaz {
 
@@ -297,7 +298,10 @@ int blaz_compress_rate(const double *A, int64_t lda, int r, blaz_cmat *out, void
     if (nblocks(out) == 0) return BLAZ_OK;
     if (!A) return BLAZ_ERR_NULL;
     if (lda < out->cols) return BLAZ_ERR_LD;
-    return launch_compress_rate(A, lda, out, r, (cudaStream_t)stream);
+    cudaStream_t st = (cudaStream_t)stream;
+    Scratch ws(st);
+    if ((rc = ws.alloc(compress_rate_scratch_bytes(nblocks(out))))) return rc;
+    return launch_compress_rate(A, lda, out, r, ws.p, st);
 }
 
 int blaz_decompress_rate(const blaz_cmat *a, int r, double *A, int64_t lda, void *stream)

@@ -158,12 +158,6 @@ int launch_decompress(const blaz_cmat *a, double *A, int64_t lda, cudaStream_t s
                       int64_t cols = -1, bool zero_fill = false);
 int launch_add(const blaz_cmat *a, const blaz_cmat *b, const blaz_cmat *out, bool subtract, cudaStream_t st);
 int launch_scale(const blaz_cmat *a, double c, const blaz_cmat *out, cudaStream_t st);
-// tunable rate r = 1..8 (checked by the caller): code arrays of nb x keep(r) bytes
-int launch_compress_rate(const double *A, int64_t lda, const blaz_cmat *out, int r, cudaStream_t st);
-int launch_decompress_rate(const blaz_cmat *a, int r, double *A, int64_t lda, cudaStream_t st);
-int launch_add_rate(const blaz_cmat *a, const blaz_cmat *b, const blaz_cmat *out, int r, bool subtract,
-                    cudaStream_t st);
-int launch_scale_rate(const blaz_cmat *a, double c, const blaz_cmat *out, int r, cudaStream_t st);
 // rows x cols: the logical shape (-1: the block grid's); for a padded pair the
 // partial blocks are summed over their logical entries by a second kernel.
 int launch_dot(const blaz_cmat *a, const blaz_cmat *b, double *result, double *partials, unsigned *counter,

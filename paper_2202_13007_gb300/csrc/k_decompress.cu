@@ -170,7 +170,8 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 if (!(h ? vB : vA)) continue;
-                const double o0 = fma(ts[h], i64_to_double(acc[2 * h]), fb[h]);
+                // M00 = f by definition (row 0 of G is zero), also when s is not finite
+                const double o0 = (nt == 0 && t == 0) ? fb[h] : fma(ts[h], i64_to_double(acc[2 * h]), fb[h]);
                 const double o1 = fma(ts[h], i64_to_double(acc[2 * h + 1]), fb[h]);
                 double *p = pb[h] + nt * lda;
                 if (inside[h]) {

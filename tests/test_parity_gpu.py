@@ -163,6 +163,21 @@ def test_decompress_parity(B, shape):
     assert_decompress_close(got, oc, *shape)
 
 
+def test_decompress_special_values(B):
+    """NaN, infinite, subnormal and huge blocks: the finite blocks within the
+    bound, the others with the oracle's NaN pattern (a NaN slope leaves M00 = f
+    and makes the rest NaN)."""
+    X = special_blocks()
+    oc = O.compress(X)
+    got = B.decompress(B.compress(dev(X))).cpu().numpy()
+    ref = O.decompress(oc)
+    assert np.array_equal(np.isnan(got), np.isnan(ref))
+    fin = np.isfinite(ref)
+    assert np.array_equal(got[~fin & ~np.isnan(ref)], ref[~fin & ~np.isnan(ref)])
+    tol = np.repeat(decompress_tol(oc), 8).reshape(1, -1).repeat(8, 0)
+    assert np.all(((np.abs(got - ref) <= tol) | (got == ref))[fin])
+
+
 def test_decompress_into_strided_output(B):
     X = W.plain_pair()[1][:64, :96]
     oc = O.compress(X)

@@ -153,3 +153,26 @@ def test_rate_argument_errors(B):
     assert B.lib().blaz_decompress_rate(d, 0, X.data_ptr(), 136, None) == -9
     e = B.CMat.empty(0, 16, rate=4)
     assert B.decompress_rate(e).shape == (0, 16)
+
+
+@pytest.mark.parametrize("r", [1, 4, 8])
+def test_compress_rate_certification_boundaries(B, r, boundary_blocks):
+    """Blocks whose phi or codes sit closest to a truncation boundary: the
+    fp32 decisions must defer them to the exact fix-up."""
+    blk, _, _ = boundary_blocks
+    X = np.ascontiguousarray(blk.transpose(1, 0, 2).reshape(8, -1))
+    assert_same(B.compress_rate(dev(X), r), O.compress_rate(X, r))
+
+
+@pytest.mark.parametrize("r", [2, 5, 8])
+def test_add_rate_structural_ties(B, r):
+    """A + A and A - A (equal phi and codes put beta_1 c_1 +- beta_2 c_2 on an
+    integer: the binary64 pass decides them) and smooth + rough pairs."""
+    X = W.bump_field(256, seed=3)
+    Y = W.random_block_matrix(256, 256, seed=8, kind="noise")
+    ga, gb = B.compress_rate(dev(X), r), B.compress_rate(dev(Y), r)
+    oa, ob = O.compress_rate(X, r), O.compress_rate(Y, r)
+    assert_same(B.add_rate(ga, ga), O.add_rate(oa, oa, r))
+    assert_same(B.sub_rate(ga, ga), O.add_rate(oa, oa, r, sub=True))
+    assert_same(B.add_rate(ga, gb), O.add_rate(oa, ob, r))
+    assert_same(B.sub_rate(gb, ga), O.add_rate(ob, oa, r, sub=True))
