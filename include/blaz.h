@@ -66,6 +66,14 @@ typedef struct blaz_cmat {
     int8_t *code;         /* device, [nb][28]                             */
 } blaz_cmat;
 
+/* Constant tables.  The first call on a device of an entry point that
+ * decompresses (blaz_decompress*, blaz_matmul*, blaz_decompress_rate) or
+ * takes a dot product (blaz_dot*, blaz_dot_rowcol) copies the library's
+ * fixed tables for it (slices of the decompression map, at most 44 KB) to
+ * that device on `stream` and waits for the copy; later calls do not.  Make
+ * that first call outside stream capture: during capture it is refused
+ * (BLAZ_ERR_CUDA, cudaErrorStreamCaptureUnsupported). */
+
 /* Human-readable name of a status code (static string). */
 const char *blaz_strerror(int status);
 /* CUDA error code (cudaError_t as int) of the last BLAZ_ERR_CUDA on this thread. */
@@ -223,7 +231,8 @@ int blaz_dot(const blaz_cmat *a, const blaz_cmat *b, double *result, void *strea
  * size fits there (the BLAZ_ERR_RANGE check before anything is enqueued
  * cannot trigger).  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  All calls share
+ * current and copies the constant tables (see above); make that first call
+ * before any stream capture.  All calls share
  * the one array (the counter is cleared on the stream at the start of each
  * call): calls that can overlap on the GPU -- on different streams without
  * ordering between them -- race and must not be issued.  No cudaMalloc,

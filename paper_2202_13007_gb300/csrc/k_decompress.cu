@@ -10,6 +10,7 @@
 #include <cuda_fp16.h>
 
 #include "blaz_internal.cuh"
+#include "const_upload.cuh"
 #include "gmap.cuh"
 
 namespace blaz {
@@ -34,6 +35,7 @@ struct DecConsts {
     uint2 bfrag[kDecSlices][2][8][32];  // B fragments [slice][k-step][n-tile][lane]
     double inv_phi_scaled[256];         // RN(1/phi) 2^E (2^E: weight of the last slice; exact scaling)
 };
+__device__ DecConsts g_dec;  // dec_consts(), copied once per device
 
 static const DecConsts &dec_consts()
 {
@@ -97,15 +99,15 @@ __device__ __forceinline__ uint32_t code_pair(const int8_t *__restrict__ c, int 
 
 template <bool kVec>
 __global__ void __launch_bounds__(128)
-    k_decompress(const __grid_constant__ DecConsts dc, const double *__restrict__ f, const double *__restrict__ s,
+    k_decompress(const double *__restrict__ f, const double *__restrict__ s,
                  const uint8_t *__restrict__ phi, const int8_t *__restrict__ code, int64_t nbc, int64_t nb,
                  double *__restrict__ A, int64_t lda, int64_t rows, int64_t cols, bool zero_fill)
 {
     __shared__ uint2 sb[kDecSlices][2][8][32];
-    __shared__ double inv_phi_scaled[256];  // indexed per lane: shared, not the parameter bank
+    __shared__ double inv_phi_scaled[256];
     for (int i = threadIdx.x; i < kDecSlices * 2 * 8 * 32; i += blockDim.x)
-        (&sb[0][0][0][0])[i] = (&dc.bfrag[0][0][0][0])[i];
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) inv_phi_scaled[i] = dc.inv_phi_scaled[i];
+        (&sb[0][0][0][0])[i] = (&g_dec.bfrag[0][0][0][0])[i];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) inv_phi_scaled[i] = g_dec.inv_phi_scaled[i];
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     const int64_t ngroups = (nb + 15) / 16;
@@ -221,12 +223,15 @@ int launch_decompress(const blaz_cmat *a, double *A, int64_t lda, cudaStream_t s
     int64_t want = ((nb + 15) / 16 + 3) / 4;
     const int64_t cap = (int64_t)num_sms() * occ;
     const int grid = (int)std::max<int64_t>(1, std::min(want, cap));
+    static DeviceTable table;
+    const int rc = table.ensure(&g_dec, &dec_consts(), sizeof(DecConsts), 0, st);
+    if (rc) return rc;
     if (vec_ok(A, lda))
-        k_decompress<true><<<grid, threads, 0, st>>>(dec_consts(), a->f, a->s, a->phi, a->code, nbc, nb, A, lda,
-                                                     rows, cols, zero_fill);
+        k_decompress<true><<<grid, threads, 0, st>>>(a->f, a->s, a->phi, a->code, nbc, nb, A, lda, rows, cols,
+                                                     zero_fill);
     else
-        k_decompress<false><<<grid, threads, 0, st>>>(dec_consts(), a->f, a->s, a->phi, a->code, nbc, nb, A, lda,
-                                                      rows, cols, zero_fill);
+        k_decompress<false><<<grid, threads, 0, st>>>(a->f, a->s, a->phi, a->code, nbc, nb, A, lda, rows, cols,
+                                                      zero_fill);
     return launch_status();
 }
 

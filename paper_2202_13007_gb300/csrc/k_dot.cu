@@ -21,6 +21,7 @@
 #include <cuda_fp16.h>
 
 #include "block_codec.cuh"
+#include "const_upload.cuh"
 #include "gmap.cuh"
 
 namespace blaz {
@@ -64,6 +65,7 @@ struct GramTC {
     int eH2, eH4, eW2, eW4;          // log2 of scaleH[2], scaleH[4], scaleW[2], scaleW[4]
     double inv_phi[256];
 };
+__device__ GramTC g_gram;  // gram_tc(), copied once per device
 
 // v 2^e as binary64 on the integer pipe (v's low bits beyond 53 truncated);
 // e keeps the result a normal number for |v| < 2^63 (the slice scales).
@@ -224,7 +226,7 @@ __device__ __forceinline__ void gram_group(const uint2 (*sbf)[2][4][32], const f
 // rows gq and gq + 8 of the first group, lanes t = 2, 3 those of the second,
 // so the binary64 tail runs on all 32 lanes, one block each.
 __global__ void __launch_bounds__(kDotThreads, 3)
-    k_dot_tc(const __grid_constant__ GramTC g, int64_t nb, const double *__restrict__ fa, const double *__restrict__ sa,
+    k_dot_tc(int64_t nb, const double *__restrict__ fa, const double *__restrict__ sa,
              const uint8_t *__restrict__ pa, const int8_t *__restrict__ ca, const double *__restrict__ fb,
              const double *__restrict__ sb, const uint8_t *__restrict__ pb, const int8_t *__restrict__ cb,
              double *__restrict__ partials, unsigned *__restrict__ counter, double *__restrict__ result,
@@ -232,12 +234,14 @@ __global__ void __launch_bounds__(kDotThreads, 3)
 {
     __shared__ uint2 sbf[kSlices][2][4][32];
     __shared__ float swl[kSlices][32][8];
-    __shared__ double inv_phi[256];  // indexed per lane: shared, not the parameter bank
+    __shared__ double inv_phi[256];
     __shared__ double red[kDotThreads / 32];
     __shared__ bool last;
+    const GramTC &g = g_gram;
     for (int i = threadIdx.x; i < kSlices * 2 * 4 * 32; i += blockDim.x) (&sbf[0][0][0][0])[i] = (&g.bfrag[0][0][0][0])[i];
     for (int i = threadIdx.x; i < kSlices * 32 * 8; i += blockDim.x) (&swl[0][0][0])[i] = (&g.wl[0][0][0])[i];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) inv_phi[i] = g.inv_phi[i];
+    const int eH2 = g.eH2, eH4 = g.eH4, eW2 = g.eW2, eW4 = g.eW4;
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gq = lane >> 2, t = lane & 3;
     const int wpc = blockDim.x >> 5;
@@ -275,9 +279,9 @@ __global__ void __launch_bounds__(kDotThreads, 3)
             }
             // ten binary64 operations: the power-of-two slice scales and the
             // factor 64 go to the exponent on the integer pipe
-            const double Q = i64_ldexp(qhi, g.eH2) + i64_ldexp(qlo, g.eH4);
-            const double Wa = i64_ldexp(ahi, g.eW2) + i64_ldexp(alo, g.eW4);
-            const double Wb = i64_ldexp(bhi, g.eW2) + i64_ldexp(blo, g.eW4);
+            const double Q = i64_ldexp(qhi, eH2) + i64_ldexp(qlo, eH4);
+            const double Wa = i64_ldexp(ahi, eW2) + i64_ldexp(alo, eW4);
+            const double Wb = i64_ldexp(bhi, eW2) + i64_ldexp(blo, eW4);
             const double ta = sa[b] * inv_phi[pa[b]], tb = sb[b] * inv_phi[pb[b]];
             const double f_a = fa[b], f_b = fb[b];
             const double t1 = fma(tb, Wb, times64(f_b));
@@ -365,9 +369,10 @@ struct RowColConsts {
     double G[64][kKeep];
     double inv_phi[256];
 };
+__device__ RowColConsts g_rowcol;  // rowcol_consts(), copied once per device
 
 __global__ void __launch_bounds__(kDotThreads)
-    k_dot_rowcol(const __grid_constant__ RowColConsts g, int64_t nkb, int64_t nbc_a, int64_t nbc_b, int64_t i,
+    k_dot_rowcol(int64_t nkb, int64_t nbc_a, int64_t nbc_b, int64_t i,
                  int64_t j, const double *__restrict__ fa, const double *__restrict__ sa,
                  const uint8_t *__restrict__ pa, const int8_t *__restrict__ ca, const double *__restrict__ fb,
                  const double *__restrict__ sb, const uint8_t *__restrict__ pb, const int8_t *__restrict__ cb,
@@ -375,15 +380,25 @@ __global__ void __launch_bounds__(kDotThreads)
 {
     __shared__ double red[kDotThreads / 32];
     __shared__ bool last;
+    // the 8 rows of G for line ri, the 8 for column cj, and 1/phi (shared:
+    // uniform reads broadcast, per-lane reads of 1/phi spread over banks)
+    __shared__ double Gr[8][kKeep], Gc[8][kKeep], inv_phi[256];
     const int64_t bi = i / 8, bj = j / 8;
     const int ri = (int)(i % 8), cj = (int)(j % 8);
+    for (int e = threadIdx.x; e < 8 * kKeep; e += blockDim.x) {
+        const int q = e / kKeep, t = e - q * kKeep;
+        Gr[q][t] = g_rowcol.G[ri * 8 + q][t];
+        Gc[q][t] = g_rowcol.G[q * 8 + cj][t];
+    }
+    for (int e = threadIdx.x; e < 256; e += blockDim.x) inv_phi[e] = g_rowcol.inv_phi[e];
+    __syncthreads();
     double acc = 0.0;
     for (int64_t kb = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; kb < nkb; kb += (int64_t)gridDim.x * blockDim.x) {
         const int64_t ba = bi * nbc_a + kb, bb = kb * nbc_b + bj;
         int8_t xa[kKeep], xb[kKeep];
         load_codes(ca + ba * kKeep, xa);
         load_codes(cb + bb * kKeep, xb);
-        const double ta = sa[ba] * g.inv_phi[pa[ba]], tb = sb[bb] * g.inv_phi[pb[bb]];
+        const double ta = sa[ba] * inv_phi[pa[ba]], tb = sb[bb] * inv_phi[pb[bb]];
         const double f_a = fa[ba], f_b = fb[bb];
         double blk = 0.0;
 #pragma unroll
@@ -391,8 +406,8 @@ __global__ void __launch_bounds__(kDotThreads)
             double ya = 0.0, yb = 0.0;
 #pragma unroll
             for (int t = 0; t < kKeep; ++t) {
-                ya = fma(g.G[ri * 8 + q][t], (double)xa[t], ya);
-                yb = fma(g.G[q * 8 + cj][t], (double)xb[t], yb);
+                ya = fma(Gr[q][t], (double)xa[t], ya);
+                yb = fma(Gc[q][t], (double)xb[t], yb);
             }
             blk = fma(fma(ta, ya, f_a), fma(tb, yb, f_b), blk);
         }
@@ -538,9 +553,12 @@ int launch_dot(const blaz_cmat *a, const blaz_cmat *b, double *result, double *p
     const bool padded = rows != a->rows || cols != a->cols;
     int grid = dot_grid(nb);
     if (grid > max_ctas) grid = (int)max_ctas;
-    k_dot_tc<<<grid, kDotThreads, 0, st>>>(gram_tc(), nb, a->f, a->s, a->phi, a->code, b->f, b->s, b->phi,
+    static DeviceTable table;
+    int rc = table.ensure(&g_gram, &gram_tc(), sizeof(GramTC), 0, st);
+    if (rc) return rc;
+    k_dot_tc<<<grid, kDotThreads, 0, st>>>(nb, a->f, a->s, a->phi, a->code, b->f, b->s, b->phi,
                                            b->code, partials, counter, result, nbc, rows, cols, padded);
-    int rc = launch_status();
+    rc = launch_status();
     if (rc || !padded) return rc;
     // The partial blocks: the last block row and/or the last block column.
     const int64_t nbr = a->rows / 8;
@@ -566,7 +584,10 @@ int launch_dot_rowcol(const blaz_cmat *a, const blaz_cmat *b, int64_t i, int64_t
 {
     const int64_t nkb = a->cols / 8;
     const int grid = rowcol_grid(nkb);
-    k_dot_rowcol<<<grid, kDotThreads, 0, st>>>(rowcol_consts(), nkb, a->cols / 8, b->cols / 8, i, j, a->f, a->s,
+    static DeviceTable table;
+    const int rc = table.ensure(&g_rowcol, &rowcol_consts(), sizeof(RowColConsts), 0, st);
+    if (rc) return rc;
+    k_dot_rowcol<<<grid, kDotThreads, 0, st>>>(nkb, a->cols / 8, b->cols / 8, i, j, a->f, a->s,
                                                a->phi, a->code, b->f, b->s, b->phi, b->code, partials, counter,
                                                result);
     return launch_status();

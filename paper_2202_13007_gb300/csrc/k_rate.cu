@@ -17,11 +17,13 @@
 // binary64 operation order of the 28-code format.
 #include <cmath>
 #include <mutex>
+#include <vector>
 
 #include <cuda_fp16.h>
 
 #include "block_ops.cuh"
 #include "compress_fix.cuh"
+#include "const_upload.cuh"
 #include "rate.cuh"
 
 namespace blaz {
@@ -423,13 +425,15 @@ static void rate_map(int r, long double (*G)[64])
 static void rate_dec_build(int r, RateDec &dc)
 {
     const int nk = rate_keep(r);
-    static long double G[64][64];
+    std::vector<long double> Gs(64 * 64);
+    long double(*G)[64] = reinterpret_cast<long double(*)[64]>(Gs.data());
     rate_map(r, G);
     long double mx = 0.0L;
     for (int p = 0; p < 64; ++p)
         for (int t = 0; t < nk; ++t) mx = fmaxl(mx, fabsl(G[p][t]));
     const int E = (int)ceill(log2l(mx)) - (kRDBits - 1);
-    static float digit[kRDSlices][64][64];  // [slice][n = p][k = t], k >= nk zero
+    std::vector<float> ds(kRDSlices * 64 * 64);  // [slice][n = p][k = t], k >= nk zero
+    float(*digit)[64][64] = reinterpret_cast<float(*)[64][64]>(ds.data());
     for (int p = 0; p < 64; ++p)
         for (int t = 0; t < 64; ++t) {
             long double v = t < nk ? G[p][t] : 0.0L;
@@ -458,29 +462,14 @@ static void rate_dec_build(int r, RateDec &dc)
 }
 
 // The constants of rate r in this device's copy of g_rate_dec (built on the
-// host once, copied once per device on the caller's stream).
+// host once, copied once per device).
 static int rate_dec_ready(int r, cudaStream_t st)
 {
-    static std::mutex mu;
+    static std::once_flag once[8];
     static RateDec host[8];
-    static bool built[8] = {};
-    static bool uploaded[64][8] = {};
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return set_cuda_error(e);
-    if (dev < 0 || dev >= 64) return BLAZ_ERR_ARG;
-    std::lock_guard<std::mutex> lk(mu);
-    if (!built[r - 1]) {
-        rate_dec_build(r, host[r - 1]);
-        built[r - 1] = true;
-    }
-    if (!uploaded[dev][r - 1]) {
-        e = cudaMemcpyToSymbolAsync(g_rate_dec, &host[r - 1], sizeof(RateDec), (size_t)(r - 1) * sizeof(RateDec),
-                                    cudaMemcpyHostToDevice, st);
-        if (e != cudaSuccess) return set_cuda_error(e);
-        uploaded[dev][r - 1] = true;
-    }
-    return BLAZ_OK;
+    static DeviceTable tables[8];
+    std::call_once(once[r - 1], [r] { rate_dec_build(r, host[r - 1]); });
+    return tables[r - 1].ensure(g_rate_dec, &host[r - 1], sizeof(RateDec), (size_t)(r - 1) * sizeof(RateDec), st);
 }
 
 __device__ __forceinline__ void rate_mma(float (&c)[4], const uint32_t (&a)[4], uint2 b)
