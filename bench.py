@@ -470,7 +470,7 @@ def shape_and_file_extras(B, W, torch, dev):
 
 def rate_extras(B, W, torch, dev):
     """Tunable rate (the first r DCT rows and columns kept): compress,
-    decompress and add of a 4096 x 4096 bump field at r = 1, 2, 4, 8, with the
+    decompress, add and dot of 4096 x 4096 bump fields at r = 1, 2, 4, 8, with the
     compression ratio 512 / (17 + keep(r)) and the relative 2-norm error of the
     round trip.  r = 2 is also timed on the 28-code kernels for comparison."""
 
@@ -489,6 +489,7 @@ def rate_extras(B, W, torch, dev):
     ta = W.bump_field_torch(n, n, dev)
     tb = W.bump_field_torch(n, n + 1, dev)
     back = torch.empty_like(ta)
+    res = torch.empty((), dtype=torch.float64, device=dev)
     out = {}
     for r in (1, 2, 4, 8):
         ga, gb = B.compress_rate(ta, r), B.compress_rate(tb, r)
@@ -498,13 +499,15 @@ def rate_extras(B, W, torch, dev):
         out[f"r{r}"] = {"keep": B.keep_count(r), "ratio": 512.0 / (17 + B.keep_count(r)), "rel_err": err,
                         "compress_ms": timed(lambda: B.compress_rate(ta, r, out=ga)),
                         "decompress_ms": timed(lambda: B.decompress_rate(ga, out=back)),
-                        "add_ms": timed(lambda: B.add_rate(ga, gb, out=gs))}
+                        "add_ms": timed(lambda: B.add_rate(ga, gb, out=gs)),
+                        "dot_ms": timed(lambda: B.dot_rate(ga, gb, out=res))}
         del ga, gb, gs
     g2, h2 = B.compress(ta), B.compress(tb)
     s2 = B.CMat.empty(n, n, dev)
     out["r2_28code_kernels"] = {"compress_ms": timed(lambda: B.compress(ta, out=g2)),
                                 "decompress_ms": timed(lambda: B.decompress(g2, out=back)),
-                                "add_ms": timed(lambda: B.add(g2, h2, out=s2))}
+                                "add_ms": timed(lambda: B.add(g2, h2, out=s2)),
+                                "dot_ms": timed(lambda: B.dot(g2, h2, out=res))}
     out["config"] = "4096x4096 bump fields (CUDA events, 5 reps after one warm-up); rate kernels: binary64, one thread per block"
     return out
 

@@ -67,8 +67,8 @@ typedef struct blaz_cmat {
 } blaz_cmat;
 
 /* Constant tables.  The first call on a device of an entry point that
- * decompresses (blaz_decompress*, blaz_matmul*, blaz_decompress_rate) or
- * takes a dot product (blaz_dot*, blaz_dot_rowcol) copies the library's
+ * decompresses (blaz_decompress*, blaz_matmul*) or takes a dot product
+ * (blaz_dot*) copies the library's
  * fixed tables for it (slices of the decompression map, at most 44 KB) to
  * that device on `stream` and waits for the copy; later calls do not.  Make
  * that first call outside stream capture: during capture it is refused
@@ -210,6 +210,21 @@ int blaz_decompress_rate(const blaz_cmat *a, int r, double *A, int64_t lda, void
 int blaz_add_rate(const blaz_cmat *a, const blaz_cmat *b, int r, blaz_cmat *out, void *stream);
 int blaz_sub_rate(const blaz_cmat *a, const blaz_cmat *b, int r, blaz_cmat *out, void *stream);
 int blaz_scale_rate(const blaz_cmat *a, double c, int r, blaz_cmat *out, void *stream);
+/* Flattened dot <vec A_hat, vec B_hat> of two rate-r matrices of the same
+ * shape (blaz_dot's definition; result: device, one binary64; within
+ * 1e-12 sum |A_hat B_hat|; deterministic; stream-ordered scratch). */
+int blaz_dot_rate(const blaz_cmat *a, const blaz_cmat *b, int r, double *result, void *stream);
+/* Algorithm 3 at rate r: line i of A_hat times column j of B_hat
+ * (a->cols == b->rows; 0 <= i < a->rows, 0 <= j < b->cols, else
+ * BLAZ_ERR_RANGE); result: device, one binary64. */
+int blaz_dot_rowcol_rate(const blaz_cmat *a, const blaz_cmat *b, int r, int64_t i, int64_t j, double *result,
+                         void *stream);
+/* blaz_matmul and blaz_matmul_cc with rate-r operands (same modes, layouts
+ * and accuracy; the operands are decoded by the rate-r decompressor). */
+int blaz_matmul_rate(const blaz_cmat *a, int r, const double *B, int64_t ldb, int64_t m, double *C, int64_t ldc,
+                     int mode, void *stream);
+int blaz_matmul_cc_rate(const blaz_cmat *a, const blaz_cmat *b, int r, double *C, int64_t ldc, int mode,
+                        void *stream);
 
 /* Flattened dot product <vec A_hat, vec B_hat> = sum_ij A_hat_ij B_hat_ij of
  * two compressed matrices of the same shape (A_hat, B_hat the decompressed

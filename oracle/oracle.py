@@ -380,3 +380,29 @@ def add_rate(a: CMat, b: CMat, r: int, sub: bool = False) -> CMat:
 def scale_rate(a: CMat, c: float) -> CMat:
     """Algorithm 2 on rate-r blocks: f and s times c, phi and the codes kept."""
     return CMat(a.rows, a.cols, a.f * float(c), a.s * float(c), a.phi.copy(), a.code.copy())
+
+
+def dot_rate(a: CMat, b: CMat, r: int):
+    """<vec A_hat, vec B_hat> of rate-r matrices from the oracle's rate-r
+    decompression; returns (value, sum |A_hat B_hat|), both summed exactly
+    (math.fsum) over the rounded products."""
+    import math
+
+    x = (decompress_rate(a, r) * decompress_rate(b, r)).ravel()
+    return math.fsum(x), math.fsum(np.abs(x))
+
+
+def dot_rowcol_rate(a: CMat, b: CMat, r: int, i: int, j: int):
+    """Line i of A_hat times column j of B_hat at rate r (Algorithm 3's
+    result, by definition from the decompressed matrices); (value, abs sum)."""
+    import math
+
+    x = decompress_rate(a, r)[i, :] * decompress_rate(b, r)[:, j]
+    return math.fsum(x), math.fsum(np.abs(x))
+
+
+def matmul_rate(a: CMat, r: int, B):
+    """A_hat @ B at rate r, and |A_hat| @ |B| (for componentwise bounds)."""
+    Ah = decompress_rate(a, r)
+    B = np.asarray(B, dtype=np.float64)
+    return Ah @ B, np.abs(Ah) @ np.abs(B)

@@ -121,6 +121,10 @@ SIGNATURES = {
     "blaz_add_rate": (ctypes.c_int, [_DESC, _DESC, ctypes.c_int, _DESC, _P]),
     "blaz_sub_rate": (ctypes.c_int, [_DESC, _DESC, ctypes.c_int, _DESC, _P]),
     "blaz_scale_rate": (ctypes.c_int, [_DESC, ctypes.c_double, ctypes.c_int, _DESC, _P]),
+    "blaz_dot_rate": (ctypes.c_int, [_DESC, _DESC, ctypes.c_int, _P, _P]),
+    "blaz_dot_rowcol_rate": (ctypes.c_int, [_DESC, _DESC, ctypes.c_int, _I64, _I64, _P, _P]),
+    "blaz_matmul_rate": (ctypes.c_int, [_DESC, ctypes.c_int, _P, _I64, _I64, _P, _I64, ctypes.c_int, _P]),
+    "blaz_matmul_cc_rate": (ctypes.c_int, [_DESC, _DESC, ctypes.c_int, _P, _I64, ctypes.c_int, _P]),
     "blaz_cmat_download": (ctypes.c_int, [_DESC, _P, _P]),
     "blaz_cmat_upload": (ctypes.c_int, [_P, _DESC, _P]),
     "blaz_cmat_save": (ctypes.c_int, [_DESC, ctypes.c_char_p, _P]),
@@ -403,6 +407,56 @@ def blaz_scale_rate(a: CMat, c: float, out: CMat | None = None, stream=None) -> 
     da, do = a.desc(), out.desc()
     _check(lib().blaz_scale_rate(ctypes.byref(da), float(c), r, ctypes.byref(do), _stream(stream)),
            "blaz_scale_rate")
+    return out
+
+
+def blaz_dot_rate(a: CMat, b: CMat, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """<vec A_hat, vec B_hat> of two matrices of the same rate."""
+    r = _same_rate(a, b)
+    out = out if out is not None else torch.empty((), dtype=torch.float64, device=a.f.device)
+    da, db = a.desc(), b.desc()
+    _check(lib().blaz_dot_rate(ctypes.byref(da), ctypes.byref(db), r, out.data_ptr(), _stream(stream)),
+           "blaz_dot_rate")
+    return out
+
+
+def blaz_dot_rowcol_rate(a: CMat, b: CMat, i: int, j: int, out: torch.Tensor | None = None, stream=None):
+    """Line i of A_hat times column j of B_hat (Algorithm 3) at the operands' rate."""
+    r = _same_rate(a, b)
+    out = out if out is not None else torch.empty((), dtype=torch.float64, device=a.f.device)
+    da, db = a.desc(), b.desc()
+    _check(lib().blaz_dot_rowcol_rate(ctypes.byref(da), ctypes.byref(db), r, int(i), int(j), out.data_ptr(),
+                                      _stream(stream)), "blaz_dot_rowcol_rate")
+    return out
+
+
+def blaz_matmul_rate(a: CMat, B: torch.Tensor, mode: str = "fp64", out: torch.Tensor | None = None,
+                     stream=None) -> torch.Tensor:
+    r = _same_rate(a)
+    _dev_f64(B, "B")
+    if B.shape[0] != a.cols:
+        raise ValueError("inner dimensions differ")
+    m = B.shape[1]
+    if out is None:
+        out = torch.empty((a.rows, m), dtype=torch.float64, device=B.device)
+    _dev_f64(out, "out")
+    da = a.desc()
+    _check(lib().blaz_matmul_rate(ctypes.byref(da), r, B.data_ptr(), _ld(B), m, out.data_ptr(), _ld(out),
+                                  _MODES[mode], _stream(stream)), "blaz_matmul_rate")
+    return out
+
+
+def blaz_matmul_cc_rate(a: CMat, b: CMat, mode: str = "fp64", out: torch.Tensor | None = None,
+                        stream=None) -> torch.Tensor:
+    r = _same_rate(a, b)
+    if a.cols != b.rows:
+        raise ValueError("inner dimensions differ")
+    if out is None:
+        out = torch.empty((a.rows, b.cols), dtype=torch.float64, device=a.f.device)
+    _dev_f64(out, "out")
+    da, db = a.desc(), b.desc()
+    _check(lib().blaz_matmul_cc_rate(ctypes.byref(da), ctypes.byref(db), r, out.data_ptr(), _ld(out),
+                                     _MODES[mode], _stream(stream)), "blaz_matmul_cc_rate")
     return out
 
 
@@ -763,3 +817,5 @@ matmul_padded, matmul_cc_padded = blaz_matmul_padded, blaz_matmul_cc_padded
 compress_host, download, upload = blaz_compress_host, blaz_cmat_download, blaz_cmat_upload
 compress_rate, decompress_rate = blaz_compress_rate, blaz_decompress_rate
 add_rate, sub_rate, scale_rate = blaz_add_rate, blaz_sub_rate, blaz_scale_rate
+dot_rate, dot_rowcol_rate = blaz_dot_rate, blaz_dot_rowcol_rate
+matmul_rate, matmul_cc_rate = blaz_matmul_rate, blaz_matmul_cc_rate

@@ -347,6 +347,102 @@ int blaz_scale_rate(const blaz_cmat *a, double c, int r, blaz_cmat *out, void *s
     return launch_scale_rate(a, c, out, r, (cudaStream_t)stream);
 }
 
+int blaz_dot_rate(const blaz_cmat *a, const blaz_cmat *b, int r, double *result, void *stream)
+{
+    BLAZ_NVTX();
+    if (blaz_keep_count(r) < 0) return BLAZ_ERR_ARG;
+    int rc;
+    if ((rc = validate_cmat(a)) || (rc = validate_cmat(b))) return rc;
+    if ((rc = same_shape(a, b))) return rc;
+    if (!result) return BLAZ_ERR_NULL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int grid = dot_rate_grid(nblocks(a));
+    Scratch ws(st);
+    if ((rc = ws.alloc(sizeof(double) * grid + 256))) return rc;
+    double *partials = (double *)ws.p;
+    unsigned *counter = (unsigned *)((char *)ws.p + ((sizeof(double) * grid + 255) & ~(size_t)255));
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    if (nblocks(a) == 0) {
+        e = cudaMemsetAsync(result, 0, sizeof(double), st);
+        return e == cudaSuccess ? BLAZ_OK : set_cuda_error(e);
+    }
+    return launch_dot_rate(a, b, r, result, partials, counter, st);
+}
+
+int blaz_dot_rowcol_rate(const blaz_cmat *a, const blaz_cmat *b, int r, int64_t i, int64_t j, double *result,
+                         void *stream)
+{
+    BLAZ_NVTX();
+    if (blaz_keep_count(r) < 0) return BLAZ_ERR_ARG;
+    int rc;
+    if ((rc = validate_cmat(a)) || (rc = validate_cmat(b))) return rc;
+    if (a->cols != b->rows) return BLAZ_ERR_SHAPE;
+    if (!result) return BLAZ_ERR_NULL;
+    if (i < 0 || i >= a->rows || j < 0 || j >= b->cols) return BLAZ_ERR_RANGE;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int grid = rowcol_rate_grid(a->cols / 8);
+    Scratch ws(st);
+    if ((rc = ws.alloc(sizeof(double) * grid + 256))) return rc;
+    double *partials = (double *)ws.p;
+    unsigned *counter = (unsigned *)((char *)ws.p + ((sizeof(double) * grid + 255) & ~(size_t)255));
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    return launch_dot_rowcol_rate(a, b, r, i, j, result, partials, counter, st);
+}
+
+int blaz_matmul_rate(const blaz_cmat *a, int r, const double *B, int64_t ldb, int64_t m, double *C, int64_t ldc,
+                     int mode, void *stream)
+{
+    BLAZ_NVTX();
+    if (blaz_keep_count(r) < 0) return BLAZ_ERR_ARG;
+    int rc;
+    if ((rc = validate_cmat(a))) return rc;
+    if (m < 0) return BLAZ_ERR_SHAPE;
+    if (mode != BLAZ_MM_FP64 && mode != BLAZ_MM_SPLIT_BF16) return BLAZ_ERR_ARG;
+    const int64_t n = a->rows, k = a->cols;
+    if (n == 0 || m == 0) return BLAZ_OK;
+    if (!C || (k > 0 && !B)) return BLAZ_ERR_NULL;
+    if (ldc < m || (k > 0 && ldb < m)) return BLAZ_ERR_LD;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t ah_bytes = (sizeof(double) * (size_t)(n * k) + 255) & ~(size_t)255;
+    const size_t extra = mode == BLAZ_MM_SPLIT_BF16 ? split_bf16_scratch_bytes(n, k, m) : 0;
+    Scratch ws(st);
+    if ((rc = ws.alloc(ah_bytes + extra))) return rc;
+    double *Ah = (double *)ws.p;
+    if (k > 0 && (rc = launch_decompress_rate(a, r, Ah, k, st))) return rc;
+    if (mode == BLAZ_MM_SPLIT_BF16)
+        return launch_matmul_split_bf16(Ah, k, B, ldb, C, ldc, n, k, m, (char *)ws.p + ah_bytes, st);
+    return launch_gemm_fp64(Ah, k, B, ldb, C, ldc, n, k, m, st);
+}
+
+int blaz_matmul_cc_rate(const blaz_cmat *a, const blaz_cmat *b, int r, double *C, int64_t ldc, int mode,
+                        void *stream)
+{
+    BLAZ_NVTX();
+    if (blaz_keep_count(r) < 0) return BLAZ_ERR_ARG;
+    int rc;
+    if ((rc = validate_cmat(a)) || (rc = validate_cmat(b))) return rc;
+    if (a->cols != b->rows) return BLAZ_ERR_SHAPE;
+    if (mode != BLAZ_MM_FP64 && mode != BLAZ_MM_SPLIT_BF16) return BLAZ_ERR_ARG;
+    const int64_t n = a->rows, k = a->cols, m = b->cols;
+    if (n == 0 || m == 0) return BLAZ_OK;
+    if (!C) return BLAZ_ERR_NULL;
+    if (ldc < m) return BLAZ_ERR_LD;
+    cudaStream_t st = (cudaStream_t)stream;
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t ah_bytes = up(sizeof(double) * (size_t)(n * k)), bh_bytes = up(sizeof(double) * (size_t)(k * m));
+    const size_t extra = mode == BLAZ_MM_SPLIT_BF16 ? split_bf16_scratch_bytes(n, k, m) : 0;
+    Scratch ws(st);
+    if ((rc = ws.alloc(ah_bytes + bh_bytes + extra))) return rc;
+    double *Ah = (double *)ws.p, *Bh = (double *)((char *)ws.p + ah_bytes);
+    if (k > 0 && (rc = launch_decompress_rate(a, r, Ah, k, st))) return rc;
+    if (k > 0 && (rc = launch_decompress_rate(b, r, Bh, m, st))) return rc;
+    if (mode == BLAZ_MM_SPLIT_BF16)
+        return launch_matmul_split_bf16(Ah, k, Bh, m, C, ldc, n, k, m, (char *)ws.p + ah_bytes + bh_bytes, st);
+    return launch_gemm_fp64(Ah, k, Bh, m, C, ldc, n, k, m, st);
+}
+
 int blaz_dot(const blaz_cmat *a, const blaz_cmat *b, double *result, void *stream)
 {
     BLAZ_NVTX();

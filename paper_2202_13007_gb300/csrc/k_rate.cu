@@ -593,6 +593,285 @@ static int decompress_rate_ks(const blaz_cmat *a, int r, double *A, int64_t lda,
     return launch_status();
 }
 
+// ---------------------------------------------------------------------------------
+// Flattened dot <vec A_hat, vec B_hat> at rate r.  Both operands' blocks are
+// decoded on the tensor cores exactly as k_decompress_rate decodes them
+// (Y = G_r c as exact integers, A_hat_p = f + (s/phi) 2^E Y_p), 16 blocks per
+// warp, without writing them: per block pair
+//   sum_p A_hat_p B_hat_p = 64 fa fb + fa tb SB + fb ta SA + ta tb P,
+// SA = sum_p YA_p and SB (exact in int64), P = sum_p YA_p YB_p (binary64),
+// t = (s/phi) 2^E.  CTA partial sums are added in a fixed order by the last
+// CTA (deterministic).
+constexpr int kDotRateThreads = 128;
+
+__device__ __forceinline__ double rate_cta_sum(double v, double *red)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0)
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) r += red[q];
+    __syncthreads();
+    return r;  // valid in thread 0
+}
+
+// One slice-assembled output pair of the decode (exact integers).
+__device__ __forceinline__ long long rate_assemble(const int (&y)[kRDSlices][4], int e)
+{
+    const int p01 = y[0][e] * (1 << kRDBits) + y[1][e];
+    const int p23 = y[2][e] * (1 << kRDBits) + y[3][e];
+    return (long long)p01 * (1ll << (3 * kRDBits)) + (long long)p23 * (1ll << kRDBits) + y[4][e];
+}
+
+template <int KS>
+__device__ __forceinline__ void rate_decode_tile(const uint2 (*sb)[KS][8][32], const uint32_t (&a)[KS][4], int nt,
+                                                 int lane, long long (&out)[4])
+{
+    int y[kRDSlices][4];
+#pragma unroll
+    for (int sl = 0; sl < kRDSlices; ++sl) {
+        float c[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int ks = 0; ks < KS; ++ks) rate_mma(c, a[ks], sb[sl][ks][nt][lane]);
+        const float2 r01 = __fadd2_rn(make_float2(c[0], c[1]), make_float2(12582912.0f, 12582912.0f));
+        const float2 r23 = __fadd2_rn(make_float2(c[2], c[3]), make_float2(12582912.0f, 12582912.0f));
+        y[sl][0] = __float_as_int(r01.x) - 0x4B400000;
+        y[sl][1] = __float_as_int(r01.y) - 0x4B400000;
+        y[sl][2] = __float_as_int(r23.x) - 0x4B400000;
+        y[sl][3] = __float_as_int(r23.y) - 0x4B400000;
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) out[e] = rate_assemble(y, e);
+}
+
+template <int KS>
+__global__ void __launch_bounds__(kDotRateThreads)
+    k_dot_rate(int r, int64_t nb, const double *__restrict__ fa, const double *__restrict__ sa,
+               const uint8_t *__restrict__ pa, const int8_t *__restrict__ ca, const double *__restrict__ fb,
+               const double *__restrict__ sb_, const uint8_t *__restrict__ pb, const int8_t *__restrict__ cb,
+               double *__restrict__ partials, unsigned *__restrict__ counter, double *__restrict__ result)
+{
+    __shared__ uint2 sbf[kRDSlices][KS][8][32];
+    __shared__ double inv_phi_scaled[256];
+    __shared__ double red[kDotRateThreads / 32];
+    __shared__ bool last;
+    const RateDec &dc = g_rate_dec[r - 1];
+    for (int i = threadIdx.x; i < kRDSlices * KS * 8 * 32; i += blockDim.x) {
+        const int sl = i / (KS * 256), rest = i - sl * KS * 256;
+        (&sbf[sl][0][0][0])[rest] = (&dc.bfrag[sl][0][0][0])[rest];
+    }
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) inv_phi_scaled[i] = dc.inv_phi_scaled[i];
+    __syncthreads();
+    const int nk = rate_keep(r);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int64_t ngroups = (nb + 15) / 16;
+    double acc = 0.0;
+    for (int64_t grp = (int64_t)blockIdx.x * 4 + warp; grp < ngroups; grp += (int64_t)gridDim.x * 4) {
+        const int64_t b0 = grp * 16 + g, b1 = b0 + 8;
+        const bool v0 = b0 < nb, v1 = b1 < nb;
+        uint32_t xa[KS][4], xb[KS][4];
+#pragma unroll
+        for (int ks = 0; ks < KS; ++ks) {
+            xa[ks][0] = rate_code_pair(ca + b0 * nk, ks * 16 + 2 * t, nk, v0);
+            xa[ks][1] = rate_code_pair(ca + b1 * nk, ks * 16 + 2 * t, nk, v1);
+            xa[ks][2] = rate_code_pair(ca + b0 * nk, ks * 16 + 2 * t + 8, nk, v0);
+            xa[ks][3] = rate_code_pair(ca + b1 * nk, ks * 16 + 2 * t + 8, nk, v1);
+            xb[ks][0] = rate_code_pair(cb + b0 * nk, ks * 16 + 2 * t, nk, v0);
+            xb[ks][1] = rate_code_pair(cb + b1 * nk, ks * 16 + 2 * t, nk, v1);
+            xb[ks][2] = rate_code_pair(cb + b0 * nk, ks * 16 + 2 * t + 8, nk, v0);
+            xb[ks][3] = rate_code_pair(cb + b1 * nk, ks * 16 + 2 * t + 8, nk, v1);
+        }
+        // per block h (0: b0, 1: b1): sum YA, sum YB, sum YA YB over this lane's 16 positions
+        long long SA[2] = {0, 0}, SB[2] = {0, 0};
+        double P[2] = {0.0, 0.0};
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            long long ya[4], yb[4];
+            rate_decode_tile<KS>(sbf, xa, nt, lane, ya);
+            rate_decode_tile<KS>(sbf, xb, nt, lane, yb);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int h = e >> 1;
+                SA[h] += ya[e];
+                SB[h] += yb[e];
+                P[h] = fma(i64_to_double(ya[e]), i64_to_double(yb[e]), P[h]);
+            }
+        }
+        // the quad (t = 0..3) holds all 64 positions of both blocks
+#pragma unroll
+        for (int o = 1; o < 4; o <<= 1) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                SA[h] += __shfl_xor_sync(0xffffffffu, SA[h], o);
+                SB[h] += __shfl_xor_sync(0xffffffffu, SB[h], o);
+                P[h] += __shfl_xor_sync(0xffffffffu, P[h], o);
+            }
+        }
+        if (t < 2 && (t ? v1 : v0)) {
+            const int64_t b = t ? b1 : b0;
+            const double f_a = fa[b], f_b = fb[b];
+            const double ta = sa[b] * inv_phi_scaled[pa[b]], tb = sb_[b] * inv_phi_scaled[pb[b]];
+            const double sA = i64_to_double(t ? SA[1] : SA[0]), sB = i64_to_double(t ? SB[1] : SB[0]);
+            const double pp = t ? P[1] : P[0];
+            acc += fma(f_a, fma(tb, sB, 64.0 * f_b), ta * fma(tb, pp, f_b * sA));
+        }
+    }
+    const double tot = rate_cta_sum(acc, red);
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = tot;
+        __threadfence();
+        last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double v = 0.0;
+    for (int q = threadIdx.x; q < (int)gridDim.x; q += blockDim.x) v += __ldcg(partials + q);
+    const double tot2 = rate_cta_sum(v, red);
+    if (threadIdx.x == 0) {
+        *result = tot2;
+        *counter = 0u;
+    }
+}
+
+int dot_rate_grid(int64_t nb)
+{
+    const int64_t want = ((nb + 15) / 16 + 3) / 4, cap = (int64_t)num_sms() * 4;
+    return (int)(want < 1 ? 1 : (want < cap ? want : cap));
+}
+
+template <int KS>
+static int dot_rate_ks(const blaz_cmat *a, const blaz_cmat *b, int r, double *result, double *partials,
+                       unsigned *counter, cudaStream_t st)
+{
+    const int64_t nb = (a->rows / 8) * (a->cols / 8);
+    k_dot_rate<KS><<<dot_rate_grid(nb), kDotRateThreads, 0, st>>>(r, nb, a->f, a->s, a->phi, a->code, b->f, b->s,
+                                                                  b->phi, b->code, partials, counter, result);
+    return launch_status();
+}
+
+int launch_dot_rate(const blaz_cmat *a, const blaz_cmat *b, int r, double *result, double *partials,
+                    unsigned *counter, cudaStream_t st)
+{
+    int rc = rate_dec_ready(r, st);
+    if (rc) return rc;
+    switch ((rate_keep(r) + 15) / 16) {
+    case 1: return dot_rate_ks<1>(a, b, r, result, partials, counter, st);
+    case 2: return dot_rate_ks<2>(a, b, r, result, partials, counter, st);
+    case 3: return dot_rate_ks<3>(a, b, r, result, partials, counter, st);
+    default: return dot_rate_ks<4>(a, b, r, result, partials, counter, st);
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Algorithm 3 at rate r: line i of A_hat times column j of B_hat, decoding
+// only that line of each block (i, kb) and that column of each block (kb, j)
+// with rows of G_r (binary64 copies of the long double map), one thread per
+// k-block; CTA partials added in order by the last CTA.
+struct RateG {
+    double G[8][64][64];  // [r-1][p][t], t < keep(r)
+    double inv_phi[256];
+};
+__device__ RateG g_rate_g;
+
+static int rate_g_ready(cudaStream_t st)
+{
+    static std::once_flag once;
+    static RateG host;
+    static DeviceTable table;
+    std::call_once(once, [] {
+        std::vector<long double> Gs(64 * 64);
+        long double(*G)[64] = reinterpret_cast<long double(*)[64]>(Gs.data());
+        for (int r = 1; r <= 8; ++r) {
+            rate_map(r, G);
+            for (int p = 0; p < 64; ++p)
+                for (int t = 0; t < 64; ++t) host.G[r - 1][p][t] = t < rate_keep(r) ? (double)G[p][t] : 0.0;
+        }
+        host.inv_phi[0] = 0.0;
+        for (int p = 1; p < 256; ++p) host.inv_phi[p] = 1.0 / (double)p;
+    });
+    return table.ensure(&g_rate_g, &host, sizeof(RateG), 0, st);
+}
+
+__global__ void __launch_bounds__(256)
+    k_dot_rowcol_rate(int r, int64_t nkb, int64_t nbc_a, int64_t nbc_b, int64_t i, int64_t j,
+                      const double *__restrict__ fa, const double *__restrict__ sa, const uint8_t *__restrict__ pa,
+                      const int8_t *__restrict__ ca, const double *__restrict__ fb, const double *__restrict__ sb,
+                      const uint8_t *__restrict__ pb, const int8_t *__restrict__ cb, double *__restrict__ partials,
+                      unsigned *__restrict__ counter, double *__restrict__ result)
+{
+    __shared__ double Gr[8][64], Gc[8][64], inv_phi[256];
+    __shared__ double red[8];
+    __shared__ bool last;
+    const int nk = rate_keep(r);
+    const int64_t bi = i / 8, bj = j / 8;
+    const int ri = (int)(i % 8), cj = (int)(j % 8);
+    for (int e = threadIdx.x; e < 8 * 64; e += blockDim.x) {
+        const int q = e >> 6, t = e & 63;
+        Gr[q][t] = g_rate_g.G[r - 1][ri * 8 + q][t];
+        Gc[q][t] = g_rate_g.G[r - 1][q * 8 + cj][t];
+    }
+    for (int e = threadIdx.x; e < 256; e += blockDim.x) inv_phi[e] = g_rate_g.inv_phi[e];
+    __syncthreads();
+    double acc = 0.0;
+    for (int64_t kb = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; kb < nkb; kb += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t ba = bi * nbc_a + kb, bb = kb * nbc_b + bj;
+        const int8_t *xa = ca + ba * nk, *xb = cb + bb * nk;
+        double ya[8] = {0, 0, 0, 0, 0, 0, 0, 0}, yb[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int t = 0; t < nk; ++t) {
+            const double ua = (double)__ldg(xa + t), ub = (double)__ldg(xb + t);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                ya[q] = fma(Gr[q][t], ua, ya[q]);
+                yb[q] = fma(Gc[q][t], ub, yb[q]);
+            }
+        }
+        const double ta = sa[ba] * inv_phi[pa[ba]], tb = sb[bb] * inv_phi[pb[bb]];
+        const double f_a = fa[ba], f_b = fb[bb];
+        double blk = 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) blk = fma(fma(ta, ya[q], f_a), fma(tb, yb[q], f_b), blk);
+        acc += blk;
+    }
+    const double tot = rate_cta_sum(acc, red);
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = tot;
+        __threadfence();
+        last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double v = 0.0;
+    for (int q = threadIdx.x; q < (int)gridDim.x; q += blockDim.x) v += __ldcg(partials + q);
+    const double tot2 = rate_cta_sum(v, red);
+    if (threadIdx.x == 0) {
+        *result = tot2;
+        *counter = 0u;
+    }
+}
+
+int rowcol_rate_grid(int64_t nkb)
+{
+    const int64_t want = (nkb + 255) / 256, cap = (int64_t)num_sms();
+    return (int)(want < 1 ? 1 : (want < cap ? want : cap));
+}
+
+int launch_dot_rowcol_rate(const blaz_cmat *a, const blaz_cmat *b, int r, int64_t i, int64_t j, double *result,
+                           double *partials, unsigned *counter, cudaStream_t st)
+{
+    int rc = rate_g_ready(st);
+    if (rc) return rc;
+    const int64_t nkb = a->cols / 8;
+    k_dot_rowcol_rate<<<rowcol_rate_grid(nkb), 256, 0, st>>>(r, nkb, a->cols / 8, b->cols / 8, i, j, a->f, a->s,
+                                                            a->phi, a->code, b->f, b->s, b->phi, b->code, partials,
+                                                            counter, result);
+    return launch_status();
+}
+
 // Algorithm 1 (kSub: the subtraction) on rate-r blocks, one block per
 // thread, with the binary64 arithmetic of add_block_fast (block_ops.cuh):
 // beta_1, beta_2 exact in binary64, each code decided in fp32 under the

@@ -176,3 +176,67 @@ def test_add_rate_structural_ties(B, r):
     assert_same(B.sub_rate(ga, ga), O.add_rate(oa, oa, r, sub=True))
     assert_same(B.add_rate(ga, gb), O.add_rate(oa, ob, r))
     assert_same(B.sub_rate(gb, ga), O.add_rate(ob, oa, r, sub=True))
+
+
+@pytest.mark.parametrize("r", RATES)
+@pytest.mark.parametrize("shape", [(8, 8), (72, 136), (264, 1000)])
+def test_dot_rate(B, r, shape):
+    """Flattened dot within 1e-12 sum |A_hat B_hat|: one block, a ragged last
+    group of 16 blocks, many groups per CTA; deterministic."""
+    X = W.random_block_matrix(*shape, seed=shape[0] + r)
+    Y = W.random_block_matrix(*shape, seed=shape[1] + r, kind="noise")
+    gx, gy = B.compress_rate(dev(X), r), B.compress_rate(dev(Y), r)
+    ref, absref = O.dot_rate(O.compress_rate(X, r), O.compress_rate(Y, r), r)
+    v = float(B.dot_rate(gx, gy).item())
+    assert abs(v - ref) <= 1e-12 * absref
+    assert float(B.dot_rate(gx, gy).item()) == v
+
+
+@pytest.mark.parametrize("r", [1, 4, 8])
+def test_dot_rate_extreme_codes(B, r):
+    """Codes of +-127 everywhere (the largest slice products) and slopes of
+    both signs."""
+    X = W.random_block_matrix(64, 8 * 129, seed=5)
+    ox, oy = O.compress_rate(X, r), O.compress_rate(X[:, ::-1].copy(), r)
+    rng = np.random.default_rng(r)
+    for om in (ox, oy):
+        om.code[:] = rng.choice(np.array([-127, 127], np.int8), size=om.code.shape)
+        om.s[:] = om.s * rng.choice([-1.0, 1.0], size=om.s.shape)
+    gx, gy = B.CMat.empty(64, 8 * 129, rate=r), B.CMat.empty(64, 8 * 129, rate=r)
+    for g, om in ((gx, ox), (gy, oy)):
+        g.f.copy_(torch.from_numpy(om.f))
+        g.s.copy_(torch.from_numpy(om.s))
+        g.phi.copy_(torch.from_numpy(om.phi))
+        g.code.copy_(torch.from_numpy(om.code))
+    ref, absref = O.dot_rate(ox, oy, r)
+    assert abs(float(B.dot_rate(gx, gy).item()) - ref) <= 1e-12 * absref
+
+
+@pytest.mark.parametrize("r", [1, 2, 5, 8])
+@pytest.mark.parametrize("ij", [(17, 200), (0, 0), (255, 255), (100, 3)])
+def test_dot_rowcol_rate(B, r, ij):
+    A, Bm = W.plain_pair()
+    ga, gb = B.compress_rate(dev(A), r), B.compress_rate(dev(Bm), r)
+    ref, absref = O.dot_rowcol_rate(O.compress_rate(A, r), O.compress_rate(Bm, r), r, *ij)
+    assert abs(float(B.dot_rowcol_rate(ga, gb, *ij).item()) - ref) <= 1e-12 * absref
+
+
+@pytest.mark.parametrize("r", [1, 3, 8])
+@pytest.mark.parametrize("n,k,m", [(72, 136, 50), (256, 256, 256)])
+def test_matmul_rate(B, r, n, k, m):
+    from conftest import split_bf16_tol
+
+    A = W.random_block_matrix(n, k, seed=n + k)
+    Bd = W.smoothed_normal(k, m, seed=7)
+    ga = B.compress_rate(dev(A), r)
+    ref, absref = O.matmul_rate(O.compress_rate(A, r), r, Bd)
+    got = B.matmul_rate(ga, dev(Bd)).cpu().numpy()
+    assert np.all(np.abs(got - ref) <= 1e-12 * absref)
+    got = B.matmul_rate(ga, dev(Bd), mode="split_bf16").cpu().numpy()
+    assert np.all(np.abs(got - ref) <= split_bf16_tol(k) * absref)
+    # compressed x compressed at the same rate
+    Y = W.random_block_matrix(k, m + (-m % 8), seed=k)
+    gy = B.compress_rate(dev(Y), r)
+    ref2, abs2 = O.matmul_rate(O.compress_rate(A, r), r, O.decompress_rate(O.compress_rate(Y, r), r))
+    got2 = B.matmul_cc_rate(ga, gy).cpu().numpy()
+    assert np.all(np.abs(got2 - ref2) <= 1e-12 * abs2)

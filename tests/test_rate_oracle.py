@@ -125,3 +125,40 @@ def test_more_coefficients_lower_the_error_on_a_smooth_field():
     assert errs[0] > errs[1] > errs[2] >= errs[3]
     assert errs[3] < 0.05
 
+
+
+def test_rate_two_dots_and_products_are_the_paper_formats():
+    """At r = 2 the rate-r dot, line x column and product equal the 28-code
+    oracle's (pinned separately), within their own rounding."""
+    A, Bm = W.plain_pair()
+    a, b = O.compress_rate(A, 2), O.compress_rate(Bm, 2)
+    v, av = O.dot_rate(a, b, 2)
+    ref, aref = O.dot(O.compress(A), O.compress(Bm))
+    assert abs(v - ref) <= 1e-14 * aref and abs(av - aref) <= 1e-14 * aref
+    for i, j in ((17, 200), (0, 0), (255, 255)):
+        v, av = O.dot_rowcol_rate(a, b, 2, i, j)
+        ref, aref = O.dot_rowcol(O.compress(A), O.compress(Bm), i, j)
+        assert abs(v - ref) <= 1e-14 * aref
+    Bd = W.smoothed_normal(256, 40, seed=3)
+    C, Cabs = O.matmul_rate(a, 2, Bd)
+    assert np.all(np.abs(C - O.matmul(O.compress(A), Bd)) <= 1e-13 * Cabs)
+
+
+def test_constant_blocks_make_the_dots_closed_form():
+    """Blocks that are constant (K = 0: s = 0) decompress exactly at every
+    rate, so <vec A_hat, vec B_hat> = 64 sum_b fa_b fb_b and line x column
+    = sum over the k-blocks of 8 fa fb."""
+    rng = np.random.default_rng(2)
+    ca, cb = rng.standard_normal((4, 6)), rng.standard_normal((6, 3))
+    A = np.kron(ca, np.ones((8, 8)))
+    Bm = np.kron(cb, np.ones((8, 8)))
+    A2 = np.kron(rng.standard_normal((4, 6)), np.ones((8, 8)))
+    import math
+    for r in (1, 3, 8):
+        a, a2, b = O.compress_rate(A, r), O.compress_rate(A2, r), O.compress_rate(Bm, r)
+        v, _ = O.dot_rate(a, a2, r)
+        assert v == math.fsum(64.0 * x for x in (ca * A2[::8, ::8]).ravel())
+        v, _ = O.dot_rowcol_rate(a, b, r, 9, 20)
+        assert v == math.fsum(8.0 * ca[1, k] * cb[k, 2] for k in range(6))
+        C, _ = O.matmul_rate(a, r, Bm)
+        assert np.allclose(C, A @ Bm, rtol=1e-15, atol=0)
