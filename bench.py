@@ -51,7 +51,7 @@ def parse():
     p.add_argument("--side", type=int, default=16384)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--workload", default="sweep", choices=["sweep", "batch", "serve", "matmul"],
+    p.add_argument("--workload", default="sweep", choices=["sweep", "batch", "serve", "matmul", "rates"],
                    help="sweep: the bandwidth-sweep step (default line); batch / serve / matmul: the batched, "
                         "served and precision (matrix product) configurations, each printed as its own line")
     p.add_argument("--mm-side", type=int, default=4096, help="matmul workload: n = k = m")
@@ -648,6 +648,25 @@ def matmul_line(args):
                                  "modes": res, "status": B.device_status()}}), flush=True)
 
 
+def rates_line(args):
+    """Tunable rate alone: the rates field of the sweep line (4096 x 4096
+    bump fields, r = 1, 2, 4, 8 and the 28-code kernels) as its own line."""
+    import torch
+
+    import workloads as W
+    from paper_2202_13007_gb300 import blaz as B
+
+    dev = torch.device("cuda", 0)
+    res = rate_extras(B, W, torch, dev)
+    r2 = res["r2"]
+    print(json.dumps({"metric": METRIC + " [tunable rate]", "value": r2["compress_ms"], "unit": "ms",
+                      "n_gpus": 1, "steps": 5, "warmup": 1, "ms_per_step": r2["compress_ms"],
+                      "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                      "data": "synthetic",
+                      "config": {"workload": "tunable rate, 4096x4096 bump fields; value: rate-2 compress ms",
+                                 "rates": res, "status": B.device_status()}}), flush=True)
+
+
 def batch_line(args):
     """2000 mixed ops (sides log-uniform over multiples of 8 in [64, 2048]) as
     one autotuned, graph-captured persistent launch, against the same ops
@@ -746,6 +765,8 @@ def main():
     if args.workload == "batch":
         batch_line(args)
         return
+    if args.workload == "rates":
+        return rates_line(args)
     if args.workload == "matmul":
         matmul_line(args)
         return

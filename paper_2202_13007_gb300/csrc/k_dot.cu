@@ -363,7 +363,7 @@ static const GramConsts &gram_consts()
 // fa + ta G_r ca (G_r: rows 8 ri .. 8 ri + 7 of the decompression map) and
 // column cj of block (kb, bj) of B is fb + tb G_c cb (rows cj, cj + 8, ...),
 // so only the needed line and column are decompressed (IPREDICT_LINES /
-// IPREDICT_COLS of Algorithm 3).  One thread per k-block; CTA partials are
+// IPREDICT_COLS of Algorithm 3).  16 lanes per k-block; CTA partials are
 // added in order by the last CTA.
 struct RowColConsts {
     double G[64][kKeep];
@@ -392,26 +392,29 @@ __global__ void __launch_bounds__(kDotThreads)
     }
     for (int e = threadIdx.x; e < 256; e += blockDim.x) inv_phi[e] = g_rowcol.inv_phi[e];
     __syncthreads();
+    // A team of 16 lanes per k-block: lane (side, q) decodes entry q of the
+    // line (side 0, block (bi, kb)) or of the column (side 1, block (kb, bj))
+    // with one row of G, so the binary64 chains of a block are spread over
+    // 16 lanes (a warp's binary64 instruction costs the same for 1 lane as
+    // for 32, and one warp per SM sub-partition issues few of them).
+    const int lane = threadIdx.x & 31, side = (lane >> 3) & 1, q = lane & 7;
+    const unsigned tmask = 0xFFFFu << (lane & 16);
+    const double *Gq = side ? Gc[q] : Gr[q];
     double acc = 0.0;
-    for (int64_t kb = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; kb < nkb; kb += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t ba = bi * nbc_a + kb, bb = kb * nbc_b + bj;
-        int8_t xa[kKeep], xb[kKeep];
-        load_codes(ca + ba * kKeep, xa);
-        load_codes(cb + bb * kKeep, xb);
-        const double ta = sa[ba] * inv_phi[pa[ba]], tb = sb[bb] * inv_phi[pb[bb]];
-        const double f_a = fa[ba], f_b = fb[bb];
-        double blk = 0.0;
+    const int64_t teams = (int64_t)gridDim.x * blockDim.x / 16;
+    for (int64_t kb = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 16; kb < nkb; kb += teams) {
+        const int64_t b = side ? kb * nbc_b + bj : bi * nbc_a + kb;
+        int8_t x[kKeep];
+        load_codes((side ? cb : ca) + b * kKeep, x);
+        double y = 0.0;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            double ya = 0.0, yb = 0.0;
+        for (int t = 0; t < kKeep; ++t) y = fma(Gq[t], i64_to_double(x[t]), y);
+        const double v = fma((side ? sb[b] : sa[b]) * inv_phi[side ? pb[b] : pa[b]], y, side ? fb[b] : fa[b]);
+        const double w = __shfl_xor_sync(tmask, v, 8);
+        double prod = side ? 0.0 : v * w;
 #pragma unroll
-            for (int t = 0; t < kKeep; ++t) {
-                ya = fma(Gr[q][t], (double)xa[t], ya);
-                yb = fma(Gc[q][t], (double)xb[t], yb);
-            }
-            blk = fma(fma(ta, ya, f_a), fma(tb, yb, f_b), blk);
-        }
-        acc += blk;
+        for (int o = 1; o < 8; o <<= 1) prod += __shfl_xor_sync(tmask, prod, o);
+        if ((lane & 15) == 0) acc += prod;
     }
     const double tot = cta_sum(acc, red);
     if (threadIdx.x == 0) {
@@ -574,7 +577,7 @@ int launch_dot(const blaz_cmat *a, const blaz_cmat *b, double *result, double *p
 
 int rowcol_grid(int64_t nkb)
 {
-    int64_t want = (nkb + kDotThreads - 1) / kDotThreads;
+    int64_t want = (nkb * 16 + kDotThreads - 1) / kDotThreads;
     const int64_t cap = (int64_t)num_sms();
     return (int)std::max<int64_t>(1, std::min(want, cap));
 }

@@ -769,7 +769,7 @@ int launch_dot_rate(const blaz_cmat *a, const blaz_cmat *b, int r, double *resul
 // ---------------------------------------------------------------------------------
 // Algorithm 3 at rate r: line i of A_hat times column j of B_hat, decoding
 // only that line of each block (i, kb) and that column of each block (kb, j)
-// with rows of G_r (binary64 copies of the long double map), one thread per
+// with rows of G_r (binary64 copies of the long double map), 16 lanes per
 // k-block; CTA partials added in order by the last CTA.
 struct RateG {
     double G[8][64][64];  // [r-1][p][t], t < keep(r)
@@ -816,25 +816,24 @@ __global__ void __launch_bounds__(256)
     }
     for (int e = threadIdx.x; e < 256; e += blockDim.x) inv_phi[e] = g_rate_g.inv_phi[e];
     __syncthreads();
+    // a team of 16 lanes per k-block, lane (side, q) decoding entry q of the
+    // line (side 0) or of the column (side 1), as k_dot_rowcol does
+    const int lane = threadIdx.x & 31, side = (lane >> 3) & 1, q = lane & 7;
+    const unsigned tmask = 0xFFFFu << (lane & 16);
+    const double *Gq = side ? Gc[q] : Gr[q];
     double acc = 0.0;
-    for (int64_t kb = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; kb < nkb; kb += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t ba = bi * nbc_a + kb, bb = kb * nbc_b + bj;
-        const int8_t *xa = ca + ba * nk, *xb = cb + bb * nk;
-        double ya[8] = {0, 0, 0, 0, 0, 0, 0, 0}, yb[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        for (int t = 0; t < nk; ++t) {
-            const double ua = (double)__ldg(xa + t), ub = (double)__ldg(xb + t);
+    const int64_t teams = (int64_t)gridDim.x * blockDim.x / 16;
+    for (int64_t kb = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 16; kb < nkb; kb += teams) {
+        const int64_t b = side ? kb * nbc_b + bj : bi * nbc_a + kb;
+        const int8_t *x = (side ? cb : ca) + b * nk;
+        double y = 0.0;
+        for (int t = 0; t < nk; ++t) y = fma(Gq[t], i64_to_double(__ldg(x + t)), y);
+        const double v = fma((side ? sb[b] : sa[b]) * inv_phi[side ? pb[b] : pa[b]], y, side ? fb[b] : fa[b]);
+        const double w = __shfl_xor_sync(tmask, v, 8);
+        double prod = side ? 0.0 : v * w;
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                ya[q] = fma(Gr[q][t], ua, ya[q]);
-                yb[q] = fma(Gc[q][t], ub, yb[q]);
-            }
-        }
-        const double ta = sa[ba] * inv_phi[pa[ba]], tb = sb[bb] * inv_phi[pb[bb]];
-        const double f_a = fa[ba], f_b = fb[bb];
-        double blk = 0.0;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) blk = fma(fma(ta, ya[q], f_a), fma(tb, yb[q], f_b), blk);
-        acc += blk;
+        for (int o = 1; o < 8; o <<= 1) prod += __shfl_xor_sync(tmask, prod, o);
+        if ((lane & 15) == 0) acc += prod;
     }
     const double tot = rate_cta_sum(acc, red);
     if (threadIdx.x == 0) {
@@ -856,7 +855,7 @@ __global__ void __launch_bounds__(256)
 
 int rowcol_rate_grid(int64_t nkb)
 {
-    const int64_t want = (nkb + 255) / 256, cap = (int64_t)num_sms();
+    const int64_t want = (nkb * 16 + 255) / 256, cap = (int64_t)num_sms();
     return (int)(want < 1 ? 1 : (want < cap ? want : cap));
 }
 
