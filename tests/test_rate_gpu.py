@@ -240,3 +240,38 @@ def test_matmul_rate(B, r, n, k, m):
     ref2, abs2 = O.matmul_rate(O.compress_rate(A, r), r, O.decompress_rate(O.compress_rate(Y, r), r))
     got2 = B.matmul_cc_rate(ga, gy).cpu().numpy()
     assert np.all(np.abs(got2 - ref2) <= 1e-12 * abs2)
+
+
+@pytest.mark.parametrize("r", [2, 8])
+def test_rate_ops_at_the_timed_size_sampled(B, r):
+    """4096 x 4096 bump fields (the size bench.py times the rate kernels at):
+    codes, phi, f and s of compress and add on 256 sampled blocks against the
+    oracle, decompression of those blocks within the bound, and the flattened
+    dot against the oracle's exact sum."""
+    n = 4096
+    X, Y = W.bump_field(n, seed=n), W.bump_field(n, seed=n + 1)
+    gx, gy = B.compress_rate(dev(X), r), B.compress_rate(dev(Y), r)
+    gs = B.add_rate(gx, gy)
+    back = B.decompress_rate(gx).cpu().numpy()
+    nbc = n // 8
+    rng = np.random.default_rng(r)
+    idx = np.unique(np.concatenate([rng.integers(0, nbc * nbc, 256), [0, nbc - 1, nbc * nbc - 1]]))
+
+    def blocks(M):
+        return np.concatenate([M[8 * (b // nbc):8 * (b // nbc) + 8, 8 * (b % nbc):8 * (b % nbc) + 8] for b in idx],
+                              axis=1)
+
+    ox, oy = O.compress_rate(blocks(X), r), O.compress_rate(blocks(Y), r)
+    for g, o in ((gx, ox), (gs, O.add_rate(ox, oy, r))):
+        f, s, phi, code = g.to_host()
+        assert np.array_equal(phi[idx], o.phi) and np.array_equal(code[idx], o.code)
+        same_bits(f[idx], o.f)
+        same_bits(s[idx], o.s)
+    ref = O.decompress_rate(ox, r)
+    scale = np.abs(ox.f) + 14 * np.abs(ox.s) * np.abs(ox.code.astype(np.float64)).sum(1) / ox.phi
+    err = np.abs(blocks(back) - ref).reshape(8, len(idx), 8).max(axis=(0, 2))
+    assert np.all(err <= 1e-12 * scale)
+    # the whole-field dot against the oracle's (every block)
+    v = float(B.dot_rate(gx, gy).item())
+    ref_v, abs_v = O.dot_rate(O.compress_rate(X, r), O.compress_rate(Y, r), r)
+    assert abs(v - ref_v) <= 1e-12 * abs_v
