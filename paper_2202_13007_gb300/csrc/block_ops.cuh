@@ -176,4 +176,33 @@ __device__ __forceinline__ void add_block_fast(int64_t b, const double *f1, cons
     for (int q = 0; q < 7; ++q) co[q] = wo[q];
 }
 
+// fp32 estimate of beta_k = RN(RN(RN(s_k / s) / phi_k) * phi) (Algorithm 1)
+// for the tiled addition (k_blockops.cu) and the rate-r addition (k_rate.cu);
+// rho = phi / phi_k, evaluated in fp32.
+//   s_k and s are truncated to fp32 after scaling both by 2^-e(s) (exponent
+//   arithmetic on the integer pipe, exact): relative error < 2^-23 each;
+//   __fdividef: < 2^-22; rho: < 2^-22; the product: < 2^-24.  So
+//   |beta - beta_k| < (2^-21 + 2^-22 + 2^-24)(1 + 2^-20) |beta_k| < 2^-20 |beta_k|
+//   (the three binary64 roundings of beta_k are below 2^-51 relative).
+// s_k == 0 gives beta = 0 exactly (beta_k is a signed zero).  Returns false
+// when s_k or s is subnormal, Inf or NaN, or when |s_k / s| leaves
+// [2^-100, 2^101): the caller then evaluates beta_k in binary64.
+__device__ __forceinline__ bool beta_f32(double sk, double ss, float rho, float &beta)
+{
+    const unsigned hk = (unsigned)__double2hiint(sk), lk = (unsigned)__double2loint(sk);
+    const unsigned hs = (unsigned)__double2hiint(ss), ls = (unsigned)__double2loint(ss);
+    if (((hk & 0x7FFFFFFFu) | lk) == 0u) {
+        beta = 0.0f;
+        return true;
+    }
+    const int ek = (int)((hk >> 20) & 0x7FF), es = (int)((hs >> 20) & 0x7FF);
+    const int d = ek - es;
+    if (ek == 0 || ek == 0x7FF || es == 0 || es == 0x7FF || d < -100 || d > 100) return false;
+    const float xk = __uint_as_float((hk & 0x80000000u) | ((unsigned)(d + 127) << 23) |
+                                     (__funnelshift_l(lk, hk, 3) & 0x7FFFFFu));
+    const float xs = __uint_as_float((hs & 0x80000000u) | (127u << 23) | (__funnelshift_l(ls, hs, 3) & 0x7FFFFFu));
+    beta = __fmul_rn(__fdividef(xk, xs), rho);
+    return true;
+}
+
 }  // namespace blaz

@@ -872,14 +872,17 @@ int launch_dot_rowcol_rate(const blaz_cmat *a, const blaz_cmat *b, int r, int64_
 }
 
 // Algorithm 1 (kSub: the subtraction) on rate-r blocks, one block per
-// thread, with the binary64 arithmetic of add_block_fast (block_ops.cuh):
-// beta_1, beta_2 exact in binary64, each code decided in fp32 under the
-// bound proven there, so that only the undecided codes need binary64.  The
-// CTA stages the codes of its 128 blocks in shared memory with word copies
-// (coalesced), queues the undecided codes and evaluates them densely
-// (binary64 costs a warp the same for one lane as for 32), then writes its
-// output codes back with word copies.  Every input of a block is read before
-// its outputs are written, so out may alias a or b.
+// thread, with the arithmetic of the tiled 28-code addition (k_blockops.cu):
+// beta_1, beta_2 estimated in fp32 (beta_f32, within 2^-20) and each code
+// decided from v = fl(beta_1 c_1 +- beta_2 c_2) when
+// [v - E, v + E], E = 1.25 2^-19 (|beta_1| |c_1| + |beta_2| |c_2|) + 2^-100,
+// truncates to one code.  The CTA stages the codes of its 128 blocks in
+// shared memory with word copies (coalesced) and queues the undecided codes;
+// then, densely (a binary64 instruction costs a warp the same for one lane
+// as for 32), the blocks with a queued code get their exact binary64 beta_k
+// as Algorithm 1 forms them, and the queued codes their binary64 value.  The
+// output codes go back as words.  Every input of a block is read before its
+// outputs are written, so out may alias a or b.
 constexpr int kAddRateThreads = 128;
 
 __device__ __forceinline__ void rate_stage_in(uint8_t *__restrict__ dst, const int8_t *__restrict__ src, int bytes)
@@ -904,18 +907,25 @@ __global__ void __launch_bounds__(kAddRateThreads)
                const double *f2, const double *s2, const uint8_t *p2, const int8_t *c2, double *f, double *s,
                uint8_t *p, int8_t *c)
 {
-    // dynamic shared memory: codes of a (reused for the output), codes of b,
-    // beta_1 and beta_2 per block, the queue of undecided codes
+    // dynamic shared memory: per block slot the exact beta_1, beta_2 (when
+    // needed), the inputs s_1, s_2 and phi_1, phi_2, phi; the codes of a
+    // (reused for the output) and of b; the queue of undecided codes
     extern __shared__ double add_rate_smem[];
     double2 *sBeta = reinterpret_cast<double2 *>(add_rate_smem);
-    const int nk = rate_keep(r);
-    uint8_t *sA = reinterpret_cast<uint8_t *>(sBeta + kAddRateThreads);
+    double2 *sS = sBeta + kAddRateThreads;
+    uint32_t *sPhi = reinterpret_cast<uint32_t *>(sS + kAddRateThreads);
+    uint32_t *sNeed = sPhi + kAddRateThreads;
+    uint8_t *sA = reinterpret_cast<uint8_t *>(sNeed + kAddRateThreads);
     uint8_t *sB = sA + kAddRateThreads * 64;
     uint32_t *sQ = reinterpret_cast<uint32_t *>(sB + kAddRateThreads * 64);
-    __shared__ unsigned sCount;
+    __shared__ unsigned sCount, sNeedCount;
+    const int nk = rate_keep(r);
     for (int64_t b0 = blockIdx.x * (int64_t)kAddRateThreads; b0 < nb; b0 += (int64_t)gridDim.x * kAddRateThreads) {
         const int nvalid = (int)(nb - b0 < kAddRateThreads ? nb - b0 : kAddRateThreads);
-        if (threadIdx.x == 0) sCount = 0u;
+        if (threadIdx.x == 0) {
+            sCount = 0u;
+            sNeedCount = 0u;
+        }
         rate_stage_in(sA, c1 + b0 * nk, nvalid * nk);
         rate_stage_in(sB, c2 + b0 * nk, nvalid * nk);
         __syncthreads();
@@ -933,36 +943,37 @@ __global__ void __launch_bounds__(kAddRateThreads)
             if (ss == 0.0) {
                 for (int t = 0; t < nk; ++t) ca[t] = 0;
             } else {
-                const double a1 = ddiv(sa, ss), a2 = ddiv(sb, ss);
-                const double phd = i64_to_double(ph);
-                const double b1 = dmul(div_small_int(a1, pa), phd);
-                const double b2 = dmul(div_small_int(a2, pb), phd);
-                sBeta[tid] = make_double2(b1, b2);
-                const unsigned e1 = ((unsigned)__double2hiint(b1) >> 20) & 0x7FF;
-                const unsigned e2 = ((unsigned)__double2hiint(b2) >> 20) & 0x7FF;
-                const bool fast = e1 < 1023 + 100 && e2 < 1023 + 100;
-                const float b1f = trunc_to_f32(b1), b2f = trunc_to_f32(b2);
-                const float ab1 = fabsf(b1f), ab2 = fabsf(b2f);
-                for (int t = 0; t < nk; ++t) {
+                const float phf = (float)ph;
+                float b1f = 0.0f, b2f = 0.0f;
+                const bool ok = beta_f32(sa, ss, __fdividef(phf, (float)pa), b1f) &
+                                beta_f32(sb, ss, __fdividef(phf, (float)pb), b2f);
+                const float e1 = 0x1.4p-19f * fabsf(b1f), e2 = 0x1.4p-19f * fabsf(b2f);
+                const float nb2 = kSub ? -b2f : b2f;
+                bool need = false;
+                // codes in rotated order from t = c tid mod nk, with c chosen per
+                // rate so that the lanes' byte accesses (slots nk bytes apart)
+                // fall on distinct banks (at most 2 words per bank; 16 for
+                // r = 8 without rotation)
+                const int rot = (0x23011100 >> (4 * (r - 1))) & 0xF;  // c = 0 0 1 1 1 0 3 2 for r = 1..8
+                int t = (rot * tid) % nk;
+                for (int k = 0; k < nk; ++k, t = (t + 1 == nk) ? 0 : t + 1) {
                     const int i1 = (int)(int8_t)ca[t], i2 = (int)(int8_t)cb[t];
-                    int code = 0;
-                    bool done = false;
-                    if (fast) {
-                        const float x1 = small_int_to_float(i1), x2 = small_int_to_float(i2);
-                        const float v = fmaf(b1f, x1, kSub ? -(b2f * x2) : b2f * x2);
-                        const float E = 0x1p-21f * fmaf(ab1, fabsf(x1), ab2 * fabsf(x2)) + 0x1p-22f * fabsf(v) + 0x1p-100f;
-                        const float lo = v - E, hi = v + E;
-                        if (lo >= 127.0f) { code = 127; done = true; }
-                        else if (hi <= -127.0f) { code = -127; done = true; }
-                        else {
-                            const int tl = (int)truncf(lo), th = (int)truncf(hi);
-                            if (tl == th) { code = tl; done = true; }
-                        }
-                    }
-                    if (!done)
-                        sQ[atomicAdd(&sCount, 1u)] = (uint32_t)tid | ((uint32_t)t << 8) | ((uint32_t)(uint8_t)i1 << 16) |
-                                                     ((uint32_t)(uint8_t)i2 << 24);
-                    ca[t] = (uint8_t)(int8_t)code;
+                    const float x1 = small_int_to_float(i1), x2 = small_int_to_float(i2);
+                    const float v = fmaf(b1f, x1, nb2 * x2);
+                    const float E = fmaf(e1, fabsf(x1), fmaf(e2, fabsf(x2), 0x1p-100f));
+                    const float hi = v + E, lo = fmaf(E, -1.0f, v);
+                    const int l = min(127, max(-127, (int)truncf(lo))), h = min(127, max(-127, (int)truncf(hi)));
+                    const bool undecided = !ok || l != h;
+                    if (undecided)
+                        sQ[atomicAdd(&sCount, 1u)] = (uint32_t)tid | ((uint32_t)t << 8) |
+                                                     ((uint32_t)(uint8_t)i1 << 16) | ((uint32_t)(uint8_t)i2 << 24);
+                    need |= undecided;
+                    ca[t] = (uint8_t)(int8_t)(undecided ? 0 : l);
+                }
+                if (need) {
+                    sS[tid] = make_double2(sa, sb);
+                    sPhi[tid] = (uint32_t)pa | ((uint32_t)pb << 8) | ((uint32_t)ph << 16);
+                    sNeed[atomicAdd(&sNeedCount, 1u)] = (uint32_t)tid;
                 }
             }
             f[b] = fs;
@@ -970,7 +981,19 @@ __global__ void __launch_bounds__(kAddRateThreads)
             p[b] = (uint8_t)ph;
         }
         __syncthreads();
-        // the undecided codes, densely, in add_block's binary64 order
+        // exact beta_k of the blocks with a queued code (Algorithm 1 in binary64)
+        for (unsigned k = threadIdx.x; k < sNeedCount; k += kAddRateThreads) {
+            const int slot = (int)sNeed[k];
+            const double2 sv = sS[slot];
+            const uint32_t pp = sPhi[slot];
+            const int pa = (int)(pp & 0xFFu), pb = (int)((pp >> 8) & 0xFFu), ph = (int)(pp >> 16);
+            const double ss = dadd(sv.x, sv.y);
+            const double a1 = ddiv(sv.x, ss), a2 = ddiv(sv.y, ss);
+            const double phd = i64_to_double(ph);
+            sBeta[slot] = make_double2(dmul(div_small_int(a1, pa), phd), dmul(div_small_int(a2, pb), phd));
+        }
+        __syncthreads();
+        // the queued codes, densely, in add_block's binary64 order
         for (unsigned q = threadIdx.x; q < sCount; q += kAddRateThreads) {
             const uint32_t e = sQ[q];
             const int slot = (int)(e & 0xFFu), t = (int)((e >> 8) & 0xFFu);
@@ -985,8 +1008,8 @@ __global__ void __launch_bounds__(kAddRateThreads)
     }
 }
 
-constexpr size_t kAddRateSmem = sizeof(double2) * kAddRateThreads + 2 * kAddRateThreads * 64 +
-                                sizeof(uint32_t) * kAddRateThreads * 64;
+constexpr size_t kAddRateSmem = (sizeof(double2) * 2 + sizeof(uint32_t) * 2) * kAddRateThreads +
+                                2 * kAddRateThreads * 64 + sizeof(uint32_t) * kAddRateThreads * 64;
 
 // Algorithm 2 on rate-r blocks: f and s times c; phi and the codes copied
 // (untouched when out is a), the codes as 4-byte words (both arrays are

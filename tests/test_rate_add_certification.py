@@ -1,6 +1,14 @@
-"""The rate-r addition (and the per-block addition kernel used for unaligned
-code arrays) forms beta_1, beta_2 exactly in binary64 as Algorithm 1 does,
-truncates them to fp32 and decides each code from
+"""Two fp32 decision rules of Algorithm 1, checked against the oracle at
+every rate.
+
+The rate-r addition uses the tiled 28-code kernel's rule (fp32 estimates of
+beta_k, bound 1.25 2^-19 (...) + 2^-100); test_add_certification's numpy
+emulation of that rule works on any number of codes per block and is reused
+here on rate-r operands (test_rate_add_uses_the_tiled_rule).
+
+The per-block addition kernel (used for unaligned code arrays) forms beta_1,
+beta_2 exactly in binary64 as Algorithm 1 does, truncates them to fp32 and
+decides each code from
     v = fl32(fma(b1f, c1, +-fl32(b2f c2))),
     E = 2^-21 fma(|b1f|, |c1|, fl32(|b2f| |c2|)) + 2^-22 |v| + 2^-100,
 when [v - E, v + E] truncates to one code (or lies beyond +-127), and in
@@ -15,6 +23,7 @@ import pytest
 
 import oracle as O
 import workloads as W
+from test_add_certification import kernel_codes
 
 F32 = np.float32
 
@@ -95,3 +104,22 @@ def test_rate_add_decisions_on_random_slopes_phi_and_codes():
     b.s[n // 4: n // 4 + 64] = 0.0
     check(a, b, r)
     check(a, b, r, sub=True)
+
+
+@pytest.mark.parametrize("r", [1, 2, 4, 8])
+def test_rate_add_uses_the_tiled_rule(r):
+    a = O.compress_rate(W.bump_field(256, 5, rows=128), r)
+    b = O.compress_rate(W.bump_field(256, 6, rows=128), r)
+    pairs = [(a, b), (a, a), (O.add_rate(a, a, r), a)] + [(a, O.scale_rate(b, c)) for c in (-0.97, -1.0, 1e-300, 1e300)]
+    worst = 0.0
+    for n_pair, (x, y) in enumerate(pairs):
+        for sub in (False, True):
+            ref = O.add_rate(x, y, r, sub=sub)
+            for p1 in (-1.0, 0.0, 1.0):
+                for p2 in (-1.0, 0.0, 1.0):
+                    code, decided = kernel_codes(x, y, p1, p2, sub)
+                    bad = decided & (code != ref.code.astype(np.float64))
+                    assert not bad.any(), (np.argwhere(bad)[:5], code[bad][:5], ref.code[bad][:5])
+                    if n_pair < 3:   # beyond: partners scaled out of the fp32 beta range go to binary64
+                        worst = max(worst, 1.0 - decided.mean())
+    assert worst < 0.5
