@@ -162,3 +162,22 @@ def test_constant_blocks_make_the_dots_closed_form():
         assert v == math.fsum(8.0 * ca[1, k] * cb[k, 2] for k in range(6))
         C, _ = O.matmul_rate(a, r, Bm)
         assert np.allclose(C, A @ Bm, rtol=1e-15, atol=0)
+
+
+def test_worked_example_at_every_rate():
+    """Sec. II, Example 5 prints all 64 re-scaled, truncated DCT values P' of
+    the example block (the kept 28 and the one other nonzero entry, (4,4)
+    1-indexed, that the 28-code format drops).  At rate r the stored codes
+    must be those entries of P' in the rate's order; r = 4 keeps the (4,4)
+    entry, and phi and f are the example's at every rate."""
+    from conftest import load_golden
+
+    g = load_golden("example_xy.txt")
+    A = np.fromfunction(lambda i, j: (0.1 * i) * (0.1 * j), (8, 8))
+    P1 = np.array([[int(x) for x in row] for row in g["P'"]])
+    for r in range(1, 9):
+        c = O.compress_rate(A, r)
+        want = [P1[i, j] for i, j in kept_set(r)]
+        assert list(c.code[0]) == want, r
+        assert c.phi[0] == int(g["phi"][0][0]) and c.f[0] == float(g["f"][0][0])
+    assert (3, 3) not in kept_set(3) and O.compress_rate(A, 4).code[0][kept_set(4).index((3, 3))] == 1
