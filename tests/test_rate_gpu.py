@@ -275,3 +275,18 @@ def test_rate_ops_at_the_timed_size_sampled(B, r):
     v = float(B.dot_rate(gx, gy).item())
     ref_v, abs_v = O.dot_rate(O.compress_rate(X, r), O.compress_rate(Y, r), r)
     assert abs(v - ref_v) <= 1e-12 * abs_v
+
+
+def test_worked_example_on_the_gpu_at_every_rate(B):
+    """Sec. II, Example 5's printed P' (all 64 entries) in each rate's order,
+    computed by the GPU compressor."""
+    from conftest import load_golden
+
+    g = load_golden("example_xy.txt")
+    P1 = np.array([[int(x) for x in row] for row in g["P'"]])
+    A = np.fromfunction(lambda i, j: (0.1 * i) * (0.1 * j), (8, 8))
+    for r in RATES:
+        f, s, phi, code = B.compress_rate(dev(A), r).to_host()
+        rows = [(i, j) for i in range(r) for j in range(8)] + [(i, j) for i in range(r, 8) for j in range(r)]
+        assert list(code[0]) == [P1[i, j] for i, j in rows], r
+        assert phi[0] == int(g["phi"][0][0])
