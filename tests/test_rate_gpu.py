@@ -290,3 +290,20 @@ def test_worked_example_on_the_gpu_at_every_rate(B):
         rows = [(i, j) for i in range(r) for j in range(8)] + [(i, j) for i in range(r, 8) for j in range(r)]
         assert list(code[0]) == [P1[i, j] for i, j in rows], r
         assert phi[0] == int(g["phi"][0][0])
+
+
+@pytest.mark.parametrize("r", [1, 5, 8])
+def test_decompress_rate_into_strided_views(B, r):
+    """Output rows longer than the matrix (lda = cols + 8) and a base 8 bytes
+    off a 16-byte boundary (no vector stores): same values as the contiguous
+    decompression, the entries outside the view untouched."""
+    X = W.random_block_matrix(72, 136, seed=r)
+    g = B.compress_rate(dev(X), r)
+    want = B.decompress_rate(g).cpu().numpy()
+    for off in (0, 1):
+        big = torch.full((72, 136 + 8 + off), -7.0, dtype=torch.float64, device="cuda")
+        view = big[:, off:off + 136]
+        B.decompress_rate(g, out=view)
+        got = big.cpu().numpy()
+        assert np.array_equal(got[:, off:off + 136], want)
+        assert np.all(got[:, :off] == -7.0) and np.all(got[:, off + 136:] == -7.0)
