@@ -237,7 +237,7 @@ __device__ __forceinline__ void rate_append(bool want, T value, T *__restrict__ 
 }
 
 template <bool kVec>
-__global__ void __launch_bounds__(kRateThreads, 2)
+__global__ void __launch_bounds__(kRateThreads, 3)
     k_compress_rate_fast(const double *__restrict__ A, int64_t lda, int64_t nbc, int64_t nb, int r,
                          double *__restrict__ f, double *__restrict__ s, uint8_t *__restrict__ phi,
                          int8_t *__restrict__ code, uint4 *__restrict__ code_list, unsigned *__restrict__ code_count,
