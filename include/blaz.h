@@ -191,9 +191,14 @@ int blaz_scale(const blaz_cmat *a, double c, blaz_cmat *out, void *stream);
  *
  * A rate-r matrix uses the blaz_cmat descriptor with code holding
  * nb x keep(r) bytes (row-major [nb][keep(r)]); the rate is not stored in the
- * descriptor and every call names it.  r outside 1..8: BLAZ_ERR_ARG.  The
- * kernels are plain binary64, one thread per block (compress, add, sub and
- * scale bit-exact with the same binary64 operation order as above). */
+ * descriptor and every call names it; a code array shorter than
+ * nb x keep(r) bytes is the caller's error (not detectable here).  The file
+ * functions, the padded-shape variants, the batch planner and the server
+ * take the 28-code format only.  r outside 1..8: BLAZ_ERR_ARG.  Results:
+ * compress, add, sub and scale bit-exact with the binary64 operation order
+ * above (the kernels reuse the 28-code format's certified fp32 decisions
+ * with exact binary64 fix-ups, and its tensor-core decoding); decompression,
+ * dots and products within that format's tolerances. */
 
 /* keep(r), or -1 when r is outside 1..8.  No GPU needed. */
 int blaz_keep_count(int r);
