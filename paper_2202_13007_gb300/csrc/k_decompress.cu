@@ -97,6 +97,20 @@ __device__ __forceinline__ uint32_t code_pair(const int8_t *__restrict__ c, int 
     return *reinterpret_cast<const uint32_t *>(&h);
 }
 
+// |v| < 2^62 -> binary64 with the significand truncated to 53 bits (exact for
+// |v| < 2^53), on the integer pipe: normalize left by the leading-zero count,
+// one fixed right shift puts the leading one on bit 52, where it carries into
+// the exponent field (hence 1085 - lz rather than 1086 - lz).
+__device__ __forceinline__ double dec_to_double(long long v)
+{
+    const unsigned long long sign = (unsigned long long)v & 0x8000000000000000ull;
+    const unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
+    const int lz = __clzll((long long)a);
+    const unsigned long long m = (a << (lz & 63)) >> 11;
+    const unsigned long long bits = sign | (m + ((unsigned long long)(1085 - lz) << 52));
+    return a ? __longlong_as_double((long long)bits) : 0.0;
+}
+
 template <bool kVec>
 __global__ void __launch_bounds__(128)
     k_decompress(const double *__restrict__ f, const double *__restrict__ s,
@@ -173,8 +187,8 @@ __global__ void __launch_bounds__(128)
             for (int h = 0; h < 2; ++h) {
                 if (!(h ? vB : vA)) continue;
                 // M00 = f by definition (row 0 of G is zero), also when s is not finite
-                const double o0 = (nt == 0 && t == 0) ? fb[h] : fma(ts[h], i64_to_double(acc[2 * h]), fb[h]);
-                const double o1 = fma(ts[h], i64_to_double(acc[2 * h + 1]), fb[h]);
+                const double o0 = (nt == 0 && t == 0) ? fb[h] : fma(ts[h], dec_to_double(acc[2 * h]), fb[h]);
+                const double o1 = fma(ts[h], dec_to_double(acc[2 * h + 1]), fb[h]);
                 double *p = pb[h] + nt * lda;
                 if (inside[h]) {
                     if (kVec) {
