@@ -243,7 +243,8 @@ int blaz_dot(const blaz_cmat *a, const blaz_cmat *b, double *result, void *strea
  * memory: a framework or server that owns all of HBM through its own
  * allocator or budget, a device or driver without stream-ordered allocation,
  * or a step that must not risk an allocation failure midway).
- * Same arguments, result and determinism as blaz_dot.  Its scratch is a fixed
+ * Same arguments, checks, status codes, result and determinism as blaz_dot
+ * (bit-identical results on the same inputs).  Its scratch is a fixed
  * 8448-byte array in the library's device memory (every GPU that loads the
  * library holds it until the process exits): 1024 per-CTA partial sums and a
  * counter.  A call needs one partial per CTA it launches, min(ceil(nb/256),

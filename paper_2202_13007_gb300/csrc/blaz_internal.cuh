@@ -162,6 +162,9 @@ int launch_scale(const blaz_cmat *a, double c, const blaz_cmat *out, cudaStream_
 // partial blocks are summed over their logical entries by a second kernel.
 int launch_dot(const blaz_cmat *a, const blaz_cmat *b, double *result, double *partials, unsigned *counter,
                int64_t max_ctas, cudaStream_t st, int64_t rows = -1, int64_t cols = -1);
+// Largest grid of the flattened dot (k_dot_tc): one partial sum per CTA, so
+// this is also the number of partial-sum slots every caller provides.
+constexpr int kDotMaxCtas = 1024;
 int dot_grid(int64_t nb);
 int rowcol_grid(int64_t nkb);
 int launch_dot_rowcol(const blaz_cmat *a, const blaz_cmat *b, int64_t i, int64_t j, double *result,

@@ -16,9 +16,9 @@
 
 namespace blaz {
 
-// Maximum number of per-CTA partial sums the static scratch holds.
-constexpr int kNoAllocMaxCtas = 1024;
-constexpr size_t kNoAllocCounterOffset = kNoAllocMaxCtas * sizeof(double);
+// The static scratch holds one partial sum for each CTA of the largest grid
+// the flattened dot launches (kDotMaxCtas), then the arrival counter.
+constexpr size_t kNoAllocCounterOffset = kDotMaxCtas * sizeof(double);
 constexpr size_t kNoAllocBytes = kNoAllocCounterOffset + 256;
 
 // Scratch of blaz_dot_noalloc: [0, 8192) partial sums, then the 32-bit arrival
@@ -61,18 +61,17 @@ using namespace blaz;
 
 extern "C" int blaz_dot_noalloc(const blaz_cmat *a, const blaz_cmat *b, double *result, void *stream)
 {
-    if (!a || !b || !result) return BLAZ_ERR_NULL;
-    if (a->rows < 0 || a->cols < 0 || a->rows % 8 || a->cols % 8) return BLAZ_ERR_SHAPE;
+    BLAZ_NVTX();
+    // The same descriptor checks as blaz_dot: sides, block-count limits, NULL
+    // arrays and alignment, so no launch ever sees an overflowing shape.
+    int rc;
+    if ((rc = validate_cmat(a)) || (rc = validate_cmat(b))) return rc;
     if (a->rows != b->rows || a->cols != b->cols) return BLAZ_ERR_SHAPE;
+    if (!result) return BLAZ_ERR_NULL;
     const int64_t nb = (a->rows / 8) * (a->cols / 8);
-    if (nb > 0 && (!a->f || !a->s || !a->phi || !a->code || !b->f || !b->s || !b->phi || !b->code))
-        return BLAZ_ERR_NULL;
-    if ((uintptr_t)a->f % 8 || (uintptr_t)a->s % 8 || (uintptr_t)a->code % 4 || (uintptr_t)b->f % 8 ||
-        (uintptr_t)b->s % 8 || (uintptr_t)b->code % 4)
-        return BLAZ_ERR_ARG;
     // The launch needs one partial-sum slot per CTA.
     const int grid = dot_grid(nb);
-    if (grid > kNoAllocMaxCtas) return BLAZ_ERR_RANGE;
+    if (grid > kDotMaxCtas) return BLAZ_ERR_RANGE;
     int status = BLAZ_OK;
     char *base = (char *)scratch_address(status);
     if (!base) return status;

@@ -97,19 +97,8 @@ __device__ __forceinline__ uint32_t code_pair(const int8_t *__restrict__ c, int 
     return *reinterpret_cast<const uint32_t *>(&h);
 }
 
-// |v| < 2^62 -> binary64 with the significand truncated to 53 bits (exact for
-// |v| < 2^53), on the integer pipe: normalize left by the leading-zero count,
-// one fixed right shift puts the leading one on bit 52, where it carries into
-// the exponent field (hence 1085 - lz rather than 1086 - lz).
-__device__ __forceinline__ double dec_to_double(long long v)
-{
-    const unsigned long long sign = (unsigned long long)v & 0x8000000000000000ull;
-    const unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
-    const int lz = __clzll((long long)a);
-    const unsigned long long m = (a << (lz & 63)) >> 11;
-    const unsigned long long bits = sign | (m + ((unsigned long long)(1085 - lz) << 52));
-    return a ? __longlong_as_double((long long)bits) : 0.0;
-}
+static_assert(slice_assembly_bound(kDecSlices, kDecDigitBits, kKeep) < (1ull << 62),
+              "the slice assembly must fit dec_to_double's input range");
 
 template <bool kVec>
 __global__ void __launch_bounds__(128)

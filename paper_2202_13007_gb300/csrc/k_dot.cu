@@ -493,8 +493,8 @@ int dot_grid(int64_t nb)
 {
     int64_t want = ((nb + 31) / 32 + (kDotThreads / 32) - 1) / (kDotThreads / 32);  // 32 blocks per warp step
     // two resident waves (3 CTAs of 256 threads per SM), never more than the
-    // 1024 partial sums of the no-allocation entry point
-    int64_t cap = std::min<int64_t>((int64_t)num_sms() * 6, 1024);
+    // kDotMaxCtas partial sums of the no-allocation entry point
+    int64_t cap = std::min<int64_t>((int64_t)num_sms() * 6, kDotMaxCtas);
     if (want > cap) want = cap;
     return (int)(want < 1 ? 1 : want);
 }

@@ -24,6 +24,7 @@
 #include "block_ops.cuh"
 #include "compress_fix.cuh"
 #include "const_upload.cuh"
+#include "gmap.cuh"
 #include "rate.cuh"
 
 namespace blaz {
@@ -472,18 +473,8 @@ static int rate_dec_ready(int r, cudaStream_t st)
     return tables[r - 1].ensure(g_rate_dec, &host[r - 1], sizeof(RateDec), (size_t)(r - 1) * sizeof(RateDec), st);
 }
 
-// |v| < 2^62 -> binary64 with the significand truncated to 53 bits (exact for
-// |v| < 2^53), on the integer pipe, as the 28-code decompressor converts: the
-// leading one normalized to bit 52 carries into the exponent field.
-__device__ __forceinline__ double rate_to_double(long long v)
-{
-    const unsigned long long sign = (unsigned long long)v & 0x8000000000000000ull;
-    const unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
-    const int lz = __clzll((long long)a);
-    const unsigned long long m = (a << (lz & 63)) >> 11;
-    const unsigned long long bits = sign | (m + ((unsigned long long)(1085 - lz) << 52));
-    return a ? __longlong_as_double((long long)bits) : 0.0;
-}
+static_assert(slice_assembly_bound(kRDSlices, kRDBits, 64) < (1ull << 62),
+              "the slice assembly must fit dec_to_double's input range");
 
 __device__ __forceinline__ void rate_mma(float (&c)[4], const uint32_t (&a)[4], uint2 b)
 {
@@ -574,8 +565,8 @@ __global__ void __launch_bounds__(128)
                     acc[q] = (long long)p01 * (1ll << (3 * kRDBits)) + (long long)p23 * (1ll << kRDBits) + y[4][e];
                 }
                 // M00 = f by definition (row 0 of G_r is zero), also when s is not finite
-                const double o0 = (nt == 0 && t == 0) ? fb[h] : fma(ts[h], rate_to_double(acc[0]), fb[h]);
-                const double o1 = fma(ts[h], rate_to_double(acc[1]), fb[h]);
+                const double o0 = (nt == 0 && t == 0) ? fb[h] : fma(ts[h], dec_to_double(acc[0]), fb[h]);
+                const double o1 = fma(ts[h], dec_to_double(acc[1]), fb[h]);
                 double *p = pb[h] + nt * lda;
                 if (kVec) {
                     *reinterpret_cast<double2 *>(p) = make_double2(o0, o1);
@@ -714,7 +705,7 @@ __global__ void __launch_bounds__(kDotRateThreads)
                 // compiler allocates 168 registers (3 CTAs per SM) and the
                 // kernel runs slower (0.167 against 0.139 ms at 4096^2, r = 4)
                 P[h] = KS == 3 ? fma(i64_to_double(ya[e]), i64_to_double(yb[e]), P[h])
-                               : fma(rate_to_double(ya[e]), rate_to_double(yb[e]), P[h]);
+                               : fma(dec_to_double(ya[e]), dec_to_double(yb[e]), P[h]);
             }
         }
         // the quad (t = 0..3) holds all 64 positions of both blocks

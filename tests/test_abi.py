@@ -131,3 +131,19 @@ def test_rate_entry_points_check_the_rate_without_a_gpu(libblaz):
     for r in (1, 8):   # empty operands need no device
         assert libblaz.blaz_compress_rate(None, 16, r, e, None) == 0
         assert libblaz.blaz_add_rate(e, e, r, e, None) == 0
+
+
+def test_dot_entry_points_reject_overflowing_shapes_without_a_gpu(libblaz):
+    """blaz_dot and blaz_dot_noalloc run the same descriptor checks: sides
+    above 2^34 (here 2^40 x 2^40, whose block count overflows int64) are
+    BLAZ_ERR_SHAPE (-1) before anything reaches a device."""
+    from paper_2202_13007_gb300 import blaz
+
+    fake = ctypes.c_void_p(256)   # never dereferenced: the shape check fails first
+    big = blaz._CMatDesc(1 << 40, 1 << 40, fake, fake, fake, fake)
+    res = ctypes.c_void_p(256)
+    assert libblaz.blaz_dot(ctypes.byref(big), ctypes.byref(big), res, None) == -1
+    assert libblaz.blaz_dot_noalloc(ctypes.byref(big), ctypes.byref(big), res, None) == -1
+    ok = blaz._CMatDesc(8, 8, fake, fake, fake, fake)
+    assert libblaz.blaz_dot_noalloc(ctypes.byref(ok), ctypes.byref(big), res, None) == -1
+    assert libblaz.blaz_dot_noalloc(ctypes.byref(ok), ctypes.byref(ok), None, None) == -2
