@@ -18,7 +18,7 @@ import torch
 
 import oracle as O
 import workloads as W
-from conftest import split_bf16_tol
+from conftest import SPLIT_BF16_LARGE_K_TOL, split_bf16_tol
 
 pytestmark = pytest.mark.gpu
 
@@ -314,6 +314,51 @@ def test_dot_rowcol_plain_pair(B, ij):
     assert abs(v - ref) <= 1e-12 * absref
 
 
+@pytest.mark.parametrize("ij", [(17, 30), (0, 0), (135, 71), (64, 8), (7, 63)])
+def test_dot_rowcol_rectangular(B, ij):
+    """Algorithm 3 for a general n x k times k x m pair (Sec. III): A is
+    136 x 1032 (129 block columns), B is 1032 x 72 (9 block columns), so a
+    kernel that indexed one operand with the other's block-column count
+    reads the wrong blocks."""
+    A = W.random_block_matrix(136, 1032, seed=41)
+    Bm = W.random_block_matrix(1032, 72, seed=42)
+    ga, gb = B.compress(dev(A)), B.compress(dev(Bm))
+    v = float(B.dot_rowcol(ga, gb, *ij).item())
+    ref, absref = O.dot_rowcol(O.compress(A), O.compress(Bm), *ij)
+    assert abs(v - ref) <= 1e-12 * absref
+
+
+def test_dot_rowcol_grid_stride(B):
+    """k = 40000 (5000 k-blocks): more k-blocks than one wave of 16-lane teams
+    over the SMs (16 x 152 = 2432 on a GB300), so every team loops."""
+    A = W.random_block_matrix(16, 40000, seed=43)
+    Bm = W.random_block_matrix(40000, 24, seed=44)
+    ga, gb = B.compress(dev(A)), B.compress(dev(Bm))
+    oa, ob = O.compress(A), O.compress(Bm)
+    for ij in [(3, 17), (15, 0), (8, 23)]:
+        v = float(B.dot_rowcol(ga, gb, *ij).item())
+        ref, absref = O.dot_rowcol(oa, ob, *ij)
+        assert abs(v - ref) <= 1e-12 * absref
+
+
+def test_dot_rowcol_bandwidth_sweep_launch(B):
+    """The benchmark's own call: line 17 times column 200 of two 16384^2 bump
+    fields.  The oracle compresses only the block row of A and the block
+    column of B the line and the column live in (compression is block-local,
+    so these are the same blocks)."""
+    n = 16384
+    ta = W.bump_field_torch(n, n, "cuda")
+    tb = W.bump_field_torch(n, n + 1, "cuda")
+    ga, gb = B.compress(ta), B.compress(tb)
+    v = float(B.dot_rowcol(ga, gb, 17, 200).item())
+    oa = O.compress(ta[16:24].cpu().numpy())
+    ob = O.compress(tb[:, 200:208].contiguous().cpu().numpy())
+    ref, absref = O.dot_rowcol(oa, ob, 1, 0)
+    assert abs(v - ref) <= 1e-12 * absref
+    del ta, tb, ga, gb
+    torch.cuda.empty_cache()
+
+
 @pytest.mark.parametrize("n,k,m", [(256, 256, 256), (72, 136, 50), (8, 8, 1), (64, 1024, 129)])
 def test_matmul_fp64(B, n, k, m):
     A = W.random_block_matrix(n, k, seed=n + k)
@@ -416,7 +461,8 @@ def test_precision_config_matmul_fp64_sampled(B):
 
 
 # --- split-precision tensor-core product -----------------------------------------------------
-@pytest.mark.parametrize("n,k,m", [(256, 256, 256), (72, 136, 50), (8, 8, 1), (64, 1024, 129), (384, 64, 520)])
+@pytest.mark.parametrize("n,k,m", [(256, 256, 256), (72, 136, 50), (8, 8, 1), (64, 8, 64), (64, 1024, 129),
+                                   (384, 64, 520)])
 def test_matmul_split_bf16(B, n, k, m):
     A = W.random_block_matrix(n, k, seed=n + k)
     Bd = W.smoothed_normal(k, m, seed=7)
@@ -428,6 +474,8 @@ def test_matmul_split_bf16(B, n, k, m):
     bound = np.abs(O.decompress(oa)) @ np.abs(Bd)
     err = np.abs(C - ref)
     assert np.all(err <= split_bf16_tol(k) * bound + 1e-300), np.max(err / (bound + 1e-300))
+    if k >= 1024:
+        assert np.all(err <= SPLIT_BF16_LARGE_K_TOL * bound + 1e-300), np.max(err / (bound + 1e-300))
 
 
 def test_matmul_split_bf16_empty_inner_dimension(B):
@@ -509,6 +557,8 @@ def test_precision_config_max_relative_error(B, mode, record_property):
     record_property("max_componentwise_error", worst_comp)
     record_property("max_relative_error", worst_rel)
     assert worst_comp <= tol
+    if mode == "split_bf16":
+        assert worst_comp <= SPLIT_BF16_LARGE_K_TOL
 
 
 # --- the stages of one block (Examples 1-5 of Sec. II) ------------------------------------------

@@ -222,6 +222,22 @@ def test_dot_rowcol_rate(B, r, ij):
 
 
 @pytest.mark.parametrize("r", [1, 3, 8])
+def test_dot_rowcol_rate_rectangular_and_grid_stride(B, r):
+    """Algorithm 3 at rate r for general shapes: A 136 x 1032 (129 block
+    columns) times B 1032 x 72 (9 block columns), then k = 40000 (5000
+    k-blocks, more than one wave of 16-lane teams, so every team loops)."""
+    for (n, k, m), seeds, ijs in [((136, 1032, 72), (51, 52), [(17, 30), (135, 71), (7, 63)]),
+                                   ((16, 40000, 24), (53, 54), [(3, 17), (15, 0)])]:
+        A = W.random_block_matrix(n, k, seed=seeds[0])
+        Bm = W.random_block_matrix(k, m, seed=seeds[1])
+        ga, gb = B.compress_rate(dev(A), r), B.compress_rate(dev(Bm), r)
+        oa, ob = O.compress_rate(A, r), O.compress_rate(Bm, r)
+        for ij in ijs:
+            ref, absref = O.dot_rowcol_rate(oa, ob, r, *ij)
+            assert abs(float(B.dot_rowcol_rate(ga, gb, *ij).item()) - ref) <= 1e-12 * absref
+
+
+@pytest.mark.parametrize("r", [1, 3, 8])
 @pytest.mark.parametrize("n,k,m", [(72, 136, 50), (256, 256, 256)])
 def test_matmul_rate(B, r, n, k, m):
     from conftest import split_bf16_tol
