@@ -31,16 +31,6 @@ sys.path.insert(0, ROOT)
 METRIC = "compressed add/scale/dot GB/s (% HBM peak), matmul TFLOP/s, serve p50/p99"
 BYTES_PER_BLOCK = {"compress": 557, "decompress": 557, "add": 135, "scale": 90, "dot": 90}
 STEP_OPS = ["compress", "compress", "decompress", "add", "scale", "dot"]
-# Algorithmic binary64 operations per block: the operations of the
-# specification outside the DCT (whose other coefficients, and the decision
-# phi = trunc(127/m), are certified in fp32): normalization 161 (the 49
-# halvings are exact exponent decrements), |D| pairwise tree 63, s and 1/s 2,
-# D' = D * (1/s) 64, DC chain 63 + 1, DC code 1.  The kernel executes fewer:
-# it certifies the DC in fp32 too for blocks that are not sign-coherent and
-# skips D' and the DC chain there (ncu: ~275 FP64 instructions per 32 blocks).
-COMPRESS_FLOPS_PER_BLOCK = 355
-FP64_PEAK_DERIVED = 2 * 152 * 2070e6  # 2 FP64 lanes/clk/SM x 152 SMs x 2070 MHz (1.25 TFLOP/s nominal, FMA=2)
-
 
 def parse():
     p = argparse.ArgumentParser()
@@ -220,6 +210,44 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def per_op_table(op_events, nb, hbm):
+    """Per operation of the timed steps: mean CUDA-event time of one call, and
+    the algorithmic bytes of one call (bytes per block x blocks; the
+    line-column dot reads 2 x 2048 blocks of 45 B) over that time, as GB/s
+    and as a fraction of the HBM peak."""
+    out = {}
+    for name, pairs in op_events.items():
+        ms = statistics.mean(a.elapsed_time(b) for a, b in pairs)
+        byts = BYTES_PER_BLOCK[name] * nb if name in BYTES_PER_BLOCK else 2 * 45 * int(round(nb ** 0.5))
+        out[name] = {"ms": ms, "bytes": byts, "gb_per_s": byts / (ms * 1e-3) / 1e9,
+                     "frac_of_hbm_peak": byts / (ms * 1e-3) / 1e9 / hbm, "calls": len(pairs)}
+    return out
+
+
+def compress_roofline(nb, comp_ms, hbm, hbm_src, fp64_probe, fp64_by_warps):
+    """Roofline of the dominant kernel pair (k_compress_fast + k_compress_fix,
+    one compress call): the algorithmic 557 B per block (512 in, 45 out)
+    over the call's mean CUDA-event time, against the measured HBM copy
+    peak.  Beside it, the binary64 instructions the kernels issue (ncu count
+    per block, committed under profiles/) over the same time, against the
+    binary64 issue ceiling measured live by the library's probe."""
+    achieved = 557 * nb / (comp_ms * 1e-3) / 1e9
+    inst = profiled("k_compress", "fp64_inst_per_block")
+    issued = inst * nb / (comp_ms * 1e-3) / 1e9 if inst else None
+    return {"kernel": "k_compress_fast + k_compress_fix", "bound": "hbm", "achieved": achieved, "peak": hbm,
+            "unit": "GB/s", "frac": achieved / hbm, "traffic": profiled_traffic("k_compress", nb),
+            "traffic_unit": "bytes per launch (ncu DRAM read + write per block x blocks)",
+            "source_sha": kernel_sha("k_compress"), "peak_source": hbm_src, "ms_per_launch": comp_ms,
+            "algorithmic_bytes_per_launch": 557 * nb,
+            "limiter": "binary64 issue: the specification's exact binary64 steps, not memory",
+            "fp64_issue": {"achieved_gops": issued, "peak_gops": fp64_probe,
+                           "frac": issued / fp64_probe if issued and fp64_probe else None,
+                           "inst_per_block": inst,
+                           "basis": "ncu binary64 warp instructions x 32 / 32 blocks per block, x blocks / launch "
+                                    "time; peak: blaz_probe_fp64_rate measured in this run",
+                           "probe_by_warps_per_sm": fp64_by_warps}}
+
+
 def run_oracle_step(O, A, Bm):
     """One step of the path evaluated by the CPU oracle (the line-column dot,
     whose bytes the step does not count, is left out); returns seconds."""
@@ -388,6 +416,21 @@ def config(side):
             "l2": "inputs larger than L2 (2 GiB per field), no flush", "parallelism": "replicas"}
 
 
+def matmul_errors(torch, Ah, Bh, C):
+    """Errors of a product C against the binary64 product of the decompressed
+    operands (cuBLAS DGEMM, whose own error, about sqrt(k) 2^-53 of
+    (|A_hat||B|)_ij, is far below the 1e-12 being checked): the componentwise
+    max_ij |C - C_ref|_ij / (|A_hat||B|)_ij, and the elementwise max relative
+    error over the entries with |C_ref| > 1e-8 max |C_ref|."""
+    ref = Ah @ Bh
+    err = (C - ref).abs()
+    comp = float((err / (Ah.abs() @ Bh.abs()).clamp_min(1e-300)).max())
+    big = ref.abs() > 1e-8 * float(ref.abs().max())
+    rel = float((err[big] / ref.abs()[big]).max())
+    return {"max_componentwise_error": comp, "max_relative_error": rel,
+            "error_basis": "against cuBLAS DGEMM of the decompressed operands"}
+
+
 def matmul_extras(B, W, torch, dev):
     """Precision configuration: compressed 4096^2 bump field times a smoothed
     N(0,1) 4096^2 matrix, FP64 DMMA path and split-bf16 tcgen05 path."""
@@ -416,6 +459,9 @@ def matmul_extras(B, W, torch, dev):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / reps
         out[name] = {"ms": ms, "tflops": 2 * n ** 3 / (ms * 1e-3) / 1e12}
+        Ah = B.decompress(ga)
+        out[name].update(matmul_errors(torch, Ah, B.decompress(gb) if name.startswith("cc_") else Bd, C))
+        del Ah
     out["shape"] = ("4096x4096x4096: compressed A times dense B (fp64, split_bf16) and times compressed B "
                     "(cc_*, both operands decompressed once)")
     return out
@@ -639,6 +685,7 @@ def matmul_line(args):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / args.steps
         res[mode] = {"ms": ms, "tflops": 2 * n ** 3 / (ms * 1e-3) / 1e12}
+        res[mode].update(matmul_errors(torch, B.decompress(ga), Bd, C))
     first = res[modes[0]]
     print(json.dumps({"metric": METRIC + " [matmul]", "value": first["tflops"], "unit": "TFLOP/s", "n_gpus": 1,
                       "steps": args.steps, "warmup": args.warmup, "ms_per_step": first["ms"],
@@ -679,6 +726,24 @@ def batch_line(args):
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     B.lib()
+    with ClockSampler(0) as clk:
+        r = run_batch(B, W, torch, dev, max(3, args.steps))
+    line = {"metric": METRIC + " [batch]", "value": r["ops"] / (r["ms"] * 1e-3), "unit": "ops/s", "n_gpus": 1,
+            "steps": r["reps"], "warmup": 1, "ms_per_step": r["ms"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "2000 mixed ops, sides log-uniform multiples of 8 in [64,2048], mix 40/30/15/10/5 % "
+                                   "compress/add/scale/dot/matmul (FP64 DMMA products), one persistent graph launch",
+                       "autotuned": r["autotuned"], "plan_seconds": r["plan_seconds"]},
+            "gb_per_s": r["gb_per_s"], "one_op_per_launch_ms": r["one_op_per_launch_ms"],
+            "speedup_vs_one_op_per_launch": r["speedup_vs_one_op_per_launch"], "items": r["items"],
+            "gpu_launches": r["reps"], "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
+def run_batch(B, W, torch, dev, reps):
+    """Builds the 2000-op batch, plans it (autotuned, graph-captured) and
+    times `reps` runs of the plan and two passes of the same ops launched one
+    by one (CUDA events)."""
     specs = W.batch_ops(count=2000, seed=11)
     ops, singles = [], []
     byts = 0
@@ -733,21 +798,15 @@ def batch_line(args):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / reps
 
-    with ClockSampler(0) as clk:
-        ms_batch = timed(plan.run, max(3, args.steps))
-        ms_single = timed(lambda: [f() for f in singles], 2)
+    ms_batch = timed(plan.run, reps)
+    ms_single = timed(lambda: [f() for f in singles], 2)
     plan.free()
-    line = {"metric": METRIC + " [batch]", "value": len(specs) / (ms_batch * 1e-3), "unit": "ops/s", "n_gpus": 1,
-            "steps": max(3, args.steps), "warmup": 1, "ms_per_step": ms_batch, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "2000 mixed ops, sides log-uniform multiples of 8 in [64,2048], mix 40/30/15/10/5 % "
-                                   "compress/add/scale/dot/matmul (FP64 DMMA products), one persistent graph launch",
-                       "autotuned": {"blocks_per_item": info["blocks_per_item"], "ctas_per_sm": info["ctas_per_sm"]},
-                       "plan_seconds": t_plan},
+    del ops, singles
+    torch.cuda.empty_cache()
+    return {"ops": len(specs), "ms": ms_batch, "reps": reps, "plan_seconds": t_plan,
+            "autotuned": {"blocks_per_item": info["blocks_per_item"], "ctas_per_sm": info["ctas_per_sm"]},
             "gb_per_s": byts / (ms_batch * 1e-3) / 1e9, "one_op_per_launch_ms": ms_single,
-            "speedup_vs_one_op_per_launch": ms_single / ms_batch, "items": info["items"],
-            "gpu_launches": max(3, args.steps), "clocks": clk.summary()}
-    print(json.dumps(line), flush=True)
+            "speedup_vs_one_op_per_launch": ms_single / ms_batch, "items": info["items"]}
 
 
 def main():
@@ -792,25 +851,25 @@ def main():
     ca, cb, cs, cc = (B.CMat.empty(n, n, dev) for _ in range(4))
     dec = torch.empty((n, n), dtype=torch.float64, device=dev)
     res = torch.empty(2, dtype=torch.float64, device=dev)
-    ev_pairs = []
+    # per operation: (name, call), in step order
+    step_ops = [("compress", lambda: B.compress(ta, out=ca)),
+                ("compress", lambda: B.compress(tb, out=cb)),
+                ("decompress", lambda: B.decompress(ca, out=dec)),
+                ("add", lambda: B.add(ca, cb, out=cs)),
+                ("scale", lambda: B.scale(ca, 3.5, out=cc)),
+                ("dot", lambda: B.dot(ca, cb, out=res[0])),
+                ("dot_rowcol", lambda: B.dot_rowcol(ca, cb, 17, 200, out=res[1]))]
+    op_events = {name: [] for name, _ in step_ops}
 
     def step(record=False):
-        if record:
-            e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-            e[0].record(st)
-        B.compress(ta, out=ca)
-        if record:
-            e[1].record(st)
-            e[2].record(st)
-        B.compress(tb, out=cb)
-        if record:
-            e[3].record(st)
-            ev_pairs.extend([(e[0], e[1]), (e[2], e[3])])
-        B.decompress(ca, out=dec)
-        B.add(ca, cb, out=cs)
-        B.scale(ca, 3.5, out=cc)
-        B.dot(ca, cb, out=res[0])
-        B.dot_rowcol(ca, cb, 17, 200, out=res[1])
+        for name, fn in step_ops:
+            if record:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+            fn()
+            if record:
+                e1.record(st)
+                op_events[name].append((e0, e1))
 
     launches_per_step = 9   # compress x2 (k_compress_fast + k_compress_fix), decompress, add, scale, dot, dot_rowcol
 
@@ -834,10 +893,10 @@ def main():
     ms_step = ms / args.steps
     value = job_throughput(world, n, args.steps, ms)
 
-    comp_ms = statistics.mean(a.elapsed_time(b) for a, b in ev_pairs)
     nb = (n // 8) ** 2
-    achieved = COMPRESS_FLOPS_PER_BLOCK * nb / (comp_ms * 1e-3) / 1e9
     hbm, hbm_src = peaks()
+    per_op = per_op_table(op_events, nb, hbm)
+    comp_ms = per_op["compress"]["ms"]
     fp64_probe, fp64_by_warps = probe_fp64(dev, st)
 
     # End to end through the public API with host buffers, every step: A and B
@@ -900,9 +959,17 @@ def main():
         torch.cuda.empty_cache()
         extras = {"matmul": matmul_extras(B, W, torch, dev), "shapes_files": shape_and_file_extras(B, W, torch, dev),
                   "plain_way": plain_way(B, torch, ca, cb, dev), "rates": rate_extras(B, W, torch, dev)}
+        keys = ("p50_ms", "p99_ms", "throughput_rps", "offered_rps", "mean_batch", "launches")
         srv = run_serve(args, B, W, torch, dev, 1.0, max_batch=0, streams=4, mode="split_bf16")
-        extras["serve"] = {k: srv[k] for k in ("p50_ms", "p99_ms", "throughput_rps", "offered_rps", "mean_batch")}
-        extras["serve"]["config"] = "1 s of the served Poisson stream (5k req/s); full line: --workload serve"
+        one = run_serve(args, B, W, torch, dev, 1.0, max_batch=1, streams=1, mode="split_bf16")
+        extras["serve"] = {k: srv[k] for k in keys}
+        extras["serve"]["one_request_per_launch"] = {k: one[k] for k in keys}
+        extras["serve"]["config"] = ("1 s of the served Poisson stream (5k req/s), continuous batching on 4 streams, "
+                                     "then the same stream one request per launch on one stream; "
+                                     "full line: --workload serve")
+        extras["batch"] = run_batch(B, W, torch, dev, 3)
+        extras["batch"]["config"] = ("2000 mixed ops, one autotuned graph-captured persistent launch (3 runs) against "
+                                     "the same ops launched one by one; full line: --workload batch")
 
     cpu = None
     cpu_par = None
@@ -916,25 +983,15 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config(n),
             "frac_of_hbm_peak": value / world / hbm,
-            "roofline": {"kernel": "k_compress_fast + k_compress_fix", "bound": "alu", "achieved": achieved,
-                         "peak": FP64_PEAK_DERIVED / 1e9, "unit": "GFLOP/s",
-                         "frac": achieved * 1e9 / FP64_PEAK_DERIVED, "traffic": profiled_traffic("k_compress", nb),
-                         "traffic_unit": "bytes per launch", "source_sha": kernel_sha("k_compress"),
-                         "peak_source": "derived: 2 FP64 lanes/clk/SM x 152 SMs x 2070 MHz",
-                         "ms_per_launch": comp_ms, "algorithmic_flops_per_launch": COMPRESS_FLOPS_PER_BLOCK * nb,
-                         "hbm_frac": 557 * nb / (comp_ms * 1e-3) / 1e9 / hbm, "hbm_peak_source": hbm_src,
-                         "fp64_issue_probe_gops": fp64_probe,
-                         "fp64_issue_probe_by_warps_per_sm": fp64_by_warps,
-                         "fp64_inst_per_block": profiled("k_compress", "fp64_inst_per_block"),
-                         "issued_frac_of_fp64_probe": (
-                             profiled("k_compress", "fp64_inst_per_block") * nb / (comp_ms * 1e-3) / 1e9 / fp64_probe
-                             if fp64_probe and profiled("k_compress", "fp64_inst_per_block") else None)},
+            "roofline": compress_roofline(nb, comp_ms, hbm, hbm_src, fp64_probe, fp64_by_warps),
+            "per_op": per_op,
             "clocks": clk.summary(),
             "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps,
             "cpu_baseline": cpu,
             "matmul_tflops": extras["matmul"] if extras else None,
             "serve": extras["serve"] if extras else None,
+            "batch": extras["batch"] if extras else None,
             "shapes_files": extras["shapes_files"] if extras else None,
             "plain_way": extras["plain_way"] if extras else None,
             "rates": extras["rates"] if extras else None,

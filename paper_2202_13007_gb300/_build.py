@@ -45,15 +45,18 @@ def _stale(target: str) -> bool:
     return any(os.path.getmtime(d) > t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    if not force and not _stale(LIB):
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra=(), build_dir: str | None = None) -> str:
+    """Compile libblaz.so (into build_dir when given, with extra nvcc flags)."""
+    bdir = build_dir or BUILD
+    lib_path = os.path.join(bdir, "libblaz.so")
+    if not force and not _stale(lib_path):
+        return lib_path
+    os.makedirs(bdir, exist_ok=True)
     cc = nvcc()
     objs = []
 
     def one(src):
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+        obj = os.path.join(bdir, src.replace(".cu", ".o"))
         flags = ARCH + COMMON + list(extra)
         if src in EXACT_TUS:
             flags = flags + ["-fmad=false"]
@@ -69,13 +72,13 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 4)) as ex:
         objs = list(ex.map(one, sources()))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib_path + f".tmp{os.getpid()}"
     cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static", "-Xcompiler", "-fPIC"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

@@ -306,9 +306,10 @@ struct FastCtx {
     float Dk[kKeep];    // fp32 kept coefficients (Dk[0]: the DC estimate)
 };
 
-// Phase 1: normalization, slope (both exact), fp32 DCT of all 64
-// coefficients.  d holds D afterwards (the dense DC pass reads it).
-__device__ __forceinline__ void cf_prepare(double (&d)[64], double &s_out, double &r_out, FastCtx &c)
+// Eq. eqnorm in place with binary64 operations, from the last element
+// backwards (M(i-1,j) and M(i,j-1) are still inputs when D(i,j) is formed);
+// the interior halving x * 0.5 is dhalf (bit-identical, integer pipe).
+__device__ __forceinline__ void normalize_block(double (&d)[64])
 {
 #pragma unroll
     for (int i = 7; i >= 0; --i) {
@@ -327,16 +328,98 @@ __device__ __forceinline__ void cf_prepare(double (&d)[64], double &s_out, doubl
             }
         }
     }
-    int K = 0;
-    unsigned pos = 0u, neg = 0u;  // any nonzero D of each sign
+}
+
+// Uniform blocks.  When the 64 entries of a block share one sign and one
+// exponent field e (54 <= e <= 2045), each is m 2^(e-1075) with an integer
+// significand m in [2^52, 2^53), and every operation of Eq. eqnorm is exact:
+// M_ij - M_i-1,j = (m - m') 2^(e-1075) with |m - m'| < 2^52, the sum of two
+// such differences stays below 2^53 units, and the halving of a normal
+// number is exact.  So D_ij = N_ij 2^(e-1076) with the integer
+//     N_ij = 2 m_ij - m_i-1,j - m_i,j-1  (interior),  2 (m_ij - m_prev) (row 0, column 0),
+// |N| < 2^53, which the integer pipe forms without any rounding.  If
+// moreover sum |N| < 2^53, every partial sum of the pairwise |D| tree is a
+// multiple of 2^(e-1076) below 2^53 of them, so each of its binary64
+// additions is exact and S = (sum |N|) 2^(e-1076) whatever the order.
+// e >= 54 keeps every D and S a normal number or an exact multiple of the
+// smallest subnormal; e <= 2045 keeps them finite.
+__device__ __forceinline__ bool block_is_uniform(const double (&d)[64])
+{
+    const unsigned se = (unsigned)__double2hiint(d[0]) >> 20;  // sign and exponent field
+    const unsigned e = se & 0x7FFu;
+    bool ok = e >= 54u && e <= 2045u;
+#pragma unroll
+    for (int p = 1; p < 64; ++p) ok &= ((unsigned)__double2hiint(d[p]) >> 20) == se;
+    return ok;
+}
+
+// a 2^(e-1076) with the given sign bit, for 0 < a < 2^53 and 54 <= e <= 2045
+// (exact; a normal number); +0 for a == 0.
+__device__ __forceinline__ double scaled_int_to_double(unsigned long long a, unsigned long long sign, int e)
+{
+    const int lz = __clzll((long long)a);  // >= 11
+    // leading one shifted to bit 52 carries into the exponent field: e + 9 - lz + 1
+    const unsigned long long bits = (sign << 63) | (((unsigned long long)(e + 9 - lz) << 52) + (a << ((lz - 11) & 63)));
+    return a ? __longlong_as_double((long long)bits) : 0.0;
+}
+
+// The integer form of Eq. eqnorm for a uniform block: d holds the input on
+// entry and the integers N (as bit patterns) on exit.  The significands are
+// magnitudes, so for a block of negative entries D = -N 2^(e-1076); a zero
+// D is +0, as the binary64 difference of equal values is (uniform_d gives
+// the binary64 D, bit-identical to normalize_block).  Returns sum |N|
+// (exact), and K, pos, neg as the caller's count loop would.
+__device__ __forceinline__ unsigned long long normalize_uniform(double (&d)[64], int e, unsigned bneg, int &K,
+                                                                unsigned &pos, unsigned &neg)
+{
+    auto sig = [&](int p) -> long long {
+        return (long long)(((unsigned long long)__double_as_longlong(d[p]) & 0x000FFFFFFFFFFFFFull) |
+                           0x0010000000000000ull);
+    };
+#pragma unroll
+    for (int i = 7; i >= 0; --i) {
+#pragma unroll
+        for (int j = 7; j >= 0; --j) {
+            long long N;
+            if (i == 0 && j == 0) N = 0;
+            else if (i == 0) N = 2 * (sig(j) - sig(j - 1));
+            else if (j == 0) N = 2 * (sig(i * 8) - sig((i - 1) * 8));
+            else N = 2 * sig(i * 8 + j) - sig((i - 1) * 8 + j) - sig(i * 8 + j - 1);
+            d[i * 8 + j] = __longlong_as_double(N);  // the integer, until converted below
+        }
+    }
+    unsigned long long sum = 0;
+    K = 0;
+    pos = neg = 0u;
 #pragma unroll
     for (int p = 0; p < 64; ++p) {
-        const int nz = nonzero_bits(d[p]);
-        K += nz;
-        const unsigned sg = (unsigned)__double2hiint(d[p]) >> 31;
-        pos |= (unsigned)nz & (sg ^ 1u);
-        neg |= (unsigned)nz & sg;
+        const long long N = __double_as_longlong(d[p]);
+        const unsigned long long a = N < 0 ? (unsigned long long)(-N) : (unsigned long long)N;
+        sum += a;
+        const unsigned nz = a != 0ull, sg = (unsigned)((unsigned long long)N >> 63) ^ bneg;
+        K += (int)nz;
+        pos |= nz & (sg ^ 1u);
+        neg |= nz & sg;
     }
+    return sum;
+}
+
+// D = N 2^(e-1076) with the block's sign (bneg) as binary64 (exact).
+__device__ __forceinline__ double uniform_d(long long N, int e, unsigned bneg)
+{
+    const unsigned long long a = N < 0 ? (unsigned long long)(-N) : (unsigned long long)N;
+    return scaled_int_to_double(a, (unsigned long long)(((unsigned)((unsigned long long)N >> 63)) ^ bneg), e);
+}
+
+// Phase 1, after the normalization (K nonzero entries, pos / neg: any
+// nonzero D of each sign; S = sum |D| when K > 0): slope, reciprocal and the
+// fp32 DCT of all 64 coefficients.  kInt: d holds the integers N of a
+// uniform block with exponent field eb (D = +-N 2^(eb-1076)); otherwise d
+// holds D.  d is left as it is (the dense DC pass reads it).
+template <bool kInt>
+__device__ __forceinline__ void cf_slope_and_dct(const double (&d)[64], int eb, unsigned bneg, int K, unsigned pos,
+                                                 unsigned neg, double S, double &s_out, double &r_out, FastCtx &c)
+{
     c.coherent = false;
     r_out = 0.0;
     if (K == 0) {
@@ -344,7 +427,6 @@ __device__ __forceinline__ void cf_prepare(double (&d)[64], double &s_out, doubl
         c.state = 1u;
         return;
     }
-    const double S = tree_sum_abs(d);
     const double s = div_by_count(S, K);
     const double r = ddiv(1.0, s);
     s_out = s;
@@ -360,35 +442,66 @@ __device__ __forceinline__ void cf_prepare(double (&d)[64], double &s_out, doubl
     c.coherent = (pos ^ neg) != 0u;
     const int e = es_field - 1023;
     const float rr = trunc_f32_scaled(r, -e);
-    float T[8][8];
+    // Both passes run two independent chains per instruction on the paired
+    // fp32 pipe of sm_103a (__fmul2_rn, __fadd2_rn, __ffma2_rn round each
+    // lane as the scalar operation does, so every coefficient is the same
+    // chain of 8 fp32 operations as before): rows u, u + 1 in the first pass,
+    // coefficients (i, j), (i + 1, j) in the second.
+    // The rows D 2^-e (1/s) 2^e in fp32.  From D: both factors truncated to
+    // fp32 (2u each) and one fp32 product (u).  From N (kInt): RN32(N) (u)
+    // times rr 2^(eb-1076-e), a power-of-two scaling of the truncated rr
+    // (exact: the exponent stays within about 60 of zero) and by the block's
+    // sign, one product (u).  Both stay within the 5u relative error of the
+    // bound in the header.
+    const float rr_int = kInt ? __int_as_float((int)(bneg << 31) | ((127 + eb - 1076 - e) << 23)) * rr : 0.0f;
+    float2 T[4][8];  // T[u / 2][j] = (T_u,j, T_u+1,j)
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-        float rf[8];
+    for (int up = 0; up < 4; ++up) {
+        const float2 rr2 = kInt ? make_float2(rr_int, rr_int) : make_float2(rr, rr);
+        float2 rf[8];
 #pragma unroll
-        for (int v = 0; v < 8; ++v) rf[v] = trunc_f32_scaled(d[u * 8 + v], e) * rr;
-        float t0 = rf[0];
+        for (int v = 0; v < 8; ++v) {
+            const double x0 = d[2 * up * 8 + v], x1 = d[(2 * up + 1) * 8 + v];
+            const float2 in = kInt ? make_float2(__ll2float_rn(__double_as_longlong(x0)),
+                                                 __ll2float_rn(__double_as_longlong(x1)))
+                                   : make_float2(trunc_f32_scaled(x0, e), trunc_f32_scaled(x1, e));
+            rf[v] = __fmul2_rn(in, rr2);
+        }
+        float2 t0 = rf[0];
 #pragma unroll
-        for (int v = 1; v < 8; ++v) t0 += rf[v];
-        T[u][0] = t0;
+        for (int v = 1; v < 8; ++v) t0 = __fadd2_rn(t0, rf[v]);
+        T[up][0] = t0;
 #pragma unroll
         for (int j = 1; j < 8; ++j) {
-            float acc = rf[0] * cos_f(j, 0);
+            float2 acc = __fmul2_rn(rf[0], make_float2(cos_f(j, 0), cos_f(j, 0)));
 #pragma unroll
-            for (int v = 1; v < 8; ++v) acc = fmaf(rf[v], cos_f(j, v), acc);
-            T[u][j] = acc;
+            for (int v = 1; v < 8; ++v) acc = __ffma2_rn(rf[v], make_float2(cos_f(j, v), cos_f(j, v)), acc);
+            T[up][j] = acc;
         }
     }
     c.base = 28.0f * 0x1p-24f * (float)(K + 1);
     float mlo = 0.0f, mhi = 0.0f;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
+        float Dij[8];
+#pragma unroll
+        for (int ip = 0; ip < 4; ++ip) {
+            const int i0 = 2 * ip, i1 = 2 * ip + 1;
+            const float T0 = T[0][j].x;
+            float2 acc = __fmul2_rn(make_float2(cos_f(i0, 0), cos_f(i1, 0)), make_float2(T0, T0));
+#pragma unroll
+            for (int u = 1; u < 8; ++u) {
+                const float Tu = (u & 1) ? T[u / 2][j].y : T[u / 2][j].x;
+                acc = __ffma2_rn(make_float2(cos_f(i0, u), cos_f(i1, u)), make_float2(Tu, Tu), acc);
+            }
+            const float2 D2 = __fmul2_rn(make_float2((float)aa_tab(i0, j), (float)aa_tab(i1, j)), acc);
+            Dij[i0] = D2.x;
+            Dij[i1] = D2.y;
+        }
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            float acc = cos_f(i, 0) * T[0][j];
-#pragma unroll
-            for (int u = 1; u < 8; ++u) acc = fmaf(cos_f(i, u), T[u][j], acc);
             const float aa = (float)aa_tab(i, j);
-            const float Df = aa * acc;
+            const float Df = Dij[i];
             if (!(i == 0 && j == 0)) {
                 const float E = c.base * aa + 1e-30f;
                 const float a = fabsf(Df);
@@ -403,15 +516,60 @@ __device__ __forceinline__ void cf_prepare(double (&d)[64], double &s_out, doubl
     c.mhi = mhi;
 }
 
-// The exact DC coefficient X00 = RN(aa00 U00) from D and r (the dense pass).
-__device__ __forceinline__ double cf_exact_dc(const double *D, double r)
+// Phase 1 on the binary64 pipe: Eq. eqnorm, the nonzero count and the
+// pairwise |D| tree as specified, then cf_slope_and_dct.
+__device__ __forceinline__ void cf_prepare(double (&d)[64], double &s_out, double &r_out, FastCtx &c)
 {
+    normalize_block(d);
+    int K = 0;
+    unsigned pos = 0u, neg = 0u;
+#pragma unroll
+    for (int p = 0; p < 64; ++p) {
+        const int nz = nonzero_bits(d[p]);
+        K += nz;
+        const unsigned sg = (unsigned)__double2hiint(d[p]) >> 31;
+        pos |= (unsigned)nz & (sg ^ 1u);
+        neg |= (unsigned)nz & sg;
+    }
+    cf_slope_and_dct<false>(d, 0, 0u, K, pos, neg, K ? tree_sum_abs(d) : 0.0, s_out, r_out, c);
+}
+
+// Phase 1 for a uniform block on the integer pipe (same bits as
+// cf_prepare).  d holds the integers N on success (meta: the exponent field
+// and the block's sign for uniform_d).  Returns false, with d no longer the
+// input, when the block is not uniform or its |N| sum could round: such
+// blocks take cf_prepare.
+__device__ __forceinline__ bool cf_prepare_uniform(double (&d)[64], double &s_out, double &r_out, FastCtx &c,
+                                                   unsigned &meta)
+{
+    if (!block_is_uniform(d)) return false;
+    const unsigned hi0 = (unsigned)__double2hiint(d[0]);
+    const int e = (int)((hi0 >> 20) & 0x7FFu);
+    const unsigned bneg = hi0 >> 31;
+    int K;
+    unsigned pos, neg;
+    const unsigned long long sum = normalize_uniform(d, e, bneg, K, pos, neg);
+    if (sum >= (1ull << 53)) return false;
+    meta = (unsigned)e | (bneg << 16);
+    cf_slope_and_dct<true>(d, e, bneg, K, pos, neg, scaled_int_to_double(sum, 0ull, e), s_out, r_out, c);
+    return true;
+}
+
+// The exact DC coefficient X00 = RN(aa00 U00) from D and r (the dense pass).
+// kInt: D holds the integers N of a uniform block (meta as set by
+// cf_prepare_uniform), converted to the exact binary64 D here.
+template <bool kInt>
+__device__ __forceinline__ double cf_exact_dc(const double *D, double r, unsigned meta)
+{
+    auto dval = [&](int p) {
+        return kInt ? uniform_d(__double_as_longlong(D[p]), (int)(meta & 0xFFFFu), meta >> 16) : D[p];
+    };
     double U00 = 0.0;
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-        double t0 = dmul(D[u * 8], r);
+        double t0 = dmul(dval(u * 8), r);
 #pragma unroll
-        for (int v = 1; v < 8; ++v) t0 = dadd(t0, dmul(D[u * 8 + v], r));
+        for (int v = 1; v < 8; ++v) t0 = dadd(t0, dmul(dval(u * 8 + v), r));
         U00 = (u == 0) ? t0 : dadd(U00, t0);
     }
     return dmul(BLAZ_A00, U00);

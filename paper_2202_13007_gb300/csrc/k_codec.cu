@@ -4,10 +4,14 @@
 // Compression is bit-exact binary64: every operation is an explicit
 // round-to-nearest intrinsic in the order fixed in include/blaz.h, so the
 // result does not depend on -fmad or on the compiler's scheduling.  The
-// compressor runs in two kernels: k_compress_fast decides every block it can
-// certify (compress_fast.cuh) and lists the codes (or whole blocks) it
-// cannot; k_compress_fix evaluates those exactly in binary64, densely, by
-// teams of 8 lanes, so the rare exact work costs no divergence.
+// compressor runs in three launches: k_compress_fast<.., true> compresses
+// the uniform blocks (one sign and one exponent field: Eq. eqnorm and the
+// slope sum exact in integer arithmetic, compress_fast.cuh) and lists the
+// others; k_compress_fast<.., false> compresses the listed blocks with the
+// binary64 normalization, densely; both decide every code they can certify
+// and list the codes (or whole blocks) they cannot, and k_compress_fix
+// evaluates those exactly in binary64, densely, by teams of 8 lanes, so the
+// rare exact work costs no divergence.
 #include <mutex>
 
 #include "compress_fast.cuh"
@@ -31,71 +35,121 @@ __device__ __forceinline__ void append(bool want, T value, T *__restrict__ list,
     if (want) list[base + __popc(need & ((1u << lane) - 1u))] = value;
 }
 
-// CTA size of the fast compressor: 128 threads (one block each), 3 CTAs per
-// SM (168 registers).  The sign-coherent blocks of a CTA share one dense
-// pass of exact DC chains, which larger CTAs fill better; CTAs stay
-// short-lived so that the warps of an SM are at different phases.
+// CTA size of the fast compressor: 128 threads (one block each), 2 CTAs per
+// SM (255 registers: with the binary64 normalization gone from the common
+// path the kernel is bound by instruction issue, and 3 CTAs per SM at 168
+// registers spilled and ran 13% slower).  The sign-coherent blocks of a CTA
+// share one dense pass of exact DC chains, which larger CTAs fill better.
 constexpr int kFastThreads = 128;
 
-// Dynamic shared memory of the fast compressor: D and r of every thread's
-// block, and the exact X00 of every slot.
-constexpr size_t kFastSmem = sizeof(double) * (size_t)kFastThreads * 66;
+// Dynamic shared memory of the fast compressor: per slot the 64 entries of
+// D (or N), r and the meta word of the block, an odd row of kSlot doubles
+// (conflict-free row reads); then the exact X00 of every slot.
+constexpr int kSlot = 67;
+constexpr size_t kFastSmem = sizeof(double) * (size_t)kFastThreads * (kSlot + 1);
 
-template <bool kVec>
-__global__ void __launch_bounds__(kFastThreads, 3)
-    k_compress_fast(const double *__restrict__ A, int64_t lda, int64_t rows, int64_t cols, int64_t nbc, int64_t nb,
-                    double *__restrict__ f, double *__restrict__ s, uint8_t *__restrict__ phi,
-                    int8_t *__restrict__ code, uint2 *__restrict__ code_list, unsigned *__restrict__ code_count,
-                    unsigned *__restrict__ block_list, unsigned *__restrict__ block_count)
+// One CTA's pass over up to kFastThreads blocks (thread t: block b when
+// `valid`).  kUniform: the first pass, which compresses the uniform blocks
+// on the integer pipe (cf_prepare_uniform) and lists every other block for
+// the second pass (general_list); otherwise the second pass, on the binary64
+// pipe (cf_prepare).  Both leave undecided codes and blocks to the fix-up
+// lists.  Every thread of the CTA calls this (it holds barriers).
+template <bool kVec, bool kUniform>
+__device__ __forceinline__ void compress_pass(const double *__restrict__ A, int64_t lda, int64_t rows, int64_t cols,
+                                              int64_t nbc, int64_t b, bool valid, double *__restrict__ f,
+                                              double *__restrict__ s, uint8_t *__restrict__ phi,
+                                              int8_t *__restrict__ code, uint2 *__restrict__ code_list,
+                                              unsigned *__restrict__ code_count, unsigned *__restrict__ block_list,
+                                              unsigned *__restrict__ block_count, unsigned *__restrict__ general_list,
+                                              unsigned *__restrict__ general_count, double (*sD)[kSlot],
+                                              double *sX, unsigned &sCount)
 {
-    // Sign-coherent blocks of the CTA leave D and r here; after the barrier
-    // the CTA's threads evaluate their exact DC chains densely (one per
-    // thread) and leave X00 in sX.  Dynamic shared memory (kFastSmem bytes):
-    // 64 D + r per slot, an odd row length keeping the row reads
-    // conflict-free.
-    extern __shared__ double fast_smem[];
-    double(*sD)[65] = reinterpret_cast<double(*)[65]>(fast_smem);
-    double *sX = fast_smem + kFastThreads * 65;
-    __shared__ unsigned sCount;
-    if (threadIdx.x == 0) sCount = 0u;
-    __syncthreads();
-    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const bool valid = b < nb;
     double d[64];
     double sv = 0.0, rv = 0.0;
     FastCtx ctx;
     ctx.state = 1u;
     ctx.coherent = false;
     int slot = -1;
+    unsigned meta = 0u;
     if (valid) {
         const int64_t bi = b / nbc, bj = b - (b / nbc) * nbc;
         if (bi * 8 + 8 <= rows && bj * 8 + 8 <= cols) load_block<kVec>(A, lda, bi, bj, d);
         else load_block_clamped(A, lda, bi, bj, rows, cols, d);  // partial block of a padded matrix
-        f[b] = d[0];
-        cf_prepare(d, sv, rv, ctx);
-        s[b] = sv;
-        if (ctx.coherent) {
-            slot = (int)atomicAdd(&sCount, 1u);
+        const double f0 = d[0];
+        if (kUniform) {
+            valid = cf_prepare_uniform(d, sv, rv, ctx, meta);
+            append(!valid, (unsigned)b, general_list, general_count);
+        } else {
+            cf_prepare(d, sv, rv, ctx);
+        }
+        if (valid) {
+            f[b] = f0;
+            s[b] = sv;
+            if (ctx.coherent) {
+                slot = (int)atomicAdd(&sCount, 1u);
 #pragma unroll
-            for (int p = 0; p < 64; ++p) sD[slot][p] = d[p];
-            sD[slot][64] = rv;
+                for (int p = 0; p < 64; ++p) sD[slot][p] = d[p];
+                sD[slot][64] = rv;
+                sD[slot][65] = __longlong_as_double((long long)meta);
+            }
         }
     }
     __syncthreads();
-    if (threadIdx.x < sCount) sX[threadIdx.x] = cf_exact_dc(sD[threadIdx.x], sD[threadIdx.x][64]);
+    if (threadIdx.x < sCount)
+        sX[threadIdx.x] = cf_exact_dc<kUniform>(sD[threadIdx.x], sD[threadIdx.x][64],
+                                                (unsigned)__double_as_longlong(sD[threadIdx.x][65]));
     __syncthreads();
-    if (!valid) return;
-    uint8_t ph = 255;
-    int8_t c[kKeep];
-    const uint32_t pending = cf_finish(ctx, slot >= 0 ? sX[slot] : 0.0, ph, c);
-    if (pending != kPendingAll) {
-        phi[b] = ph;
-        store_codes(code + b * kKeep, c);
+    if (valid) {
+        uint8_t ph = 255;
+        int8_t c[kKeep];
+        const uint32_t pending = cf_finish(ctx, slot >= 0 ? sX[slot] : 0.0, ph, c);
+        if (pending != kPendingAll) {
+            phi[b] = ph;
+            store_codes(code + b * kKeep, c);
+        }
+        // Undecided codes and whole blocks go to separate lists, so that the
+        // fix-up kernel runs without divergence between the two cases.
+        append(pending != 0u && pending != kPendingAll, make_uint2((unsigned)b, pending), code_list, code_count);
+        append(pending == kPendingAll, (unsigned)b, block_list, block_count);
     }
-    // Undecided codes and whole blocks go to separate lists, so that the
-    // fix-up kernel runs without divergence between the two cases.
-    append(pending != 0u && pending != kPendingAll, make_uint2((unsigned)b, pending), code_list, code_count);
-    append(pending == kPendingAll, (unsigned)b, block_list, block_count);
+}
+
+// The certified compressor.  kUniform: one CTA per kFastThreads consecutive
+// blocks, the first pass of compress_pass.  Otherwise the second pass over
+// the blocks the first one listed, the CTAs striding over the list.
+template <bool kVec, bool kUniform>
+__global__ void __launch_bounds__(kFastThreads, 2)
+    k_compress_fast(const double *__restrict__ A, int64_t lda, int64_t rows, int64_t cols, int64_t nbc, int64_t nb,
+                    double *__restrict__ f, double *__restrict__ s, uint8_t *__restrict__ phi,
+                    int8_t *__restrict__ code, uint2 *__restrict__ code_list, unsigned *__restrict__ code_count,
+                    unsigned *__restrict__ block_list, unsigned *__restrict__ block_count,
+                    unsigned *__restrict__ general_list, unsigned *__restrict__ general_count)
+{
+    // Sign-coherent blocks of the CTA leave D and r here; after a barrier
+    // the CTA's threads evaluate their exact DC chains densely (one per
+    // thread) and leave X00 in sX (kFastSmem bytes of dynamic shared memory).
+    extern __shared__ double fast_smem[];
+    double(*sD)[kSlot] = reinterpret_cast<double(*)[kSlot]>(fast_smem);
+    double *sX = fast_smem + kFastThreads * kSlot;
+    __shared__ unsigned sCount;
+    if (kUniform) {
+        if (threadIdx.x == 0) sCount = 0u;
+        __syncthreads();
+        const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+        compress_pass<kVec, true>(A, lda, rows, cols, nbc, b, b < nb, f, s, phi, code, code_list, code_count,
+                                  block_list, block_count, general_list, general_count, sD, sX, sCount);
+    } else {
+        const int64_t n = *general_count;  // the first pass completed before this launch
+        for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+            if (threadIdx.x == 0) sCount = 0u;
+            __syncthreads();
+            const int64_t i = base + threadIdx.x;
+            const int64_t b = i < n ? (int64_t)general_list[i] : 0;
+            compress_pass<kVec, false>(A, lda, rows, cols, nbc, b, i < n, f, s, phi, code, code_list, code_count,
+                                       block_list, block_count, general_list, general_count, sD, sX, sCount);
+            __syncthreads();  // sCount and the shared slots are reused by the next chunk
+        }
+    }
 }
 
 // The exact fix-up of both lists in one launch, a team of 8 lanes per entry:
@@ -134,10 +188,32 @@ static int fast_grid(int64_t nb)
     return (int)(want < 1 ? 1 : (want > 0x7FFFFFFF ? 0x7FFFFFFF : want));
 }
 
+// Scratch of one compression: the undecided-code list (8 B per entry), the
+// whole-block list and the list of blocks for the second pass (4 B each),
+// then the three counts.
 size_t compress_scratch_bytes(int64_t nb)
 {
     auto up = [](size_t x) { return (x + 255) / 256 * 256; };
-    return up((size_t)nb * 8) + up((size_t)nb * 4) + 256;
+    return up((size_t)nb * 8) + 2 * up((size_t)nb * 4) + 256;
+}
+
+template <bool kVec>
+static void compress_launches(const double *A, int64_t lda, int64_t rows, int64_t cols, int64_t nbc, int64_t nb,
+                              const blaz_cmat *out, uint2 *code_list, unsigned *block_list, unsigned *general_list,
+                              unsigned *counts, cudaStream_t st)
+{
+    // counts[0]: undecided codes, [1]: whole blocks, [2]: second-pass blocks
+    k_compress_fast<kVec, true><<<fast_grid(nb), kFastThreads, kFastSmem, st>>>(
+        A, lda, rows, cols, nbc, nb, out->f, out->s, out->phi, out->code, code_list, counts, block_list, counts + 1,
+        general_list, counts + 2);
+    // the second pass strides over its list (at most nb blocks) with up to
+    // two resident waves of CTAs
+    const int64_t want = (nb + kFastThreads - 1) / kFastThreads, cap = (int64_t)num_sms() * 6;
+    k_compress_fast<kVec, false><<<(int)(want < cap ? want : cap), kFastThreads, kFastSmem, st>>>(
+        A, lda, rows, cols, nbc, nb, out->f, out->s, out->phi, out->code, code_list, counts, block_list, counts + 1,
+        general_list, counts + 2);
+    k_compress_fix<kVec><<<num_sms() * 4, 128, 0, st>>>(A, lda, rows, cols, nbc, block_list, code_list, counts,
+                                                         out->s, out->phi, out->code);
 }
 
 int launch_compress(const double *A, int64_t lda, int64_t rows, int64_t cols, const blaz_cmat *out, void *scratch,
@@ -149,31 +225,27 @@ int launch_compress(const double *A, int64_t lda, int64_t rows, int64_t cols, co
     auto up = [](size_t x) { return (x + 255) / 256 * 256; };
     uint2 *code_list = (uint2 *)scratch;
     unsigned *block_list = (unsigned *)((char *)scratch + up((size_t)nb * 8));
-    unsigned *counts = (unsigned *)((char *)scratch + up((size_t)nb * 8) + up((size_t)nb * 4));
-    cudaError_t e = cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned), st);
+    unsigned *general_list = (unsigned *)((char *)scratch + up((size_t)nb * 8) + up((size_t)nb * 4));
+    unsigned *counts = (unsigned *)((char *)scratch + up((size_t)nb * 8) + 2 * up((size_t)nb * 4));
+    cudaError_t e = cudaMemsetAsync(counts, 0, 3 * sizeof(unsigned), st);
     if (e != cudaSuccess) return set_cuda_error(e);
-    const int threads = 128;
-    const int fix_grid = num_sms() * 4;  // one resident wave (72 registers per thread)
     static const bool smem_ok = [] {
-        return cudaFuncSetAttribute(k_compress_fast<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)kFastSmem) == cudaSuccess &&
-               cudaFuncSetAttribute(k_compress_fast<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)kFastSmem) == cudaSuccess;
+        bool ok = true;
+        ok &= cudaFuncSetAttribute(k_compress_fast<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)kFastSmem) == cudaSuccess;
+        ok &= cudaFuncSetAttribute(k_compress_fast<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)kFastSmem) == cudaSuccess;
+        ok &= cudaFuncSetAttribute(k_compress_fast<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)kFastSmem) == cudaSuccess;
+        ok &= cudaFuncSetAttribute(k_compress_fast<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)kFastSmem) == cudaSuccess;
+        return ok;
     }();
     if (!smem_ok) return set_cuda_error(cudaGetLastError());
-    if (vec_ok(A, lda)) {
-        k_compress_fast<true><<<fast_grid(nb), kFastThreads, kFastSmem, st>>>(A, lda, rows, cols, nbc, nb, out->f,
-                                                                      out->s, out->phi, out->code, code_list,
-                                                                      counts, block_list, counts + 1);
-        k_compress_fix<true><<<fix_grid, threads, 0, st>>>(A, lda, rows, cols, nbc, block_list, code_list, counts,
-                                                            out->s, out->phi, out->code);
-    } else {
-        k_compress_fast<false><<<fast_grid(nb), kFastThreads, kFastSmem, st>>>(A, lda, rows, cols, nbc, nb, out->f,
-                                                                       out->s, out->phi, out->code, code_list,
-                                                                       counts, block_list, counts + 1);
-        k_compress_fix<false><<<fix_grid, threads, 0, st>>>(A, lda, rows, cols, nbc, block_list, code_list, counts,
-                                                             out->s, out->phi, out->code);
-    }
+    if (vec_ok(A, lda)) compress_launches<true>(A, lda, rows, cols, nbc, nb, out, code_list, block_list,
+                                                general_list, counts, st);
+    else compress_launches<false>(A, lda, rows, cols, nbc, nb, out, code_list, block_list, general_list, counts,
+                                  st);
     return launch_status();
 }
 

@@ -7,10 +7,13 @@ the same summation order) and checks |D_f - X| <= E_ij against the binary64
 coefficients X of the oracle, on random blocks and on blocks built to make
 the fp32 error large (long same-sign sums, wide dynamic range, few nonzeros).
 
-Two forms of the estimate are checked:
+Three forms of the estimate are checked:
   * rows from the exact D' = RN64(D r), truncated to fp32, E = 24u aa (K+1);
   * rows from D 2^-e and r 2^e truncated to fp32 and multiplied in fp32
     (e the exponent of s), E = 28u aa (K+1);
+  * the uniform-block form: D 2^-e rounded to nearest in fp32 (the kernel
+    converts the integer N of D = N 2^k to fp32 and scales it by a power of
+    two, which is exact), times r 2^e truncated to fp32, E = 28u aa (K+1);
 with u = 2^-24 and an absolute 2^-100."""
 import numpy as np
 import pytest
@@ -44,7 +47,8 @@ def estimates(d, r, s, K, scaled):
         rr = trunc32(np.ldexp(r, e))
         for u in range(8):
             for v in range(8):
-                rows[u, v] = F32(np.float64(trunc32(np.ldexp(d[u, v], -e))) * np.float64(rr))
+                x = F32(np.ldexp(d[u, v], -e)) if scaled == "uniform" else trunc32(np.ldexp(d[u, v], -e))
+                rows[u, v] = F32(np.float64(x) * np.float64(rr))
     else:
         for u in range(8):
             for v in range(8):
@@ -83,7 +87,7 @@ def adversarial_blocks(rng):
                               (8, 8)).cumsum(0).cumsum(1)                       # energy in one coefficient
 
 
-@pytest.mark.parametrize("scaled", [False, True])
+@pytest.mark.parametrize("scaled", [False, True, "uniform"])
 def test_fp32_estimates_are_within_the_certification_bound(scaled):
     rng = np.random.default_rng(2026)
     blocks = list(adversarial_blocks(rng))
