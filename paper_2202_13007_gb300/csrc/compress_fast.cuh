@@ -517,8 +517,11 @@ __device__ __forceinline__ void cf_slope_and_dct(const double (&d)[64], int eb, 
 }
 
 // Phase 1 on the binary64 pipe: Eq. eqnorm, the nonzero count and the
-// pairwise |D| tree as specified, then cf_slope_and_dct.
-__device__ __forceinline__ void cf_prepare(double (&d)[64], double &s_out, double &r_out, FastCtx &c)
+// pairwise |D| tree as specified, then cf_slope_and_dct.  stash(d, meta) is
+// called between the two for a block whose nonzero D all have one sign (the
+// dense DC pass will need D), so that d can die row by row in the DCT.
+template <typename Stash>
+__device__ __forceinline__ void cf_prepare(double (&d)[64], double &s_out, double &r_out, FastCtx &c, Stash stash)
 {
     normalize_block(d);
     int K = 0;
@@ -531,6 +534,7 @@ __device__ __forceinline__ void cf_prepare(double (&d)[64], double &s_out, doubl
         pos |= (unsigned)nz & (sg ^ 1u);
         neg |= (unsigned)nz & sg;
     }
+    if (K && (pos ^ neg)) stash(d, 0u);
     cf_slope_and_dct<false>(d, 0, 0u, K, pos, neg, K ? tree_sum_abs(d) : 0.0, s_out, r_out, c);
 }
 
@@ -538,9 +542,10 @@ __device__ __forceinline__ void cf_prepare(double (&d)[64], double &s_out, doubl
 // cf_prepare).  d holds the integers N on success (meta: the exponent field
 // and the block's sign for uniform_d).  Returns false, with d no longer the
 // input, when the block is not uniform or its |N| sum could round: such
-// blocks take cf_prepare.
+// blocks take cf_prepare.  stash as in cf_prepare (d then holds N).
+template <typename Stash>
 __device__ __forceinline__ bool cf_prepare_uniform(double (&d)[64], double &s_out, double &r_out, FastCtx &c,
-                                                   unsigned &meta)
+                                                   Stash stash)
 {
     if (!block_is_uniform(d)) return false;
     const unsigned hi0 = (unsigned)__double2hiint(d[0]);
@@ -550,7 +555,7 @@ __device__ __forceinline__ bool cf_prepare_uniform(double (&d)[64], double &s_ou
     unsigned pos, neg;
     const unsigned long long sum = normalize_uniform(d, e, bneg, K, pos, neg);
     if (sum >= (1ull << 53)) return false;
-    meta = (unsigned)e | (bneg << 16);
+    if (K && (pos ^ neg)) stash(d, (unsigned)e | (bneg << 16));
     cf_slope_and_dct<true>(d, e, bneg, K, pos, neg, scaled_int_to_double(sum, 0ull, e), s_out, r_out, c);
     return true;
 }

@@ -35,11 +35,13 @@ __device__ __forceinline__ void append(bool want, T value, T *__restrict__ list,
     if (want) list[base + __popc(need & ((1u << lane) - 1u))] = value;
 }
 
-// CTA size of the fast compressor: 128 threads (one block each), 2 CTAs per
-// SM (255 registers: with the binary64 normalization gone from the common
-// path the kernel is bound by instruction issue, and 3 CTAs per SM at 168
-// registers spilled and ran 13% slower).  The sign-coherent blocks of a CTA
-// share one dense pass of exact DC chains, which larger CTAs fill better.
+// CTA size of the fast compressor: 128 threads (one block each).  The
+// uniform pass runs 3 CTAs per SM (166 registers, no spills: D leaves the
+// registers row by row during the DCT); the binary64 pass needs 237
+// registers and runs 2 (at 168 it spills).  Both are bound by instruction
+// issue and latency rather than by the binary64 pipe.  The sign-coherent
+// blocks of a CTA share one dense pass of exact DC chains, which larger CTAs
+// fill better.
 constexpr int kFastThreads = 128;
 
 // Dynamic shared memory of the fast compressor: per slot the 64 entries of
@@ -70,28 +72,29 @@ __device__ __forceinline__ void compress_pass(const double *__restrict__ A, int6
     ctx.state = 1u;
     ctx.coherent = false;
     int slot = -1;
-    unsigned meta = 0u;
+    // A block that may need the exact DC chain leaves D (or N) in a slot as
+    // soon as it is normalized; r follows once it is known.
+    auto stash = [&](const double (&dd)[64], unsigned meta) {
+        slot = (int)atomicAdd(&sCount, 1u);
+#pragma unroll
+        for (int p = 0; p < 64; ++p) sD[slot][p] = dd[p];
+        sD[slot][65] = __longlong_as_double((long long)meta);
+    };
     if (valid) {
         const int64_t bi = b / nbc, bj = b - (b / nbc) * nbc;
         if (bi * 8 + 8 <= rows && bj * 8 + 8 <= cols) load_block<kVec>(A, lda, bi, bj, d);
         else load_block_clamped(A, lda, bi, bj, rows, cols, d);  // partial block of a padded matrix
         const double f0 = d[0];
         if (kUniform) {
-            valid = cf_prepare_uniform(d, sv, rv, ctx, meta);
+            valid = cf_prepare_uniform(d, sv, rv, ctx, stash);
             append(!valid, (unsigned)b, general_list, general_count);
         } else {
-            cf_prepare(d, sv, rv, ctx);
+            cf_prepare(d, sv, rv, ctx, stash);
         }
+        if (slot >= 0) sD[slot][64] = rv;
         if (valid) {
             f[b] = f0;
             s[b] = sv;
-            if (ctx.coherent) {
-                slot = (int)atomicAdd(&sCount, 1u);
-#pragma unroll
-                for (int p = 0; p < 64; ++p) sD[slot][p] = d[p];
-                sD[slot][64] = rv;
-                sD[slot][65] = __longlong_as_double((long long)meta);
-            }
         }
     }
     __syncthreads();
@@ -118,7 +121,7 @@ __device__ __forceinline__ void compress_pass(const double *__restrict__ A, int6
 // blocks, the first pass of compress_pass.  Otherwise the second pass over
 // the blocks the first one listed, the CTAs striding over the list.
 template <bool kVec, bool kUniform>
-__global__ void __launch_bounds__(kFastThreads, 2)
+__global__ void __launch_bounds__(kFastThreads, kUniform ? 3 : 2)
     k_compress_fast(const double *__restrict__ A, int64_t lda, int64_t rows, int64_t cols, int64_t nbc, int64_t nb,
                     double *__restrict__ f, double *__restrict__ s, uint8_t *__restrict__ phi,
                     int8_t *__restrict__ code, uint2 *__restrict__ code_list, unsigned *__restrict__ code_count,

@@ -131,6 +131,28 @@ def test_compress_certification_boundaries(B, boundary_blocks):
     assert_cmat_equal(B.compress(tb[:, 8:]), O.compress(Y))
 
 
+def test_compress_uniform_block_edges(B):
+    """Blocks at the edges of the compressor's integer path (one sign and one
+    exponent field e, 54 <= e <= 2045, sum |N| < 2^53) and just outside it,
+    bit for bit against the oracle: both signs; e = 54 and 2045 and their
+    neighbours 53 and 2046; a checkerboard of 1 and 2 - 2^-52 whose integer
+    slope sum reaches 2^53 (the binary64 tree then rounds); constant blocks;
+    a zero entry; one entry across a binade."""
+    rng = np.random.default_rng(71)
+    base = 1.5 + np.cumsum(np.cumsum(rng.uniform(0, 1e-3, (8, 8)), 0), 1)      # in [1, 2)
+    checker = np.where(np.add.outer(np.arange(8), np.arange(8)) % 2 == 0, 1.0, 2.0 - 2.0 ** -52)
+    blocks = [base, -base, np.full((8, 8), 1.25), np.full((8, 8), -3.0), checker, -checker]
+    for k in (-969, -970, 1021, 1022):          # exponent fields 54, 53, 2044, 2045 for values in [1, 2)
+        blocks += [np.ldexp(base, k), -np.ldexp(base, k)]
+    blocks.append(np.ldexp(base / 1.5 * 1.9, 1023 - 1))   # values in [2^1022, 2^1023]: e = 2045 and 2046
+    z = base.copy(); z[3, 4] = 0.0; blocks.append(z)
+    x = base.copy(); x[5, 6] = 2.0 + 1e-3; blocks.append(x)
+    blocks += [np.ldexp(base, int(k)) * rng.choice([-1.0, 1.0]) for k in rng.integers(-1000, 1000, 47)]
+    M = np.concatenate([np.concatenate(blocks[r * 8:(r + 1) * 8], axis=1) for r in range(len(blocks) // 8)], axis=0)
+    g = B.compress(dev(M))
+    assert_cmat_equal(g, O.compress(M))
+
+
 @pytest.mark.parametrize("shape", [(0, 0), (0, 16), (16, 0)])
 def test_empty_matrices(B, shape):
     X = torch.zeros(shape, dtype=torch.float64, device="cuda")
