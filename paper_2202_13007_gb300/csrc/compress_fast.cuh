@@ -345,12 +345,14 @@ __device__ __forceinline__ void normalize_block(double (&d)[64])
 // smallest subnormal; e <= 2045 keeps them finite.
 __device__ __forceinline__ bool block_is_uniform(const double (&d)[64])
 {
-    const unsigned se = (unsigned)__double2hiint(d[0]) >> 20;  // sign and exponent field
-    const unsigned e = se & 0x7FFu;
-    bool ok = e >= 54u && e <= 2045u;
+    const unsigned h0 = (unsigned)__double2hiint(d[0]);
+    const unsigned e = (h0 >> 20) & 0x7FFu;
+    // the OR of hi(M) ^ hi(M00) over the block (one three-input logic
+    // operation per entry) is below 2^20 iff all share sign and exponent
+    unsigned diff = 0u;
 #pragma unroll
-    for (int p = 1; p < 64; ++p) ok &= ((unsigned)__double2hiint(d[p]) >> 20) == se;
-    return ok;
+    for (int p = 1; p < 64; ++p) diff |= (unsigned)__double2hiint(d[p]) ^ h0;
+    return diff < (1u << 20) && e >= 54u && e <= 2045u;
 }
 
 // a 2^(e-1076) with the given sign bit, for 0 < a < 2^53 and 54 <= e <= 2045
@@ -388,19 +390,23 @@ __device__ __forceinline__ unsigned long long normalize_uniform(double (&d)[64],
             d[i * 8 + j] = __longlong_as_double(N);  // the integer, until converted below
         }
     }
+    // sum |N| and sum N: all nonzero N have one sign iff |sum N| = sum |N|
     unsigned long long sum = 0;
+    long long tot = 0;
     K = 0;
-    pos = neg = 0u;
 #pragma unroll
     for (int p = 0; p < 64; ++p) {
         const long long N = __double_as_longlong(d[p]);
         const unsigned long long a = N < 0 ? (unsigned long long)(-N) : (unsigned long long)N;
         sum += a;
-        const unsigned nz = a != 0ull, sg = (unsigned)((unsigned long long)N >> 63) ^ bneg;
-        K += (int)nz;
-        pos |= nz & (sg ^ 1u);
-        neg |= nz & sg;
+        tot += N;
+        K += (int)(a != 0ull);
     }
+    const bool coherent = (unsigned long long)(tot < 0 ? -tot : tot) == sum;
+    // as the caller's flags would be: D has the sign of N, flipped for a negative block
+    const unsigned tneg = (unsigned)((unsigned long long)tot >> 63) ^ bneg;
+    pos = K && (!coherent || !tneg) ? 1u : 0u;
+    neg = K && (!coherent || tneg) ? 1u : 0u;
     return sum;
 }
 
@@ -570,7 +576,9 @@ __device__ __forceinline__ double cf_exact_dc(const double *D, double r, unsigne
         return kInt ? uniform_d(__double_as_longlong(D[p]), (int)(meta & 0xFFFFu), meta >> 16) : D[p];
     };
     double U00 = 0.0;
-#pragma unroll
+    // rows not unrolled: D is in shared memory, and a short loop keeps this
+    // rarely run code small in the instruction cache
+#pragma unroll 1
     for (int u = 0; u < 8; ++u) {
         double t0 = dmul(dval(u * 8), r);
 #pragma unroll
