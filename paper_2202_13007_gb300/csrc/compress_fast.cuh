@@ -486,7 +486,7 @@ __device__ __forceinline__ void cf_slope_and_dct(const double (&d)[64], int eb, 
         }
     }
     c.base = 28.0f * 0x1p-24f * (float)(K + 1);
-    float mlo = 0.0f, mhi = 0.0f;
+    float max0k = 0.0f, maxkk = 0.0f;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         float Dij[8];
@@ -506,20 +506,23 @@ __device__ __forceinline__ void cf_slope_and_dct(const double (&d)[64], int eb, 
         }
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            const float aa = (float)aa_tab(i, j);
             const float Df = Dij[i];
-            if (!(i == 0 && j == 0)) {
-                const float E = c.base * aa + 1e-30f;
-                const float a = fabsf(Df);
-                mhi = fmaxf(mhi, a + E);
-                mlo = fmaxf(mlo, a - E);
+            // the largest |D_f| per alpha_i alpha_j class (E_ij depends on the
+            // class only; fp32 addition is monotone, so adding E to the
+            // class maximum gives the maximum of |D_f| + E and of |D_f| - E)
+            if (i == 0 && j == 0) {
+            } else if (i == 0 || j == 0) {
+                max0k = fmaxf(max0k, fabsf(Df));
+            } else {
+                maxkk = fmaxf(maxkk, fabsf(Df));
             }
             const int t = kept_index(i, j);
             if (t >= 0) c.Dk[t] = Df;
         }
     }
-    c.mlo = mlo;
-    c.mhi = mhi;
+    const float E0k = c.base * (float)BLAZ_A0K + 1e-30f, Ekk = c.base * (float)BLAZ_AKK + 1e-30f;
+    c.mhi = fmaxf(max0k + E0k, maxkk + Ekk);
+    c.mlo = fmaxf(fmaxf(max0k - E0k, maxkk - Ekk), 0.0f);
 }
 
 // Phase 1 on the binary64 pipe: Eq. eqnorm, the nonzero count and the
@@ -633,15 +636,20 @@ __device__ __forceinline__ uint32_t cf_finish(const FastCtx &c, double X00, uint
     const float phif = (float)phi;
     uint32_t pending = 0u;
 #pragma unroll
-    for (int t = 0; t < kKeep; ++t) {
-        if (t == 0 && c.coherent) {
-            code[0] = quantize_bits(dmul(X00, i64_to_double(phi)));
-            continue;
-        }
+    // Each code from the interval v -+ Ev, v = D_f phi, with
+    // Ev = E_ij phi (1 + 2^-20) + 2^-22 (|v| + 1) + 2^-16 (the last two
+    // terms cover the fp32 roundings of v and of the interval ends); two
+    // codes per paired fp32 instruction, one constant per alpha class.
+    auto cls = [&](int t) {
         const float aa = (float)aa_tab(kept_row(t), kept_col(t));
-        const float v = c.Dk[t] * phif;
-        const float Ev = (c.base * aa * phif) * (1.0f + 0x1p-20f) + 0x1p-22f * (fabsf(v) + 1.0f) + 0x1p-16f;
-        const float lo = v - Ev, hi = v + Ev;
+        return (c.base * aa * phif) * (1.0f + 0x1p-20f) + (0x1p-22f + 0x1p-16f);
+    };
+    const float C00 = cls(0), C0k = cls(1), Ckk = cls(9);
+    auto cst = [&](int t) {
+        const int i = kept_row(t), j = kept_col(t);
+        return (i == 0 && j == 0) ? C00 : (i == 0 || j == 0) ? C0k : Ckk;
+    };
+    auto decide = [&](float lo, float hi, int t) {
         int cc = 0;
         if (lo >= 127.0f) cc = 127;
         else if (hi <= -127.0f) cc = -127;
@@ -651,6 +659,21 @@ __device__ __forceinline__ uint32_t cf_finish(const FastCtx &c, double X00, uint
             else cc = tl;
         }
         code[t] = (int8_t)cc;
+    };
+    const float2 phi2 = make_float2(phif, phif), k22 = make_float2(0x1p-22f, 0x1p-22f),
+                 neg1 = make_float2(-1.0f, -1.0f);
+#pragma unroll
+    for (int q = 0; q < kKeep / 2; ++q) {
+        const int t0 = 2 * q, t1 = 2 * q + 1;
+        const float2 v = __fmul2_rn(make_float2(c.Dk[t0], c.Dk[t1]), phi2);
+        const float2 Ev = __ffma2_rn(make_float2(fabsf(v.x), fabsf(v.y)), k22, make_float2(cst(t0), cst(t1)));
+        const float2 lo = __ffma2_rn(Ev, neg1, v), hi = __fadd2_rn(v, Ev);
+        decide(lo.x, hi.x, t0);
+        decide(lo.y, hi.y, t1);
+    }
+    if (c.coherent) {  // the DC of a sign-coherent block from its exact X00
+        code[0] = quantize_bits(dmul(X00, i64_to_double(phi)));
+        pending &= ~1u;
     }
     return pending;
 }
