@@ -685,41 +685,4 @@ __constant__ double c_cos[64] = {
 #undef BLAZ_ROW
 };
 
-// Code t of a block from the exact D' (binary64 order of the specification):
-// T[u] = sum_v D'[u][v] cos[j][v], U = sum_u cos[i][u] T[u], X = aa_ij U,
-// code = quantize(X * phi).
-__device__ __forceinline__ int8_t exact_code(const double (&dp)[64], int t, int phi)
-{
-    const int i = kept_row(t), j = kept_col(t);
-    double U = 0.0;
-    for (int u = 0; u < 8; ++u) {
-        double T = (j == 0) ? dp[u * 8] : dmul(dp[u * 8], c_cos[j * 8]);
-#pragma unroll
-        for (int v = 1; v < 8; ++v) T = dadd(T, (j == 0) ? dp[u * 8 + v] : dmul(dp[u * 8 + v], c_cos[j * 8 + v]));
-        const double term = (i == 0) ? T : dmul(c_cos[i * 8 + u], T);
-        U = (u == 0) ? term : dadd(U, term);
-    }
-    const double aa = (i == 0 && j == 0) ? BLAZ_A00 : (i == 0 || j == 0) ? BLAZ_A0K : BLAZ_AKK;
-    return quantize_bits(dmul(dmul(aa, U), i64_to_double(phi)));
-}
-
-// D' = D * (1/s) of a block in d (input block on entry), as compress_block
-// forms it; s is the block's exact stored slope (> 0).
-__device__ __forceinline__ void exact_dprime(double (&d)[64], double s)
-{
-#pragma unroll
-    for (int i = 7; i >= 0; --i) {
-#pragma unroll
-        for (int j = 7; j >= 0; --j) {
-            if (i == 0 && j == 0) d[0] = 0.0;
-            else if (i == 0) d[j] = dsub(d[j], d[j - 1]);
-            else if (j == 0) d[i * 8] = dsub(d[i * 8], d[(i - 1) * 8]);
-            else d[i * 8 + j] = dhalf(dadd(dsub(d[i * 8 + j], d[(i - 1) * 8 + j]), dsub(d[i * 8 + j], d[i * 8 + j - 1])));
-        }
-    }
-    const double r = ddiv(1.0, s);
-#pragma unroll
-    for (int p = 0; p < 64; ++p) d[p] = dmul(d[p], r);
-}
-
 }  // namespace blaz

@@ -128,4 +128,61 @@ __device__ __forceinline__ void fix_codes_of_block(const double *__restrict__ A,
     }
 }
 
+// Undecided codes of block b (bit t of `pending`: code t) by one lane, phi
+// already set: the block's D by the integer form of Eq. eqnorm when the
+// block is uniform (else on the binary64 pipe), D' = D (1/s) with s as
+// stored, and each listed code in the specified order,
+//     T_u = sum_v D'_uv cos_jv (v ascending),  U = sum_u cos_iu T_u (u ascending),
+//     code = quantize(RN(aa_ij U) phi),
+// where products by cos 0 = 1 are exact (same bits as omitting them).
+// cs: the cosine table in shared memory (the lanes of a warp evaluate
+// different codes).  One lane per block costs a quarter of the binary64
+// warp instructions of a team of 8 lanes for the usual single code.
+template <bool kVec>
+__device__ __forceinline__ void fix_codes_lane(const double *__restrict__ A, int64_t lda, int64_t rows, int64_t cols,
+                                               int64_t nbc, int64_t b, uint32_t pending,
+                                               const double *__restrict__ s, const uint8_t *__restrict__ phi,
+                                               int8_t *__restrict__ code, const double *cs)
+{
+    double d[64];
+    const int64_t bi = b / nbc, bj = b - bi * nbc;
+    if (bi * 8 + 8 <= rows && bj * 8 + 8 <= cols) load_block<kVec>(A, lda, bi, bj, d);
+    else load_block_clamped(A, lda, bi, bj, rows, cols, d);
+    if (block_is_uniform(d)) {
+        const unsigned hi0 = (unsigned)__double2hiint(d[0]);
+        const int e = (int)((hi0 >> 20) & 0x7FFu);
+        int K;
+        unsigned pos, neg;
+        normalize_uniform(d, e, hi0 >> 31, K, pos, neg);
+#pragma unroll
+        for (int p = 0; p < 64; ++p) d[p] = uniform_d(__double_as_longlong(d[p]), e, hi0 >> 31);
+    } else {
+        normalize_block(d);
+    }
+    const double r = ddiv(1.0, s[b]);
+#pragma unroll
+    for (int p = 0; p < 64; ++p) d[p] = dmul(d[p], r);
+    const double phd = i64_to_double(phi[b]);
+    for (uint32_t m = pending; m; m &= m - 1u) {
+        const int t = __ffs(m) - 1, i = kept_row(t), j = kept_col(t);
+        double cj[8], ci[8];
+#pragma unroll
+        for (int x = 0; x < 8; ++x) {
+            cj[x] = cs[j * 8 + x];
+            ci[x] = cs[i * 8 + x];
+        }
+        double U = 0.0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            double T = dmul(d[u * 8], cj[0]);
+#pragma unroll
+            for (int v = 1; v < 8; ++v) T = dadd(T, dmul(d[u * 8 + v], cj[v]));
+            const double term = dmul(ci[u], T);
+            U = (u == 0) ? term : dadd(U, term);
+        }
+        const double aa = (i == 0 && j == 0) ? BLAZ_A00 : (i == 0 || j == 0) ? BLAZ_A0K : BLAZ_AKK;
+        code[b * kKeep + t] = quantize_bits(dmul(dmul(aa, U), phd));
+    }
+}
+
 }  // namespace blaz

@@ -155,9 +155,10 @@ __global__ void __launch_bounds__(kFastThreads, kUniform ? 3 : 2)
     }
 }
 
-// The exact fix-up of both lists in one launch, a team of 8 lanes per entry:
-// entries [0, #blocks) of the whole-block list, then the code list.  The two
-// lists hold different blocks, so the entries are independent.
+// The exact fix-up of both lists in one launch: the whole-block list by
+// teams of 8 lanes (fix_whole_block), then the undecided codes by one lane
+// per block (fix_codes_lane).  The two lists hold different blocks, so the
+// entries are independent.
 template <bool kVec>
 __global__ void __launch_bounds__(128)
     k_compress_fix(const double *__restrict__ A, int64_t lda, int64_t rows, int64_t cols, int64_t nbc,
@@ -165,17 +166,18 @@ __global__ void __launch_bounds__(128)
                    const uint2 *__restrict__ code_list, const unsigned *__restrict__ counts,
                    const double *__restrict__ s, uint8_t *__restrict__ phi, int8_t *__restrict__ code)
 {
+    __shared__ double cs[64];
+    if (threadIdx.x < 64) cs[threadIdx.x] = c_cos[threadIdx.x];
+    __syncthreads();
     const int lane = threadIdx.x & 31, u = lane & 7, tbase = lane & ~7;
     const unsigned tmask = 0xFFu << tbase;
     const int64_t ncodes = counts[0], nblocks = counts[1];
-    const int64_t teams = (int64_t)gridDim.x * blockDim.x / 8;
-    for (int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 8; q < nblocks + ncodes; q += teams) {
-        if (q < nblocks) {
-            fix_whole_block<kVec>(A, lda, rows, cols, nbc, block_list[q], s, phi, code, u, tbase, tmask);
-        } else {
-            const uint2 e = code_list[q - nblocks];
-            fix_codes_of_block<kVec>(A, lda, rows, cols, nbc, e.x, e.y, s, phi, code, u, tbase, tmask);
-        }
+    const int64_t threads = (int64_t)gridDim.x * blockDim.x, tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    for (int64_t q = tid / 8; q < nblocks; q += threads / 8)
+        fix_whole_block<kVec>(A, lda, rows, cols, nbc, block_list[q], s, phi, code, u, tbase, tmask);
+    for (int64_t q = tid; q < ncodes; q += threads) {
+        const uint2 e = code_list[q];
+        fix_codes_lane<kVec>(A, lda, rows, cols, nbc, e.x, e.y, s, phi, code, cs);
     }
 }
 
