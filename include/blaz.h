@@ -350,8 +350,11 @@ int blaz_cmat_load(const char *path, blaz_cmat *out, void *stream);
  * run in issue order), and `stream` compresses every slab as it lands, so
  * the compression hides behind the transfer.  Asynchronous: A must stay valid
  * and unchanged until `stream` has passed the call.  Same bits as
- * blaz_compress.  Device memory: the ring plus 12 bytes per block of a slab,
- * stream-ordered. */
+ * blaz_compress.  Device memory: the ring (allocated by the first call on a
+ * device, grown when a call needs larger slabs, kept for later calls until
+ * the process exits, so that no call waits on the host for an allocation)
+ * plus 12 bytes per block of a slab, stream-ordered.  Calls on one device
+ * issue their copies one call at a time. */
 int blaz_compress_host(const double *A, int64_t lda, blaz_cmat *out, void *stream);
 /* The packed payload of a compressed matrix (the file payload layout:
  * f[nb], s[nb], phi[nb], code[nb][28]; 45 nb bytes) to / from host memory,

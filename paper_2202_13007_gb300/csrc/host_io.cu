@@ -7,8 +7,9 @@
 // The host-to-device link is the bound of compressing a host matrix (about
 // 210 GB/s on this machine against ~700 GB/s of compression throughput), so
 // the matrix is moved in slabs of block rows on a copy stream into a ring of
-// device staging buffers (up to 512 MB) while the caller's stream compresses the slabs
-// already landed; every slab's blocks form a contiguous range of the output.
+// device staging buffers (up to 512 MB, kept from call to call) while the
+// caller's stream compresses the slabs already landed; every slab's blocks
+// form a contiguous range of the output.
 #include <mutex>
 #include <vector>
 
@@ -37,22 +38,78 @@ cudaStream_t copy_stream(int dev)
     return streams[dev];
 }
 
-struct Events {
-    cudaEvent_t e[2 * kRingMax + 1] = {};
-    int n = 0;
-    ~Events()
-    {
-        for (int i = 0; i < n; ++i) cudaEventDestroy(e[i]);  // released once the recorded work completes
-    }
-    cudaError_t create(int count)
-    {
-        for (; n < count; ++n) {
-            cudaError_t r = cudaEventCreateWithFlags(&e[n], cudaEventDisableTiming);
-            if (r != cudaSuccess) return r;
-        }
-        return cudaSuccess;
-    }
+// The staging ring of one device, kept from call to call.  Allocating a
+// fresh ring per call made each call wait on the host (inside the
+// stream-ordered allocation) for the previous call's ring to be released,
+// i.e. for the previous transfer to end, so the next call's copies were
+// issued late.  Buffer b of the ring is reused once the compression of its
+// previous slab has passed `freed[b]`; `landed[b]` orders that compression
+// after the copy.  Calls on one device issue under the ring's mutex.
+struct Ring {
+    std::mutex mu;
+    char *base = nullptr;
+    size_t bytes = 0;       // allocated
+    size_t buf_bytes = 0;   // current partition
+    int nbuf = 0, next = 0;
+    bool used[kRingMax] = {};
+    cudaEvent_t freed[kRingMax] = {}, landed[kRingMax] = {};
 };
+
+Ring &ring_of(int dev)
+{
+    static std::mutex mu;
+    static std::vector<Ring *> rings;
+    std::lock_guard<std::mutex> lk(mu);
+    if ((int)rings.size() <= dev) rings.resize(dev + 1, nullptr);
+    if (!rings[dev]) rings[dev] = new Ring();  // lives until the process exits
+    return *rings[dev];
+}
+
+// Makes `cs` wait until every buffer of the current partition is free.
+cudaError_t ring_drain(Ring &r, cudaStream_t cs)
+{
+    for (int b = 0; b < r.nbuf; ++b)
+        if (r.used[b]) {
+            cudaError_t e = cudaStreamWaitEvent(cs, r.freed[b], 0);
+            if (e != cudaSuccess) return e;
+            r.used[b] = false;
+        }
+    return cudaSuccess;
+}
+
+// Partitions the ring into `nbuf` buffers of `buf_bytes`, growing the
+// allocation (stream-ordered on the copy stream) when it is too small.
+int ring_prepare(Ring &r, size_t buf_bytes, int nbuf, cudaStream_t cs)
+{
+    cudaError_t e;
+    for (int b = 0; b < kRingMax; ++b)
+        if (!r.freed[b]) {
+            if ((e = cudaEventCreateWithFlags(&r.freed[b], cudaEventDisableTiming)) != cudaSuccess ||
+                (e = cudaEventCreateWithFlags(&r.landed[b], cudaEventDisableTiming)) != cudaSuccess)
+                return set_cuda_error(e);
+        }
+    if (r.buf_bytes == buf_bytes && r.nbuf == nbuf && r.base) return BLAZ_OK;
+    // a new partition: every buffer of the old one must be free first
+    if ((e = ring_drain(r, cs)) != cudaSuccess) return set_cuda_error(e);
+    const size_t need = buf_bytes * (size_t)nbuf;
+    if (need > r.bytes) {
+        if (r.base) cudaFreeAsync(r.base, cs);
+        r.base = nullptr;
+        r.bytes = 0;
+        keep_pool_cached();
+        void *p = nullptr;
+        if ((e = cudaMallocAsync(&p, need, cs)) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return e == cudaErrorMemoryAllocation ? BLAZ_ERR_OOM : set_cuda_error(e);
+        }
+        r.base = (char *)p;
+        r.bytes = need;
+    }
+    r.buf_bytes = buf_bytes;
+    r.nbuf = nbuf;
+    r.next = 0;
+    return BLAZ_OK;
+}
 
 }  // namespace
 }  // namespace blaz
@@ -86,44 +143,36 @@ int blaz_compress_host(const double *A, int64_t lda, blaz_cmat *out, void *strea
     const size_t buf_bytes = up(row_bytes * (size_t)slab);
     int64_t ring = (int64_t)(kRingBytes / buf_bytes);
     ring = ring < 2 ? 2 : (ring > kRingMax ? kRingMax : ring);
-    const int nbuf = (int)(nslab < ring ? nslab : ring);
-    Events ev;  // [0, nbuf): slab landed in buffer b; [nbuf, 2 nbuf): buffer b free again; last: early exit
-    if ((e = ev.create(2 * nbuf + 1)) != cudaSuccess) return set_cuda_error(e);
     Scratch ws(st);  // compress lists, reused slab after slab on `st`
     if ((rc = ws.alloc(compress_scratch_bytes((slab / 8) * nbc)))) return rc;
-    // The staging ring is allocated on the copy stream (so the transfers do
-    // not wait for earlier work on `st`) and freed on `st` after the last
-    // slab, which has waited for every transfer.
-    void *stage = nullptr;
-    keep_pool_cached();
-    if ((e = cudaMallocAsync(&stage, nbuf * buf_bytes, cs)) != cudaSuccess) {
-        (void)cudaGetLastError();
-        return e == cudaErrorMemoryAllocation ? BLAZ_ERR_OOM : set_cuda_error(e);
-    }
-    auto finish = [&](int status) {
-        // on an early exit, `st` first waits for whatever the copy stream holds
-        cudaEvent_t last = ev.e[2 * nbuf];
-        if (status != BLAZ_OK && cudaEventRecord(last, cs) == cudaSuccess) cudaStreamWaitEvent(st, last, 0);
-        cudaFreeAsync(stage, st);
-        return status;
-    };
+    Ring &R = ring_of(dev);
+    std::lock_guard<std::mutex> lk(R.mu);
+    // keep the largest partition the ring has (fewer re-partitions for a
+    // stream of smaller calls); grow it when this call needs more
+    int nbuf = (int)(nslab < ring ? nslab : ring);
+    if (R.base && R.buf_bytes >= buf_bytes && R.nbuf >= 2) nbuf = R.nbuf;
+    const size_t bbytes = (R.base && R.buf_bytes >= buf_bytes && R.nbuf >= 2) ? R.buf_bytes : buf_bytes;
+    if ((rc = ring_prepare(R, bbytes, nbuf, cs))) return rc;
     for (int64_t k = 0; k < nslab; ++k) {
-        const int b = (int)(k % nbuf);
+        const int b = R.next;
+        R.next = (R.next + 1) % R.nbuf;
         const int64_t r0 = k * slab, nr = rows - r0 < slab ? rows - r0 : slab;
-        double *buf = (double *)((char *)stage + b * buf_bytes);
-        if (k >= nbuf && (e = cudaStreamWaitEvent(cs, ev.e[nbuf + b], 0)) != cudaSuccess)
-            return finish(set_cuda_error(e));
-        e = cudaMemcpy2DAsync(buf, row_bytes, A + r0 * lda, sizeof(double) * (size_t)lda, row_bytes, (size_t)nr,
-                              cudaMemcpyHostToDevice, cs);
-        if (e == cudaSuccess) e = cudaEventRecord(ev.e[b], cs);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev.e[b], 0);
-        if (e != cudaSuccess) return finish(set_cuda_error(e));
+        double *buf = (double *)(R.base + (size_t)b * R.buf_bytes);
+        if (R.used[b] && (e = cudaStreamWaitEvent(cs, R.freed[b], 0)) != cudaSuccess) return set_cuda_error(e);
+        // contiguous rows: one linear copy; otherwise a pitched copy
+        e = lda == cols ? cudaMemcpyAsync(buf, A + r0 * lda, row_bytes * (size_t)nr, cudaMemcpyHostToDevice, cs)
+                        : cudaMemcpy2DAsync(buf, row_bytes, A + r0 * lda, sizeof(double) * (size_t)lda, row_bytes,
+                                            (size_t)nr, cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess) e = cudaEventRecord(R.landed[b], cs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, R.landed[b], 0);
+        if (e != cudaSuccess) return set_cuda_error(e);
         const int64_t b0 = (r0 / 8) * nbc;
         blaz_cmat sub{nr, cols, out->f + b0, out->s + b0, out->phi + b0, out->code + b0 * kKeep};
-        if ((rc = launch_compress(buf, cols, nr, cols, &sub, ws.p, st))) return finish(rc);
-        if ((e = cudaEventRecord(ev.e[nbuf + b], st)) != cudaSuccess) return finish(set_cuda_error(e));
+        if ((rc = launch_compress(buf, cols, nr, cols, &sub, ws.p, st))) return rc;
+        if ((e = cudaEventRecord(R.freed[b], st)) != cudaSuccess) return set_cuda_error(e);
+        R.used[b] = true;
     }
-    return finish(BLAZ_OK);
+    return BLAZ_OK;
 }
 
 // Packed payload layout (as in a file): f[nb], s[nb] (binary64), phi[nb], code[nb][28].

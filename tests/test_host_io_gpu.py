@@ -85,3 +85,27 @@ def test_host_entry_point_errors(B):
     assert B.lib().blaz_compress_host(ctypes.c_void_p(h.data_ptr()), 23, ctypes.byref(d), st) == -3
     assert B.lib().blaz_compress_host(None, 24, ctypes.byref(d), st) == -2
     assert B.lib().blaz_cmat_download(ctypes.byref(d), None, st) == -2
+
+
+def test_back_to_back_calls_reuse_the_staging_ring(B):
+    """The staging ring persists from call to call: calls of different slab
+    sizes issued back to back, alternating between two streams and with no
+    synchronization between them, each give the device path's bits (a
+    buffer is refilled only after the compression of its previous slab)."""
+    shapes = [(88, 786432), (72, 136), (40, 327680), (88, 786432), (16, 1048576), (72, 136)]
+    srcs, outs = [], []
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    for k, (rows, cols) in enumerate(shapes):
+        t = W.bump_field_torch(cols, 7 * k + rows, "cuda", rows=rows)
+        h = torch.empty((rows, cols), dtype=torch.float64, pin_memory=True)
+        h.copy_(t)
+        srcs.append((t, h))
+    torch.cuda.synchronize()
+    for k, (t, h) in enumerate(srcs):
+        st = streams[k % 2]
+        with torch.cuda.stream(st):
+            outs.append(B.compress_host(h, stream=st))
+    torch.cuda.synchronize()
+    assert B.device_status() == 0
+    for (t, h), g in zip(srcs, outs):
+        same(g, B.compress(t))
