@@ -273,11 +273,13 @@ int blaz_dot_rowcol(const blaz_cmat *a, const blaz_cmat *b, int64_t i, int64_t j
  * decompressed once).  B: device, ldb >= m; C: device, ldc >= m.
  * mode BLAZ_MM_FP64: binary64 products on the FP64 tensor path (DMMA);
  * mode BLAZ_MM_SPLIT_BF16: A_hat and B each split into three bf16 slices; the
- * six slice products with i+j <= 4 run as one bf16 GEMM of inner dimension 6k
- * on the 5th-generation tensor cores (tcgen05, fp32 accumulation in tensor
- * memory), stored as binary64; relative error about 1e-6 of (|A_hat||B|)_ij.
- * Uses stream-ordered scratch: 8nk bytes for the decompressed operand, plus
- * 12k(n+m) bytes of slices in split mode. */
+ * six slice products with i+j <= 4 run as one bf16 GEMM of inner dimension
+ * 6kp (kp: k rounded up to a multiple of 64, the padding zero) on the
+ * 5th-generation tensor cores (tcgen05, fp32 accumulation in tensor memory),
+ * stored as binary64; componentwise error about 1e-6 to 1e-5 of
+ * (|A_hat||B|)_ij.  A's slices are decoded straight from the codes.
+ * Uses stream-ordered scratch: 8nk bytes for the decompressed operand in
+ * FP64 mode; 6kp(n+m) bytes of slices in split mode. */
 enum { BLAZ_MM_FP64 = 0, BLAZ_MM_SPLIT_BF16 = 1 };
 int blaz_matmul(const blaz_cmat *a, const double *B, int64_t ldb, int64_t m, double *C, int64_t ldc,
                 int mode, void *stream);
@@ -287,8 +289,9 @@ int blaz_matmul(const blaz_cmat *a, const double *B, int64_t ldb, int64_t m, dou
  * decompressed block computed once).  a: n x k, b: k x m (a->cols must equal
  * b->rows, else BLAZ_ERR_SHAPE); C: device, n x m binary64, ldc >= m.  Both
  * operands are decompressed once into stream-ordered scratch (8nk + 8km
- * bytes, plus 12k(n+m) bytes of slices in split mode), then multiplied as in
- * blaz_matmul with the same modes and accuracy (relative to |A_hat||B_hat|). */
+ * bytes; in split mode 8km bytes for B_hat, A's slices straight from its
+ * codes, and 6kp(n+m) bytes of slices), then multiplied as in blaz_matmul
+ * with the same modes and accuracy (relative to |A_hat||B_hat|). */
 int blaz_matmul_cc(const blaz_cmat *a, const blaz_cmat *b, double *C, int64_t ldc, int mode, void *stream);
 
 /* ---- Matrices of any shape (padding) ----------------------------------------

@@ -512,14 +512,14 @@ int blaz_matmul(const blaz_cmat *a, const double *B, int64_t ldb, int64_t m, dou
     if (!C || (k > 0 && !B)) return BLAZ_ERR_NULL;
     if (ldc < m || (k > 0 && ldb < m)) return BLAZ_ERR_LD;
     cudaStream_t st = (cudaStream_t)stream;
-    const size_t ah_bytes = (sizeof(double) * (size_t)(n * k) + 255) & ~(size_t)255;
-    const size_t extra = mode == BLAZ_MM_SPLIT_BF16 ? split_bf16_scratch_bytes(n, k, m) : 0;
     Scratch ws(st);
-    if ((rc = ws.alloc(ah_bytes + extra))) return rc;
+    if (mode == BLAZ_MM_SPLIT_BF16) {  // A's bf16 slices straight from the codes
+        if ((rc = ws.alloc(split_bf16_scratch_bytes(n, k, m)))) return rc;
+        return launch_matmul_split_bf16_cmat(a, B, ldb, C, ldc, m, ws.p, st);
+    }
+    if ((rc = ws.alloc(sizeof(double) * (size_t)(n * k)))) return rc;
     double *Ah = (double *)ws.p;
     if (k > 0 && (rc = launch_decompress(a, Ah, k, st))) return rc;
-    if (mode == BLAZ_MM_SPLIT_BF16)
-        return launch_matmul_split_bf16(Ah, k, B, ldb, C, ldc, n, k, m, (char *)ws.p + ah_bytes, st);
     return launch_gemm_fp64(Ah, k, B, ldb, C, ldc, n, k, m, st);
 }
 
@@ -537,14 +537,17 @@ int blaz_matmul_cc(const blaz_cmat *a, const blaz_cmat *b, double *C, int64_t ld
     cudaStream_t st = (cudaStream_t)stream;
     auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t ah_bytes = up(sizeof(double) * (size_t)(n * k)), bh_bytes = up(sizeof(double) * (size_t)(k * m));
-    const size_t extra = mode == BLAZ_MM_SPLIT_BF16 ? split_bf16_scratch_bytes(n, k, m) : 0;
     Scratch ws(st);
-    if ((rc = ws.alloc(ah_bytes + bh_bytes + extra))) return rc;
+    if (mode == BLAZ_MM_SPLIT_BF16) {  // A's slices from its codes, B decoded once, then split
+        if ((rc = ws.alloc(bh_bytes + split_bf16_scratch_bytes(n, k, m)))) return rc;
+        double *Bh = (double *)ws.p;
+        if (k > 0 && (rc = launch_decompress(b, Bh, m, st))) return rc;
+        return launch_matmul_split_bf16_cmat(a, Bh, m, C, ldc, m, (char *)ws.p + bh_bytes, st);
+    }
+    if ((rc = ws.alloc(ah_bytes + bh_bytes))) return rc;
     double *Ah = (double *)ws.p, *Bh = (double *)((char *)ws.p + ah_bytes);
     if (k > 0 && (rc = launch_decompress(a, Ah, k, st))) return rc;
     if (k > 0 && (rc = launch_decompress(b, Bh, m, st))) return rc;
-    if (mode == BLAZ_MM_SPLIT_BF16)
-        return launch_matmul_split_bf16(Ah, k, Bh, m, C, ldc, n, k, m, (char *)ws.p + ah_bytes + bh_bytes, st);
     return launch_gemm_fp64(Ah, k, Bh, m, C, ldc, n, k, m, st);
 }
 

@@ -156,6 +156,9 @@ int launch_compress(const double *A, int64_t lda, int64_t rows, int64_t cols, co
 // blocks beyond it are skipped, or written as 0 when zero_fill is set.
 int launch_decompress(const blaz_cmat *a, double *A, int64_t lda, cudaStream_t st, int64_t rows = -1,
                       int64_t cols = -1, bool zero_fill = false);
+// The split-precision product's A operand straight from the codes: the three
+// bf16 slices of A_hat into Sl = [A1 A2 A3] (rows x 3kp), padding zeroed.
+int launch_decompress_slices(const blaz_cmat *a, void *Sl, int64_t kp, cudaStream_t st);
 int launch_add(const blaz_cmat *a, const blaz_cmat *b, const blaz_cmat *out, bool subtract, cudaStream_t st);
 int launch_scale(const blaz_cmat *a, double c, const blaz_cmat *out, cudaStream_t st);
 // rows x cols: the logical shape (-1: the block grid's); for a padded pair the
@@ -170,6 +173,10 @@ int rowcol_grid(int64_t nkb);
 int launch_dot_rowcol(const blaz_cmat *a, const blaz_cmat *b, int64_t i, int64_t j, double *result,
                       double *partials, unsigned *counter, cudaStream_t st);
 size_t split_bf16_scratch_bytes(int64_t n, int64_t k, int64_t m);
+int launch_gemm_split_bf16(const void *Ap, const void *Bt, double *C, int64_t ldc, int64_t n, int64_t m, int64_t kp,
+                           cudaStream_t st);
+int launch_matmul_split_bf16_cmat(const blaz_cmat *a, const double *B, int64_t ldb, double *C, int64_t ldc,
+                                  int64_t m, void *scratch, cudaStream_t st);
 int launch_matmul_split_bf16(const double *Ah, int64_t lda, const double *B, int64_t ldb, double *C, int64_t ldc,
                              int64_t n, int64_t k, int64_t m, void *scratch, cudaStream_t st);
 int device_status(cudaStream_t st);

@@ -12,6 +12,7 @@
 #include "blaz_internal.cuh"
 #include "const_upload.cuh"
 #include "gmap.cuh"
+#include "split_bf16.cuh"
 
 namespace blaz {
 
@@ -100,11 +101,15 @@ __device__ __forceinline__ uint32_t code_pair(const int8_t *__restrict__ c, int 
 static_assert(slice_assembly_bound(kDecSlices, kDecDigitBits, kKeep) < (1ull << 62),
               "the slice assembly must fit dec_to_double's input range");
 
-template <bool kVec>
+// kSlices: instead of the binary64 matrix, the three bf16 slices of every
+// decoded value (split3) go to Sl = [A1 A2 A3] (rows x 3kp, row-major: the
+// split-precision product's A operand); full blocks only.
+template <bool kVec, bool kSlices = false>
 __global__ void __launch_bounds__(128)
     k_decompress(const double *__restrict__ f, const double *__restrict__ s,
                  const uint8_t *__restrict__ phi, const int8_t *__restrict__ code, int64_t nbc, int64_t nb,
-                 double *__restrict__ A, int64_t lda, int64_t rows, int64_t cols, bool zero_fill)
+                 double *__restrict__ A, int64_t lda, int64_t rows, int64_t cols, bool zero_fill,
+                 __nv_bfloat16 *__restrict__ Sl = nullptr, int64_t kp = 0)
 {
     __shared__ uint2 sb[kDecSlices][2][8][32];
     __shared__ double inv_phi_scaled[256];
@@ -178,6 +183,17 @@ __global__ void __launch_bounds__(128)
                 // M00 = f by definition (row 0 of G is zero), also when s is not finite
                 const double o0 = (nt == 0 && t == 0) ? fb[h] : fma(ts[h], dec_to_double(acc[2 * h]), fb[h]);
                 const double o1 = fma(ts[h], dec_to_double(acc[2 * h + 1]), fb[h]);
+                if (kSlices) {
+                    const int64_t b = h ? bB : bA, bi = b / nbc, bj = b - bi * nbc;
+                    __nv_bfloat16 *q = Sl + (bi * 8 + nt) * 3 * kp + bj * 8 + 2 * t;
+                    __nv_bfloat16 x1, x2, x3, y1, y2, y3;
+                    split3(o0, x1, x2, x3);
+                    split3(o1, y1, y2, y3);
+                    *reinterpret_cast<__nv_bfloat162 *>(q) = __halves2bfloat162(x1, y1);
+                    *reinterpret_cast<__nv_bfloat162 *>(q + kp) = __halves2bfloat162(x2, y2);
+                    *reinterpret_cast<__nv_bfloat162 *>(q + 2 * kp) = __halves2bfloat162(x3, y3);
+                    continue;
+                }
                 double *p = pb[h] + nt * lda;
                 if (inside[h]) {
                     if (kVec) {
@@ -203,6 +219,14 @@ __global__ void __launch_bounds__(128)
     }
 }
 
+// The once-per-device copy of the decompression constants (shared by both
+// launchers).
+static DeviceTable &dec_table()
+{
+    static DeviceTable t;
+    return t;
+}
+
 static bool vec_ok(const void *p, int64_t ld) { return ((uintptr_t)p % 16 == 0) && (ld % 2 == 0); }
 
 int launch_decompress(const blaz_cmat *a, double *A, int64_t lda, cudaStream_t st, int64_t rows, int64_t cols,
@@ -226,8 +250,7 @@ int launch_decompress(const blaz_cmat *a, double *A, int64_t lda, cudaStream_t s
     int64_t want = ((nb + 15) / 16 + 3) / 4;
     const int64_t cap = (int64_t)num_sms() * occ;
     const int grid = (int)std::max<int64_t>(1, std::min(want, cap));
-    static DeviceTable table;
-    const int rc = table.ensure(&g_dec, &dec_consts(), sizeof(DecConsts), 0, st);
+    const int rc = dec_table().ensure(&g_dec, &dec_consts(), sizeof(DecConsts), 0, st);
     if (rc) return rc;
     if (vec_ok(A, lda))
         k_decompress<true><<<grid, threads, 0, st>>>(a->f, a->s, a->phi, a->code, nbc, nb, A, lda, rows, cols,
@@ -235,6 +258,36 @@ int launch_decompress(const blaz_cmat *a, double *A, int64_t lda, cudaStream_t s
     else
         k_decompress<false><<<grid, threads, 0, st>>>(a->f, a->s, a->phi, a->code, nbc, nb, A, lda, rows, cols,
                                                       zero_fill);
+    return launch_status();
+}
+
+// The three bf16 slices of A_hat (a: full blocks, n = a->rows, k = a->cols)
+// into Sl = [A1 A2 A3] (n x 3kp), columns k..kp-1 of each slice zeroed.
+int launch_decompress_slices(const blaz_cmat *a, void *Sl, int64_t kp, cudaStream_t st)
+{
+    const int64_t nbc = a->cols / 8, nb = (a->rows / 8) * nbc, k = a->cols;
+    if (nb == 0) return BLAZ_OK;
+    __nv_bfloat16 *S = (__nv_bfloat16 *)Sl;
+    if (kp > k) {
+        // the padding columns of the 3 n rows of kp elements
+        cudaError_t e = cudaMemset2DAsync(S + k, (size_t)kp * 2, 0, (size_t)(kp - k) * 2, (size_t)(3 * a->rows), st);
+        if (e != cudaSuccess) return set_cuda_error(e);
+    }
+    static const int occ = [] {
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_decompress<true, true>, 128, 0) != cudaSuccess) {
+            (void)cudaGetLastError();
+            n = 4;
+        }
+        return n > 0 ? n : 1;
+    }();
+    int64_t want = ((nb + 15) / 16 + 3) / 4;
+    const int64_t cap = (int64_t)num_sms() * occ;
+    const int grid = (int)std::max<int64_t>(1, std::min(want, cap));
+    const int rc = dec_table().ensure(&g_dec, &dec_consts(), sizeof(DecConsts), 0, st);
+    if (rc) return rc;
+    k_decompress<true, true><<<grid, 128, 0, st>>>(a->f, a->s, a->phi, a->code, nbc, nb, nullptr, 0, a->rows,
+                                                   a->cols, false, S, kp);
     return launch_status();
 }
 
