@@ -36,14 +36,16 @@ __global__ void __launch_bounds__(128)
 // to a per-tile list with copies of its inputs.  Undecided codes are
 // structural rather than rare: equal phi and equal codes in both operands put
 // y on an integer (y = c phi / phi_k in real arithmetic), about one block in
-// ten of two smooth fields.  A ninth warp, the fixer, evaluates the listed
+// ten of two smooth fields.  Two more warps, the fixers, evaluate the listed
 // blocks in binary64 (add_block's arithmetic, undecided codes only; up to 32
-// blocks per pass of the warp, since a binary64 instruction costs a warp the
-// same for one lane as for 32), patches the tile's output codes in shared
-// memory and stores them with 16-byte writes, while the compute warps
-// already decide the next tile: the two share double-buffered output tiles
-// and lists through mbarriers (bounded waits; BLAZ_ERR_TIMEOUT in the status
-// word of these kernels).
+// blocks per pass of a warp, since a binary64 instruction costs a warp the
+// same for one lane as for 32): one forms beta_1 and the other beta_2 of
+// every listed block, so the division chains run on two warps at once, then
+// each evaluates the undecided codes of one bit parity; they patch the
+// tile's output codes in shared memory and store them with 16-byte writes,
+// while the compute warps already decide the next tile: the two sides share
+// double-buffered output tiles and lists through mbarriers (bounded waits;
+// BLAZ_ERR_TIMEOUT in the status word of these kernels).
 //
 // Every input of a tile is read before any output of it is written, so out
 // may alias a or b.  Requires 16-byte aligned code arrays (the launcher
@@ -122,6 +124,38 @@ __device__ __forceinline__ void add_fix_block(double sa, double sb, int pa, int 
     }
 }
 
+// The two halves of add_fix_block for a pair of fixer warps: side k (0: the
+// first operand, 1: the second) forms beta_k = RN(RN(RN(s_k / s) / phi_k) phi)
+// as add_fix_block does, so the binary64 division chains of a tile's list
+// run on two warps (the binary64 issue rate is per warp instruction, not per
+// lane: splitting lanes would not shorten the chain, splitting instructions
+// does).
+__device__ __forceinline__ double add_fix_beta(double sa, double sb, int pa, int pb, int side)
+{
+    const double ss = dadd(sa, sb);
+    int ph = (pa * pb) / (pa + pb);
+    ph = ph < 1 ? 1 : ph;
+    const double ak = ddiv(side ? sb : sa, ss);
+    return dmul(div_small_int(ak, side ? pb : pa), i64_to_double(ph));
+}
+
+// The undecided codes of one block whose bit index has parity `par` (the
+// other fixer warp takes the others), from beta_1 and beta_2.
+template <bool kSub>
+__device__ __forceinline__ void add_fix_codes(double b1, double b2, const uint32_t *wa, const uint32_t *wb,
+                                              uint32_t undecided, int par, uint32_t *wo)
+{
+    for (uint32_t m = undecided & (par ? 0xAAAAAAAAu : 0x55555555u); m; m &= m - 1u) {
+        const int bit = __ffs(m) - 1, q = bit >> 2, k = bit & 3;
+        const double x1 = (double)(int8_t)(uint8_t)(wa[q] >> (8 * k));
+        const double x2 = (double)(int8_t)(uint8_t)(wb[q] >> (8 * k));
+        const double y = kSub ? dsub(dmul(b1, x1), dmul(b2, x2)) : dadd(dmul(b1, x1), dmul(b2, x2));
+        reinterpret_cast<int8_t *>(wo + q)[k] = quantize(y);
+    }
+}
+
+__device__ __forceinline__ void fixer_bar() { asm volatile("bar.sync 2, %0;" ::"n"(2 * 32) : "memory"); }
+
 __device__ __forceinline__ bool ops_wait(uint64_t *bar, uint32_t parity)
 {
     const long long t0 = clock64();
@@ -135,8 +169,10 @@ __device__ __forceinline__ bool ops_wait(uint64_t *bar, uint32_t parity)
 
 __device__ __forceinline__ void compute_bar() { asm volatile("bar.sync 1, %0;" ::"n"(kAddTile) : "memory"); }
 
+constexpr int kAddFixers = 2;  // fixer warps per CTA
+
 template <bool kSub>
-__global__ void __launch_bounds__(kAddTile + 32, 3)
+__global__ void __launch_bounds__(kAddTile + 32 * kAddFixers, 3)
     k_add_tile(int64_t nb, const double *f1, const double *s1, const uint8_t *p1, const int8_t *c1,
                const double *f2, const double *s2, const uint8_t *p2, const int8_t *c2, double *f, double *s,
                uint8_t *p, int8_t *c)
@@ -149,6 +185,8 @@ __global__ void __launch_bounds__(kAddTile + 32, 3)
     AddFix(*fix)[kAddFixCap] = reinterpret_cast<AddFix(*)[kAddFixCap]>(add_smem + 6 * kAddTile * 7 * 4);
     __shared__ int nfix[2];
     __shared__ __align__(8) uint64_t work_ready[2], out_free[2];
+    __shared__ double fbeta[kAddFixers][kAddFixCap];  // beta_1, beta_2 of the listed blocks
+    __shared__ volatile int fix_ok;
     __shared__ volatile int abort_flag;
     const int t = threadIdx.x;
     const int64_t ntiles = (nb + kAddTile - 1) / kAddTile;
@@ -164,36 +202,44 @@ __global__ void __launch_bounds__(kAddTile + 32, 3)
     __syncthreads();
 
     if (t >= kAddTile) {
-        // the fixer warp
-        const int lane = t - kAddTile;
+        // the two fixer warps: fixer fw forms beta_(fw+1) of every listed
+        // block, then the listed codes of bit parity fw; both store the tile
+        const int fw = (t - kAddTile) >> 5, lane = t & 31, ft = t - kAddTile;
         for (int it = 0;; ++it) {
             const int64_t tile = blockIdx.x + (int64_t)it * gridDim.x;
             if (tile >= ntiles) break;
             const int u = it & 1;
-            bool ok = true;
-            if (lane == 0) ok = ops_wait(&work_ready[u], (it >> 1) & 1);
-            if (!__shfl_sync(0xffffffffu, ok, 0)) {
+            // fixer 0 waits for the tile; both learn the outcome after one
+            // barrier, so they always leave the loop together
+            if (ft == 0) fix_ok = ops_wait(&work_ready[u], (it >> 1) & 1) ? 1 : 0;
+            fixer_bar();
+            if (!fix_ok) {
                 abort_flag = 1;
                 break;
             }
             const int n = min(nfix[u], kAddFixCap);
             for (int e = lane; e < n; e += 32) {
                 const AddFix &x = fix[u][e];
-                add_fix_block<kSub>(x.sa, x.sb, x.pa, x.pb, x.wa, x.wb, x.undecided, so_st[u] + x.t * 7);
+                fbeta[fw][e] = add_fix_beta(x.sa, x.sb, x.pa, x.pb, fw);
             }
-            __syncwarp();
+            fixer_bar();
+            for (int e = lane; e < n; e += 32) {
+                const AddFix &x = fix[u][e];
+                add_fix_codes<kSub>(fbeta[0][e], fbeta[1][e], x.wa, x.wb, x.undecided, fw, so_st[u] + x.t * 7);
+            }
+            fixer_bar();
             const int64_t b0 = tile * kAddTile;
             const int nt = (int)(nb - b0 < kAddTile ? nb - b0 : (int64_t)kAddTile);
             uint32_t *go = reinterpret_cast<uint32_t *>(c + b0 * kKeep);
             if (nt == kAddTile) {
                 uint4 *vo = reinterpret_cast<uint4 *>(go);
-                for (int i = lane; i < kAddTile * 7 / 4; i += 32)
+                for (int i = ft; i < kAddTile * 7 / 4; i += 32 * kAddFixers)
                     __stcs(vo + i, reinterpret_cast<const uint4 *>(so_st[u])[i]);
             } else {
-                for (int i = lane; i < nt * 7; i += 32) __stcs(go + i, so_st[u][i]);
+                for (int i = ft; i < nt * 7; i += 32 * kAddFixers) __stcs(go + i, so_st[u][i]);
             }
-            __syncwarp();
-            if (lane == 0) {
+            fixer_bar();  // both warps' reads of the output tile and the list are done
+            if (ft == 0) {
                 nfix[u] = 0;
                 umma::mbar_arrive(&out_free[u]);
             }
@@ -420,10 +466,10 @@ int launch_add(const blaz_cmat *a, const blaz_cmat *b, const blaz_cmat *o, bool 
         }();
         if (!smem_ok) return set_cuda_error(cudaGetLastError());
         if (subtract)
-            k_add_tile<true><<<grid, kAddTile + 32, kAddSmem, st>>>(nb, a->f, a->s, a->phi, a->code, b->f, b->s, b->phi,
+            k_add_tile<true><<<grid, kAddTile + 32 * kAddFixers, kAddSmem, st>>>(nb, a->f, a->s, a->phi, a->code, b->f, b->s, b->phi,
                                                         b->code, o->f, o->s, o->phi, o->code);
         else
-            k_add_tile<false><<<grid, kAddTile + 32, kAddSmem, st>>>(nb, a->f, a->s, a->phi, a->code, b->f, b->s, b->phi,
+            k_add_tile<false><<<grid, kAddTile + 32 * kAddFixers, kAddSmem, st>>>(nb, a->f, a->s, a->phi, a->code, b->f, b->s, b->phi,
                                                          b->code, o->f, o->s, o->phi, o->code);
         return launch_status();
     }
