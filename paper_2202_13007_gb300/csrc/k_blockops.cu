@@ -28,9 +28,15 @@ __global__ void __launch_bounds__(128)
 // code from v = fl(beta_1 c_1 +- beta_2 c_2) and the bound
 //   |v - y| <= 2^-19 (|beta_1 c_1| + |beta_2 c_2|) + 2^-22 |v| + 2^-100
 // (2^-20 from beta, 2^-23 from the fp32 product and fma, the binary64
-// roundings of the specification far below), evaluated per code as
-// E = 1.25 2^-19 (|beta_1| |c_1| + |beta_2| |c_2|) + 2^-100 (two fma).
-// f and s are two binary64 additions per block.
+// roundings of the specification far below).  With |c_k| <= 128 and
+// |v| <= (|beta_1 c_1| + |beta_2 c_2|)(1 + 2^-20) the bound is at most
+// 1.125 2^-12 (|beta_1| + |beta_2|) + 2^-100, so one half-width serves the
+// whole block: E = 1.25 2^-12 (|beta_1| + |beta_2|) + 2^-100 (the factor
+// 1.25 covers the fp32 roundings of E and of v +- E).  A code is decided
+// when v - E and v + E truncate to the same int8 (saturating conversions,
+// four codes per word compared at once) other than -128, the saturated
+// value below quantize's -127.  f and s are two binary64 additions per
+// block.
 //
 // A block with an undecided code, or whose beta_k has no fp32 estimate, goes
 // to a per-tile list with copies of its inputs.  Undecided codes are
@@ -56,7 +62,7 @@ constexpr int kAddFixCap = 64;  // list entries per tile; beyond, the block's ow
 struct AddFix {
     double sa, sb;
     uint32_t wa[7], wb[7];  // the block's codes (the input stage is reused before the fixer runs)
-    uint32_t undecided;     // bit 4q+k: code 4q+k
+    uint32_t undecided;     // bit 8k+q: code 4q+k (byte k of word q)
     int t, pa, pb;
 };
 
@@ -100,7 +106,7 @@ __device__ __forceinline__ void add_stage_codes(int64_t tile, int64_t nb, const 
     }
 }
 
-// binary64 Algorithm 1 for the undecided codes of one block (bit 4q+k of
+// binary64 Algorithm 1 for the undecided codes of one block (bit 8k+q of
 // `undecided`: code k of word q), patched into its output words.
 template <bool kSub>
 __device__ __forceinline__ void add_fix_block(double sa, double sb, int pa, int pb, const uint32_t *wa,
@@ -116,7 +122,7 @@ __device__ __forceinline__ void add_fix_block(double sa, double sb, int pa, int 
     const double b2 = dmul(div_small_int(a2, pb), phd);
     // one pass per undecided code (the lane's set bits, lowest first)
     for (uint32_t m = undecided; m; m &= m - 1u) {
-        const int bit = __ffs(m) - 1, q = bit >> 2, k = bit & 3;
+        const int bit = __ffs(m) - 1, q = bit & 7, k = bit >> 3;
         const double x1 = (double)(int8_t)(uint8_t)(wa[q] >> (8 * k));
         const double x2 = (double)(int8_t)(uint8_t)(wb[q] >> (8 * k));
         const double y = kSub ? dsub(dmul(b1, x1), dmul(b2, x2)) : dadd(dmul(b1, x1), dmul(b2, x2));
@@ -139,19 +145,41 @@ __device__ __forceinline__ double add_fix_beta(double sa, double sb, int pa, int
     return dmul(div_small_int(ak, side ? pb : pa), i64_to_double(ph));
 }
 
-// The undecided codes of one block whose bit index has parity `par` (the
-// other fixer warp takes the others), from beta_1 and beta_2.
+// The undecided codes 4q+k of one block with k of parity `par` (the other
+// fixer warp takes the others), from beta_1 and beta_2.
 template <bool kSub>
 __device__ __forceinline__ void add_fix_codes(double b1, double b2, const uint32_t *wa, const uint32_t *wb,
                                               uint32_t undecided, int par, uint32_t *wo)
 {
-    for (uint32_t m = undecided & (par ? 0xAAAAAAAAu : 0x55555555u); m; m &= m - 1u) {
-        const int bit = __ffs(m) - 1, q = bit >> 2, k = bit & 3;
+    for (uint32_t m = undecided & (par ? 0xFF00FF00u : 0x00FF00FFu); m; m &= m - 1u) {
+        const int bit = __ffs(m) - 1, q = bit & 7, k = bit >> 3;
         const double x1 = (double)(int8_t)(uint8_t)(wa[q] >> (8 * k));
         const double x2 = (double)(int8_t)(uint8_t)(wb[q] >> (8 * k));
         const double y = kSub ? dsub(dmul(b1, x1), dmul(b2, x2)) : dadd(dmul(b1, x1), dmul(b2, x2));
         reinterpret_cast<int8_t *>(wo + q)[k] = quantize(y);
     }
+}
+
+// Truncation toward zero to int8, saturated to [-128, 127] (the low byte of
+// the result register).
+__device__ __forceinline__ uint32_t cvt_s8_rz(float x)
+{
+    uint32_t r;
+    asm("cvt.rzi.s8.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+// Bit 7 of byte k set when byte k of the truncations of the two ends differs,
+// or when that of the lower end is -128 (0x80: saturated, below quantize's
+// range): the undecided codes of a word.  Per byte x, (x & 0x7F) + 0x7F sets
+// bit 7 exactly when the low 7 bits are not all zero, with no carry into the
+// next byte.
+__device__ __forceinline__ uint32_t undecided_bytes(uint32_t lw, uint32_t hw)
+{
+    const uint32_t d = lw ^ hw;
+    const uint32_t ne = ((d & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | d;
+    const uint32_t m128 = ~((lw & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) & lw;
+    return (ne | m128) & 0x80808080u;
 }
 
 __device__ __forceinline__ void fixer_bar() { asm volatile("bar.sync 2, %0;" ::"n"(2 * 32) : "memory"); }
@@ -304,20 +332,16 @@ __global__ void __launch_bounds__(kAddTile + 32 * kAddFixers, 3)
                 float b1f = 0.0f, b2f = 0.0f;
                 const bool ok = beta_f32(sa, ss, __fdividef(phf, (float)pa), b1f) &
                                 beta_f32(sb, ss, __fdividef(phf, (float)pb), b2f);
-                // |v| <= (|beta_1 c_1| + |beta_2 c_2|)(1 + 2^-20), so the bound is at most
-                // 1.125 2^-19 (|beta_1 c_1| + |beta_2 c_2|) + 2^-100; 1.25 covers the fp32
-                // roundings of E = e_1 |c_1| + e_2 |c_2| + 2^-100 with e_k = 1.25 2^-19 |beta_k|
-                const float e1 = 0x1.4p-19f * fabsf(b1f), e2 = 0x1.4p-19f * fabsf(b2f);
+                const float E = __fmaf_rn(0x1.4p-12f, __fadd_rn(fabsf(b1f), fabsf(b2f)), 0x1p-100f);
                 // two codes at a time on the paired fp32 pipe (same per-lane roundings)
                 const float2 B1 = make_float2(b1f, b1f), B2 = make_float2(kSub ? -b2f : b2f, kSub ? -b2f : b2f);
-                const float2 E1 = make_float2(e1, e1), E2 = make_float2(e2, e2);
-                const float2 bias = make_float2(-12583040.0f, -12583040.0f), tiny = make_float2(0x1p-100f, 0x1p-100f);
-                const float2 neg1 = make_float2(-1.0f, -1.0f);
+                const float2 EP = make_float2(E, E), EN = make_float2(-E, -E);
+                const float2 bias = make_float2(-12583040.0f, -12583040.0f);
 #pragma unroll
                 for (int q = 0; q < 7; ++q) {
                     // byte k of (w ^ 0x80808080) in the low byte of 1.5 2^23: the float 12583040 + c
                     const uint32_t wa = sa_w[t * 7 + q] ^ 0x80808080u, wb = sb_w[t * 7 + q] ^ 0x80808080u;
-                    uint32_t v32 = 0;
+                    uint32_t lo8[4], hi8[4];
 #pragma unroll
                     for (int k = 0; k < 4; k += 2) {
                         const float2 x1 = __fadd2_rn(make_float2(__uint_as_float(__byte_perm(wa, 0x4B400000u, 0x7640 + k)),
@@ -327,19 +351,18 @@ __global__ void __launch_bounds__(kAddTile + 32 * kAddFixers, 3)
                                                                  __uint_as_float(__byte_perm(wb, 0x4B400000u, 0x7641 + k))),
                                                      bias);
                         const float2 v = __ffma2_rn(B1, x1, __fmul2_rn(B2, x2));
-                        const float2 E = __ffma2_rn(E1, make_float2(fabsf(x1.x), fabsf(x1.y)),
-                                                    __ffma2_rn(E2, make_float2(fabsf(x2.x), fabsf(x2.y)), tiny));
-                        const float2 hi = __fadd2_rn(v, E), lo = __ffma2_rn(E, neg1, v);
-                        // trunc of both ends, saturated to +-127: one code when they agree
-                        const int l0 = min(127, max(-127, (int)truncf(lo.x))), h0 = min(127, max(-127, (int)truncf(hi.x)));
-                        const int l1 = min(127, max(-127, (int)truncf(lo.y))), h1 = min(127, max(-127, (int)truncf(hi.y)));
-                        undecided |= (uint32_t)(l0 != h0) << (4 * q + k);
-                        undecided |= (uint32_t)(l1 != h1) << (4 * q + k + 1);
-                        v32 |= ((uint32_t)(uint8_t)(int8_t)l0 << (8 * k)) | ((uint32_t)(uint8_t)(int8_t)l1 << (8 * k + 8));
+                        const float2 hi = __fadd2_rn(v, EP), lo = __fadd2_rn(v, EN);
+                        lo8[k] = cvt_s8_rz(lo.x);
+                        lo8[k + 1] = cvt_s8_rz(lo.y);
+                        hi8[k] = cvt_s8_rz(hi.x);
+                        hi8[k + 1] = cvt_s8_rz(hi.y);
                     }
-                    so_w[t * 7 + q] = v32;
+                    const uint32_t lw = __byte_perm(__byte_perm(lo8[0], lo8[1], 0x0040), __byte_perm(lo8[2], lo8[3], 0x0040), 0x5410);
+                    const uint32_t hw = __byte_perm(__byte_perm(hi8[0], hi8[1], 0x0040), __byte_perm(hi8[2], hi8[3], 0x0040), 0x5410);
+                    so_w[t * 7 + q] = lw;
+                    undecided |= undecided_bytes(lw, hw) >> (7 - q);  // bit 8k + q
                 }
-                if (!ok) undecided = 0x0FFFFFFFu;
+                if (!ok) undecided = 0x7F7F7F7Fu;
             }
             if (undecided) {
                 const int i = atomicAdd(&nfix[u], 1);

@@ -1,12 +1,13 @@
 """The tiled addition kernel decides each code of Algorithm 1 from fp32
 estimates of beta_k = RN(RN(RN(s_k/s)/phi_k) phi) and the bound
     |v - y| <= 2^-19 (|beta_1 c_1| + |beta_2 c_2|) + 2^-22 |v| + 2^-100,
-evaluated as E = 1.25 2^-19 (|beta_1| |c_1| + |beta_2| |c_2|) + 2^-100 (two fma),
-falling back to binary64 when the interval [v - E, v + E] does not truncate
-to one code.  This test emulates the kernel's fp32 arithmetic in numpy (the
-scaled truncations of s_k and s, a quotient perturbed to both ends of the
-2-ulp error of the fast division, the fp32 product and fused multiply-add,
-the bound evaluated in the kernel's order) and checks every decided code
+taken over |c_k| <= 128 as one half-width per block,
+E = 1.25 2^-12 (|beta_1| + |beta_2|) + 2^-100, falling back to binary64 when
+v - E and v + E do not truncate to the same int8 (saturated to [-128, 127];
+-128 is left undecided).  This test emulates the kernel's fp32 arithmetic in
+numpy (the scaled truncations of s_k and s, a quotient perturbed to both ends
+of the 2-ulp error of the fast division, the fp32 product and fused
+multiply-add, the bound in the kernel's order) and checks every decided code
 against the oracle's binary64 Algorithm 1: on pairs of compressed fields, on
 self-additions (v sits on integers), on partners scaled by negative, tiny and
 huge constants, and on random slopes, phi and codes over a wide exponent
@@ -60,23 +61,26 @@ def kernel_codes(a, b, pert1, pert2, sub=False):
     if sub:
         p2 = -p2
     v = (b1.astype(np.float64) * x1.astype(np.float64) + p2.astype(np.float64)).astype(F32)
-    e1 = F32(F32(1.25 * 2.0 ** -19) * np.abs(b1))
-    e2 = F32(F32(1.25 * 2.0 ** -19) * np.abs(b2))
-    inner = (e2.astype(np.float64) * np.abs(x2).astype(np.float64) + 2.0 ** -100).astype(F32)
-    E = (e1.astype(np.float64) * np.abs(x1).astype(np.float64) + inner.astype(np.float64)).astype(F32)
+    # E = fma(1.25 2^-12, |b1| + |b2|, 2^-100): the product is exact in binary64
+    S = (np.abs(b1).astype(np.float64) + np.abs(b2).astype(np.float64)).astype(F32)
+    E = (1.25 * 2.0 ** -12 * S.astype(np.float64) + 2.0 ** -100).astype(F32)
     lo, hi = F32(v - E), F32(v + E)
     with np.errstate(invalid="ignore", over="ignore"):
         tl, th = np.trunc(lo), np.trunc(hi)
-    code = np.where(lo >= 127, 127, np.where(hi <= -127, -127, tl))
-    decided = (lo >= 127) | (hi <= -127) | (tl == th)
-    # the same decisions as trunc of both ends saturated to +-127 (the
-    # kernels' branch-free form): decided when the two agree, code = that value
-    with np.errstate(invalid="ignore"):
-        cl = np.clip(np.nan_to_num(tl, nan=0.0), -127, 127)
-        ch = np.clip(np.nan_to_num(th, nan=0.0), -127, 127)
     finite = np.isfinite(lo) & np.isfinite(hi)
-    assert np.array_equal((cl == ch)[finite], decided[finite])
-    assert np.array_equal(np.where(cl == ch, cl, 0)[finite], np.where(decided, code, 0)[finite])
+    # the kernel: saturating int8 truncations of both ends, decided when they
+    # agree and are not -128
+    cl = np.clip(np.nan_to_num(tl, nan=0.0), -128, 127)
+    ch = np.clip(np.nan_to_num(th, nan=0.0), -128, 127)
+    decided = (cl == ch) & (cl != -128)
+    code = cl
+    # every such decision is one of quantize's: y in [lo, hi] and trunc
+    # saturated to +-127 is constant there
+    math_code = np.where(lo >= 127, 127, np.where(hi <= -127, -127, tl))
+    math_decided = (lo >= 127) | (hi <= -127) | (tl == th)
+    assert np.all(math_decided[decided & finite])
+    assert np.array_equal(code[decided & finite], math_code[decided & finite])
+    decided &= finite
     decided &= (ok1 & ok2)[:, None]
     zero_s = (ss == 0.0)[:, None]
     code = np.where(zero_s, 0, code)
@@ -111,10 +115,11 @@ def fields():
 
 def test_decided_codes_of_field_pairs_match_the_oracle(fields):
     a, b = fields
-    # blocks with an undecided code go to binary64: about one in ten here, most
-    # of them equal phi and equal codes in both operands (y on an integer)
-    check_pair(a, b, max_undecided=0.15)
-    check_pair(a, b, sub=True, max_undecided=0.15)
+    # blocks with an undecided code go to binary64: about one in ten here (one
+    # in seven for the difference), most of them equal phi and equal codes in
+    # both operands (y on an integer)
+    check_pair(a, b, max_undecided=0.12)
+    check_pair(a, b, sub=True, max_undecided=0.17)
 
 
 def test_decided_codes_of_self_additions_match_the_oracle(fields):

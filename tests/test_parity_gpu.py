@@ -291,6 +291,40 @@ def test_add_tiles_ragged_aliased_and_unaligned(B):
     assert_cmat_equal(B.add(a, gy), O.add(ox, oy))
 
 
+def test_add_tiles_of_random_payloads(B):
+    """The tiled kernel on payloads no compressor writes: codes over the whole
+    int8 range (-128 included), slopes over 2^+-115, near-cancelling and equal
+    slopes (huge and integer-valued beta, saturated codes, tiles with more
+    listed blocks than the list holds), zero slopes; 7 tiles and a ragged
+    one.  Same bits as the oracle for the sum and the difference."""
+    rng = np.random.default_rng(77)
+    n = 7 * 256 + 37
+    mats = []
+    for _ in range(2):
+        m = O.CMat.empty(8, 8 * n)
+        m.f[:] = rng.normal(size=n)
+        m.s[:] = rng.choice([-1.0, 1.0], n) * np.exp(rng.uniform(-80, 80, n))
+        m.phi[:] = rng.integers(1, 256, n)
+        m.code[:] = rng.integers(-128, 128, (n, 28))
+        mats.append(m)
+    a, b = mats
+    b.s[: n // 8] = -a.s[: n // 8] * (1 + rng.uniform(-1e-12, 1e-12, n // 8))
+    b.s[n // 8: n // 4] = a.s[n // 8: n // 4]
+    b.s[n // 4: n // 4 + 64] = 0.0
+    a.s[n // 4 + 64: n // 4 + 80] = 0.0
+    b.phi[n // 2: n // 2 + 300] = a.phi[n // 2: n // 2 + 300]
+    b.code[n // 2: n // 2 + 300] = a.code[n // 2: n // 2 + 300]
+
+    def gpu(m):
+        t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+        return B.CMat(m.rows, m.cols, t(m.f), t(m.s), t(m.phi), t(m.code))
+
+    ga, gb = gpu(a), gpu(b)
+    assert_cmat_equal(B.add(ga, gb), O.add(a, b))
+    assert_cmat_equal(B.sub(ga, gb), O.sub(a, b))
+    assert_cmat_equal(B.add(gb, ga), O.add(b, a))
+
+
 # --- dot products and matmul -----------------------------------------------------------------
 def test_dot_plain_pair(B):
     A, Bm = W.plain_pair()
