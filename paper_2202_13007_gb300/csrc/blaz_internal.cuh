@@ -88,6 +88,22 @@ __device__ __forceinline__ int8_t quantize(double v)
     return (int8_t)__double2int_rz(v);
 }
 
+// The same function on the integer pipe (the binary64 pipe is the scarce
+// one): trunc toward zero saturated to [-127, 127], NaN -> 0, from the bits.
+__device__ __forceinline__ int8_t quantize_bits(double v)
+{
+    const long long b = __double_as_longlong(v);
+    const bool neg = b < 0;
+    const int e = (int)((b >> 52) & 0x7FF);
+    if (e == 0x7FF) return (b & 0x000FFFFFFFFFFFFFll) ? 0 : (neg ? -127 : 127);
+    if (e < 1023) return 0;
+    if (e >= 1023 + 7) return neg ? -127 : 127;
+    const unsigned long long m = ((unsigned long long)b & 0x000FFFFFFFFFFFFFull) | (1ull << 52);
+    int mag = (int)(m >> (52 - (e - 1023)));
+    mag = mag > 127 ? 127 : mag;
+    return (int8_t)(neg ? -mag : mag);
+}
+
 // ---- host-side launch plumbing (defined in blaz_api.cu) ------------------------
 int set_cuda_error(cudaError_t e);   // records e, returns BLAZ_ERR_CUDA
 int launch_status();                 // cudaGetLastError -> BLAZ_OK / BLAZ_ERR_CUDA

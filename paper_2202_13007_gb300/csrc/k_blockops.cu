@@ -56,25 +56,55 @@ __global__ void __launch_bounds__(128)
 // Every input of a tile is read before any output of it is written, so out
 // may alias a or b.  Requires 16-byte aligned code arrays (the launcher
 // checks).
-constexpr int kAddTile = 256;
-constexpr int kAddFixCap = 64;  // list entries per tile; beyond, the block's own thread fixes it
+#ifndef BLAZ_ADD_TILE
+#define BLAZ_ADD_TILE 256
+#endif
+#ifndef BLAZ_ADD_STAGES
+#define BLAZ_ADD_STAGES 2
+#endif
+#ifndef BLAZ_ADD_OUT
+#define BLAZ_ADD_OUT 2
+#endif
+#ifndef BLAZ_ADD_CTAS
+#define BLAZ_ADD_CTAS 3
+#endif
+constexpr int kAddTile = BLAZ_ADD_TILE;     // blocks per tile (one per compute thread)
+constexpr int kAddStages = BLAZ_ADD_STAGES; // input stages: tiles in flight ahead of the one decided
+constexpr int kAddOut = BLAZ_ADD_OUT;       // output tiles and lists shared with the fixers
+constexpr int kAddCtas = BLAZ_ADD_CTAS;     // resident CTAs per SM
+constexpr int kAddFixCap = kAddTile / 4;    // list entries per tile; beyond, the block's own thread fixes it
 
 struct AddFix {
-    double sa, sb;
-    uint32_t wa[7], wb[7];  // the block's codes (the input stage is reused before the fixer runs)
+    double sa, sb, ss;      // s_1, s_2 and s = s_1 + s_2
+    uint32_t wa[7], wb[7];  // the block's codes (the input stage is refilled before the fixers run)
     uint32_t undecided;     // bit 8k+q: code 4q+k (byte k of word q)
-    int t, pa, pb;
+    int t, pa, pb, ph;
 };
+
+// Every input of one tile: the codes of both operands (7 words per block),
+// f, s and phi of both.  16-byte aligned arrays (kAddTile a multiple of 16).
+struct AddStage {
+    uint32_t ca[kAddTile * 7], cb[kAddTile * 7];
+    double fa[kAddTile], fb[kAddTile], sa[kAddTile], sb[kAddTile];
+    uint8_t pa[kAddTile], pb[kAddTile];
+};
+static_assert(kAddTile % 16 == 0 && sizeof(AddStage) == 90 * kAddTile && kAddStages >= 2, "stage layout");
 
 __device__ int g_ops_status;  // 0 or BLAZ_ERR_TIMEOUT (tiled addition)
 
-// two input stages of each operand, two output tiles, two lists
-constexpr size_t kAddSmem = 6 * kAddTile * 7 * 4 + 2 * kAddFixCap * sizeof(AddFix);
+// input stages, output tiles, lists
+constexpr size_t kAddSmem =
+    kAddStages * sizeof(AddStage) + kAddOut * kAddTile * 7 * 4 + kAddOut * kAddFixCap * sizeof(AddFix);
 
 __device__ __forceinline__ void cp_async16(void *dst, const void *src)
 {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
                  "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
                  : "memory");
 }
 __device__ __forceinline__ void cp_async4(void *dst, const void *src)
@@ -83,25 +113,52 @@ __device__ __forceinline__ void cp_async4(void *dst, const void *src)
                  : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+// this thread's copies of all but the newest kAddStages - 2 groups have
+// landed (the groups of the tiles ahead of the current one, committed after
+// its barrier)
+__device__ __forceinline__ void cp_async_wait_stage()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(kAddStages - 2) : "memory");
+}
 
-// Starts the copies of the codes of both operands of one tile into a stage.
-__device__ __forceinline__ void add_stage_codes(int64_t tile, int64_t nb, const int8_t *c1, const int8_t *c2,
-                                                uint32_t *da, uint32_t *db, int t)
+// 16-byte copies of `bytes` (a multiple of 16) by the kAddTile compute threads.
+__device__ __forceinline__ void stage_copy16(void *dst, const void *src, int bytes, int t)
+{
+    for (int i = t; i < bytes / 16; i += kAddTile)
+        cp_async16(static_cast<uint4 *>(dst) + i, static_cast<const uint4 *>(src) + i);
+}
+
+// Starts the copies of every input of one tile into a stage.  A ragged last
+// tile copies words (codes), 8-byte elements (f, s) and, phi, plain bytes.
+__device__ __forceinline__ void add_stage(int64_t tile, int64_t nb, const double *f1, const double *s1,
+                                          const uint8_t *p1, const int8_t *c1, const double *f2, const double *s2,
+                                          const uint8_t *p2, const int8_t *c2, AddStage &st, int t)
 {
     const int64_t b0 = tile * kAddTile;
     const int nt = (int)(nb - b0 < kAddTile ? nb - b0 : (int64_t)kAddTile);
-    const uint32_t *ga = reinterpret_cast<const uint32_t *>(c1 + b0 * kKeep);
-    const uint32_t *gb = reinterpret_cast<const uint32_t *>(c2 + b0 * kKeep);
     if (nt == kAddTile) {
-        for (int i = t; i < kAddTile * 7 / 4; i += kAddTile) {
-            cp_async16(da + 4 * i, ga + 4 * i);
-            cp_async16(db + 4 * i, gb + 4 * i);
-        }
+        stage_copy16(st.ca, c1 + b0 * kKeep, kAddTile * kKeep, t);
+        stage_copy16(st.cb, c2 + b0 * kKeep, kAddTile * kKeep, t);
+        stage_copy16(st.fa, f1 + b0, kAddTile * 8, t);
+        stage_copy16(st.fb, f2 + b0, kAddTile * 8, t);
+        stage_copy16(st.sa, s1 + b0, kAddTile * 8, t);
+        stage_copy16(st.sb, s2 + b0, kAddTile * 8, t);
+        stage_copy16(st.pa, p1 + b0, kAddTile, t);
+        stage_copy16(st.pb, p2 + b0, kAddTile, t);
     } else {
+        const uint32_t *ga = reinterpret_cast<const uint32_t *>(c1 + b0 * kKeep);
+        const uint32_t *gb = reinterpret_cast<const uint32_t *>(c2 + b0 * kKeep);
         for (int i = t; i < nt * 7; i += kAddTile) {
-            cp_async4(da + i, ga + i);
-            cp_async4(db + i, gb + i);
+            cp_async4(st.ca + i, ga + i);
+            cp_async4(st.cb + i, gb + i);
+        }
+        if (t < nt) {
+            cp_async8(st.fa + t, f1 + b0 + t);
+            cp_async8(st.fb + t, f2 + b0 + t);
+            cp_async8(st.sa + t, s1 + b0 + t);
+            cp_async8(st.sb + t, s2 + b0 + t);
+            st.pa[t] = p1[b0 + t];
+            st.pb[t] = p2[b0 + t];
         }
     }
 }
@@ -123,26 +180,25 @@ __device__ __forceinline__ void add_fix_block(double sa, double sb, int pa, int 
     // one pass per undecided code (the lane's set bits, lowest first)
     for (uint32_t m = undecided; m; m &= m - 1u) {
         const int bit = __ffs(m) - 1, q = bit & 7, k = bit >> 3;
-        const double x1 = (double)(int8_t)(uint8_t)(wa[q] >> (8 * k));
-        const double x2 = (double)(int8_t)(uint8_t)(wb[q] >> (8 * k));
+        // the conversions and quantize on the integer pipe: three binary64
+        // operations per code
+        const double x1 = i64_to_double((int8_t)(uint8_t)(wa[q] >> (8 * k)));
+        const double x2 = i64_to_double((int8_t)(uint8_t)(wb[q] >> (8 * k)));
         const double y = kSub ? dsub(dmul(b1, x1), dmul(b2, x2)) : dadd(dmul(b1, x1), dmul(b2, x2));
-        reinterpret_cast<int8_t *>(wo + q)[k] = quantize(y);
+        reinterpret_cast<int8_t *>(wo + q)[k] = quantize_bits(y);
     }
 }
 
-// The two halves of add_fix_block for a pair of fixer warps: side k (0: the
-// first operand, 1: the second) forms beta_k = RN(RN(RN(s_k / s) / phi_k) phi)
-// as add_fix_block does, so the binary64 division chains of a tile's list
+// The two halves of add_fix_block for a pair of fixer warps: each forms one
+// beta_k = RN(RN(RN(s_k / s) / phi_k) phi) (s and phi as the compute warps
+// formed them) as add_fix_block does, so the binary64 division chains of a
+// tile's list
 // run on two warps (the binary64 issue rate is per warp instruction, not per
 // lane: splitting lanes would not shorten the chain, splitting instructions
 // does).
-__device__ __forceinline__ double add_fix_beta(double sa, double sb, int pa, int pb, int side)
+__device__ __forceinline__ double add_fix_beta(double sk, double ss, int pk, int ph)
 {
-    const double ss = dadd(sa, sb);
-    int ph = (pa * pb) / (pa + pb);
-    ph = ph < 1 ? 1 : ph;
-    const double ak = ddiv(side ? sb : sa, ss);
-    return dmul(div_small_int(ak, side ? pb : pa), i64_to_double(ph));
+    return dmul(div_small_int(ddiv(sk, ss), pk), i64_to_double(ph));
 }
 
 // The undecided codes 4q+k of one block with k of parity `par` (the other
@@ -153,10 +209,12 @@ __device__ __forceinline__ void add_fix_codes(double b1, double b2, const uint32
 {
     for (uint32_t m = undecided & (par ? 0xFF00FF00u : 0x00FF00FFu); m; m &= m - 1u) {
         const int bit = __ffs(m) - 1, q = bit & 7, k = bit >> 3;
-        const double x1 = (double)(int8_t)(uint8_t)(wa[q] >> (8 * k));
-        const double x2 = (double)(int8_t)(uint8_t)(wb[q] >> (8 * k));
+        // the conversions and quantize on the integer pipe: three binary64
+        // operations per code
+        const double x1 = i64_to_double((int8_t)(uint8_t)(wa[q] >> (8 * k)));
+        const double x2 = i64_to_double((int8_t)(uint8_t)(wb[q] >> (8 * k)));
         const double y = kSub ? dsub(dmul(b1, x1), dmul(b2, x2)) : dadd(dmul(b1, x1), dmul(b2, x2));
-        reinterpret_cast<int8_t *>(wo + q)[k] = quantize(y);
+        reinterpret_cast<int8_t *>(wo + q)[k] = quantize_bits(y);
     }
 }
 
@@ -200,26 +258,27 @@ __device__ __forceinline__ void compute_bar() { asm volatile("bar.sync 1, %0;" :
 constexpr int kAddFixers = 2;  // fixer warps per CTA
 
 template <bool kSub>
-__global__ void __launch_bounds__(kAddTile + 32 * kAddFixers, 3)
+__global__ void __launch_bounds__(kAddTile + 32 * kAddFixers, kAddCtas)
     k_add_tile(int64_t nb, const double *f1, const double *s1, const uint8_t *p1, const int8_t *c1,
                const double *f2, const double *s2, const uint8_t *p2, const int8_t *c2, double *f, double *s,
                uint8_t *p, int8_t *c)
 {
     // dynamic shared memory (kAddSmem bytes): input stages, output tiles, lists
     extern __shared__ __align__(16) uint8_t add_smem[];
-    uint32_t(*sa_st)[kAddTile * 7] = reinterpret_cast<uint32_t(*)[kAddTile * 7]>(add_smem);
-    uint32_t(*sb_st)[kAddTile * 7] = sa_st + 2;
-    uint32_t(*so_st)[kAddTile * 7] = sa_st + 4;
-    AddFix(*fix)[kAddFixCap] = reinterpret_cast<AddFix(*)[kAddFixCap]>(add_smem + 6 * kAddTile * 7 * 4);
-    __shared__ int nfix[2];
-    __shared__ __align__(8) uint64_t work_ready[2], out_free[2];
+    AddStage *stages = reinterpret_cast<AddStage *>(add_smem);
+    uint32_t(*so_st)[kAddTile * 7] = reinterpret_cast<uint32_t(*)[kAddTile * 7]>(add_smem + kAddStages * sizeof(AddStage));
+    AddFix(*fix)[kAddFixCap] = reinterpret_cast<AddFix(*)[kAddFixCap]>(
+        add_smem + kAddStages * sizeof(AddStage) + kAddOut * kAddTile * 7 * 4);
+    __shared__ int nfix[kAddOut];
+    __shared__ __align__(8) uint64_t work_ready[kAddOut], out_free[kAddOut];
     __shared__ double fbeta[kAddFixers][kAddFixCap];  // beta_1, beta_2 of the listed blocks
     __shared__ volatile int fix_ok;
     __shared__ volatile int abort_flag;
+    __shared__ volatile int go_on[2];  // written by thread 0 only, before the compute barrier
     const int t = threadIdx.x;
     const int64_t ntiles = (nb + kAddTile - 1) / kAddTile;
     if (t == 0) {
-        for (int q = 0; q < 2; ++q) {
+        for (int q = 0; q < kAddOut; ++q) {
             umma::mbar_init(&work_ready[q], kAddTile);
             umma::mbar_init(&out_free[q], 1);
             nfix[q] = 0;
@@ -231,15 +290,16 @@ __global__ void __launch_bounds__(kAddTile + 32 * kAddFixers, 3)
 
     if (t >= kAddTile) {
         // the two fixer warps: fixer fw forms beta_(fw+1) of every listed
-        // block, then the listed codes of bit parity fw; both store the tile
+        // block, then the listed codes 4q+k with k of parity fw; both store
+        // the tile
         const int fw = (t - kAddTile) >> 5, lane = t & 31, ft = t - kAddTile;
         for (int it = 0;; ++it) {
             const int64_t tile = blockIdx.x + (int64_t)it * gridDim.x;
             if (tile >= ntiles) break;
-            const int u = it & 1;
+            const int u = it % kAddOut;
             // fixer 0 waits for the tile; both learn the outcome after one
             // barrier, so they always leave the loop together
-            if (ft == 0) fix_ok = ops_wait(&work_ready[u], (it >> 1) & 1) ? 1 : 0;
+            if (ft == 0) fix_ok = ops_wait(&work_ready[u], (it / kAddOut) & 1) ? 1 : 0;
             fixer_bar();
             if (!fix_ok) {
                 abort_flag = 1;
@@ -248,7 +308,7 @@ __global__ void __launch_bounds__(kAddTile + 32 * kAddFixers, 3)
             const int n = min(nfix[u], kAddFixCap);
             for (int e = lane; e < n; e += 32) {
                 const AddFix &x = fix[u][e];
-                fbeta[fw][e] = add_fix_beta(x.sa, x.sb, x.pa, x.pb, fw);
+                fbeta[fw][e] = add_fix_beta(fw ? x.sb : x.sa, x.ss, fw ? x.pb : x.pa, x.ph);
             }
             fixer_bar();
             for (int e = lane; e < n; e += 32) {
@@ -275,49 +335,46 @@ __global__ void __launch_bounds__(kAddTile + 32 * kAddFixers, 3)
         return;
     }
 
-    // the compute warps
-    int64_t tile = blockIdx.x;
-    if (tile < ntiles) add_stage_codes(tile, nb, c1, c2, sa_st[0], sb_st[0], t);
-    cp_async_commit();
-    // f, s and phi of the current tile, loaded one tile ahead
-    double nfa = 0.0, nfb = 0.0, nsa = 0.0, nsb = 0.0;
-    int npa = 1, npb = 1;
-    if (tile < ntiles && tile * kAddTile + t < nb) {
-        const int64_t b = tile * kAddTile + t;
-        nfa = __ldcs(f1 + b);
-        nfb = __ldcs(f2 + b);
-        nsa = __ldcs(s1 + b);
-        nsb = __ldcs(s2 + b);
-        npa = __ldcs(p1 + b);
-        npb = __ldcs(p2 + b);
+    // the compute warps: the inputs of kAddStages - 1 tiles in flight ahead
+    // of the tile being decided
+#pragma unroll
+    for (int k = 0; k < kAddStages - 1; ++k) {
+        const int64_t tk = blockIdx.x + (int64_t)k * gridDim.x;
+        if (tk < ntiles) add_stage(tk, nb, f1, s1, p1, c1, f2, s2, p2, c2, stages[k], t);
+        cp_async_commit();
     }
+    int64_t tile = blockIdx.x;
     for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
-        const int stg = it & 1, u = it & 1;
-        const uint32_t *sa_w = sa_st[stg], *sb_w = sb_st[stg];
+        const int u = it % kAddOut;
+        const AddStage &stg = stages[it % kAddStages];
+        const uint32_t *sa_w = stg.ca, *sb_w = stg.cb;
         uint32_t *so_w = so_st[u];
         const int64_t b0 = tile * kAddTile;
         const int nt = (int)(nb - b0 < kAddTile ? nb - b0 : (int64_t)kAddTile);
-        const int64_t next = tile + gridDim.x;
-        if (next < ntiles) add_stage_codes(next, nb, c1, c2, sa_st[stg ^ 1], sb_st[stg ^ 1], t);
-        cp_async_commit();
-        const double fa = nfa, fb = nfb, sa = nsa, sb = nsb;
-        const int pa = npa, pb = npb;
-        if (next < ntiles && next * kAddTile + t < nb) {
-            const int64_t bn = next * kAddTile + t;
-            nfa = __ldcs(f1 + bn);
-            nfb = __ldcs(f2 + bn);
-            nsa = __ldcs(s1 + bn);
-            nsb = __ldcs(s2 + bn);
-            npa = __ldcs(p1 + bn);
-            npb = __ldcs(p2 + bn);
+        // output tile u is free once the fixers have stored tile it - kAddOut;
+        // thread 0 takes the decision to go on for all compute threads (a
+        // fixer may set abort_flag at any time: reading it after the barrier
+        // could split the threads, and the next barrier has no time limit;
+        // two copies, so that thread 0 never rewrites the one a thread may
+        // still be about to read)
+        if (t == 0) {
+            if (!ops_wait(&out_free[u], ((it / kAddOut) & 1) ^ 1)) abort_flag = 1;
+            go_on[it & 1] = !abort_flag;
         }
-        const int64_t b = b0 + t;
-        // the output tile u is free once the fixer has stored tile it - 2
-        if (t == 0 && !ops_wait(&out_free[u], ((it >> 1) & 1) ^ 1)) abort_flag = 1;
-        cp_async_wait_prev();  // this thread's copies of the current stage have landed
+        cp_async_wait_stage();  // this thread's copies of the current stage have landed
+        // the one barrier of the tile: every copy of this stage is visible,
+        // and every thread is done with the stage of tile it - 1, which the
+        // copies for tile it + kAddStages - 1 now refill
         compute_bar();
-        if (abort_flag) break;
+        if (!go_on[it & 1]) break;
+        const int64_t ahead = tile + (int64_t)(kAddStages - 1) * gridDim.x;
+        if (ahead < ntiles)
+            add_stage(ahead, nb, f1, s1, p1, c1, f2, s2, p2, c2, stages[(it + kAddStages - 1) % kAddStages], t);
+        cp_async_commit();
         if (t < nt) {
+            const int64_t b = b0 + t;
+            const double fa = stg.fa[t], fb = stg.fb[t], sa = stg.sa[t], sb = stg.sb[t];
+            const int pa = stg.pa[t], pb = stg.pb[t];
             const double fs = kSub ? dsub(fa, fb) : dadd(fa, fb);
             const double ss = dadd(sa, sb);
             int ph = (pa * pb) / (pa + pb);
@@ -370,6 +427,7 @@ __global__ void __launch_bounds__(kAddTile + 32 * kAddFixers, 3)
                     AddFix &x = fix[u][i];
                     x.sa = sa;
                     x.sb = sb;
+                    x.ss = ss;
 #pragma unroll
                     for (int q = 0; q < 7; ++q) {
                         x.wa[q] = sa_w[t * 7 + q];
@@ -379,6 +437,7 @@ __global__ void __launch_bounds__(kAddTile + 32 * kAddFixers, 3)
                     x.t = t;
                     x.pa = pa;
                     x.pb = pb;
+                    x.ph = ph;
                 } else {
                     add_fix_block<kSub>(sa, sb, pa, pb, sa_w + t * 7, sb_w + t * 7, undecided, so_w + t * 7);
                 }
@@ -388,7 +447,6 @@ __global__ void __launch_bounds__(kAddTile + 32 * kAddFixers, 3)
             p[b] = (uint8_t)ph;
         }
         umma::mbar_arrive(&work_ready[u]);
-        compute_bar();  // every thread is done with this input stage before it is refilled
     }
     asm volatile("cp.async.wait_all;" ::: "memory");  // nothing in flight at exit (an aborted loop)
 }
@@ -476,11 +534,12 @@ int launch_add(const blaz_cmat *a, const blaz_cmat *b, const blaz_cmat *o, bool 
     const int64_t nb = (a->rows / 8) * (a->cols / 8);
     if (nb == 0) return BLAZ_OK;
     auto a16 = [](const void *q) { return ((uintptr_t)q & 15) == 0; };
-    if (a16(a->code) && a16(b->code) && a16(o->code)) {
-        // tiles of 256 blocks; one wave of 3 resident CTAs per SM, each
-        // looping over its tiles with the next tile's codes in flight
+    if (a16(a->code) && a16(b->code) && a16(o->code) && a16(a->f) && a16(b->f) && a16(a->s) && a16(b->s) &&
+        a16(a->phi) && a16(b->phi)) {
+        // one wave of kAddCtas resident CTAs per SM, each looping over its
+        // tiles with the inputs of the next kAddStages - 1 tiles in flight
         const int64_t ntiles = (nb + kAddTile - 1) / kAddTile;
-        const int grid = (int)std::min<int64_t>(ntiles, (int64_t)num_sms() * 3);
+        const int grid = (int)std::min<int64_t>(ntiles, (int64_t)num_sms() * kAddCtas);
         static const bool smem_ok = [] {
             return cudaFuncSetAttribute(k_add_tile<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)kAddSmem) == cudaSuccess &&
