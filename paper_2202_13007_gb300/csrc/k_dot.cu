@@ -53,15 +53,20 @@ struct GramConsts {
 };
 
 
-// Tensor-core form of the Gram dot, 16 blocks per warp.  Y_s = C_b H_s
-// (plus the column w_s) on mma.sync m16n8k16 with fp16 digits of H_s and w_s
-// (|digit| <= 2^10, exact in fp16) and fp16 codes; every product sum is an
-// integer below 2^22, exact in the fp32 accumulators.  Then, per row of the
-// accumulator fragment, sum_k ca_k Y_s[k] with Y split into exact 12-bit
-// halves, reduced over the four lanes that hold the row.
+// Tensor-core form of the Gram dot, 16 blocks per warp group.  Per slice s:
+// Y_s = C_b H_s on mma.sync m16n8k16 with fp16 digits of H_s (|digit| <=
+// 2^10, exact in fp16) and fp16 codes, every product sum an integer below
+// 2^22, exact in the fp32 accumulators; w_s.c_b and w_s.c_a on two more
+// products whose B operand holds w_s in every even column, so that every
+// lane of a row's quad receives both rows' values; and sum_k c_a[k] Y_s[k]
+// on the integer pipe: adding 1.5 2^23 to an accumulator makes its bits
+// 0x4B400000 + Y_s[k], and 64-bit multiply-adds accumulate c_a[k] times those
+// bits over the slices in Horner form (slices 0-2 and 3-4 in two
+// accumulators).  The constant the offset contributes is taken off once,
+// and the four lanes of a quad are summed once per group, not per slice.
 struct GramTC {
-    uint2 bfrag[kSlices][2][4][32];  // [slice][k-step][n-tile][lane]: H_s (columns 0..27) and w_s (column 28)
-    float wl[kSlices][32][8];        // w_s digits at the 8 code positions a lane holds
+    uint2 bfrag[kSlices][2][4][32];  // [slice][k-step][n-tile][lane]: H_s (columns 0..27)
+    uint2 wfrag[kSlices][2][32];     // [slice][k-step][lane]: w_s in the even columns of one n-tile
     int eH2, eH4, eW2, eW4;          // log2 of scaleH[2], scaleH[4], scaleW[2], scaleW[4]
     double inv_phi[256];
 };
@@ -121,104 +126,105 @@ __device__ __forceinline__ uint32_t code_pair_h(const int8_t *__restrict__ c, in
     return pair_to_h2(code_pair_raw(c, k, valid));
 }
 
-// Code k (0 or 1) of a raw pair as fp32 (exact).
-__device__ __forceinline__ float pair_code_f(uint32_t v, int k)
-{
-    return __uint_as_float(__byte_perm(v ^ 0x8080u, 0x4B400000u, 0x7640 + k)) - 12583040.0f;
-}
-
-// rint of an integer-valued x / 4096 with |x| < 2^33 (so |x / 4096| < 2^21).
-__device__ __forceinline__ float rint_div4096(float x)
-{
-    return (x * (1.0f / 4096.0f) + 12582912.0f) - 12582912.0f;
-}
-
-// One group of 16 blocks (rows gq and gq + 8 of the fragments): the slice
-// products C_b H_s and w_s.c_b on the tensor cores, the exact contraction
-// with c_a and w_s.c_a in the fragments, reduced over the 4 lanes of a row.
-// Every lane of a quad ends with the sums of both of its rows; the lane keeps
-// those of row `row` when `keep` holds.
-__device__ __forceinline__ void gram_group(const uint2 (*sbf)[2][4][32], const float (*swl)[32][8], int64_t grp,
+// One group of 16 blocks (rows gq and gq + 8 of the fragments).  On return
+// every lane of a quad holds, for the row `row` it keeps (when `keep`), Q in
+// two parts (qhi: slices 0-2 in units of slice 2, qlo: slices 3-4 in units of
+// slice 4) and the per-slice values of w_s.c_a and w_s.c_b.
+__device__ __forceinline__ void gram_group(const uint2 (*sbf)[2][4][32], const uint2 (*swf)[2][32], int64_t grp,
                                            int64_t nb, const int8_t *__restrict__ ca, const int8_t *__restrict__ cb,
-                                           int lane, int gq, int t, int row, bool keep, float (&qh)[kSlices],
-                                           float (&ql)[kSlices], float (&wbs)[kSlices], float (&was)[kSlices])
+                                           int lane, int gq, int t, int row, bool keep, long long &qhi,
+                                           long long &qlo, float (&was)[kSlices], float (&wbs)[kSlices])
 {
     const int64_t bA = grp * 16 + gq, bB = bA + 8;
     const bool vA = bA < nb, vB = bB < nb;
-    // A fragments: codes of B-matrix blocks (rows gq and gq + 8).
     const int8_t *cbA = cb + bA * kKeep, *cbB = cb + bB * kKeep;
-    uint32_t a0[4], a1[4];
-    a0[0] = code_pair_h(cbA, 2 * t, vA);
-    a0[1] = code_pair_h(cbB, 2 * t, vB);
-    a0[2] = code_pair_h(cbA, 2 * t + 8, vA);
-    a0[3] = code_pair_h(cbB, 2 * t + 8, vB);
-    a1[0] = code_pair_h(cbA, 16 + 2 * t, vA);
-    a1[1] = code_pair_h(cbB, 16 + 2 * t, vB);
-    a1[2] = code_pair_h(cbA, 24 + 2 * t, vA);
-    a1[3] = code_pair_h(cbB, 24 + 2 * t, vB);
-    // ca at the 8 code positions this lane holds (k = nt*8 + 2t + {0,1}), rows gq and gq+8.
-    float xa[2][8];
-    {
-        const int8_t *caA = ca + bA * kKeep, *caB = ca + bB * kKeep;
+    const int8_t *caA = ca + bA * kKeep, *caB = ca + bB * kKeep;
+    // A fragments of the codes of both operands (k-steps 0 and 1)
+    uint32_t b0[4], b1[4], a0[4], a1[4];
+    b0[0] = code_pair_h(cbA, 2 * t, vA);
+    b0[1] = code_pair_h(cbB, 2 * t, vB);
+    b0[2] = code_pair_h(cbA, 2 * t + 8, vA);
+    b0[3] = code_pair_h(cbB, 2 * t + 8, vB);
+    b1[0] = code_pair_h(cbA, 16 + 2 * t, vA);
+    b1[1] = code_pair_h(cbB, 16 + 2 * t, vB);
+    b1[2] = code_pair_h(cbA, 24 + 2 * t, vA);
+    b1[3] = code_pair_h(cbB, 24 + 2 * t, vB);
+    // c_a at the 8 code positions this lane holds (k = nt*8 + 2t + {0,1}),
+    // rows gq and gq + 8: raw pairs, their fp16 fragments and the integers
+    uint32_t pA[4], pB[4];
 #pragma unroll
-        for (int nt = 0; nt < 4; ++nt) {
-            const uint32_t pA = code_pair_raw(caA, nt * 8 + 2 * t, vA), pB = code_pair_raw(caB, nt * 8 + 2 * t, vB);
-            xa[0][2 * nt] = pair_code_f(pA, 0);
-            xa[0][2 * nt + 1] = pair_code_f(pA, 1);
-            xa[1][2 * nt] = pair_code_f(pB, 0);
-            xa[1][2 * nt + 1] = pair_code_f(pB, 1);
-        }
+    for (int nt = 0; nt < 4; ++nt) {
+        pA[nt] = code_pair_raw(caA, nt * 8 + 2 * t, vA);
+        pB[nt] = code_pair_raw(caB, nt * 8 + 2 * t, vB);
     }
+    a0[0] = pair_to_h2(pA[0]);
+    a0[1] = pair_to_h2(pB[0]);
+    a0[2] = pair_to_h2(pA[1]);
+    a0[3] = pair_to_h2(pB[1]);
+    a1[0] = pair_to_h2(pA[2]);
+    a1[1] = pair_to_h2(pB[2]);
+    a1[2] = pair_to_h2(pA[3]);
+    a1[3] = pair_to_h2(pB[3]);
+    int xA[4][2], xB[4][2];
+    int sA = 0, sB = 0;
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            xA[nt][q] = (int)(int8_t)(uint8_t)(pA[nt] >> (8 * q));
+            xB[nt][q] = (int)(int8_t)(uint8_t)(pB[nt] >> (8 * q));
+            sA += xA[nt][q];
+            sB += xB[nt][q];
+        }
+    long long hA = 0, lA = 0, hB = 0, lB = 0;
+    const float2 magic = make_float2(12582912.0f, 12582912.0f);
 #pragma unroll
     for (int sl = 0; sl < kSlices; ++sl) {
-        // rows gq and gq + 8 side by side on the paired fp32 instructions
-        // (the same per-lane roundings as scalar fmas; every value is an
-        // exact integer)
-        float2 H = make_float2(0.f, 0.f), L = H, WA = H;
-        float w0 = 0.f, w1 = 0.f;
-        const float2 inv4096 = make_float2(1.0f / 4096.0f, 1.0f / 4096.0f), m4096 = make_float2(-4096.0f, -4096.0f);
-        const float2 rnd = make_float2(12582912.0f, 12582912.0f), nrnd = make_float2(-12582912.0f, -12582912.0f);
+        long long &accA = sl < 3 ? hA : lA, &accB = sl < 3 ? hB : lB;
+        if (sl != 0 && sl != 3) {
+            accA *= 2048;
+            accB *= 2048;
+        }
 #pragma unroll
         for (int nt = 0; nt < 4; ++nt) {
             float c[4] = {0.f, 0.f, 0.f, 0.f};
-            mma_f16x(c, a0, sbf[sl][0][nt][lane]);
-            mma_f16x(c, a1, sbf[sl][1][nt][lane]);
+            mma_f16x(c, b0, sbf[sl][0][nt][lane]);
+            mma_f16x(c, b1, sbf[sl][1][nt][lane]);
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
-                const int k = nt * 8 + 2 * t + q;
-                if (k < kKeep) {
-                    const float2 y = make_float2(c[q], c[2 + q]);
-                    const float2 yh = __fadd2_rn(__ffma2_rn(y, inv4096, rnd), nrnd);  // rint(y / 4096)
-                    const float2 x = make_float2(xa[0][2 * nt + q], xa[1][2 * nt + q]);
-                    H = __ffma2_rn(x, yh, H);
-                    L = __ffma2_rn(x, __ffma2_rn(m4096, yh, y), L);
-                    const float wd = swl[sl][lane][2 * nt + q];
-                    WA = __ffma2_rn(x, make_float2(wd, wd), WA);
-                } else if (k == kKeep) {  // column 28: w_s . cb
-                    w0 = c[q];
-                    w1 = c[2 + q];
-                }
+                const float2 y = __fadd2_rn(make_float2(c[q], c[2 + q]), magic);
+                accA += (long long)xA[nt][q] * __float_as_int(y.x);
+                accB += (long long)xB[nt][q] * __float_as_int(y.y);
             }
         }
-        float h0 = H.x, h1 = H.y, l0 = L.x, l1 = L.y, wa0 = WA.x, wa1 = WA.y;
-        // reduce over the four lanes of the row (exact integer sums)
-#pragma unroll
-        for (int o = 1; o < 4; o <<= 1) {
-            h0 += __shfl_xor_sync(0xffffffffu, h0, o);
-            l0 += __shfl_xor_sync(0xffffffffu, l0, o);
-            h1 += __shfl_xor_sync(0xffffffffu, h1, o);
-            l1 += __shfl_xor_sync(0xffffffffu, l1, o);
-            w0 += __shfl_xor_sync(0xffffffffu, w0, o);
-            w1 += __shfl_xor_sync(0xffffffffu, w1, o);
-            wa0 += __shfl_xor_sync(0xffffffffu, wa0, o);
-            wa1 += __shfl_xor_sync(0xffffffffu, wa1, o);
-        }
+        float d[4] = {0.f, 0.f, 0.f, 0.f}, e[4] = {0.f, 0.f, 0.f, 0.f};
+        mma_f16x(d, b0, swf[sl][0][lane]);
+        mma_f16x(d, b1, swf[sl][1][lane]);
+        mma_f16x(e, a0, swf[sl][0][lane]);
+        mma_f16x(e, a1, swf[sl][1][lane]);
         if (keep) {
-            qh[sl] = row ? h1 : h0;
-            ql[sl] = row ? l1 : l0;
-            wbs[sl] = row ? w1 : w0;
-            was[sl] = row ? wa1 : wa0;
+            wbs[sl] = row ? d[2] : d[0];
+            was[sl] = row ? e[2] : e[0];
         }
+    }
+    // the offset: sum_k c_a[k] 0x4B400000 per slice, times the Horner weights
+    // (|sum| < 2^63 before and after: per slice and lane below 2^40.2)
+    constexpr long long kOffHi = 0x4B400000ll * ((1ll << 22) + (1ll << 11) + 1);
+    constexpr long long kOffLo = 0x4B400000ll * ((1ll << 11) + 1);
+    hA -= kOffHi * sA;
+    lA -= kOffLo * sA;
+    hB -= kOffHi * sB;
+    lB -= kOffLo * sB;
+#pragma unroll
+    for (int o = 1; o < 4; o <<= 1) {
+        hA += __shfl_xor_sync(0xffffffffu, hA, o);
+        lA += __shfl_xor_sync(0xffffffffu, lA, o);
+        hB += __shfl_xor_sync(0xffffffffu, hB, o);
+        lB += __shfl_xor_sync(0xffffffffu, lB, o);
+    }
+    if (keep) {
+        qhi = row ? hB : hA;
+        qlo = row ? lB : lA;
     }
 }
 
@@ -233,13 +239,13 @@ __global__ void __launch_bounds__(kDotThreads, 3)
              int64_t nbc, int64_t rows, int64_t cols, bool padded)
 {
     __shared__ uint2 sbf[kSlices][2][4][32];
-    __shared__ float swl[kSlices][32][8];
+    __shared__ uint2 swf[kSlices][2][32];
     __shared__ double inv_phi[256];
     __shared__ double red[kDotThreads / 32];
     __shared__ bool last;
     const GramTC &g = g_gram;
     for (int i = threadIdx.x; i < kSlices * 2 * 4 * 32; i += blockDim.x) (&sbf[0][0][0][0])[i] = (&g.bfrag[0][0][0][0])[i];
-    for (int i = threadIdx.x; i < kSlices * 32 * 8; i += blockDim.x) (&swl[0][0][0])[i] = (&g.wl[0][0][0])[i];
+    for (int i = threadIdx.x; i < kSlices * 2 * 32; i += blockDim.x) (&swf[0][0][0])[i] = (&g.wfrag[0][0][0])[i];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) inv_phi[i] = g.inv_phi[i];
     const int eH2 = g.eH2, eH4 = g.eH4, eW2 = g.eW2, eW4 = g.eW4;
     __syncthreads();
@@ -248,10 +254,12 @@ __global__ void __launch_bounds__(kDotThreads, 3)
     const int64_t npairs = (nb + 31) / 32;
     double acc1 = 0.0, acc2 = 0.0;
     for (int64_t pr = (int64_t)blockIdx.x * wpc + warp; pr < npairs; pr += (int64_t)gridDim.x * wpc) {
-        float qh[kSlices], ql[kSlices], wbs[kSlices], was[kSlices];
+        long long qhi = 0, qlo = 0;
+        float was[kSlices], wbs[kSlices];
 #pragma unroll 1
         for (int half = 0; half < 2; ++half)  // not unrolled: one group's registers at a time
-            gram_group(sbf, swl, 2 * pr + half, nb, ca, cb, lane, gq, t, t & 1, (t >> 1) == half, qh, ql, wbs, was);
+            gram_group(sbf, swf, 2 * pr + half, nb, ca, cb, lane, gq, t, t & 1, (t >> 1) == half, qhi, qlo, was,
+                       wbs);
         // This lane's block: group 2 pr + (t >> 1), row gq + 8 (t & 1).
         const int64_t b = (2 * pr + (t >> 1)) * 16 + gq + 8 * (t & 1);
         bool use = b < nb;
@@ -260,19 +268,16 @@ __global__ void __launch_bounds__(kDotThreads, 3)
             use = bi * 8 + 8 <= rows && bj * 8 + 8 <= cols;
         }
         if (use) {
-            // slices assembled in int64 (0-2 and 3-4), then
+            // w slices assembled in int64 (0-2 and 3-4), then
             // fa (64 fb + tb Wb) + ta (fb Wa + tb Q)
-            long long qhi = 0, qlo = 0, ahi = 0, alo = 0, bhi = 0, blo = 0;
+            long long ahi = 0, alo = 0, bhi = 0, blo = 0;
 #pragma unroll
             for (int sl = 0; sl < kSlices; ++sl) {
-                const long long T = 4096ll * f2i_small(qh[sl]) + f2i_small(ql[sl]);
                 const long long A = f2i_small(was[sl]), Bw = f2i_small(wbs[sl]);
                 if (sl < 3) {
-                    qhi = qhi * 2048 + T;
                     ahi = ahi * 2048 + A;
                     bhi = bhi * 2048 + Bw;
                 } else {
-                    qlo = qlo * 2048 + T;
                     alo = alo * 2048 + A;
                     blo = blo * 2048 + Bw;
                 }
@@ -458,28 +463,22 @@ static const GramTC &gram_tc()
             const __half a = __float2half_rn(lo), b = __float2half_rn(hi);
             return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
         };
-        // B[k = l (code of cb)][n]: n < 28 -> H_s[n][l]; n == 28 -> w_s[l]; else 0.
-        auto bval = [&](int s, int l, int n) -> float {
-            if (l >= kKeep) return 0.0f;
-            if (n < kKeep) return gc.H[s][n][l];
-            if (n == kKeep) return gc.w[s][l];
-            return 0.0f;
-        };
+        // B[k = l (code of cb)][n] = H_s[n][l] for n, l < 28, else 0.
+        auto bval = [&](int s, int l, int n) -> float { return l < kKeep && n < kKeep ? gc.H[s][n][l] : 0.0f; };
+        // B[k = l][n] = w_s[l] in the even columns n of the w product.
+        auto wval = [&](int s, int l, int n) -> float { return l < kKeep && n % 2 == 0 ? gc.w[s][l] : 0.0f; };
         for (int s = 0; s < kSlices; ++s)
             for (int ks = 0; ks < 2; ++ks)
-                for (int nt = 0; nt < 4; ++nt)
-                    for (int lane = 0; lane < 32; ++lane) {
-                        const int gg = lane >> 2, t = lane & 3, n = nt * 8 + gg, k = ks * 16 + 2 * t;
+                for (int lane = 0; lane < 32; ++lane) {
+                    const int gg = lane >> 2, t = lane & 3, k = ks * 16 + 2 * t;
+                    for (int nt = 0; nt < 4; ++nt) {
+                        const int n = nt * 8 + gg;
                         tcc.bfrag[s][ks][nt][lane].x = h2(bval(s, k, n), bval(s, k + 1, n));
                         tcc.bfrag[s][ks][nt][lane].y = h2(bval(s, k + 8, n), bval(s, k + 9, n));
                     }
-        for (int s = 0; s < kSlices; ++s)
-            for (int lane = 0; lane < 32; ++lane)
-                for (int nt = 0; nt < 4; ++nt)
-                    for (int q = 0; q < 2; ++q) {
-                        const int k = nt * 8 + 2 * (lane & 3) + q;
-                        tcc.wl[s][lane][2 * nt + q] = k < kKeep ? gc.w[s][k] : 0.0f;
-                    }
+                    tcc.wfrag[s][ks][lane].x = h2(wval(s, k, gg), wval(s, k + 1, gg));
+                    tcc.wfrag[s][ks][lane].y = h2(wval(s, k + 8, gg), wval(s, k + 9, gg));
+                }
         tcc.eH2 = std::ilogb(gc.scaleH[2]);
         tcc.eH4 = std::ilogb(gc.scaleH[4]);
         tcc.eW2 = std::ilogb(gc.scaleW[2]);
