@@ -871,7 +871,7 @@ def main():
                 e1.record(st)
                 op_events[name].append((e0, e1))
 
-    launches_per_step = 9   # compress x2 (k_compress_fast + k_compress_fix), decompress, add, scale, dot, dot_rowcol
+    launches_per_step = 11  # compress x2 (uniform pass, binary64 pass, fix-up), decompress, add, scale, dot, dot_rowcol
 
     for _ in range(args.warmup):
         step()
