@@ -22,10 +22,11 @@ __global__ void __launch_bounds__(128)
 
 // Algorithm 1 over tiles of kAddTile blocks with the four binary64 divisions
 // taken out of the common path.  Eight compute warps (one block per thread)
-// stage the codes of both operands with 16-byte asynchronous copies into
-// shared memory, two tiles deep (a thread's 28 codes are then 7 words at
-// stride 7: conflict-free), form beta_k in fp32 (beta_f32) and decide each
-// code from v = fl(beta_1 c_1 +- beta_2 c_2) and the bound
+// stage every input of a tile (the codes, f, s and phi of both operands)
+// with asynchronous copies into shared memory, the next tile's copies in
+// flight while the current one is decided (a thread's 28 codes are 7 words
+// at stride 7: conflict-free), form beta_k in fp32 (beta_f32) and decide
+// each code from v = fl(beta_1 c_1 +- beta_2 c_2) and the bound
 //   |v - y| <= 2^-19 (|beta_1 c_1| + |beta_2 c_2|) + 2^-22 |v| + 2^-100
 // (2^-20 from beta, 2^-23 from the fp32 product and fma, the binary64
 // roundings of the specification far below).  With |c_k| <= 128 and
@@ -36,42 +37,32 @@ __global__ void __launch_bounds__(128)
 // when v - E and v + E truncate to the same int8 (saturating conversions,
 // four codes per word compared at once) other than -128, the saturated
 // value below quantize's -127.  f and s are two binary64 additions per
-// block.
+// block.  One CTA barrier per tile: the copies of the next tile go out just
+// after it, into the stage every thread has finished with.
 //
 // A block with an undecided code, or whose beta_k has no fp32 estimate, goes
 // to a per-tile list with copies of its inputs.  Undecided codes are
 // structural rather than rare: equal phi and equal codes in both operands put
-// y on an integer (y = c phi / phi_k in real arithmetic), about one block in
-// ten of two smooth fields.  Two more warps, the fixers, evaluate the listed
-// blocks in binary64 (add_block's arithmetic, undecided codes only; up to 32
-// blocks per pass of a warp, since a binary64 instruction costs a warp the
-// same for one lane as for 32): one forms beta_1 and the other beta_2 of
-// every listed block, so the division chains run on two warps at once, then
-// each evaluates the undecided codes of one bit parity; they patch the
-// tile's output codes in shared memory and store them with 16-byte writes,
-// while the compute warps already decide the next tile: the two sides share
-// double-buffered output tiles and lists through mbarriers (bounded waits;
-// BLAZ_ERR_TIMEOUT in the status word of these kernels).
+// y on an integer (y = c phi / phi_k in real arithmetic).  Two more warps,
+// the fixers, evaluate the listed blocks in binary64 (add_block's
+// arithmetic, undecided codes only; up to 32 blocks per pass of a warp,
+// since a binary64 instruction costs a warp the same for one lane as for
+// 32): one forms beta_1 and the other beta_2 of every listed block, so the
+// division chains run on two warps at once, then each evaluates the
+// undecided codes of one parity, with conversions and quantize on the
+// integer pipe; they patch the tile's output codes in shared memory and
+// store them with 16-byte writes, while the compute warps already decide the
+// next tile: the two sides share double-buffered output tiles and lists
+// through mbarriers (bounded waits; BLAZ_ERR_TIMEOUT in the status word of
+// these kernels).
 //
 // Every input of a tile is read before any output of it is written, so out
-// may alias a or b.  Requires 16-byte aligned code arrays (the launcher
-// checks).
-#ifndef BLAZ_ADD_TILE
-#define BLAZ_ADD_TILE 256
-#endif
-#ifndef BLAZ_ADD_STAGES
-#define BLAZ_ADD_STAGES 2
-#endif
-#ifndef BLAZ_ADD_OUT
-#define BLAZ_ADD_OUT 2
-#endif
-#ifndef BLAZ_ADD_CTAS
-#define BLAZ_ADD_CTAS 3
-#endif
-constexpr int kAddTile = BLAZ_ADD_TILE;     // blocks per tile (one per compute thread)
-constexpr int kAddStages = BLAZ_ADD_STAGES; // input stages: tiles in flight ahead of the one decided
-constexpr int kAddOut = BLAZ_ADD_OUT;       // output tiles and lists shared with the fixers
-constexpr int kAddCtas = BLAZ_ADD_CTAS;     // resident CTAs per SM
+// may alias a or b.  Requires 16-byte aligned code, f, s and phi arrays of
+// both operands and an aligned output code array (the launcher checks).
+constexpr int kAddTile = 256;   // blocks per tile (one per compute thread)
+constexpr int kAddStages = 2;   // input stages: the tile decided and the next one
+constexpr int kAddOut = 2;      // output tiles and lists shared with the fixers
+constexpr int kAddCtas = 3;     // resident CTAs per SM (shared memory: 3 x 74 KB)
 constexpr int kAddFixCap = kAddTile / 4;    // list entries per tile; beyond, the block's own thread fixes it
 
 struct AddFix {
