@@ -348,7 +348,7 @@ int blaz_cmat_load(const char *path, blaz_cmat *out, void *stream);
 /* ---- Host buffers ----------------------------------------------------------
  * blaz_compress of a matrix in HOST memory (A: host pointer, lda >= cols;
  * page-locked memory runs at the link rate).  The matrix moves in slabs of
- * block rows (~48 MB) into a ring of device staging buffers (up to 512 MB) on a copy
+ * block rows (~128 MB) into a ring of device staging buffers (up to 512 MB) on a copy
  * stream owned by the library (one per device; transfers of successive calls
  * run in issue order), and `stream` compresses every slab as it lands, so
  * the compression hides behind the transfer.  Asynchronous: A must stay valid

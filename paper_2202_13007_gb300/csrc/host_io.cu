@@ -18,8 +18,14 @@
 namespace blaz {
 namespace {
 
-constexpr size_t kSlabBytes = (size_t)48 << 20;   // target bytes per slab
-// Staging in flight: up to 512 MB (ten slabs), so that the transfer can run
+// Target bytes per slab.  Each slab costs nine host calls (a copy, events,
+// the compressor's memset and three launches); at 48 MB slabs a 2 GB matrix
+// took 43 of them and 4-7 ms of host time per call, enough on a slow host to
+// fall behind the copy engine (21-27 ms for a 4.3 GB step against a 20.3 ms
+// copy); at 128 MB the host spends 0.16 ms per call and the step stays at
+// 20.9 ms, the longer first slab being the only cost.
+constexpr size_t kSlabBytes = (size_t)128 << 20;
+// Staging in flight: up to 512 MB (four slabs), so that the transfer can run
 // ~2.4 ms ahead of compressions queued behind other work on the caller's
 // stream.
 constexpr size_t kRingBytes = (size_t)512 << 20;

@@ -27,9 +27,10 @@ def same(g, h):
         assert x.tobytes() == y.tobytes()
 
 
-# (rows, cols): one slab; 11 slabs of 8 rows (48 MB each: the ring of 10
-# staging buffers is reused); slabs of 16, 16 and 8 rows (a ragged last slab)
-@pytest.mark.parametrize("shape", [(72, 136), (88, 786432), (40, 327680)])
+# (rows, cols): one slab; six slabs of 16 rows (128 MB each) and a ragged
+# last one of 8 rows (the ring of 4 staging buffers is reused); slabs of 16,
+# 16 and 8 rows
+@pytest.mark.parametrize("shape", [(72, 136), (88, 1048576), (40, 786432)])
 def test_compress_from_pinned_host_memory(B, shape):
     rows, cols = shape
     t = W.bump_field_torch(cols, rows + cols, "cuda", rows=rows)
