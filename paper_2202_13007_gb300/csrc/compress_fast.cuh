@@ -263,12 +263,17 @@ __device__ __forceinline__ uint32_t compress_block_fast(double (&d)[64], double 
 // coefficient under the bound below, and an undecided DC code goes to the
 // fix-up like any other code.
 //
-// Rows in fp32 from D and r directly: with e the exponent of s, D 2^-e and
-// r 2^e are exact (power-of-two scaling) and of order 1; both are truncated
-// to fp32 (relative error < 2u each, u = 2^-24) and multiplied in fp32 (u):
-// |D'_f - D'| <= 5u |D'| + 2^-126 against D' = RN64(D r), so the first term
-// of the bound in the header becomes 5u and E_ij = 28u aa_ij (K + 1) + 2^-100
-// covers the total of 25u + O(u^2).
+// Rows in fp32 from D and s directly: with e the exponent of s, D 2^-e is
+// exact (power-of-two scaling) and of order 1 and is truncated to fp32
+// (relative error < 2u, u = 2^-24); the row scale rr = RN32(1 /
+// trunc32(s 2^-e)) is within 3u of 2^e RN64(1/s) (a truncation below 2u, one
+// correctly rounded fp32 reciprocal, the binary64 rounding far below); one
+// fp32 product (u): |D'_f - D'| <= 6u |D'| + 2^-126 against D' = RN64(D r)
+// with r = RN64(1/s), so the first term of the bound in the header becomes 6u
+// and E_ij = 28u aa_ij (K + 1) + 2^-100 covers the total of 26u + O(u^2).
+// The exact r is formed only for the blocks whose exact DC chain needs it
+// (sign-coherent blocks, in the dense pass), off every block's path to the
+// DCT.
 
 // binary64 -> binary32 of x 2^-e by truncating the significand (x 2^-e < 2^127);
 // values below 2^-126 (after scaling) and subnormal x become 0.
@@ -403,36 +408,33 @@ __device__ __forceinline__ double uniform_d(long long N, int e, unsigned bneg)
 }
 
 // Phase 1, after the normalization (K nonzero entries, pos / neg: any
-// nonzero D of each sign; S = sum |D| when K > 0): slope, reciprocal and the
-// fp32 DCT of all 64 coefficients.  kInt: d holds the integers N of a
+// nonzero D of each sign; S = sum |D| when K > 0): slope, the fp32 row scale
+// and the fp32 DCT of all 64 coefficients.  kInt: d holds the integers N of a
 // uniform block with exponent field eb (D = +-N 2^(eb-1076)); otherwise d
 // holds D.  d is left as it is (the dense DC pass reads it).
 template <bool kInt>
 __device__ __forceinline__ void cf_slope_and_dct(const double (&d)[64], int eb, unsigned bneg, int K, unsigned pos,
-                                                 unsigned neg, double S, double &s_out, double &r_out, FastCtx &c)
+                                                 unsigned neg, double S, double &s_out, FastCtx &c)
 {
     c.coherent = false;
-    r_out = 0.0;
     if (K == 0) {
         s_out = 0.0;
         c.state = 1u;
         return;
     }
     const double s = div_by_count(S, K);
-    const double r = ddiv(1.0, s);
     s_out = s;
-    r_out = r;
     const int es_field = (int)((__double_as_longlong(s) >> 52) & 0x7FF);
-    // Inf / NaN / overflow, or a subnormal s: exact path
-    if (((__double_as_longlong(S) >> 52) & 0x7FF) >= 0x7FE || ((__double_as_longlong(r) >> 52) & 0x7FF) >= 0x7FE ||
-        es_field == 0) {
+    // Inf / NaN / overflow, or a subnormal s: exact path (a normal s has a
+    // finite normal 1/s)
+    if (((__double_as_longlong(S) >> 52) & 0x7FF) >= 0x7FE || es_field == 0) {
         c.state = kPendingAll;
         return;
     }
     c.state = 0u;
     c.coherent = (pos ^ neg) != 0u;
     const int e = es_field - 1023;
-    const float rr = trunc_f32_scaled(r, -e);
+    const float rr = __frcp_rn(trunc_f32_scaled(s, e));  // 2^e / s within 3u
     // Both passes run two independent chains per instruction on the paired
     // fp32 pipe of sm_103a (__fmul2_rn, __fadd2_rn, __ffma2_rn round each
     // lane as the scalar operation does, so every coefficient is the same
@@ -515,7 +517,7 @@ __device__ __forceinline__ void cf_slope_and_dct(const double (&d)[64], int eb, 
 // called between the two for a block whose nonzero D all have one sign (the
 // dense DC pass will need D), so that d can die row by row in the DCT.
 template <typename Stash>
-__device__ __forceinline__ void cf_prepare(double (&d)[64], double &s_out, double &r_out, FastCtx &c, Stash stash)
+__device__ __forceinline__ void cf_prepare(double (&d)[64], double &s_out, FastCtx &c, Stash stash)
 {
     normalize_block(d);
     int K = 0;
@@ -529,7 +531,7 @@ __device__ __forceinline__ void cf_prepare(double (&d)[64], double &s_out, doubl
         neg |= (unsigned)nz & sg;
     }
     if (K && (pos ^ neg)) stash(d, 0u);
-    cf_slope_and_dct<false>(d, 0, 0u, K, pos, neg, K ? tree_sum_abs(d) : 0.0, s_out, r_out, c);
+    cf_slope_and_dct<false>(d, 0, 0u, K, pos, neg, K ? tree_sum_abs(d) : 0.0, s_out, c);
 }
 
 // Phase 1 for a uniform block on the integer pipe (same bits as
@@ -538,8 +540,7 @@ __device__ __forceinline__ void cf_prepare(double (&d)[64], double &s_out, doubl
 // input, when the block is not uniform or its |N| sum could round: such
 // blocks take cf_prepare.  stash as in cf_prepare (d then holds N).
 template <typename Stash>
-__device__ __forceinline__ bool cf_prepare_uniform(double (&d)[64], double &s_out, double &r_out, FastCtx &c,
-                                                   Stash stash)
+__device__ __forceinline__ bool cf_prepare_uniform(double (&d)[64], double &s_out, FastCtx &c, Stash stash)
 {
     if (!block_is_uniform(d)) return false;
     const unsigned hi0 = (unsigned)__double2hiint(d[0]);
@@ -550,7 +551,7 @@ __device__ __forceinline__ bool cf_prepare_uniform(double (&d)[64], double &s_ou
     const unsigned long long sum = normalize_uniform(d, e, bneg, K, pos, neg);
     if (sum >= (1ull << 53)) return false;
     if (K && (pos ^ neg)) stash(d, (unsigned)e | (bneg << 16));
-    cf_slope_and_dct<true>(d, e, bneg, K, pos, neg, scaled_int_to_double(sum, 0ull, e), s_out, r_out, c);
+    cf_slope_and_dct<true>(d, e, bneg, K, pos, neg, scaled_int_to_double(sum, 0ull, e), s_out, c);
     return true;
 }
 

@@ -45,7 +45,7 @@ __device__ __forceinline__ void append(bool want, T value, T *__restrict__ list,
 constexpr int kFastThreads = 128;
 
 // Dynamic shared memory of the fast compressor: per slot the 64 entries of
-// D (or N), r and the meta word of the block, an odd row of kSlot doubles
+// D (or N), s and the meta word of the block, an odd row of kSlot doubles
 // (conflict-free row reads); then the exact X00 of every slot.
 constexpr int kSlot = 67;
 constexpr size_t kFastSmem = sizeof(double) * (size_t)kFastThreads * (kSlot + 1);
@@ -67,13 +67,13 @@ __device__ __forceinline__ void compress_pass(const double *__restrict__ A, int6
                                               double *sX, unsigned &sCount)
 {
     double d[64];
-    double sv = 0.0, rv = 0.0;
+    double sv = 0.0;
     FastCtx ctx;
     ctx.state = 1u;
     ctx.coherent = false;
     int slot = -1;
     // A block that may need the exact DC chain leaves D (or N) in a slot as
-    // soon as it is normalized; r follows once it is known.
+    // soon as it is normalized; s follows once it is known.
     auto stash = [&](const double (&dd)[64], unsigned meta) {
         slot = (int)atomicAdd(&sCount, 1u);
 #pragma unroll
@@ -86,12 +86,12 @@ __device__ __forceinline__ void compress_pass(const double *__restrict__ A, int6
         else load_block_clamped(A, lda, bi, bj, rows, cols, d);  // partial block of a padded matrix
         const double f0 = d[0];
         if (kUniform) {
-            valid = cf_prepare_uniform(d, sv, rv, ctx, stash);
+            valid = cf_prepare_uniform(d, sv, ctx, stash);
             append(!valid, (unsigned)b, general_list, general_count);
         } else {
-            cf_prepare(d, sv, rv, ctx, stash);
+            cf_prepare(d, sv, ctx, stash);
         }
-        if (slot >= 0) sD[slot][64] = rv;
+        if (slot >= 0) sD[slot][64] = sv;  // the dense pass forms r = RN(1/s)
         if (valid) {
             f[b] = f0;
             s[b] = sv;
@@ -99,7 +99,7 @@ __device__ __forceinline__ void compress_pass(const double *__restrict__ A, int6
     }
     __syncthreads();
     if (threadIdx.x < sCount)
-        sX[threadIdx.x] = cf_exact_dc<kUniform>(sD[threadIdx.x], sD[threadIdx.x][64],
+        sX[threadIdx.x] = cf_exact_dc<kUniform>(sD[threadIdx.x], ddiv(1.0, sD[threadIdx.x][64]),
                                                 (unsigned)__double_as_longlong(sD[threadIdx.x][65]));
     __syncthreads();
     if (valid) {

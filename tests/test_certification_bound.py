@@ -9,11 +9,12 @@ the fp32 error large (long same-sign sums, wide dynamic range, few nonzeros).
 
 Three forms of the estimate are checked:
   * rows from the exact D' = RN64(D r), truncated to fp32, E = 24u aa (K+1);
-  * rows from D 2^-e and r 2^e truncated to fp32 and multiplied in fp32
-    (e the exponent of s), E = 28u aa (K+1);
+  * rows from D 2^-e truncated to fp32 times the row scale
+    rr = RN32(1 / trunc32(s 2^-e)) (e the exponent of s; within 3u of
+    2^e RN64(1/s)), multiplied in fp32, E = 28u aa (K+1);
   * the uniform-block form: D 2^-e rounded to nearest in fp32 (the kernel
     converts the integer N of D = N 2^k to fp32 and scales it by a power of
-    two, which is exact), times r 2^e truncated to fp32, E = 28u aa (K+1);
+    two, which is exact), times the same rr, E = 28u aa (K+1);
 with u = 2^-24 and an absolute 2^-100."""
 import numpy as np
 import pytest
@@ -44,7 +45,7 @@ def estimates(d, r, s, K, scaled):
     rows = np.zeros((8, 8), F32)
     if scaled:
         e = int(np.frexp(s)[1]) - 1               # s = m 2^e, 1 <= m < 2
-        rr = trunc32(np.ldexp(r, e))
+        rr = F32(1.0) / trunc32(np.ldexp(s, -e))    # RN32 of the reciprocal of an fp32
         for u in range(8):
             for v in range(8):
                 x = F32(np.ldexp(d[u, v], -e)) if scaled == "uniform" else trunc32(np.ldexp(d[u, v], -e))
