@@ -368,6 +368,12 @@ __device__ __forceinline__ unsigned long long normalize_uniform(double (&d)[64],
         return (long long)(((unsigned long long)__double_as_longlong(d[p]) & 0x000FFFFFFFFFFFFFull) |
                            0x0010000000000000ull);
     };
+    // sum N telescopes to the boundary: row 0 and column 0 give
+    // 2 (m_07 - m_00) + 2 (m_70 - m_00); the interior's column differences
+    // give sum_j>0 (m_7j - m_0j) and its row differences sum_i>0 (m_i7 - m_i0)
+    long long tot = 2 * ((sig(7) - sig(0)) + (sig(56) - sig(0)));
+#pragma unroll
+    for (int q = 1; q < 8; ++q) tot += (sig(56 + q) - sig(q)) + (sig(q * 8 + 7) - sig(q * 8));
 #pragma unroll
     for (int i = 7; i >= 0; --i) {
 #pragma unroll
@@ -380,18 +386,17 @@ __device__ __forceinline__ unsigned long long normalize_uniform(double (&d)[64],
             d[i * 8 + j] = __longlong_as_double(N);  // the integer, until converted below
         }
     }
-    // sum |N| and sum N: all nonzero N have one sign iff |sum N| = sum |N|
-    unsigned long long sum = 0;
-    long long tot = 0;
+    // sum |N| = 2 sum_{N>0} N - sum N; all nonzero N have one sign iff
+    // |sum N| = sum |N|
+    long long psum = 0;
     K = 0;
 #pragma unroll
     for (int p = 0; p < 64; ++p) {
         const long long N = __double_as_longlong(d[p]);
-        const unsigned long long a = N < 0 ? (unsigned long long)(-N) : (unsigned long long)N;
-        sum += a;
-        tot += N;
-        K += (int)(a != 0ull);
+        psum += N > 0 ? N : 0ll;
+        K += (int)(N != 0ll);
     }
+    const unsigned long long sum = (unsigned long long)(2 * psum - tot);
     const bool coherent = (unsigned long long)(tot < 0 ? -tot : tot) == sum;
     // as the caller's flags would be: D has the sign of N, flipped for a negative block
     const unsigned tneg = (unsigned)((unsigned long long)tot >> 63) ^ bneg;
