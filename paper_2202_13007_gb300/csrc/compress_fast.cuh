@@ -585,12 +585,12 @@ __device__ __forceinline__ double cf_exact_dc(const double *D, double r, unsigne
 // Phase 2: phi and the codes, with the exact X00 of a coherent block.
 // Returns 0, kPendingAll or the mask of undecided codes (as
 // compress_block_fast).
-__device__ __forceinline__ uint32_t cf_finish(const FastCtx &c, double X00, uint8_t &phi_out, int8_t (&code)[kKeep])
+__device__ __forceinline__ uint32_t cf_finish(const FastCtx &c, double X00, uint8_t &phi_out, uint32_t (&cw)[7])
 {
     if (c.state == 1u) {
         phi_out = 255;
 #pragma unroll
-        for (int t = 0; t < kKeep; ++t) code[t] = 0;
+        for (int q = 0; q < 7; ++q) cw[q] = 0u;
         return 0u;
     }
     if (c.state == kPendingAll) return kPendingAll;
@@ -626,7 +626,6 @@ __device__ __forceinline__ uint32_t cf_finish(const FastCtx &c, double X00, uint
     phi_out = (uint8_t)phi;
     const float phif = (float)phi;
     uint32_t pending = 0u;
-#pragma unroll
     // Each code from the interval v -+ Ev, v = D_f phi, with
     // Ev = E_ij phi (1 + 2^-20) + 2^-22 (|v| + 1) + 2^-16 (the last two
     // terms cover the fp32 roundings of v and of the interval ends); two
@@ -640,30 +639,36 @@ __device__ __forceinline__ uint32_t cf_finish(const FastCtx &c, double X00, uint
         const int i = kept_row(t), j = kept_col(t);
         return (i == 0 && j == 0) ? C00 : (i == 0 || j == 0) ? C0k : Ckk;
     };
-    auto decide = [&](float lo, float hi, int t) {
-        int cc = 0;
-        if (lo >= 127.0f) cc = 127;
-        else if (hi <= -127.0f) cc = -127;
-        else {
-            const int tl = (int)truncf(lo), th = (int)truncf(hi);
-            if (tl != th || tl >= 127 || tl <= -127) pending |= 1u << t;
-            else cc = tl;
-        }
-        code[t] = (int8_t)cc;
-    };
+    // A code is decided when the saturating int8 truncations of both ends
+    // agree and are not -128 (below quantize's -127): the same decisions as
+    // the truncations of both ends saturated to +-127 agreeing, except that
+    // an interval reaching below -128 goes to the fix-up.  Four codes per
+    // word, compared at once (undecided_bytes); bit t of the returned mask:
+    // code t.
     const float2 phi2 = make_float2(phif, phif), k22 = make_float2(0x1p-22f, 0x1p-22f),
                  neg1 = make_float2(-1.0f, -1.0f);
 #pragma unroll
-    for (int q = 0; q < kKeep / 2; ++q) {
-        const int t0 = 2 * q, t1 = 2 * q + 1;
-        const float2 v = __fmul2_rn(make_float2(c.Dk[t0], c.Dk[t1]), phi2);
-        const float2 Ev = __ffma2_rn(make_float2(fabsf(v.x), fabsf(v.y)), k22, make_float2(cst(t0), cst(t1)));
-        const float2 lo = __ffma2_rn(Ev, neg1, v), hi = __fadd2_rn(v, Ev);
-        decide(lo.x, hi.x, t0);
-        decide(lo.y, hi.y, t1);
+    for (int q = 0; q < 7; ++q) {
+        uint32_t l8[4], h8[4];
+#pragma unroll
+        for (int k = 0; k < 4; k += 2) {
+            const int t0 = 4 * q + k, t1 = t0 + 1;
+            const float2 v = __fmul2_rn(make_float2(c.Dk[t0], c.Dk[t1]), phi2);
+            const float2 Ev = __ffma2_rn(make_float2(fabsf(v.x), fabsf(v.y)), k22, make_float2(cst(t0), cst(t1)));
+            const float2 lo = __ffma2_rn(Ev, neg1, v), hi = __fadd2_rn(v, Ev);
+            l8[k] = cvt_s8_rz(lo.x);
+            l8[k + 1] = cvt_s8_rz(lo.y);
+            h8[k] = cvt_s8_rz(hi.x);
+            h8[k + 1] = cvt_s8_rz(hi.y);
+        }
+        const uint32_t lw = __byte_perm(__byte_perm(l8[0], l8[1], 0x0040), __byte_perm(l8[2], l8[3], 0x0040), 0x5410);
+        const uint32_t hw = __byte_perm(__byte_perm(h8[0], h8[1], 0x0040), __byte_perm(h8[2], h8[3], 0x0040), 0x5410);
+        cw[q] = lw;
+        // bits 7, 15, 23, 31 of the byte mask to bits 28..31, then to 4q..4q+3
+        pending |= ((undecided_bytes(lw, hw) * 0x00204081u) >> 28) << (4 * q);
     }
     if (c.coherent) {  // the DC of a sign-coherent block from its exact X00
-        code[0] = quantize_bits(dmul(X00, i64_to_double(phi)));
+        cw[0] = (cw[0] & 0xFFFFFF00u) | (uint32_t)(uint8_t)quantize_bits(dmul(X00, i64_to_double(phi)));
         pending &= ~1u;
     }
     return pending;

@@ -209,28 +209,6 @@ __device__ __forceinline__ void add_fix_codes(double b1, double b2, const uint32
     }
 }
 
-// Truncation toward zero to int8, saturated to [-128, 127] (the low byte of
-// the result register).
-__device__ __forceinline__ uint32_t cvt_s8_rz(float x)
-{
-    uint32_t r;
-    asm("cvt.rzi.s8.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
-}
-
-// Bit 7 of byte k set when byte k of the truncations of the two ends differs,
-// or when that of the lower end is -128 (0x80: saturated, below quantize's
-// range): the undecided codes of a word.  Per byte x, (x & 0x7F) + 0x7F sets
-// bit 7 exactly when the low 7 bits are not all zero, with no carry into the
-// next byte.
-__device__ __forceinline__ uint32_t undecided_bytes(uint32_t lw, uint32_t hw)
-{
-    const uint32_t d = lw ^ hw;
-    const uint32_t ne = ((d & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | d;
-    const uint32_t m128 = ~((lw & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) & lw;
-    return (ne | m128) & 0x80808080u;
-}
-
 __device__ __forceinline__ void fixer_bar() { asm volatile("bar.sync 2, %0;" ::"n"(2 * 32) : "memory"); }
 
 __device__ __forceinline__ bool ops_wait(uint64_t *bar, uint32_t parity)

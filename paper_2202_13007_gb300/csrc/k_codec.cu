@@ -104,11 +104,13 @@ __device__ __forceinline__ void compress_pass(const double *__restrict__ A, int6
     __syncthreads();
     if (valid) {
         uint8_t ph = 255;
-        int8_t c[kKeep];
-        const uint32_t pending = cf_finish(ctx, slot >= 0 ? sX[slot] : 0.0, ph, c);
+        uint32_t cw[7];
+        const uint32_t pending = cf_finish(ctx, slot >= 0 ? sX[slot] : 0.0, ph, cw);
         if (pending != kPendingAll) {
             phi[b] = ph;
-            store_codes(code + b * kKeep, c);
+            uint32_t *w = reinterpret_cast<uint32_t *>(code + b * kKeep);  // 28 bytes, 4-byte aligned
+#pragma unroll
+            for (int q = 0; q < 7; ++q) w[q] = cw[q];
         }
         // Undecided codes and whole blocks go to separate lists, so that the
         // fix-up kernel runs without divergence between the two cases.
