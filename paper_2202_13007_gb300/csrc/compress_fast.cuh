@@ -273,7 +273,10 @@ __device__ __forceinline__ uint32_t compress_block_fast(double (&d)[64], double 
 // and E_ij = 28u aa_ij (K + 1) + 2^-100 covers the total of 26u + O(u^2).
 // The exact r is formed only for the blocks whose exact DC chain needs it
 // (sign-coherent blocks, in the dense pass), off every block's path to the
-// DCT.
+// DCT.  Both passes of this form add and subtract mirrored entries first
+// (cos_kx is even or odd under x -> 7 - x, exactly in the table) and run
+// 4-term chains: one rounding of |a| + |b| and gamma_4 of the chain stay
+// within the 8u per pass that the bound allows for 8-term chains.
 
 // binary64 -> binary32 of x 2^-e by truncating the significand (x 2^-e < 2^127);
 // values below 2^-126 (after scaling) and subnormal x become 0.
@@ -465,15 +468,26 @@ __device__ __forceinline__ void cf_slope_and_dct(const double (&d)[64], int eb, 
                                    : make_float2(trunc_f32_scaled(x0, e), trunc_f32_scaled(x1, e));
             rf[v] = __fmul2_rn(in, rr2);
         }
-        float2 t0 = rf[0];
+        // cos_jx is even in x -> 7 - x for even j and odd for odd j, exactly
+        // (the table is built so), so each row's sums and differences of
+        // mirrored entries feed 4-term chains (error below 5u of the sum of
+        // |terms|, against gamma_8 for the 8-term chains the bound allows)
+        float2 sv[4], dv[4];
 #pragma unroll
-        for (int v = 1; v < 8; ++v) t0 = __fadd2_rn(t0, rf[v]);
+        for (int v = 0; v < 4; ++v) {
+            sv[v] = __fadd2_rn(rf[v], rf[7 - v]);
+            dv[v] = __ffma2_rn(rf[7 - v], make_float2(-1.0f, -1.0f), rf[v]);  // rf_v - rf_7-v, one rounding
+        }
+        float2 t0 = sv[0];
+#pragma unroll
+        for (int v = 1; v < 4; ++v) t0 = __fadd2_rn(t0, sv[v]);
         T[up][0] = t0;
 #pragma unroll
         for (int j = 1; j < 8; ++j) {
-            float2 acc = __fmul2_rn(rf[0], make_float2(cos_f(j, 0), cos_f(j, 0)));
+            const float2 *x = (j & 1) ? dv : sv;
+            float2 acc = __fmul2_rn(x[0], make_float2(cos_f(j, 0), cos_f(j, 0)));
 #pragma unroll
-            for (int v = 1; v < 8; ++v) acc = __ffma2_rn(rf[v], make_float2(cos_f(j, v), cos_f(j, v)), acc);
+            for (int v = 1; v < 4; ++v) acc = __ffma2_rn(x[v], make_float2(cos_f(j, v), cos_f(j, v)), acc);
             T[up][j] = acc;
         }
     }
@@ -482,16 +496,22 @@ __device__ __forceinline__ void cf_slope_and_dct(const double (&d)[64], int eb, 
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         float Dij[8];
+        // the same symmetry over u: (T_u + T_7-u, T_u - T_7-u) in one paired
+        // operation, the sum for the even output row i0 and the difference
+        // for the odd one i1 of each pair
+        float2 SD[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float Tu = (u & 1) ? T[u / 2][j].y : T[u / 2][j].x;
+            const float Tm = ((7 - u) & 1) ? T[(7 - u) / 2][j].y : T[(7 - u) / 2][j].x;
+            SD[u] = __ffma2_rn(make_float2(Tm, Tm), make_float2(1.0f, -1.0f), make_float2(Tu, Tu));
+        }
 #pragma unroll
         for (int ip = 0; ip < 4; ++ip) {
             const int i0 = 2 * ip, i1 = 2 * ip + 1;
-            const float T0 = T[0][j].x;
-            float2 acc = __fmul2_rn(make_float2(cos_f(i0, 0), cos_f(i1, 0)), make_float2(T0, T0));
+            float2 acc = __fmul2_rn(make_float2(cos_f(i0, 0), cos_f(i1, 0)), SD[0]);
 #pragma unroll
-            for (int u = 1; u < 8; ++u) {
-                const float Tu = (u & 1) ? T[u / 2][j].y : T[u / 2][j].x;
-                acc = __ffma2_rn(make_float2(cos_f(i0, u), cos_f(i1, u)), make_float2(Tu, Tu), acc);
-            }
+            for (int u = 1; u < 4; ++u) acc = __ffma2_rn(make_float2(cos_f(i0, u), cos_f(i1, u)), SD[u], acc);
             const float2 D2 = __fmul2_rn(make_float2((float)aa_tab(i0, j), (float)aa_tab(i1, j)), acc);
             Dij[i0] = D2.x;
             Dij[i1] = D2.y;

@@ -15,7 +15,10 @@ Three forms of the estimate are checked:
   * the uniform-block form: D 2^-e rounded to nearest in fp32 (the kernel
     converts the integer N of D = N 2^k to fp32 and scales it by a power of
     two, which is exact), times the same rr, E = 28u aa (K+1);
-with u = 2^-24 and an absolute 2^-100."""
+with u = 2^-24 and an absolute 2^-100.  The first form runs 8-term fp32
+chains in both passes; the other two, as the certified kernels, sums and
+differences of mirrored entries (the DCT basis is even or odd under
+x -> 7 - x) feeding 4-term chains."""
 import numpy as np
 import pytest
 
@@ -55,22 +58,49 @@ def estimates(d, r, s, K, scaled):
             for v in range(8):
                 rows[u, v] = trunc32(np.float64(d[u, v]) * np.float64(r))
     T = np.zeros((8, 8), F32)
+    D = np.zeros((8, 8), np.float64)
+    if not scaled:
+        # 8-term chains in both passes (the one-kernel form)
+        for u in range(8):
+            t0 = rows[u, 0]
+            for v in range(1, 8):
+                t0 = F32(t0 + rows[u, v])
+            T[u, 0] = t0
+            for j in range(1, 8):
+                acc = F32(rows[u, 0] * cf[j, 0])
+                for v in range(1, 8):
+                    acc = fma32(rows[u, v], cf[j, v], acc)
+                T[u, j] = acc
+        for j in range(8):
+            for i in range(8):
+                acc = F32(cf[i, 0] * T[0, j])
+                for u in range(1, 8):
+                    acc = fma32(cf[i, u], T[u, j], acc)
+                D[i, j] = F32(F32(aa[i, j]) * acc)
+        return D, aa
+    # the certified passes: sums and differences of mirrored entries (cos_jx
+    # is even or odd in x -> 7 - x with j) feeding 4-term chains
     for u in range(8):
-        t0 = rows[u, 0]
-        for v in range(1, 8):
-            t0 = F32(t0 + rows[u, v])
+        sv = [F32(rows[u, v] + rows[u, 7 - v]) for v in range(4)]
+        dv = [F32(rows[u, v] - rows[u, 7 - v]) for v in range(4)]
+        t0 = sv[0]
+        for v in range(1, 4):
+            t0 = F32(t0 + sv[v])
         T[u, 0] = t0
         for j in range(1, 8):
-            acc = F32(rows[u, 0] * cf[j, 0])
-            for v in range(1, 8):
-                acc = fma32(rows[u, v], cf[j, v], acc)
+            x = dv if j % 2 else sv
+            acc = F32(x[0] * cf[j, 0])
+            for v in range(1, 4):
+                acc = fma32(x[v], cf[j, v], acc)
             T[u, j] = acc
-    D = np.zeros((8, 8), np.float64)
     for j in range(8):
+        S = [F32(T[u, j] + T[7 - u, j]) for u in range(4)]
+        Dd = [F32(T[u, j] - T[7 - u, j]) for u in range(4)]
         for i in range(8):
-            acc = F32(cf[i, 0] * T[0, j])
-            for u in range(1, 8):
-                acc = fma32(cf[i, u], T[u, j], acc)
+            x = Dd if i % 2 else S
+            acc = F32(cf[i, 0] * x[0])
+            for u in range(1, 4):
+                acc = fma32(cf[i, u], x[u], acc)
             D[i, j] = F32(F32(aa[i, j]) * acc)
     return D, aa
 
