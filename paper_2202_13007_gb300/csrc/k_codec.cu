@@ -35,11 +35,12 @@ __device__ __forceinline__ void append(bool want, T value, T *__restrict__ list,
     if (want) list[base + __popc(need & ((1u << lane) - 1u))] = value;
 }
 
-// CTA size of the fast compressor: 128 threads (one block each).  The
-// uniform pass runs 3 CTAs per SM (166 registers, no spills: D leaves the
-// registers row by row during the DCT); the binary64 pass needs 237
-// registers and runs 2 (at 168 it spills).  Both are bound by instruction
-// issue and latency rather than by the binary64 pipe.  The sign-coherent
+// CTA size of the fast compressor: 128 threads (one block each).  Both
+// passes run 3 CTAs per SM: the uniform pass in 161 registers without spills
+// (D leaves the registers row by row during the DCT), the binary64 pass in
+// 168 with ~100 bytes of spills, which measured faster than 2 CTAs at 224
+// registers.  Both are bound by instruction issue and latency rather than
+// by the binary64 pipe.  The sign-coherent
 // blocks of a CTA share one dense pass of exact DC chains, which larger CTAs
 // fill better.
 constexpr int kFastThreads = 128;
@@ -123,7 +124,7 @@ __device__ __forceinline__ void compress_pass(const double *__restrict__ A, int6
 // blocks, the first pass of compress_pass.  Otherwise the second pass over
 // the blocks the first one listed, the CTAs striding over the list.
 template <bool kVec, bool kUniform>
-__global__ void __launch_bounds__(kFastThreads, kUniform ? 3 : 2)
+__global__ void __launch_bounds__(kFastThreads, 3)
     k_compress_fast(const double *__restrict__ A, int64_t lda, int64_t rows, int64_t cols, int64_t nbc, int64_t nb,
                     double *__restrict__ f, double *__restrict__ s, uint8_t *__restrict__ phi,
                     int8_t *__restrict__ code, uint2 *__restrict__ code_list, unsigned *__restrict__ code_count,
