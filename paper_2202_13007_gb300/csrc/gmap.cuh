@@ -42,7 +42,7 @@ constexpr unsigned long long slice_assembly_bound(int slices, int bits, int term
 // |v| < 2^53), on the integer pipe: normalize left by the leading-zero count,
 // one fixed right shift puts the leading one on bit 52, where it carries into
 // the exponent field (hence 1085 - lz rather than 1086 - lz).  The decoders'
-// assembled sums stay below 2^57 (slice_assembly_bound of five 9-bit slices
+// assembled sums stay far below 2^62 (slice_assembly_bound of their slices
 // over at most 64 codes; each decoder checks its own with a static_assert).
 __device__ __forceinline__ double dec_to_double(long long v)
 {

@@ -19,19 +19,18 @@ namespace blaz {
 // ---------------------------------------------------------------------------------
 // Decompression as a product with the fixed map G (gmap.cuh): Y = C G^T for 16
 // blocks per warp on the tensor cores (mma.sync m16n8k16, fp16 inputs, fp32
-// accumulation).  G is split into five fixed-point slices of 9 bits whose
-// digits (|d| <= 2^8) and the codes (|c| <= 127) are exact in fp16; every
-// product sum is an integer below 2^20, exact in fp32.  Two such slices
-// combine in 32-bit integers (Y_0 2^9 + Y_1 < 2^30), so the assembly
-//     Y = (Y_0 2^9 + Y_1) 2^27 + (Y_2 2^9 + Y_3) 2^9 + Y_4
-// takes two 32-bit and one 64-bit multiply-add instead of four 64-bit
-// shift-adds, and each output is one binary64 fma:
+// accumulation).  G is split into four fixed-point slices of 11 bits whose
+// digits (|d| <= 2^10) and the codes (|c| <= 128) are exact in fp16; every
+// product sum is an integer below 2^22 (28 * 2^7 * 2^10), exact in fp32 and
+// within the range of the fp32 -> integer step below.  The assembly
+//     Y = Y_0 2^33 + Y_1 2^22 + Y_2 2^11 + Y_3
+// is exact in int64, and each output is one binary64 fma:
 //     out = f + (s / phi) 2^E Y.
-// G is represented to 2^-45 of its largest entry, so outputs differ from the
-// binary64 evaluation of the definition by far less than 1e-12 of the block's
-// scale |f| + 14 |s| sum|c| / phi.
-constexpr int kDecSlices = 5;
-constexpr int kDecDigitBits = 9;
+// G is represented to 2^-44 of its largest entry (1.75), so outputs differ
+// from the binary64 evaluation of the definition by far less than 1e-12 of
+// the block's scale |f| + 14 |s| sum|c| / phi.
+constexpr int kDecSlices = 4;
+constexpr int kDecDigitBits = 11;
 struct DecConsts {
     uint2 bfrag[kDecSlices][2][8][32];  // B fragments [slice][k-step][n-tile][lane]
     double inv_phi_scaled[256];         // RN(1/phi) 2^E (2^E: weight of the last slice; exact scaling)
@@ -100,6 +99,8 @@ __device__ __forceinline__ uint32_t code_pair(const int8_t *__restrict__ c, int 
 
 static_assert(slice_assembly_bound(kDecSlices, kDecDigitBits, kKeep) < (1ull << 62),
               "the slice assembly must fit dec_to_double's input range");
+static_assert((long long)kKeep * 128 * (1 << (kDecDigitBits - 1)) < (1ll << 22),
+              "slice sums below 2^22 (exact in fp32 and in the fp32 -> int step)");
 
 // kSlices: instead of the binary64 matrix, the three bf16 slices of every
 // decoded value (split3) go to Sl = [A1 A2 A3] (rows x 3kp, row-major: the
@@ -172,9 +173,10 @@ __global__ void __launch_bounds__(128)
             long long acc[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const int p01 = y[0][q] * (1 << kDecDigitBits) + y[1][q];
-                const int p23 = y[2][q] * (1 << kDecDigitBits) + y[3][q];
-                acc[q] = (long long)p01 * (1ll << (3 * kDecDigitBits)) + (long long)p23 * (1ll << kDecDigitBits) + y[4][q];
+                acc[q] = (long long)y[0][q] * (1ll << (3 * kDecDigitBits)) +
+                         (long long)y[1][q] * (1ll << (2 * kDecDigitBits)) +
+                         (long long)y[2][q] * (1ll << kDecDigitBits) + y[3][q];
+
             }
             // c0, c1: block bA, row nt, columns 2t, 2t+1; c2, c3: block bB.
 #pragma unroll
