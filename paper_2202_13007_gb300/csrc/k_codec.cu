@@ -99,9 +99,19 @@ __device__ __forceinline__ void compress_pass(const double *__restrict__ A, int6
         }
     }
     __syncthreads();
-    if (threadIdx.x < sCount)
-        sX[threadIdx.x] = cf_exact_dc<kUniform>(sD[threadIdx.x], ddiv(1.0, sD[threadIdx.x][64]),
-                                                (unsigned)__double_as_longlong(sD[threadIdx.x][65]));
+    // the exact DC chains of the slots, one team of 8 lanes per slot (teams
+    // never straddle a warp; a team is wholly active or idle)
+    {
+        const unsigned n = sCount;
+        const int lane = threadIdx.x & 31, u = lane & 7, tbase = lane & ~7;
+        const unsigned tmask = 0xFFu << tbase;
+        for (unsigned w = threadIdx.x; w < 8u * n; w += blockDim.x) {
+            const unsigned q = w >> 3;
+            const double x = cf_exact_dc_team<kUniform>(sD[q], sD[q][64], (unsigned)__double_as_longlong(sD[q][65]),
+                                                        u, tmask, tbase);
+            if (u == 0) sX[q] = x;
+        }
+    }
     __syncthreads();
     if (valid) {
         uint8_t ph = 255;
