@@ -419,7 +419,7 @@ __device__ __forceinline__ double uniform_d(long long N, int e, unsigned bneg)
 // nonzero D of each sign; S = sum |D| when K > 0): slope, the fp32 row scale
 // and the fp32 DCT of all 64 coefficients.  kInt: d holds the integers N of a
 // uniform block with exponent field eb (D = +-N 2^(eb-1076)); otherwise d
-// holds D.  d is left as it is (the dense DC pass reads it).
+// holds D.  d is left as it is.
 template <bool kInt>
 __device__ __forceinline__ void cf_slope_and_dct(const double (&d)[64], int eb, unsigned bneg, int K, unsigned pos,
                                                  unsigned neg, double S, double &s_out, FastCtx &c)
@@ -540,7 +540,8 @@ __device__ __forceinline__ void cf_slope_and_dct(const double (&d)[64], int eb, 
 // Phase 1 on the binary64 pipe: Eq. eqnorm, the nonzero count and the
 // pairwise |D| tree as specified, then cf_slope_and_dct.  stash(d, meta) is
 // called between the two for a block whose nonzero D all have one sign (the
-// dense DC pass will need D), so that d can die row by row in the DCT.
+// dense DC pass will need D: the caller keeps a copy, or in the uniform pass
+// only the block's index), so that d can die row by row in the DCT.
 template <typename Stash>
 __device__ __forceinline__ void cf_prepare(double (&d)[64], double &s_out, FastCtx &c, Stash stash)
 {
@@ -580,50 +581,94 @@ __device__ __forceinline__ bool cf_prepare_uniform(double (&d)[64], double &s_ou
     return true;
 }
 
-// The exact DC coefficient X00 = RN(aa00 U00) from D and r (the dense pass).
-// kInt: D holds the integers N of a uniform block (meta as set by
-// cf_prepare_uniform), converted to the exact binary64 D here.
-template <bool kInt>
-__device__ __forceinline__ double cf_exact_dc(const double *D, double r, unsigned meta)
+// The exact DC coefficient X00 = RN(aa00 U00) from D and r.
+__device__ __forceinline__ double cf_exact_dc(const double *D, double r)
 {
-    auto dval = [&](int p) {
-        return kInt ? uniform_d(__double_as_longlong(D[p]), (int)(meta & 0xFFFFu), meta >> 16) : D[p];
-    };
     double U00 = 0.0;
     // rows not unrolled: D is in shared memory, and a short loop keeps this
     // rarely run code small in the instruction cache
 #pragma unroll 1
     for (int u = 0; u < 8; ++u) {
-        double t0 = dmul(dval(u * 8), r);
+        double t0 = dmul(D[u * 8], r);
 #pragma unroll
-        for (int v = 1; v < 8; ++v) t0 = dadd(t0, dmul(dval(u * 8 + v), r));
+        for (int v = 1; v < 8; ++v) t0 = dadd(t0, dmul(D[u * 8 + v], r));
         U00 = (u == 0) ? t0 : dadd(U00, t0);
     }
     return dmul(BLAZ_A00, U00);
 }
 
-// The same X00 by a team of 8 lanes (lane u of the team: row u), for the
-// dense pass of a CTA: the row chains t_u = sum_v RN(D_uv r) (v ascending)
-// are independent, and lane 0 of the team adds them in the specified order
-// (u ascending) from the team's shuffles, so the chain is ~25 binary64
-// operations deep instead of ~130.  Same bits as cf_exact_dc.  Every lane
-// of the team forms r = RN(1/s) (a binary64 instruction costs a warp the
-// same for 8 lanes as for one).  Returns X00 in lane 0 of the team.
-template <bool kInt>
-__device__ __forceinline__ double cf_exact_dc_team(const double *D, double s, unsigned meta, int u, unsigned tmask,
-                                                   int tbase)
+// The same X00 by a team of 8 lanes, lane u holding row u of D (drow(v) =
+// D_uv): the row chains t_u = sum_v RN(D_uv r) (v ascending) are
+// independent, and lane 0 of the team adds them in the specified order (u
+// ascending) from the team's shuffles, so the chain is ~25 binary64
+// operations deep instead of ~130.  Same bits as cf_exact_dc.  Every lane of
+// the team forms r = RN(1/s) (a binary64 instruction costs a warp the same
+// for 8 lanes as for one).  Returns X00 in lane 0 of the team.
+template <typename Row>
+__device__ __forceinline__ double cf_exact_dc_rows(Row drow, double s, unsigned tmask, int tbase)
 {
-    auto dval = [&](int p) {
-        return kInt ? uniform_d(__double_as_longlong(D[p]), (int)(meta & 0xFFFFu), meta >> 16) : D[p];
-    };
     const double r = ddiv(1.0, s);
-    double t = dmul(dval(u * 8), r);
+    double t = dmul(drow(0), r);
 #pragma unroll
-    for (int v = 1; v < 8; ++v) t = dadd(t, dmul(dval(u * 8 + v), r));
+    for (int v = 1; v < 8; ++v) t = dadd(t, dmul(drow(v), r));
     double U00 = __shfl_sync(tmask, t, tbase);
 #pragma unroll
     for (int uu = 1; uu < 8; ++uu) U00 = dadd(U00, __shfl_sync(tmask, t, tbase + uu));
     return dmul(BLAZ_A00, U00);
+}
+
+// X00 by a team from D in shared memory (the binary64 pass).
+__device__ __forceinline__ double cf_exact_dc_team(const double *D, double s, int u, unsigned tmask, int tbase)
+{
+    return cf_exact_dc_rows([&](int v) { return D[u * 8 + v]; }, s, tmask, tbase);
+}
+
+// X00 by a team for a uniform block from its integers N in shared memory
+// (meta as cf_prepare_uniform sets it).
+__device__ __forceinline__ double cf_exact_dc_team_n(const double *N, double s, unsigned meta, int u, unsigned tmask,
+                                                     int tbase)
+{
+    const int e = (int)(meta & 0xFFFFu);
+    const unsigned bneg = meta >> 16;
+    return cf_exact_dc_rows([&](int v) { return uniform_d(__double_as_longlong(N[u * 8 + v]), e, bneg); }, s, tmask,
+                            tbase);
+}
+
+// X00 by a team for a uniform block b (meta as cf_prepare_uniform sets it)
+// from the input itself: lane u reloads rows u and u - 1 of the block
+// (clamped to the rows x cols matrix as load_block_clamped is) and forms row
+// u of the integers N as normalize_uniform does, then the exact D =
+// uniform_d(N).  The block's own lane has just loaded these rows (an L1 or
+// L2 hit), and the CTA keeps no copy of the block.
+__device__ __forceinline__ double cf_exact_dc_team_uniform(const double *__restrict__ A, int64_t lda, int64_t rows,
+                                                           int64_t cols, int64_t nbc, int64_t b, double s,
+                                                           unsigned meta, int u, unsigned tmask, int tbase)
+{
+    const int64_t bi = b / nbc, bj = b - (b / nbc) * nbc;
+    const int64_t r = bi * 8 + u < rows ? bi * 8 + u : rows - 1;
+    const int64_t rp = bi * 8 + u - 1 < rows ? bi * 8 + u - 1 : rows - 1;  // read for u > 0 only
+    auto sig = [](double x) -> long long {
+        return (long long)(((unsigned long long)__double_as_longlong(x) & 0x000FFFFFFFFFFFFFull) |
+                           0x0010000000000000ull);
+    };
+    long long cur[8], prev[8];
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+        const int64_t c = bj * 8 + v < cols ? bj * 8 + v : cols - 1;
+        cur[v] = sig(__ldg(A + r * lda + c));
+        prev[v] = u > 0 ? sig(__ldg(A + rp * lda + c)) : 0ll;
+    }
+    const int e = (int)(meta & 0xFFFFu);
+    const unsigned bneg = meta >> 16;
+    return cf_exact_dc_rows(
+        [&](int v) {
+            long long N;
+            if (u == 0) N = v == 0 ? 0ll : 2 * (cur[v] - cur[v - 1]);
+            else if (v == 0) N = 2 * (cur[0] - prev[0]);
+            else N = 2 * cur[v] - prev[v] - cur[v - 1];
+            return uniform_d(N, e, bneg);
+        },
+        s, tmask, tbase);
 }
 
 // Phase 2: phi and the codes, with the exact X00 of a coherent block.

@@ -40,51 +40,103 @@ __device__ __forceinline__ void append(bool want, T value, T *__restrict__ list,
 // (D leaves the registers row by row during the DCT), the binary64 pass in
 // 168 with ~100 bytes of spills, which measured faster than 2 CTAs at 224
 // registers.  Both are bound by instruction issue and latency rather than
-// by the binary64 pipe.  The sign-coherent
-// blocks of a CTA share one dense pass of exact DC chains, which larger CTAs
-// fill better.
+// by the binary64 pipe.  The sign-coherent blocks of a CTA share one dense
+// pass of exact DC chains, which larger CTAs fill better.
 constexpr int kFastThreads = 128;
 
-// Dynamic shared memory of the fast compressor: per slot the 64 entries of
-// D (or N), s and the meta word of the block, an odd row of kSlot doubles
-// (conflict-free row reads); then the exact X00 of every slot.
+// Dynamic shared memory of the fast compressor, one slot per block of the
+// CTA, then the exact X00 of every slot.  The binary64 pass keeps D in its
+// slots: 64 entries and s in an odd row of kSlot doubles (conflict-free row
+// reads).  The uniform pass keeps the block, s and the meta word in every
+// slot and the integers N in rows like those for its first kCopySlots
+// slots; the dense pass reloads the rows of the blocks in the other slots
+// (cf_exact_dc_team_uniform).  So a CTA needs 54 KB instead of 70, and the
+// SM keeps 60 KB or more of L1 instead of ~28 KB, which also bounds the block
+// loads in flight (a warp loads 16 KB per round); few CTAs of a smooth field
+// have more than 96 sign-coherent blocks.  Measured at 16384^2: 1.276 /
+// 1.181 ms per compression of the two bump fields with 128 copied slots,
+// 1.203 / 1.097 with 96 (with 32-byte loads), 1.253 / 1.104 with every slot
+// reloaded.
 constexpr int kSlot = 67;
-constexpr size_t kFastSmem = sizeof(double) * (size_t)kFastThreads * (kSlot + 1);
+constexpr int kCopySlots = 96;
+struct UniformSlot {
+    double s;
+    unsigned b, meta;
+};
+constexpr size_t kGeneralSmem = sizeof(double) * (size_t)kFastThreads * (kSlot + 1);
+constexpr size_t kUniformSmem =
+    (sizeof(UniformSlot) + sizeof(double)) * (size_t)kFastThreads + sizeof(double) * (size_t)kCopySlots * kSlot;
+
+// A full block with 32-byte loads: two per row of 64 B, so that every load
+// instruction of a warp uses whole 32-byte sectors (with 16-byte loads two
+// instructions share each sector).  Needs the base 32-byte aligned and lda
+// a multiple of 4 (compress_ld_width).
+__device__ __forceinline__ void load_block_wide(const double *__restrict__ A, int64_t lda, int64_t bi, int64_t bj,
+                                                double (&d)[64])
+{
+    const double *p = A + (bi * 8) * lda + bj * 8;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const double *q = p + i * lda + 4 * h;
+            asm("ld.global.nc.v4.f64 {%0, %1, %2, %3}, [%4];"
+                : "=d"(d[i * 8 + 4 * h]), "=d"(d[i * 8 + 4 * h + 1]), "=d"(d[i * 8 + 4 * h + 2]),
+                  "=d"(d[i * 8 + 4 * h + 3])
+                : "l"(q));
+        }
+    }
+}
 
 // One CTA's pass over up to kFastThreads blocks (thread t: block b when
 // `valid`).  kUniform: the first pass, which compresses the uniform blocks
 // on the integer pipe (cf_prepare_uniform) and lists every other block for
 // the second pass (general_list); otherwise the second pass, on the binary64
 // pipe (cf_prepare).  Both leave undecided codes and blocks to the fix-up
-// lists.  Every thread of the CTA calls this (it holds barriers).
-template <bool kVec, bool kUniform>
+// lists.  Every thread of the CTA calls this (it holds barriers).  kLd: the
+// width of the block loads, 0 scalar, 1 16 bytes, 2 32 bytes.
+template <int kLd, bool kUniform>
 __device__ __forceinline__ void compress_pass(const double *__restrict__ A, int64_t lda, int64_t rows, int64_t cols,
                                               int64_t nbc, int64_t b, bool valid, double *__restrict__ f,
                                               double *__restrict__ s, uint8_t *__restrict__ phi,
                                               int8_t *__restrict__ code, uint2 *__restrict__ code_list,
                                               unsigned *__restrict__ code_count, unsigned *__restrict__ block_list,
                                               unsigned *__restrict__ block_count, unsigned *__restrict__ general_list,
-                                              unsigned *__restrict__ general_count, double (*sD)[kSlot],
-                                              double *sX, unsigned &sCount)
+                                              unsigned *__restrict__ general_count, double *smem,
+                                              unsigned &sCount)
 {
+    UniformSlot *uS = reinterpret_cast<UniformSlot *>(smem);  // the uniform pass
+    double *sX = kUniform ? reinterpret_cast<double *>(uS + kFastThreads) : smem + kFastThreads * kSlot;
+    // D of the binary64 pass, or N of the uniform pass's first kCopySlots slots
+    double(*sD)[kSlot] = reinterpret_cast<double(*)[kSlot]>(kUniform ? sX + kFastThreads : smem);
     double d[64];
     double sv = 0.0;
     FastCtx ctx;
     ctx.state = 1u;
     ctx.coherent = false;
     int slot = -1;
-    // A block that may need the exact DC chain leaves D (or N) in a slot as
-    // soon as it is normalized; s follows once it is known.
+    // A block that may need the exact DC chain takes a slot as soon as it is
+    // normalized (the binary64 pass leaves D there); s follows once it is
+    // known.
     auto stash = [&](const double (&dd)[64], unsigned meta) {
         slot = (int)atomicAdd(&sCount, 1u);
+        if (kUniform) {
+            uS[slot].b = (unsigned)b;
+            uS[slot].meta = meta;
+        }
+        if (!kUniform || slot < kCopySlots) {
 #pragma unroll
-        for (int p = 0; p < 64; ++p) sD[slot][p] = dd[p];
-        sD[slot][65] = __longlong_as_double((long long)meta);
+            for (int p = 0; p < 64; ++p) sD[slot][p] = dd[p];
+        }
     };
     if (valid) {
         const int64_t bi = b / nbc, bj = b - (b / nbc) * nbc;
-        if (bi * 8 + 8 <= rows && bj * 8 + 8 <= cols) load_block<kVec>(A, lda, bi, bj, d);
-        else load_block_clamped(A, lda, bi, bj, rows, cols, d);  // partial block of a padded matrix
+        if (bi * 8 + 8 <= rows && bj * 8 + 8 <= cols) {
+            if (kLd == 2) load_block_wide(A, lda, bi, bj, d);
+            else load_block<kLd == 1>(A, lda, bi, bj, d);
+        } else {
+            load_block_clamped(A, lda, bi, bj, rows, cols, d);  // partial block of a padded matrix
+        }
         const double f0 = d[0];
         if (kUniform) {
             valid = cf_prepare_uniform(d, sv, ctx, stash);
@@ -92,7 +144,10 @@ __device__ __forceinline__ void compress_pass(const double *__restrict__ A, int6
         } else {
             cf_prepare(d, sv, ctx, stash);
         }
-        if (slot >= 0) sD[slot][64] = sv;  // the dense pass forms r = RN(1/s)
+        if (slot >= 0) {  // the dense pass forms r = RN(1/s)
+            if (kUniform) uS[slot].s = sv;
+            else sD[slot][64] = sv;
+        }
         if (valid) {
             f[b] = f0;
             s[b] = sv;
@@ -107,8 +162,10 @@ __device__ __forceinline__ void compress_pass(const double *__restrict__ A, int6
         const unsigned tmask = 0xFFu << tbase;
         for (unsigned w = threadIdx.x; w < 8u * n; w += blockDim.x) {
             const unsigned q = w >> 3;
-            const double x = cf_exact_dc_team<kUniform>(sD[q], sD[q][64], (unsigned)__double_as_longlong(sD[q][65]),
-                                                        u, tmask, tbase);
+            double x;
+            if (!kUniform) x = cf_exact_dc_team(sD[q], sD[q][64], u, tmask, tbase);
+            else if (q < kCopySlots) x = cf_exact_dc_team_n(sD[q], uS[q].s, uS[q].meta, u, tmask, tbase);
+            else x = cf_exact_dc_team_uniform(A, lda, rows, cols, nbc, uS[q].b, uS[q].s, uS[q].meta, u, tmask, tbase);
             if (u == 0) sX[q] = x;
         }
     }
@@ -133,7 +190,7 @@ __device__ __forceinline__ void compress_pass(const double *__restrict__ A, int6
 // The certified compressor.  kUniform: one CTA per kFastThreads consecutive
 // blocks, the first pass of compress_pass.  Otherwise the second pass over
 // the blocks the first one listed, the CTAs striding over the list.
-template <bool kVec, bool kUniform>
+template <int kLd, bool kUniform>
 __global__ void __launch_bounds__(kFastThreads, 3)
     k_compress_fast(const double *__restrict__ A, int64_t lda, int64_t rows, int64_t cols, int64_t nbc, int64_t nb,
                     double *__restrict__ f, double *__restrict__ s, uint8_t *__restrict__ phi,
@@ -141,19 +198,17 @@ __global__ void __launch_bounds__(kFastThreads, 3)
                     unsigned *__restrict__ block_list, unsigned *__restrict__ block_count,
                     unsigned *__restrict__ general_list, unsigned *__restrict__ general_count)
 {
-    // Sign-coherent blocks of the CTA leave D and r here; after a barrier
-    // the CTA's threads evaluate their exact DC chains densely (one per
-    // thread) and leave X00 in sX (kFastSmem bytes of dynamic shared memory).
+    // Sign-coherent blocks of the CTA take slots here; after a barrier teams
+    // of the CTA's threads evaluate their exact DC chains densely and leave
+    // X00 beside the slots (dynamic shared memory).
     extern __shared__ double fast_smem[];
-    double(*sD)[kSlot] = reinterpret_cast<double(*)[kSlot]>(fast_smem);
-    double *sX = fast_smem + kFastThreads * kSlot;
     __shared__ unsigned sCount;
     if (kUniform) {
         if (threadIdx.x == 0) sCount = 0u;
         __syncthreads();
         const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-        compress_pass<kVec, true>(A, lda, rows, cols, nbc, b, b < nb, f, s, phi, code, code_list, code_count,
-                                  block_list, block_count, general_list, general_count, sD, sX, sCount);
+        compress_pass<kLd, true>(A, lda, rows, cols, nbc, b, b < nb, f, s, phi, code, code_list, code_count,
+                                  block_list, block_count, general_list, general_count, fast_smem, sCount);
     } else {
         const int64_t n = *general_count;  // the first pass completed before this launch
         for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
@@ -161,8 +216,8 @@ __global__ void __launch_bounds__(kFastThreads, 3)
             __syncthreads();
             const int64_t i = base + threadIdx.x;
             const int64_t b = i < n ? (int64_t)general_list[i] : 0;
-            compress_pass<kVec, false>(A, lda, rows, cols, nbc, b, i < n, f, s, phi, code, code_list, code_count,
-                                       block_list, block_count, general_list, general_count, sD, sX, sCount);
+            compress_pass<kLd, false>(A, lda, rows, cols, nbc, b, i < n, f, s, phi, code, code_list, code_count,
+                                       block_list, block_count, general_list, general_count, fast_smem, sCount);
             __syncthreads();  // sCount and the shared slots are reused by the next chunk
         }
     }
@@ -215,23 +270,43 @@ size_t compress_scratch_bytes(int64_t nb)
     return up((size_t)nb * 8) + 2 * up((size_t)nb * 4) + 256;
 }
 
-template <bool kVec>
+// The widest block load that every full block of A allows: 32 bytes when
+// the base is 32-byte aligned and lda a multiple of 4 (every row of every
+// block then starts on a 32-byte boundary), 16 bytes for 16 and 2, else 8.
+static int compress_ld_width(const void *p, int64_t ld)
+{
+    if ((uintptr_t)p % 32 == 0 && ld % 4 == 0) return 2;
+    return vec_ok(p, ld) ? 1 : 0;
+}
+
+template <int kLd>
 static void compress_launches(const double *A, int64_t lda, int64_t rows, int64_t cols, int64_t nbc, int64_t nb,
                               const blaz_cmat *out, uint2 *code_list, unsigned *block_list, unsigned *general_list,
                               unsigned *counts, cudaStream_t st)
 {
     // counts[0]: undecided codes, [1]: whole blocks, [2]: second-pass blocks
-    k_compress_fast<kVec, true><<<fast_grid(nb), kFastThreads, kFastSmem, st>>>(
+    k_compress_fast<kLd, true><<<fast_grid(nb), kFastThreads, kUniformSmem, st>>>(
         A, lda, rows, cols, nbc, nb, out->f, out->s, out->phi, out->code, code_list, counts, block_list, counts + 1,
         general_list, counts + 2);
     // the second pass strides over its list (at most nb blocks) with up to
     // two resident waves of CTAs
     const int64_t want = (nb + kFastThreads - 1) / kFastThreads, cap = (int64_t)num_sms() * 6;
-    k_compress_fast<kVec, false><<<(int)(want < cap ? want : cap), kFastThreads, kFastSmem, st>>>(
+    k_compress_fast<kLd, false><<<(int)(want < cap ? want : cap), kFastThreads, kGeneralSmem, st>>>(
         A, lda, rows, cols, nbc, nb, out->f, out->s, out->phi, out->code, code_list, counts, block_list, counts + 1,
         general_list, counts + 2);
-    k_compress_fix<kVec><<<num_sms() * 4, 128, 0, st>>>(A, lda, rows, cols, nbc, block_list, code_list, counts,
-                                                         out->s, out->phi, out->code);
+    k_compress_fix<(kLd > 0)><<<num_sms() * 4, 128, 0, st>>>(A, lda, rows, cols, nbc, block_list, code_list, counts,
+                                                              out->s, out->phi, out->code);
+}
+
+// Both passes need more than the default 48 KB of dynamic shared memory per
+// CTA.
+template <int kLd>
+static bool compress_smem_attribute()
+{
+    return cudaFuncSetAttribute(k_compress_fast<kLd, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kUniformSmem) == cudaSuccess &&
+           cudaFuncSetAttribute(k_compress_fast<kLd, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kGeneralSmem) == cudaSuccess;
 }
 
 int launch_compress(const double *A, int64_t lda, int64_t rows, int64_t cols, const blaz_cmat *out, void *scratch,
@@ -247,23 +322,14 @@ int launch_compress(const double *A, int64_t lda, int64_t rows, int64_t cols, co
     unsigned *counts = (unsigned *)((char *)scratch + up((size_t)nb * 8) + 2 * up((size_t)nb * 4));
     cudaError_t e = cudaMemsetAsync(counts, 0, 3 * sizeof(unsigned), st);
     if (e != cudaSuccess) return set_cuda_error(e);
-    static const bool smem_ok = [] {
-        bool ok = true;
-        ok &= cudaFuncSetAttribute(k_compress_fast<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)kFastSmem) == cudaSuccess;
-        ok &= cudaFuncSetAttribute(k_compress_fast<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)kFastSmem) == cudaSuccess;
-        ok &= cudaFuncSetAttribute(k_compress_fast<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)kFastSmem) == cudaSuccess;
-        ok &= cudaFuncSetAttribute(k_compress_fast<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)kFastSmem) == cudaSuccess;
-        return ok;
-    }();
+    static const bool smem_ok =
+        compress_smem_attribute<0>() && compress_smem_attribute<1>() && compress_smem_attribute<2>();
     if (!smem_ok) return set_cuda_error(cudaGetLastError());
-    if (vec_ok(A, lda)) compress_launches<true>(A, lda, rows, cols, nbc, nb, out, code_list, block_list,
-                                                general_list, counts, st);
-    else compress_launches<false>(A, lda, rows, cols, nbc, nb, out, code_list, block_list, general_list, counts,
-                                  st);
+    switch (compress_ld_width(A, lda)) {
+    case 2: compress_launches<2>(A, lda, rows, cols, nbc, nb, out, code_list, block_list, general_list, counts, st); break;
+    case 1: compress_launches<1>(A, lda, rows, cols, nbc, nb, out, code_list, block_list, general_list, counts, st); break;
+    default: compress_launches<0>(A, lda, rows, cols, nbc, nb, out, code_list, block_list, general_list, counts, st);
+    }
     return launch_status();
 }
 

@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(kRateThreads, 3)
         s[b] = sv;
     }
     __syncthreads();
-    if (threadIdx.x < sCount) sX[threadIdx.x] = cf_exact_dc<false>(sD[threadIdx.x], sD[threadIdx.x][64], 0u);
+    if (threadIdx.x < sCount) sX[threadIdx.x] = cf_exact_dc(sD[threadIdx.x], sD[threadIdx.x][64]);
     __syncthreads();
     uint64_t pending = 0u;
     if (valid) {

@@ -92,6 +92,17 @@ def test_compress_strided_and_unaligned_views(B):
     assert_cmat_equal(B.compress(view), O.compress(big[:, 1:137]))
     view2 = tb[8:40, 64:128]          # lda = 200, aligned
     assert_cmat_equal(B.compress(view2), O.compress(big[8:40, 64:128]))
+    # the compressor's three load widths: 32-byte (base on 32 bytes, lda % 4
+    # == 0, as view2), 16-byte (base on 16 bytes only, or lda % 4 == 2) and
+    # scalar (view)
+    view3 = tb[:, 2:130]              # lda = 200, base 16 bytes off a 32-byte boundary
+    assert view3.data_ptr() % 32 == 16
+    assert_cmat_equal(B.compress(view3), O.compress(big[:, 2:130]))
+    big2 = np.concatenate([big, big[:, :2]], axis=1)
+    tb2 = dev(big2)
+    view4 = tb2[:, 0:136]             # lda = 202
+    assert view4.stride(0) == 202 and view4.data_ptr() % 32 == 0
+    assert_cmat_equal(B.compress(view4), O.compress(big2[:, 0:136]))
 
 
 def special_blocks():
@@ -151,6 +162,29 @@ def test_compress_uniform_block_edges(B):
     M = np.concatenate([np.concatenate(blocks[r * 8:(r + 1) * 8], axis=1) for r in range(len(blocks) // 8)], axis=0)
     g = B.compress(dev(M))
     assert_cmat_equal(g, O.compress(M))
+
+
+def test_compress_all_blocks_sign_coherent(B):
+    """Every block uniform and sign-coherent (increasing along both axes, so
+    every N > 0; the negative copies all N < 0), 3 block rows of 300 blocks,
+    so that every CTA of the compressor's integer pass fills all its exact-DC
+    slots, whose chains reload the rows of their blocks; the last block rows
+    and columns of a padded copy take the clamped reload.  Some blocks are
+    constant (K = 0); with phi = 16 and K = 63 the others have their DC
+    exactly on an integer code (8 | K phi).  Bit for bit against the
+    oracle."""
+    rng = np.random.default_rng(73)
+    blocks = []
+    for q in range(900):
+        steps = rng.integers(1, 4, (8, 8)) * 2.0 ** -20 if q % 3 else rng.uniform(0, 1e-3, (8, 8))
+        blk = 1.0 + np.cumsum(np.cumsum(steps, 0), 1)
+        if q % 50 == 7:
+            blk = np.full((8, 8), 1.75)
+        blocks.append(-blk if q % 4 == 1 else blk)
+    M = np.concatenate([np.concatenate(blocks[r * 300:(r + 1) * 300], axis=1) for r in range(3)], axis=0)
+    assert_cmat_equal(B.compress(dev(M)), O.compress(M))
+    R = np.ascontiguousarray(M[:21, :2395])   # edge-replicated to 24 x 2400: the blocks stay coherent
+    assert_cmat_equal(B.compress_padded(dev(R)), O.compress_padded(R))
 
 
 @pytest.mark.parametrize("shape", [(0, 0), (0, 16), (16, 0)])
