@@ -272,8 +272,8 @@ __device__ __forceinline__ uint32_t compress_block_fast(double (&d)[64], double 
 // with r = RN64(1/s), so the first term of the bound in the header becomes 6u
 // and E_ij = 28u aa_ij (K + 1) + 2^-100 covers the total of 26u + O(u^2).
 // The exact r is formed only for the blocks whose exact DC chain needs it
-// (sign-coherent blocks, in the dense pass), off every block's path to the
-// DCT.  Both passes of this form add and subtract mirrored entries first
+// (sign-coherent blocks, by the block's lane after its DCT), off every
+// block's path to the DCT.  Both passes of this form add and subtract mirrored entries first
 // (cos_kx is even or odd under x -> 7 - x, exactly in the table) and run
 // 4-term chains: one rounding of |a| + |b| and gamma_4 of the chain stay
 // within the 8u per pass that the bound allows for 8-term chains.
@@ -598,16 +598,14 @@ __device__ __forceinline__ double cf_exact_dc(const double *D, double r)
 }
 
 // The same X00 by a team of 8 lanes, lane u holding row u of D (drow(v) =
-// D_uv): the row chains t_u = sum_v RN(D_uv r) (v ascending) are
-// independent, and lane 0 of the team adds them in the specified order (u
-// ascending) from the team's shuffles, so the chain is ~25 binary64
-// operations deep instead of ~130.  Same bits as cf_exact_dc.  Every lane of
-// the team forms r = RN(1/s) (a binary64 instruction costs a warp the same
-// for 8 lanes as for one).  Returns X00 in lane 0 of the team.
+// D_uv) and r = RN(1/s): the row chains t_u = sum_v RN(D_uv r) (v
+// ascending) are independent, and lane 0 of the team adds them in the
+// specified order (u ascending) from the team's shuffles, so the chain is
+// ~16 binary64 operations deep instead of ~130.  Same bits as cf_exact_dc.
+// Returns X00 in lane 0 of the team.
 template <typename Row>
-__device__ __forceinline__ double cf_exact_dc_rows(Row drow, double s, unsigned tmask, int tbase)
+__device__ __forceinline__ double cf_exact_dc_rows(Row drow, double r, unsigned tmask, int tbase)
 {
-    const double r = ddiv(1.0, s);
     double t = dmul(drow(0), r);
 #pragma unroll
     for (int v = 1; v < 8; ++v) t = dadd(t, dmul(drow(v), r));
@@ -618,19 +616,19 @@ __device__ __forceinline__ double cf_exact_dc_rows(Row drow, double s, unsigned 
 }
 
 // X00 by a team from D in shared memory (the binary64 pass).
-__device__ __forceinline__ double cf_exact_dc_team(const double *D, double s, int u, unsigned tmask, int tbase)
+__device__ __forceinline__ double cf_exact_dc_team(const double *D, double r, int u, unsigned tmask, int tbase)
 {
-    return cf_exact_dc_rows([&](int v) { return D[u * 8 + v]; }, s, tmask, tbase);
+    return cf_exact_dc_rows([&](int v) { return D[u * 8 + v]; }, r, tmask, tbase);
 }
 
 // X00 by a team for a uniform block from its integers N in shared memory
 // (meta as cf_prepare_uniform sets it).
-__device__ __forceinline__ double cf_exact_dc_team_n(const double *N, double s, unsigned meta, int u, unsigned tmask,
+__device__ __forceinline__ double cf_exact_dc_team_n(const double *N, double r, unsigned meta, int u, unsigned tmask,
                                                      int tbase)
 {
     const int e = (int)(meta & 0xFFFFu);
     const unsigned bneg = meta >> 16;
-    return cf_exact_dc_rows([&](int v) { return uniform_d(__double_as_longlong(N[u * 8 + v]), e, bneg); }, s, tmask,
+    return cf_exact_dc_rows([&](int v) { return uniform_d(__double_as_longlong(N[u * 8 + v]), e, bneg); }, r, tmask,
                             tbase);
 }
 
@@ -641,12 +639,12 @@ __device__ __forceinline__ double cf_exact_dc_team_n(const double *N, double s, 
 // uniform_d(N).  The block's own lane has just loaded these rows (an L1 or
 // L2 hit), and the CTA keeps no copy of the block.
 __device__ __forceinline__ double cf_exact_dc_team_uniform(const double *__restrict__ A, int64_t lda, int64_t rows,
-                                                           int64_t cols, int64_t nbc, int64_t b, double s,
+                                                           int64_t cols, int64_t nbc, int64_t b, double r,
                                                            unsigned meta, int u, unsigned tmask, int tbase)
 {
     const int64_t bi = b / nbc, bj = b - (b / nbc) * nbc;
-    const int64_t r = bi * 8 + u < rows ? bi * 8 + u : rows - 1;
-    const int64_t rp = bi * 8 + u - 1 < rows ? bi * 8 + u - 1 : rows - 1;  // read for u > 0 only
+    const int64_t row = bi * 8 + u < rows ? bi * 8 + u : rows - 1;
+    const int64_t rowp = bi * 8 + u - 1 < rows ? bi * 8 + u - 1 : rows - 1;  // read for u > 0 only
     auto sig = [](double x) -> long long {
         return (long long)(((unsigned long long)__double_as_longlong(x) & 0x000FFFFFFFFFFFFFull) |
                            0x0010000000000000ull);
@@ -655,8 +653,8 @@ __device__ __forceinline__ double cf_exact_dc_team_uniform(const double *__restr
 #pragma unroll
     for (int v = 0; v < 8; ++v) {
         const int64_t c = bj * 8 + v < cols ? bj * 8 + v : cols - 1;
-        cur[v] = sig(__ldg(A + r * lda + c));
-        prev[v] = u > 0 ? sig(__ldg(A + rp * lda + c)) : 0ll;
+        cur[v] = sig(__ldg(A + row * lda + c));
+        prev[v] = u > 0 ? sig(__ldg(A + rowp * lda + c)) : 0ll;
     }
     const int e = (int)(meta & 0xFFFFu);
     const unsigned bneg = meta >> 16;
@@ -668,7 +666,7 @@ __device__ __forceinline__ double cf_exact_dc_team_uniform(const double *__restr
             else N = 2 * cur[v] - prev[v] - cur[v - 1];
             return uniform_d(N, e, bneg);
         },
-        s, tmask, tbase);
+        r, tmask, tbase);
 }
 
 // Phase 2: phi and the codes, with the exact X00 of a coherent block.

@@ -9,12 +9,11 @@
 
 namespace blaz {
 
-// Row u of D' for block b, exactly as compress_block forms it: Eq. eqnorm
-// from rows u and u-1 of the input, then times r = 1/s (s as stored).  Rows
-// and columns beyond the logical rows x cols repeat the last one (padding).
-template <bool kVec>
-__device__ __forceinline__ void team_dprime_row(const double *__restrict__ A, int64_t lda, int64_t rows, int64_t cols,
-                                                int64_t nbc, int64_t b, int u, double s, double (&dp)[8])
+// Row u of D for block b, exactly as compress_block forms it: Eq. eqnorm
+// from rows u and u-1 of the input.  Rows and columns beyond the logical
+// rows x cols repeat the last one (padding).
+__device__ __forceinline__ void team_d_row(const double *__restrict__ A, int64_t lda, int64_t rows, int64_t cols,
+                                           int64_t nbc, int64_t b, int u, double (&dp)[8])
 {
     const int64_t bi = b / nbc, bj = b - (b / nbc) * nbc;
     const int64_t r = bi * 8 + u < rows ? bi * 8 + u : rows - 1;
@@ -32,6 +31,14 @@ __device__ __forceinline__ void team_dprime_row(const double *__restrict__ A, in
         else if (v == 0) dp[v] = dsub(cur[0], prev[0]);
         else dp[v] = dhalf(dadd(dsub(cur[v], prev[v]), dsub(cur[v], cur[v - 1])));
     }
+}
+
+// Row u of D' = D times r = 1/s (s as stored).
+template <bool kVec>
+__device__ __forceinline__ void team_dprime_row(const double *__restrict__ A, int64_t lda, int64_t rows, int64_t cols,
+                                                int64_t nbc, int64_t b, int u, double s, double (&dp)[8])
+{
+    team_d_row(A, lda, rows, cols, nbc, b, u, dp);
     const double rs = ddiv(1.0, s);
 #pragma unroll
     for (int v = 0; v < 8; ++v) dp[v] = dmul(dp[v], rs);

@@ -44,28 +44,39 @@ __device__ __forceinline__ void append(bool want, T value, T *__restrict__ list,
 // pass of exact DC chains, which larger CTAs fill better.
 constexpr int kFastThreads = 128;
 
-// Dynamic shared memory of the fast compressor, one slot per block of the
-// CTA, then the exact X00 of every slot.  The binary64 pass keeps D in its
-// slots: 64 entries and s in an odd row of kSlot doubles (conflict-free row
-// reads).  The uniform pass keeps the block, s and the meta word in every
-// slot and the integers N in rows like those for its first kCopySlots
-// slots; the dense pass reloads the rows of the blocks in the other slots
-// (cf_exact_dc_team_uniform).  So a CTA needs 54 KB instead of 70, and the
-// SM keeps 60 KB or more of L1 instead of ~28 KB, which also bounds the block
-// loads in flight (a warp loads 16 KB per round); few CTAs of a smooth field
-// have more than 96 sign-coherent blocks.  Measured at 16384^2: 1.276 /
+// Dynamic shared memory of the fast compressor: one slot per block of the
+// CTA (the block, r = RN(1/s) and the meta word), the exact X00 of every
+// slot, then a copy of the block's N (uniform pass) or D (binary64 pass) in
+// an odd row of kSlot doubles (conflict-free row reads) for the first
+// kCopySlots slots only.  The dense pass reloads the two rows each team lane
+// needs for the other slots (cf_exact_dc_team_uniform, cf_exact_dc_team_d),
+// so no block leaves a pass for lack of room.  A CTA needs 54 KB instead of
+// 70, and the SM keeps 60 KB or more of L1 instead of ~28 KB, which also
+// bounds the block loads in flight (a warp loads 16 KB per round) and holds
+// the binary64 pass's spills; few CTAs of a smooth field have more than 96
+// sign-coherent blocks.  Measured at 16384^2 on the uniform pass: 1.276 /
 // 1.181 ms per compression of the two bump fields with 128 copied slots,
 // 1.203 / 1.097 with 96 (with 32-byte loads), 1.253 / 1.104 with every slot
-// reloaded.
+// reloaded; the binary64 pass's 96 copies took another 0.002-0.004 ms off.
 constexpr int kSlot = 67;
 constexpr int kCopySlots = 96;
-struct UniformSlot {
-    double s;
+struct FastSlot {
+    double r;
     unsigned b, meta;
 };
-constexpr size_t kGeneralSmem = sizeof(double) * (size_t)kFastThreads * (kSlot + 1);
-constexpr size_t kUniformSmem =
-    (sizeof(UniformSlot) + sizeof(double)) * (size_t)kFastThreads + sizeof(double) * (size_t)kCopySlots * kSlot;
+constexpr size_t kFastSmem =
+    (sizeof(FastSlot) + sizeof(double)) * (size_t)kFastThreads + sizeof(double) * (size_t)kCopySlots * kSlot;
+
+// X00 by a team for a block of the binary64 pass, from the input itself:
+// lane u forms row u of D as compress_block does (team_d_row).
+__device__ __forceinline__ double cf_exact_dc_team_d(const double *__restrict__ A, int64_t lda, int64_t rows,
+                                                     int64_t cols, int64_t nbc, int64_t b, double r, int u,
+                                                     unsigned tmask, int tbase)
+{
+    double dr[8];
+    team_d_row(A, lda, rows, cols, nbc, b, u, dr);
+    return cf_exact_dc_rows([&](int v) { return dr[v]; }, r, tmask, tbase);
+}
 
 // A full block with 32-byte loads: two per row of 64 B, so that every load
 // instruction of a warp uses whole 32-byte sectors (with 16-byte loads two
@@ -105,10 +116,9 @@ __device__ __forceinline__ void compress_pass(const double *__restrict__ A, int6
                                               unsigned *__restrict__ general_count, double *smem,
                                               unsigned &sCount)
 {
-    UniformSlot *uS = reinterpret_cast<UniformSlot *>(smem);  // the uniform pass
-    double *sX = kUniform ? reinterpret_cast<double *>(uS + kFastThreads) : smem + kFastThreads * kSlot;
-    // D of the binary64 pass, or N of the uniform pass's first kCopySlots slots
-    double(*sD)[kSlot] = reinterpret_cast<double(*)[kSlot]>(kUniform ? sX + kFastThreads : smem);
+    FastSlot *uS = reinterpret_cast<FastSlot *>(smem);
+    double *sX = reinterpret_cast<double *>(uS + kFastThreads);
+    double(*sD)[kSlot] = reinterpret_cast<double(*)[kSlot]>(sX + kFastThreads);  // N or D, first kCopySlots
     double d[64];
     double sv = 0.0;
     FastCtx ctx;
@@ -116,15 +126,12 @@ __device__ __forceinline__ void compress_pass(const double *__restrict__ A, int6
     ctx.coherent = false;
     int slot = -1;
     // A block that may need the exact DC chain takes a slot as soon as it is
-    // normalized (the binary64 pass leaves D there); s follows once it is
-    // known.
+    // normalized; r follows once s is known.
     auto stash = [&](const double (&dd)[64], unsigned meta) {
         slot = (int)atomicAdd(&sCount, 1u);
-        if (kUniform) {
-            uS[slot].b = (unsigned)b;
-            uS[slot].meta = meta;
-        }
-        if (!kUniform || slot < kCopySlots) {
+        uS[slot].b = (unsigned)b;
+        uS[slot].meta = meta;
+        if (slot < kCopySlots) {
 #pragma unroll
             for (int p = 0; p < 64; ++p) sD[slot][p] = dd[p];
         }
@@ -144,10 +151,11 @@ __device__ __forceinline__ void compress_pass(const double *__restrict__ A, int6
         } else {
             cf_prepare(d, sv, ctx, stash);
         }
-        if (slot >= 0) {  // the dense pass forms r = RN(1/s)
-            if (kUniform) uS[slot].s = sv;
-            else sD[slot][64] = sv;
-        }
+        // r = RN(1/s) for the dense pass, formed here, where it overlaps the
+        // other warps' work, rather than at the head of the team's chain
+        // (1.205 / 1.101 -> 1.182 / 1.100 ms at 16384^2, 0.220 -> 0.203 ms
+        // for a 4096^2 field of sign-coherent blocks)
+        if (slot >= 0) uS[slot].r = ddiv(1.0, sv);
         if (valid) {
             f[b] = f0;
             s[b] = sv;
@@ -162,10 +170,14 @@ __device__ __forceinline__ void compress_pass(const double *__restrict__ A, int6
         const unsigned tmask = 0xFFu << tbase;
         for (unsigned w = threadIdx.x; w < 8u * n; w += blockDim.x) {
             const unsigned q = w >> 3;
+            const double r = uS[q].r;
             double x;
-            if (!kUniform) x = cf_exact_dc_team(sD[q], sD[q][64], u, tmask, tbase);
-            else if (q < kCopySlots) x = cf_exact_dc_team_n(sD[q], uS[q].s, uS[q].meta, u, tmask, tbase);
-            else x = cf_exact_dc_team_uniform(A, lda, rows, cols, nbc, uS[q].b, uS[q].s, uS[q].meta, u, tmask, tbase);
+            if (q < (unsigned)kCopySlots)
+                x = kUniform ? cf_exact_dc_team_n(sD[q], r, uS[q].meta, u, tmask, tbase)
+                             : cf_exact_dc_team(sD[q], r, u, tmask, tbase);
+            else
+                x = kUniform ? cf_exact_dc_team_uniform(A, lda, rows, cols, nbc, uS[q].b, r, uS[q].meta, u, tmask, tbase)
+                             : cf_exact_dc_team_d(A, lda, rows, cols, nbc, uS[q].b, r, u, tmask, tbase);
             if (u == 0) sX[q] = x;
         }
     }
@@ -285,13 +297,13 @@ static void compress_launches(const double *A, int64_t lda, int64_t rows, int64_
                               unsigned *counts, cudaStream_t st)
 {
     // counts[0]: undecided codes, [1]: whole blocks, [2]: second-pass blocks
-    k_compress_fast<kLd, true><<<fast_grid(nb), kFastThreads, kUniformSmem, st>>>(
+    k_compress_fast<kLd, true><<<fast_grid(nb), kFastThreads, kFastSmem, st>>>(
         A, lda, rows, cols, nbc, nb, out->f, out->s, out->phi, out->code, code_list, counts, block_list, counts + 1,
         general_list, counts + 2);
     // the second pass strides over its list (at most nb blocks) with up to
     // two resident waves of CTAs
     const int64_t want = (nb + kFastThreads - 1) / kFastThreads, cap = (int64_t)num_sms() * 6;
-    k_compress_fast<kLd, false><<<(int)(want < cap ? want : cap), kFastThreads, kGeneralSmem, st>>>(
+    k_compress_fast<kLd, false><<<(int)(want < cap ? want : cap), kFastThreads, kFastSmem, st>>>(
         A, lda, rows, cols, nbc, nb, out->f, out->s, out->phi, out->code, code_list, counts, block_list, counts + 1,
         general_list, counts + 2);
     k_compress_fix<(kLd > 0)><<<num_sms() * 4, 128, 0, st>>>(A, lda, rows, cols, nbc, block_list, code_list, counts,
@@ -304,9 +316,9 @@ template <int kLd>
 static bool compress_smem_attribute()
 {
     return cudaFuncSetAttribute(k_compress_fast<kLd, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)kUniformSmem) == cudaSuccess &&
+                                (int)kFastSmem) == cudaSuccess &&
            cudaFuncSetAttribute(k_compress_fast<kLd, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)kGeneralSmem) == cudaSuccess;
+                                (int)kFastSmem) == cudaSuccess;
 }
 
 int launch_compress(const double *A, int64_t lda, int64_t rows, int64_t cols, const blaz_cmat *out, void *scratch,
