@@ -924,9 +924,22 @@ def main():
             B.download(cs, hs)
             hr.copy_(res, non_blocking=True)
 
+        # the link floor: the same host-to-device bytes as plain page-locked
+        # copies, taken before and after the timed steps, so that a slow
+        # timed region can be told apart from a link that was slow throughout
+        def copy_floor():
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record(st)
+            ta.copy_(ha, non_blocking=True)
+            tb.copy_(hb, non_blocking=True)
+            f1.record(st)
+            torch.cuda.synchronize()
+            return f0.elapsed_time(f1)
+
         for _ in range(args.warmup):
             e2e_step()
         torch.cuda.synchronize()
+        floor_before = [copy_floor() for _ in range(3)]
         if dist:
             dist.barrier()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -937,21 +950,13 @@ def main():
         e1.record(st)
         torch.cuda.synchronize()
         ems = max_over_ranks(e0.elapsed_time(e1), dist, dev)
-        # the link floor: the same host-to-device bytes as plain page-locked copies
-        floor = []
-        for _ in range(3):
-            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            f0.record(st)
-            ta.copy_(ha, non_blocking=True)
-            tb.copy_(hb, non_blocking=True)
-            f1.record(st)
-            torch.cuda.synchronize()
-            floor.append(f0.elapsed_time(f1))
+        floor_after = [copy_floor() for _ in range(3)]
         h2d = 2 * n * n * 8
         d2h = cs.nbytes + 16
         e2e = {"value": job_throughput(world, n, args.steps, ems), "unit": "GB/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ems / args.steps,
-               "h2d_copy_ms_per_step": min(floor)}
+               "h2d_copy_ms_per_step": min(floor_before + floor_after),
+               "h2d_copy_ms_before_after": [round(min(floor_before), 3), round(min(floor_after), 3)]}
 
     extras = None
     if rank == 0 and not args.no_extras:
