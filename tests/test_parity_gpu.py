@@ -187,6 +187,25 @@ def test_compress_all_blocks_sign_coherent(B):
     assert_cmat_equal(B.compress_padded(dev(R)), O.compress_padded(R))
 
 
+def test_compress_coherent_blocks_across_a_binade(B):
+    """Sign-coherent blocks that each cross 1.0 (so none is uniform): 885 of
+    900 go to the compressor's binary64 pass, whose every chunk of 128 then
+    has more sign-coherent blocks than copies of D, and the dense pass forms
+    the rows of the others from the input.  Bit for bit against the oracle,
+    plain and with a padded copy."""
+    rng = np.random.default_rng(79)
+    blocks = []
+    for q in range(900):
+        blk = 0.99 + np.cumsum(np.cumsum(rng.uniform(0, 1e-3, (8, 8)), 0), 1)
+        if q % 60 == 11:
+            blk = np.full((8, 8), 1.25)
+        blocks.append(-blk if q % 4 == 1 else blk)
+    M = np.concatenate([np.concatenate(blocks[r * 300:(r + 1) * 300], axis=1) for r in range(3)], axis=0)
+    assert_cmat_equal(B.compress(dev(M)), O.compress(M))
+    R = np.ascontiguousarray(M[:23, :2397])
+    assert_cmat_equal(B.compress_padded(dev(R)), O.compress_padded(R))
+
+
 @pytest.mark.parametrize("shape", [(0, 0), (0, 16), (16, 0)])
 def test_empty_matrices(B, shape):
     X = torch.zeros(shape, dtype=torch.float64, device="cuda")
